@@ -1,0 +1,475 @@
+/*
+ * DB-TSDF reference integrator (the oracle) -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded C restatement of the scan integration of
+ * DB-TSDF (arXiv 2509.20081, Sec. III).  It exists so that the CUDA library
+ * can be checked voxel by voxel.  Only tests/, the smoke check and the CPU
+ * baseline leg of bench.py may load it; the product path never does.  It
+ * shares no code, header, table or constant with the CUDA library.
+ *
+ * Floating point: every step that turns a float into an integer (voxel index,
+ * direction bin) is evaluated in IEEE binary64 with basic operations only, in
+ * the order written here, and this file must be compiled with
+ * -ffp-contract=off so that no multiply-add is fused.
+ *
+ * Readings of the paper taken where it is silent or ambiguous (each is listed
+ * with its reason in the design notes of the repository):
+ *   - Eq. 3 uses the Euclidean r and ceil(r) bits (not the "L1" of Sec. III-A).
+ *   - a return is discarded when a coordinate is not finite, when it is the
+ *     origin, or when its K^3 neighbourhood leaves the grid (Sec. III-C):
+ *     kept iff R <= c_i <= N_i - 1 - R on every axis.
+ *   - the direction that selects the bin is the map-frame ray d = R p.
+ *   - Eq. 2 azimuth is taken modulo 2 pi, the elevation bin is clamped to
+ *     B_el - 1, and both are decided by comparing against the bin edges
+ *     (ties go to the higher bin) instead of calling atan2/asin.
+ *   - octahedral bins (not in the paper) follow the octahedral map.
+ *   - the shadow set S_b = { o : |o|^2 <= r_s^2 and o . u_b >= 0 }, plane and
+ *     centre included, sign of o . u_b decided exactly.
+ *   - "only the first is integrated" (Sec. IV-B): first = lowest array index
+ *     among returns that survived the discards, per contact voxel, per scan.
+ *   - Eq. 6 with h_new >= T; T and H_max are parameters with 1 <= T <= H_max.
+ * Parity unpinned: the defaults of T, H_max and r_s (the paper gives none).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* pi rounded to the nearest binary64 value */
+#define ORC_PI 3.14159265358979323846
+
+#define ORC_SCHEME_OCTA 0
+#define ORC_SCHEME_AZEL 1
+
+typedef struct {
+    int kernel_size;      /* K, odd; the neighbourhood is [-R, R]^3, R = (K-1)/2 */
+    int scheme;           /* ORC_SCHEME_OCTA or ORC_SCHEME_AZEL */
+    int bins_a;           /* octa: n (n x n cells); azel: B_az */
+    int bins_b;           /* octa: n;               azel: B_el */
+    double shadow_radius; /* r_s in voxels */
+    int hit_threshold;    /* T */
+    int hit_max;          /* H_max */
+    int dedup_first;      /* 1: only the first return per contact voxel */
+} orc_params;
+
+typedef struct {
+    int64_t nx, ny, nz;   /* voxels per axis; dense, x fastest, no padding */
+    double res;           /* voxel edge in metres */
+    double origin[3];     /* map-frame position of the corner of voxel (0,0,0) */
+    uint32_t *mask;
+    uint8_t *sign;
+    uint16_t *hits;
+} orc_grid;
+
+typedef struct {
+    int64_t n_input;      /* returns handed in */
+    int64_t n_valid;      /* finite and not the origin */
+    int64_t n_inside;     /* neighbourhood inside the map */
+    int64_t n_kept;       /* integrated (after first-per-voxel) */
+    int64_t n_mask_writes;/* Eq. 4 writes that changed a mask */
+    int64_t n_shadow_incs;/* Eq. 5 applications (before saturation) */
+} orc_stats;
+
+/* ------------------------------------------------------------------ */
+/* Sec. III-A: initial voxel state -- all mask bits set, sign free (1),
+ * counter zero.                                                       */
+void orc_grid_init(orc_grid *g)
+{
+    int64_t nv = g->nx * g->ny * g->nz;
+    for (int64_t i = 0; i < nv; i++) {
+        g->mask[i] = 0xFFFFFFFFu;
+        g->sign[i] = 1;
+        g->hits[i] = 0;
+    }
+}
+
+/* Eq. 1: M_grid = Nx Ny Nz S_voxel, with the paper's S_voxel = 8 bytes. */
+int64_t orc_grid_bytes_eq1(int64_t nx, int64_t ny, int64_t nz)
+{
+    return nx * ny * nz * 8;
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 3: m(x,y,z) = 0 when r = 0, else (2^32 - 1) >> (32 - ceil(r)),
+ * r = sqrt(x^2 + y^2 + z^2) in voxel units.  For ceil(r) >= 32 no bit is
+ * shifted out and the mask stays all ones.                            */
+uint32_t orc_distance_mask(int x, int y, int z)
+{
+    double r = sqrt((double)x * x + (double)y * y + (double)z * z);
+    if (r == 0.0)
+        return 0u;
+    int c = (int)ceil(r);
+    if (c >= 32)
+        return 0xFFFFFFFFu;
+    return 0xFFFFFFFFu >> (32 - c);
+}
+
+/* ------------------------------------------------------------------ */
+/* Direction bins.                                                       */
+
+static double orc_sgn(double v) { return v < 0.0 ? -1.0 : 1.0; }
+
+/* Octahedral bins (the workloads' 8x8 scheme; not in the paper).  The ray d is
+ * projected on the octahedron |x|+|y|+|z| = 1; the lower half (z < 0) is
+ * folded over the diagonals; the square [-1,1]^2 is cut into n x n cells.
+ * Returns j * n + i for the cell (i along u, j along v).               */
+int orc_bin_octa(double dx, double dy, double dz, int n)
+{
+    double s = (fabs(dx) + fabs(dy)) + fabs(dz);
+    if (!(s > 0.0))
+        return 0;                       /* no direction (not reached for a rotation) */
+    double u = dx / s;
+    double v = dy / s;
+    if (dz < 0.0) {
+        double fu = (1.0 - fabs(v)) * orc_sgn(u);
+        double fv = (1.0 - fabs(u)) * orc_sgn(v);
+        u = fu;
+        v = fv;
+    }
+    int i = (int)floor(((u + 1.0) * 0.5) * (double)n);
+    int j = (int)floor(((v + 1.0) * 0.5) * (double)n);
+    if (i > n - 1) i = n - 1;
+    if (j > n - 1) j = n - 1;
+    if (i < 0) i = 0;
+    if (j < 0) j = 0;
+    return j * n + i;
+}
+
+/* Representative direction of octahedral cell b: the octahedral decode of
+ * the cell centre, scaled by n so that every component is an integer (the
+ * scale is positive, so the sign of o . u_b is unchanged).            */
+void orc_bin_octa_dir(int b, int n, double out[3])
+{
+    int i = b % n, j = b / n;
+    double U = (double)(2 * i + 1 - n);   /* n times the centre's u */
+    double V = (double)(2 * j + 1 - n);
+    double Z = (double)n - fabs(U) - fabs(V);
+    if (Z < 0.0) {
+        double fu = ((double)n - fabs(V)) * orc_sgn(U);
+        double fv = ((double)n - fabs(U)) * orc_sgn(V);
+        U = fu;
+        V = fv;
+    }
+    out[0] = U;
+    out[1] = V;
+    out[2] = Z;
+}
+
+/* Bin edges of Eq. 2.  Azimuth edge k: theta_k = (2 pi k) / B_az; elevation
+ * edge k: phi_k = (pi k) / B_el - pi / 2.                              */
+static double orc_az_edge(int k, int baz) { return ((2.0 * ORC_PI) * (double)k) / (double)baz; }
+static double orc_el_edge(int k, int bel) { return (ORC_PI * (double)k) / (double)bel - ORC_PI / 2.0; }
+
+/* Eq. 2, azimuth: b_az = floor(theta / (2 pi) * B_az), theta = atan2(y, x)
+ * taken in [0, 2 pi).  In exact arithmetic this is the number of edges
+ * theta_k (k = 1 .. B_az-1) with theta >= theta_k.  For theta and theta_k
+ * on the same side of the pi line (or theta_k < pi <= theta) the test is
+ * the sign of sin(theta - theta_k) = cos(theta_k) y - sin(theta_k) x.   */
+int orc_bin_az(double x, double y, int baz)
+{
+    if (x == 0.0 && y == 0.0)
+        return 0;                                     /* atan2(0, 0) = 0 */
+    int upper = (y > 0.0) || (y == 0.0 && x >= 0.0);  /* theta in [0, pi) */
+    int b = 0;
+    for (int k = 1; k < baz; k++) {
+        double t = orc_az_edge(k, baz);
+        int edge_upper = t < ORC_PI;
+        int ge;
+        if (upper && !edge_upper)
+            ge = 0;                       /* theta < pi <= theta_k */
+        else if (!upper && edge_upper)
+            ge = 1;                       /* theta_k < pi <= theta */
+        else
+            ge = (cos(t) * y - sin(t) * x) >= 0.0;
+        b += ge;
+    }
+    return b;
+}
+
+/* Eq. 2, elevation: b_el = floor((asin(z/|p|) + pi/2) / pi * B_el), clamped
+ * to B_el - 1.  asin is increasing, so this counts the edges k = 1..B_el-1
+ * with z/|p| >= sin(phi_k).                                            */
+int orc_bin_el(double x, double y, double z, int bel)
+{
+    double norm = sqrt((x * x + y * y) + z * z);
+    double s = z / norm;
+    int b = 0;
+    for (int k = 1; k < bel; k++)
+        b += s >= sin(orc_el_edge(k, bel));
+    return b;
+}
+
+/* Eq. 2 bin id, az-major: b = b_el * B_az + b_az.                      */
+int orc_bin_azel(double x, double y, double z, int baz, int bel)
+{
+    return orc_bin_el(x, y, z, bel) * baz + orc_bin_az(x, y, baz);
+}
+
+/* Representative unit vector of az/el bin b: the centre of its azimuth
+ * and elevation intervals (Sec. III-B).                                */
+void orc_bin_azel_dir(int b, int baz, int bel, double out[3])
+{
+    int a = b % baz, e = b / baz;
+    double alpha = ((2.0 * ORC_PI) * ((double)a + 0.5)) / (double)baz;
+    double eps = (ORC_PI * ((double)e + 0.5)) / (double)bel - ORC_PI / 2.0;
+    out[0] = cos(eps) * cos(alpha);
+    out[1] = cos(eps) * sin(alpha);
+    out[2] = sin(eps);
+}
+
+int orc_bin(const orc_params *p, double dx, double dy, double dz)
+{
+    if (p->scheme == ORC_SCHEME_OCTA)
+        return orc_bin_octa(dx, dy, dz, p->bins_a);
+    return orc_bin_azel(dx, dy, dz, p->bins_a, p->bins_b);
+}
+
+int orc_num_bins(const orc_params *p)
+{
+    return p->bins_a * p->bins_b;
+}
+
+void orc_bin_dir(const orc_params *p, int b, double out[3])
+{
+    if (p->scheme == ORC_SCHEME_OCTA)
+        orc_bin_octa_dir(b, p->bins_a, out);
+    else
+        orc_bin_azel_dir(b, p->bins_a, p->bins_b, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. III-B: hemispherical shadow set.  Offset o is in the shadow of bin b
+ * when its centre lies in the Euclidean ball of radius r_s around the
+ * contact voxel and not in the half facing the sensor: o . u_b >= 0.    */
+int orc_in_shadow(const orc_params *p, int b, int ox, int oy, int oz)
+{
+    double r2 = (double)ox * ox + (double)oy * oy + (double)oz * oz;
+    if (!(r2 <= p->shadow_radius * p->shadow_radius))
+        return 0;
+    double u[3];
+    orc_bin_dir(p, b, u);
+    double dot = ((double)ox * u[0] + (double)oy * u[1]) + (double)oz * u[2];
+    return dot >= 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. III-C, first steps for one return: map-frame transform with the pose
+ * (row-major 3x4 [R | t]), voxel of contact, boundary discard and bin.
+ * Returns 0 when the return is discarded.                              */
+int orc_contact(const orc_params *p, const orc_grid *g, const float *xyz,
+                const double pose[12], int64_t c[3], int *bin, int *valid)
+{
+    double px = xyz[0], py = xyz[1], pz = xyz[2];
+    *valid = 0;
+    if (!isfinite(px) || !isfinite(py) || !isfinite(pz))
+        return 0;
+    if (px == 0.0 && py == 0.0 && pz == 0.0)
+        return 0;
+    *valid = 1;
+    double d[3], w[3];
+    for (int r = 0; r < 3; r++) {
+        d[r] = (pose[4 * r + 0] * px + pose[4 * r + 1] * py) + pose[4 * r + 2] * pz;
+        w[r] = d[r] + pose[4 * r + 3];
+    }
+    int R = (p->kernel_size - 1) / 2;
+    int64_t n[3] = {g->nx, g->ny, g->nz};
+    for (int a = 0; a < 3; a++) {
+        double q = floor((w[a] - g->origin[a]) / g->res);
+        if (!(q >= (double)R && q <= (double)(n[a] - 1 - R)))
+            return 0;
+        c[a] = (int64_t)q;
+    }
+    *bin = orc_bin(p, d[0], d[1], d[2]);
+    return 1;
+}
+
+/* Eqs. 4-6 for one kept return with contact voxel c and bin b: every voxel
+ * of the K^3 neighbourhood gets its mask ANDed with the kernel mask (the
+ * write skipped when nothing changes); voxels of the shadow set get their
+ * saturating counter bumped and their sign set to occupied when the counter
+ * crosses T.                                                            */
+static void orc_apply_kernel(orc_grid *g, const orc_params *p, const int64_t c[3], int b,
+                             orc_stats *st)
+{
+    int R = (p->kernel_size - 1) / 2;
+    for (int oz = -R; oz <= R; oz++)
+        for (int oy = -R; oy <= R; oy++)
+            for (int ox = -R; ox <= R; ox++) {
+                int64_t v = ((c[2] + oz) * g->ny + (c[1] + oy)) * g->nx + (c[0] + ox);
+                uint32_t m = g->mask[v];
+                uint32_t k = orc_distance_mask(ox, oy, oz);
+                if (m != (m & k)) {                          /* Eq. 4 */
+                    g->mask[v] = m & k;
+                    st->n_mask_writes++;
+                }
+                if (orc_in_shadow(p, b, ox, oy, oz)) {
+                    int h_old = g->hits[v];
+                    int h_new = h_old + 1;                   /* Eq. 5 */
+                    if (h_new > p->hit_max)
+                        h_new = p->hit_max;
+                    g->hits[v] = (uint16_t)h_new;
+                    if (h_old < p->hit_threshold && h_new >= p->hit_threshold)
+                        g->sign[v] = 0;                      /* Eq. 6 */
+                    st->n_shadow_incs++;
+                }
+            }
+}
+
+/* One scan, returns in array order (Sec. III-C with the first-return rule
+ * of Sec. IV-B).  Returns the number of kept returns, or -1 on a bad
+ * argument or an allocation failure.                                   */
+int64_t orc_integrate_scan(orc_grid *g, const orc_params *p, const float *xyz, int64_t n,
+                           const double pose[12], orc_stats *st_out)
+{
+    orc_stats st;
+    memset(&st, 0, sizeof st);
+    if (p->kernel_size < 1 || (p->kernel_size & 1) == 0)
+        return -1;
+    int64_t nv = g->nx * g->ny * g->nz;
+    uint8_t *seen = NULL;
+    if (p->dedup_first) {
+        seen = (uint8_t *)calloc((size_t)((nv + 7) / 8), 1);
+        if (!seen)
+            return -1;
+    }
+    st.n_input = n;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t c[3];
+        int b, valid;
+        int inside = orc_contact(p, g, xyz + 3 * i, pose, c, &b, &valid);
+        st.n_valid += valid;
+        if (!inside)
+            continue;
+        st.n_inside++;
+        if (seen) {
+            int64_t v = (c[2] * g->ny + c[1]) * g->nx + c[0];
+            if (seen[v >> 3] & (1u << (v & 7)))
+                continue;
+            seen[v >> 3] |= (uint8_t)(1u << (v & 7));
+        }
+        st.n_kept++;
+        orc_apply_kernel(g, p, c, b, &st);
+    }
+    free(seen);
+    if (st_out)
+        *st_out = st;
+    return st.n_kept;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sampled check for grids too large to integrate whole: the state of single
+ * voxels after a sequence of scans, from the same definitions.  A voxel's
+ * final state depends only on the kept returns whose neighbourhood covers
+ * it, folded in scan order; the first-return rule only needs the contact
+ * voxels seen so far in the same scan, kept here in a small hash set.
+ *
+ * Step 1: orc_scan_kept() lists the kept returns of one scan (contact voxel
+ * and bin) in array order.
+ * Step 2: orc_query_voxels() folds Eqs. 4-6 over such lists for each query
+ * voxel, starting from the given state.                                 */
+typedef struct {
+    uint64_t *keys;
+    int64_t cap;
+} orc_set;
+
+static int orc_set_insert(orc_set *s, uint64_t key)
+{
+    /* returns 1 when key was new; keys are stored + 1 so that 0 is empty */
+    uint64_t k = key + 1;
+    uint64_t h = (k * 0x9E3779B97F4A7C15ull) >> 20;
+    for (int64_t probe = 0; probe < s->cap; probe++) {
+        int64_t slot = (int64_t)((h + (uint64_t)probe) & (uint64_t)(s->cap - 1));
+        if (s->keys[slot] == k)
+            return 0;
+        if (s->keys[slot] == 0) {
+            s->keys[slot] = k;
+            return 1;
+        }
+    }
+    return -1;
+}
+
+/* Writes up to n kept returns: c_out[3*m..3*m+2] contact voxel, b_out[m] bin.
+ * Returns the count, or -1 on failure.                                  */
+int64_t orc_scan_kept(const orc_params *p, const orc_grid *g, const float *xyz, int64_t n,
+                      const double pose[12], int64_t *c_out, int32_t *b_out)
+{
+    orc_set set = {NULL, 1};
+    while (set.cap < 2 * n + 2)
+        set.cap <<= 1;
+    if (p->dedup_first) {
+        set.keys = (uint64_t *)calloc((size_t)set.cap, sizeof(uint64_t));
+        if (!set.keys)
+            return -1;
+    }
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t c[3];
+        int b, valid;
+        if (!orc_contact(p, g, xyz + 3 * i, pose, c, &b, &valid))
+            continue;
+        if (p->dedup_first) {
+            uint64_t key = (uint64_t)((c[2] * g->ny + c[1]) * g->nx + c[0]);
+            int r = orc_set_insert(&set, key);
+            if (r < 0) {
+                free(set.keys);
+                return -1;
+            }
+            if (r == 0)
+                continue;
+        }
+        c_out[3 * m + 0] = c[0];
+        c_out[3 * m + 1] = c[1];
+        c_out[3 * m + 2] = c[2];
+        b_out[m] = b;
+        m++;
+    }
+    free(set.keys);
+    return m;
+}
+
+/* Folds the kept returns (already in scan order, several scans concatenated)
+ * into the state of each query voxel q[3*j..3*j+2].  mask/sign/hits hold the
+ * starting state on entry and the final state on return.                */
+void orc_query_voxels(const orc_params *p, int64_t n_kept, const int64_t *c, const int32_t *b,
+                      int64_t nq, const int64_t *q, uint32_t *mask, uint8_t *sign, uint16_t *hits)
+{
+    int R = (p->kernel_size - 1) / 2;
+    for (int64_t j = 0; j < nq; j++) {
+        uint32_t m = mask[j];
+        int h = hits[j];
+        int s = sign[j];
+        for (int64_t i = 0; i < n_kept; i++) {
+            int64_t ox = q[3 * j + 0] - c[3 * i + 0];
+            int64_t oy = q[3 * j + 1] - c[3 * i + 1];
+            int64_t oz = q[3 * j + 2] - c[3 * i + 2];
+            if (ox < -R || ox > R || oy < -R || oy > R || oz < -R || oz > R)
+                continue;
+            uint32_t k = orc_distance_mask((int)ox, (int)oy, (int)oz);
+            if (m != (m & k))
+                m &= k;
+            if (orc_in_shadow(p, b[i], (int)ox, (int)oy, (int)oz)) {
+                int h_new = h + 1;
+                if (h_new > p->hit_max)
+                    h_new = p->hit_max;
+                if (h < p->hit_threshold && h_new >= p->hit_threshold)
+                    s = 0;
+                h = h_new;
+            }
+        }
+        mask[j] = m;
+        hits[j] = (uint16_t)h;
+        sign[j] = (uint8_t)s;
+    }
+}
+
+/* Proposed readout (the paper gives none; parity unpinned): distance in
+ * voxels = popcount(mask) (Sec. III-A: the distance is the number of set
+ * bits), signed by the sign flag (1 free -> +, 0 occupied -> -), times res. */
+double orc_signed_distance(uint32_t mask, uint8_t sign, double res)
+{
+    int bits = 0;
+    for (int i = 0; i < 32; i++)
+        bits += (mask >> i) & 1u;
+    return (sign ? 1.0 : -1.0) * (double)bits * res;
+}

@@ -1,0 +1,368 @@
+"""Seeded synthetic LiDAR workloads (inputs only; none of the method's arithmetic).
+
+This module is the one source of inputs shared by the oracle tests, the CUDA
+parity tests and ``bench.py``.  It builds scenes (box room, urban block),
+trajectories and spinning-LiDAR scans by analytic ray casting.  It never
+quantises, bins or integrates anything: it only produces float32 returns in
+the sensor frame and float64 SE(3) poses.
+
+Random numbers come from a counter-based SplitMix64 (Steele, Lea, Flood,
+"Fast splittable pseudorandom number generators", OOPSLA 2014) with uniform
+doubles from the top 53 bits and normals by Box-Muller, so a seed gives the
+same scan on every machine and numpy version.
+
+Workloads (the stand-in for the paper's Newer College / Mai City datasets,
+which are not available here):
+  * ``room_scan``      box room 12.8 m cube, 16 x 900 scan, +-15 deg, 0.5-12 m
+  * ``urban_sequence`` urban block (ground, 40 buildings, 200 poles),
+                       64 x 1024 scans, +-22.5 deg, 1-60 m, 1 m per scan
+  * ``batched_maps``   uneven maps each with a few room scans
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 2509200810
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+class Rng:
+    """Counter-based SplitMix64 stream: draw k returns mix(seed + (c+1..c+k) * golden)."""
+
+    def __init__(self, seed: int):
+        self.seed = np.uint64(seed & 0xFFFFFFFFFFFFFFFF)
+        self.counter = 0
+
+    def u64(self, n: int) -> np.ndarray:
+        idx = np.arange(self.counter + 1, self.counter + 1 + n, dtype=np.uint64)
+        self.counter += n
+        with np.errstate(over="ignore"):
+            return _mix64(self.seed + idx * _GOLDEN)
+
+    def uniform(self, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+        u = (self.u64(n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+        return lo + (hi - lo) * u
+
+    def normal(self, n: int, sigma: float = 1.0) -> np.ndarray:
+        u1 = 1.0 - self.uniform(n)          # (0, 1]
+        u2 = self.uniform(n)
+        return sigma * np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+    def log_uniform(self, n: int, lo: float, hi: float) -> np.ndarray:
+        return np.exp(self.uniform(n, math.log(lo), math.log(hi)))
+
+    def integers(self, n: int, lo: int, hi: int) -> np.ndarray:
+        """Uniform integers in [lo, hi)."""
+        return lo + np.floor(self.uniform(n) * (hi - lo)).astype(np.int64)
+
+
+# ---------------------------------------------------------------- scenes
+@dataclass
+class Scene:
+    """Analytic scene: horizontal planes, inward walls, boxes, vertical cylinders."""
+    ground_z: float | None = None                 # infinite floor plane z = ground_z
+    walls: tuple | None = None                     # (x0, x1, y0, y1, z_top) inner faces
+    boxes: np.ndarray = field(default_factory=lambda: np.zeros((0, 6)))   # x0 y0 z0 x1 y1 z1
+    cylinders: np.ndarray = field(default_factory=lambda: np.zeros((0, 5)))  # cx cy r z0 z1
+
+
+def room_scene(rng: Rng, extent: float = 12.8, sensor=(6.4, 6.4, 6.4), n_boxes: int = 6) -> Scene:
+    """Box room: floor at 3/8 of the height, 4 walls up to 3/4, no ceiling,
+    n_boxes axis-aligned boxes on the floor at least 1/12.8 of the extent
+    (1 m at 12.8 m) away from the sensor.  Lengths scale with ``extent``."""
+    s = extent / 12.8
+    x0, x1 = 0.8 * s, 12.0 * s
+    floor = 4.8 * s
+    top = 9.6 * s
+    boxes = []
+    while len(boxes) < n_boxes:
+        sx, sy, sz = rng.uniform(3, 0.3 * s, 2.0 * s)
+        cx, cy = rng.uniform(2, x0 + 0.2 * s, x1 - 0.2 * s)
+        bx0, bx1 = cx - sx / 2, cx + sx / 2
+        by0, by1 = cy - sy / 2, cy + sy / 2
+        if bx0 < x0 or bx1 > x1 or by0 < x0 or by1 > x1:
+            continue
+        # horizontal distance from sensor to the box footprint
+        dx = max(bx0 - sensor[0], 0.0, sensor[0] - bx1)
+        dy = max(by0 - sensor[1], 0.0, sensor[1] - by1)
+        if math.hypot(dx, dy) < 1.0 * s:
+            continue
+        boxes.append((bx0, by0, floor, bx1, by1, floor + sz))
+    return Scene(ground_z=floor, walls=(x0, x1, x0, x1, top), boxes=np.array(boxes))
+
+
+def closed_path(t: np.ndarray, centre, radius: float):
+    """Smooth closed curve (Lissajous-like) of the given radius around centre."""
+    cx, cy = centre
+    x = cx + radius * np.cos(t)
+    y = cy + 0.88 * radius * np.sin(t) + 0.12 * radius * np.sin(2.0 * t)
+    return x, y
+
+
+def urban_scene(rng: Rng, extent: float = 80.0, height: float = 16.0, ground: float = 1.0,
+                n_buildings: int = 40, n_poles: int = 200, path_radius: float = 25.0,
+                corridor: float = 6.0, scale: float = 1.0) -> Scene:
+    """Ground plane, box buildings (footprint 4-15 m, height 3-14 m) clear of a
+    ``corridor`` around the closed path, and vertical poles (r 0.1-0.4 m,
+    height 2-6 m) at least 1 m off the path; every length times ``scale``."""
+    centre = (extent / 2.0, extent / 2.0)
+    tt = np.linspace(0.0, 2.0 * np.pi, 2000, endpoint=False)
+    px, py = closed_path(tt, centre, path_radius)
+    margin = 1.0 * scale
+
+    def path_dist_box(x0, y0, x1, y1):
+        dx = np.maximum(np.maximum(x0 - px, 0.0), px - x1)
+        dy = np.maximum(np.maximum(y0 - py, 0.0), py - y1)
+        return float(np.min(np.hypot(dx, dy)))
+
+    boxes = []
+    tries = 0
+    while len(boxes) < n_buildings and tries < 100000:
+        tries += 1
+        fx, fy = rng.uniform(2, 4.0 * scale, 15.0 * scale)
+        h = float(rng.uniform(1, 3.0 * scale, 14.0 * scale)[0])
+        cx, cy = rng.uniform(2, margin + fx / 2, extent - margin - fx / 2)
+        x0, x1, y0, y1 = cx - fx / 2, cx + fx / 2, cy - fy / 2, cy + fy / 2
+        if x0 < margin or y0 < margin or x1 > extent - margin or y1 > extent - margin:
+            continue
+        if path_dist_box(x0, y0, x1, y1) < corridor * scale:
+            continue
+        boxes.append((x0, y0, ground, x1, y1, min(ground + h, height - margin)))
+    cyl = []
+    tries = 0
+    while len(cyl) < n_poles and tries < 100000:
+        tries += 1
+        r = float(rng.uniform(1, 0.1 * scale, 0.4 * scale)[0])
+        h = float(rng.uniform(1, 2.0 * scale, 6.0 * scale)[0])
+        cx, cy = rng.uniform(2, margin, extent - margin)
+        if float(np.min(np.hypot(px - cx, py - cy))) < r + 1.0 * scale:
+            continue
+        cyl.append((cx, cy, r, ground, ground + h))
+    return Scene(ground_z=ground, walls=None, boxes=np.array(boxes), cylinders=np.array(cyl))
+
+
+# ---------------------------------------------------------------- ray casting
+def _raycast(scene: Scene, origin: np.ndarray, dirs: np.ndarray) -> np.ndarray:
+    """Nearest positive hit distance along unit rays (inf = no hit)."""
+    n = dirs.shape[0]
+    best = np.full(n, np.inf)
+    ox, oy, oz = origin
+    dx, dy, dz = dirs[:, 0], dirs[:, 1], dirs[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        if scene.ground_z is not None:
+            t = (scene.ground_z - oz) / dz
+            ok = (dz < 0) & (t > 0)
+            best = np.where(ok & (t < best), t, best)
+        if scene.walls is not None:
+            x0, x1, y0, y1, top = scene.walls
+            for (plane, comp, o, sgn) in ((x0, dx, ox, -1), (x1, dx, ox, 1),
+                                          (y0, dy, oy, -1), (y1, dy, oy, 1)):
+                t = (plane - o) / comp
+                ok = (sgn * comp > 0) & (t > 0)
+                z = oz + t * dz
+                ok &= z <= top
+                if scene.ground_z is not None:
+                    ok &= z >= scene.ground_z
+                best = np.where(ok & (t < best), t, best)
+        inv = 1.0 / np.where(dirs == 0.0, 1e-300, dirs)
+        for b in scene.boxes:
+            t1 = (b[0:3] - origin) * inv
+            t2 = (b[3:6] - origin) * inv
+            tn = np.max(np.minimum(t1, t2), axis=1)
+            tf = np.min(np.maximum(t1, t2), axis=1)
+            ok = (tn <= tf) & (tn > 0)
+            best = np.where(ok & (tn < best), tn, best)
+        if scene.cylinders.shape[0]:
+            a = dx * dx + dy * dy
+            for c in scene.cylinders:
+                cx, cy, r, z0, z1 = c
+                fx, fy = ox - cx, oy - cy
+                bb = 2.0 * (fx * dx + fy * dy)
+                cc = fx * fx + fy * fy - r * r
+                disc = bb * bb - 4.0 * a * cc
+                t = (-bb - np.sqrt(np.maximum(disc, 0.0))) / (2.0 * a)
+                z = oz + t * dz
+                ok = (disc >= 0) & (a > 0) & (t > 0) & (z >= z0) & (z <= z1)
+                best = np.where(ok & (t < best), t, best)
+                # top cap
+                tc = (z1 - oz) / dz
+                hx, hy = ox + tc * dx - cx, oy + tc * dy - cy
+                okc = (dz < 0) & (tc > 0) & (hx * hx + hy * hy <= r * r)
+                best = np.where(okc & (tc < best), tc, best)
+    return best
+
+
+def rotation_rpy(roll: float, pitch: float, yaw: float) -> np.ndarray:
+    """R = Rz(yaw) Ry(pitch) Rx(roll)."""
+    cr, sr = math.cos(roll), math.sin(roll)
+    cp, sp = math.cos(pitch), math.sin(pitch)
+    cy, sy = math.cos(yaw), math.sin(yaw)
+    Rz = np.array([[cy, -sy, 0], [sy, cy, 0], [0, 0, 1]])
+    Ry = np.array([[cp, 0, sp], [0, 1, 0], [-sp, 0, cp]])
+    Rx = np.array([[1, 0, 0], [0, cr, -sr], [0, sr, cr]])
+    return Rz @ Ry @ Rx
+
+
+def make_pose(R: np.ndarray, t) -> np.ndarray:
+    """Row-major 3x4 [R | t] float64."""
+    P = np.zeros((3, 4))
+    P[:, :3] = R
+    P[:, 3] = t
+    return P
+
+
+def lidar_scan(scene: Scene, pose: np.ndarray, beams: int, width: int, fov_deg: float,
+               rmin: float, rmax: float, sigma: float, dropout: float, rng: Rng,
+               chunk: int = 16384) -> np.ndarray:
+    """Spinning LiDAR: ``beams`` elevations in [-fov/2, +fov/2], ``width``
+    azimuths k 2 pi / width; returns (beams * width, 3) float32 in the sensor
+    frame, beam-major; misses, out-of-range and dropped returns are NaN."""
+    el = np.deg2rad(np.linspace(-fov_deg / 2.0, fov_deg / 2.0, beams))
+    az = np.arange(width) * (2.0 * np.pi / width)
+    E, A = np.meshgrid(el, az, indexing="ij")
+    ds = np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1).reshape(-1, 3)
+    R = pose[:, :3]
+    origin = pose[:, 3]
+    dw = ds @ R.T
+    n = ds.shape[0]
+    t = np.empty(n)
+    for s in range(0, n, chunk):
+        t[s:s + chunk] = _raycast(scene, origin, dw[s:s + chunk])
+    t = t + rng.normal(n, sigma)
+    drop = rng.uniform(n) < dropout
+    bad = ~np.isfinite(t) | (t < rmin) | (t > rmax) | drop
+    pts = ds * t[:, None]
+    pts[bad] = np.nan
+    return pts.astype(np.float32)
+
+
+# ---------------------------------------------------------------- workloads
+@dataclass
+class GridSpec:
+    nx: int
+    ny: int
+    nz: int
+    res: float
+    origin: tuple = (0.0, 0.0, 0.0)
+
+
+@dataclass
+class Workload:
+    name: str
+    grid: GridSpec
+    scans: list           # list of (points float32 (n,3), pose float64 (3,4))
+    params: dict          # kernel_size, scheme, bins_a, bins_b, shadow_radius, ...
+
+
+DEFAULT_PARAMS = dict(kernel_size=11, scheme=0, bins_a=8, bins_b=8, shadow_radius=3.0,
+                      hit_threshold=3, hit_max=255, dedup_first=1)
+
+
+def room_scan(seed_offset: int = 0, side: int = 128, res: float = 0.10, beams: int = 16,
+              width: int = 900, sigma: float = 0.01, n_scans: int = 1) -> Workload:
+    """Single-scan room workload: side^3 grid at res, sensor at the centre,
+    identity pose, 16 x 900 returns, +-15 deg, 0.5-12 m (scaled with the room)."""
+    rng = Rng(BASE_SEED + seed_offset)
+    extent = side * res
+    c = extent / 2.0
+    scene = room_scene(rng, extent=extent, sensor=(c, c, c))
+    scans = []
+    for k in range(n_scans):
+        # later scans (if any) jitter the sensor a little inside the room
+        off = np.zeros(3) if k == 0 else rng.uniform(3, -0.05 * extent, 0.05 * extent)
+        pose = make_pose(np.eye(3) if k == 0 else rotation_rpy(0.0, 0.0, float(rng.uniform(1, 0, 6.283)[0])),
+                         np.array([c, c, c]) + off)
+        scale = extent / 12.8
+        pts = lidar_scan(scene, pose, beams, width, 30.0, 0.5 * scale, 12.0 * scale, sigma, 0.0, rng)
+        scans.append((pts, pose))
+    return Workload("room", GridSpec(side, side, side, res), scans, dict(DEFAULT_PARAMS))
+
+
+def urban_sequence(n_scans: int = 100, seed_offset: int = 1, scale: float = 1.0,
+                   res: float = 0.05, beams: int = 64, width: int = 1024,
+                   rmax: float = 60.0) -> Workload:
+    """Urban sequence: grid (80x80x16 m) * scale at res; poses every 1 m * scale
+    along a closed path of radius 25 m * scale, yaw along the tangent with
+    +-3 deg roll/pitch sinusoids; 2 cm * scale range noise; 2 % dropouts."""
+    rng = Rng(BASE_SEED + seed_offset)
+    extent, height, ground = 80.0 * scale, 16.0 * scale, 1.0 * scale
+    scene = urban_scene(rng, extent=extent, height=height, ground=ground,
+                        path_radius=25.0 * scale, scale=scale)
+    nx = int(round(extent / res))
+    nz = int(round(height / res))
+    centre = (extent / 2.0, extent / 2.0)
+    # arc-length sampling of the path every 1 m * scale
+    tt = np.linspace(0.0, 2.0 * np.pi, 20001)
+    x, y = closed_path(tt, centre, 25.0 * scale)
+    seg = np.hypot(np.diff(x), np.diff(y))
+    s = np.concatenate([[0.0], np.cumsum(seg)])
+    scans = []
+    for k in range(n_scans):
+        sk = (k * 1.0 * scale) % s[-1]
+        i = int(np.searchsorted(s, sk))
+        i = min(max(i, 1), len(tt) - 1)
+        yaw = math.atan2(y[i] - y[i - 1], x[i] - x[i - 1])
+        roll = math.radians(3.0) * math.sin(0.31 * k)
+        pitch = math.radians(3.0) * math.sin(0.17 * k + 1.0)
+        pose = make_pose(rotation_rpy(roll, pitch, yaw), (x[i], y[i], ground + 1.8 * scale))
+        pts = lidar_scan(scene, pose, beams, width, 45.0, 1.0 * scale, rmax, 0.02 * scale,
+                         0.02, rng)
+        scans.append((pts, pose))
+    return Workload("urban", GridSpec(nx, nx, nz, res), scans, dict(DEFAULT_PARAMS))
+
+
+def batched_maps(n_maps: int = 32, scans_per_map: int = 8, seed_offset: int = 3,
+                 side_lo: int = 64, side_hi: int = 512, n_lo: int = 4096,
+                 n_hi: int = 131072) -> list:
+    """Uneven independent maps: side log-uniform in [side_lo, side_hi] rounded
+    to a multiple of 32, res uniform in [0.05, 0.2] m, the room scene scaled
+    to the map, scans of n log-uniform in [n_lo, n_hi] returns as 16 beams x
+    n/16 azimuths, per-map seeds."""
+    rng = Rng(BASE_SEED + seed_offset)
+    sides = np.maximum(32, np.round(rng.log_uniform(n_maps, side_lo, side_hi) / 32.0) * 32).astype(int)
+    ress = rng.uniform(n_maps, 0.05, 0.2)
+    out = []
+    for m in range(n_maps):
+        mrng = Rng(BASE_SEED + 1000 * (seed_offset + 1) + m)
+        side, res = int(sides[m]), float(ress[m])
+        extent = side * res
+        c = extent / 2.0
+        scene = room_scene(mrng, extent=extent, sensor=(c, c, c))
+        scans = []
+        for k in range(scans_per_map):
+            n = int(mrng.log_uniform(1, n_lo, n_hi)[0])
+            width = max(1, n // 16)
+            off = mrng.uniform(3, -0.08 * extent, 0.08 * extent)
+            pose = make_pose(rotation_rpy(0.0, 0.0, float(mrng.uniform(1, 0.0, 6.283)[0])),
+                             np.array([c, c, c]) + off)
+            scale = extent / 12.8
+            pts = lidar_scan(scene, pose, 16, width, 30.0, 0.5 * scale, 12.0 * scale,
+                             0.01 * scale, 0.0, mrng)
+            scans.append((pts, pose))
+        out.append(Workload(f"map{m}", GridSpec(side, side, side, res), scans, dict(DEFAULT_PARAMS)))
+    return out
+
+
+def random_points(rng: Rng, n: int, lo, hi) -> np.ndarray:
+    """Uniform float32 points in the box [lo, hi) (tiny brute-force cases)."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    u = rng.uniform(3 * n).reshape(n, 3)
+    return (lo + (hi - lo) * u).astype(np.float32)
+
+
+def random_rotation(rng: Rng) -> np.ndarray:
+    """Uniform-ish random rotation from three angles."""
+    a = rng.uniform(3, -math.pi, math.pi)
+    return rotation_rpy(float(a[0]), float(a[1]) / 2.0, float(a[2]))
