@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""DB-TSDF scan-integration benchmark (one JSON line on stdout).
+
+Default workload: the urban sequence -- 100 scans of a 64-beam spinning
+LiDAR (64 x 1024 = 65,536 float32 returns, +-22.5 deg, 1-60 m, 2 cm noise,
+2 % dropouts) along a closed trajectory (1 m per scan, float64 SE(3) poses)
+through a synthetic urban block (ground, 40 buildings, 200 poles), into a
+dense 1600 x 1600 x 320 grid at 0.05 m (80 x 80 x 16 m), K = 11, 64
+octahedral bins, r_s = 3, T = 3, H_max = 255.  Synthetic data stands in for
+the paper's Newer College / Mai City sequences.
+
+A step is one scan through the whole path (transform, voxel, bin, first
+return rule, brick binning, integration of Eqs. 4-6).  W warm-up scans run
+on the grid, which is then re-initialised, and K scans are timed in
+trajectory order from an empty map (scan k = trajectory scan k mod 100), as
+in online mapping.  The 5.7 GB grid exceeds the 129 MB L2; consecutive scans
+share map regions as a moving robot's do, and no L2 flush is inserted.
+
+value: returns/s with the scans resident in HBM; e2e: the same through the
+host-buffer entry point dbt_integrate_scan_host (pinned host scans copied
+in, scan counters copied out, inside the timed region).  roofline: the brick
+integration kernel's algorithmic bytes (4 U + 4 W + 6 U_s per scan: read
+every covered mask, write the masks that change, read and write counter and
+sign of every shadow voxel; U, U_s and W counted exactly per scan before
+timing) over its CUDA-event time, against the measured HBM copy bandwidth.
+
+--impl reference times the oracle (plain single-threaded C) on the same
+workload and metric, on a bounded sample of returns per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "LiDAR points integrated/sec (ms/scan)"
+UNIT = "points/s"
+INTEGRATE_SRC = os.path.join(ROOT, "paper_2509_20081_gb300", "csrc", "integrate.cu")
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_integrate, per kept
+# return, from the capture summarised under profiles/ (valid only for the
+# integrate.cu source with this sha256 prefix; otherwise traffic is null).
+NCU_TRAFFIC = {"integrate_sha": None, "bytes_per_kept_return": None}
+
+WORKLOADS = {
+    "urban": dict(n_scans=100, scale=1.0, res=0.05, beams=64, width=1024, seed_offset=1),
+    "urban_half": dict(n_scans=20, scale=0.5, res=0.05, beams=64, width=1024, seed_offset=1),
+    "highres": dict(n_scans=50, scale=0.5, res=0.02, beams=128, width=2048, seed_offset=2),
+}
+
+
+def load_workload(name: str) -> synth.Workload:
+    """Generate (or reuse from a per-machine cache) the workload's scans."""
+    if name == "room":
+        return synth.room_scan()
+    kw = WORKLOADS[name]
+    key = hashlib.sha256((name + json.dumps(kw, sort_keys=True) +
+                          open(os.path.join(ROOT, "synth", "__init__.py")).read()).encode()).hexdigest()[:16]
+    cache = os.path.join(tempfile.gettempdir(), f"dbtsdf_{name}_{key}.npz")
+    w0 = None
+    if os.path.exists(cache):
+        try:
+            z = np.load(cache)
+            g = synth.GridSpec(*[int(v) for v in z["dims"]], float(z["res"]))
+            scans = [(z["pts"][i], z["poses"][i]) for i in range(z["pts"].shape[0])]
+            return synth.Workload(name, g, scans, dict(synth.DEFAULT_PARAMS))
+        except Exception:
+            pass
+    w0 = synth.urban_sequence(**kw)
+    tmp = cache + f".{os.getpid()}.npz"
+    np.savez(tmp, pts=np.stack([s[0] for s in w0.scans]), poses=np.stack([s[1] for s in w0.scans]),
+             dims=np.array([w0.grid.nx, w0.grid.ny, w0.grid.nz]), res=np.array(w0.grid.res))
+    os.replace(tmp, cache)
+    return w0
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (SM clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def integrate_sha() -> str:
+    return hashlib.sha256(open(INTEGRATE_SRC, "rb").read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ CPU baseline
+def cpu_baseline(w: synth.Workload, budget_s: float = 15.0, max_scans: int | None = None):
+    """Oracle (single-threaded C) on the first scans of the workload until
+    ~budget_s of CPU work; returns (points/s, scans run, seconds)."""
+    import oracle
+    g = oracle.Grid.create(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.res, w.grid.origin)
+    p = oracle.params(**w.params)
+    t0 = time.perf_counter()
+    done = 0
+    pts_total = 0
+    for pts, pose in w.scans:
+        oracle.integrate_scan(g, p, pts, pose)
+        done += 1
+        pts_total += len(pts)
+        if time.perf_counter() - t0 > budget_s or (max_scans and done >= max_scans):
+            break
+    dt = time.perf_counter() - t0
+    return pts_total / dt, done, dt
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w = load_workload(args.workload)
+    import oracle
+    p = oracle.params(**w.params)
+    g = oracle.Grid.create(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.res, w.grid.origin)
+    stride = args.ref_stride
+    times = []
+    pts_done = 0
+    for s in range(args.warmup + args.steps):
+        pts, pose = w.scans[s % len(w.scans)]
+        sample = np.ascontiguousarray(pts[::stride])
+        t0 = time.perf_counter()
+        oracle.integrate_scan(g, p, sample, pose)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            pts_done += len(sample)
+    total = sum(times)
+    value = pts_done / total
+    sample_desc = (f"every {stride}th return of each scan ({pts_done // max(1, args.steps)} "
+                   f"returns/step) of the {args.workload} workload, grid at full size")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": workload_config(args, w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample_desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args, w):
+    return {"workload": f"{args.workload}: {len(w.scans)} scans x {len(w.scans[0][0])} returns, "
+                        f"grid {w.grid.nx}x{w.grid.ny}x{w.grid.nz} at {w.grid.res} m",
+            "kernel": w.params["kernel_size"], "bins": "octahedral 8x8",
+            "shadow_radius": w.params["shadow_radius"], "T": w.params["hit_threshold"],
+            "H_max": w.params["hit_max"], "points_per_scan": len(w.scans[0][0]),
+            "parallelism": f"replicas x{args.gpus}",
+            "l2": "grid larger than L2 (no flush); consecutive scans overlap as on a trajectory"}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2509_20081_gb300 as dbt
+    from paper_2509_20081_gb300 import dbtsdf as B
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = load_workload(args.workload)
+    nsc = len(w.scans)
+    npts = len(w.scans[0][0])
+    p = dbt.make_params(**w.params)
+    k = dbt.Kernels(p)
+    g = dbt.Grid(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.res, w.grid.origin)
+    ws = dbt.Workspace(g, k, npts)
+    d_scans = [torch.from_numpy(s[0]).to(dev) for s in w.scans]
+    poses = [s[1] for s in w.scans]
+    stream = torch.cuda.current_stream()
+
+    # exact footprint (U, U_s) and changed masks W per scan, from an empty map
+    bits = torch.empty(B.footprint_bytes(g), dtype=torch.uint8, device=dev)
+    alg = []
+    kept = []
+    for s in range(nsc):
+        u, us = B.dbt_scan_footprint(g, k, ws, d_scans[s], poses[s], bits)
+        before = g.mask.clone()
+        dbt.dbt_integrate_scan(g, k, ws, d_scans[s], poses[s])
+        st = dbt.dbt_get_scan_stats(ws)
+        wchg = int((g.mask != before).sum())
+        del before
+        alg.append(4 * u + 4 * wchg + 6 * us)
+        kept.append(st["n_kept"])
+    del bits
+    torch.cuda.empty_cache()
+
+    # warm-up, then a fresh map
+    for s in range(args.warmup):
+        dbt.dbt_integrate_scan(g, k, ws, d_scans[s % nsc], poses[s % nsc])
+    dbt.dbt_grid_init(g)
+    ws.reset()
+    evb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    eve = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index) if rank == 0 else None
+    t0.record(stream)
+    for s in range(args.steps):
+        B.dbt_workspace_set_timing(ws, evb[s], eve[s])
+        dbt.dbt_integrate_scan(g, k, ws, d_scans[s % nsc], poses[s % nsc])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    B.dbt_workspace_set_timing(ws, None, None)
+    ms = t0.elapsed_time(t1)
+    st = dbt.dbt_get_scan_stats(ws)
+    assert st["error"] == 0, st
+    t_int = [evb[s].elapsed_time(eve[s]) for s in range(args.steps)]
+    bytes_alg = sum(alg[s % nsc] for s in range(args.steps))
+    kept_timed = sum(kept[s % nsc] for s in range(args.steps))
+
+    # end to end through the host-buffer entry point
+    dbt.dbt_grid_init(g)
+    ws.reset()
+    h_scans = [torch.from_numpy(s[0]).pin_memory() for s in w.scans]
+    h_stats = torch.zeros((args.steps, 64), dtype=torch.uint8).pin_memory()
+    st_ptrs = [B.dbt_scan_stats.from_address(h_stats[s].data_ptr()) for s in range(args.steps)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(args.steps):
+        B.dbt_integrate_scan_host(g, k, ws, h_scans[s % nsc], poses[s % nsc], st_ptrs[s])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    assert all(sp.error == 0 for sp in st_ptrs)
+
+    tmax = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    ms, ms_e2e = float(tmax[0]), float(tmax[1])
+    if rank != 0:
+        return 0
+
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_alg / (sum(t_int) * 1e-3) / 1e9
+    traffic = None
+    if NCU_TRAFFIC["integrate_sha"] == integrate_sha() and NCU_TRAFFIC["bytes_per_kept_return"]:
+        traffic = NCU_TRAFFIC["bytes_per_kept_return"] * kept_timed / args.steps
+    line = {
+        "metric": METRIC, "value": world * args.steps * npts / (ms * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": workload_config(args, w),
+        "kept_points_per_s": world * kept_timed / (ms * 1e-3),
+        "e2e": {"value": world * args.steps * npts / (ms_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": npts * 12, "d2h_bytes_per_step": 64,
+                "ms_per_step": ms_e2e / args.steps},
+        "gpu_launches": 5 * args.steps,
+        "roofline": {"bound": "hbm", "kernel": "k_integrate", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "alg_bytes_per_launch": bytes_alg / args.steps,
+                     "ms_per_launch": statistics.mean(t_int),
+                     "share_of_step": sum(t_int) / ms},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world >= 1:
+        v, nsc_run, secs = cpu_baseline(w, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {nsc_run} scans of the workload, full grid, "
+                                          f"{secs:.1f} s of single-thread CPU"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["urban", "urban_half", "highres"], default="urban")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-stride", type=int, default=16,
+                    help="reference arm: integrate every n-th return of each scan")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,233 @@
+/*
+ * dbtsdf.h -- C ABI of the GB300 DB-TSDF scan-integration library.
+ *
+ * DB-TSDF (arXiv 2509.20081) stores a dense voxel grid whose voxels hold a
+ * 32-bit distance mask, a sign flag and a hit counter (Sec. III-A).  Each
+ * LiDAR return selects a precomputed directional kernel by its direction
+ * bin (Sec. III-B, Eq. 2) and updates the K^3 neighbourhood of its contact
+ * voxel: masks are ANDed with the kernel's distance masks (Eqs. 3-4), and
+ * the voxels of the hemispherical shadow get a saturating hit count and,
+ * on crossing the threshold, the occupied sign (Eqs. 5-6).
+ *
+ * Conventions
+ *  - Every function returns a dbt_status; nothing throws across the ABI.
+ *    Argument errors are reported synchronously (DBT_EINVAL) with a message
+ *    in dbt_last_error().  Work is enqueued asynchronously on the given
+ *    CUDA stream (a cudaStream_t passed as void*; NULL = legacy default
+ *    stream).  Device-side errors are latched in the workspace and reported
+ *    by dbt_sync() / dbt_get_scan_stats().
+ *  - The caller owns every device buffer (grid arrays, point buffers, the
+ *    workspace scratch) and every stream.  The library owns only the kernel
+ *    tables made by dbt_kernels_build() and small host-side handles.
+ *  - Device pointers are marked d_, host pointers h_.  Pointers must stay
+ *    valid until the enqueued work has finished.
+ *  - Grid layout: three Structure-of-Arrays planes, each [nz][ny][pitch_x]
+ *    with x fastest; voxel (x, y, z) is element (z * ny + y) * pitch_x + x.
+ *    pitch_x = nx rounded up to a multiple of 32 (dbt_grid_layout); mask
+ *    rows are 128-byte aligned when the array base is 256-byte aligned,
+ *    which every base pointer must be.  Padding voxels (x >= nx) are
+ *    initialised and never changed by integration.
+ *  - Thread safety: calls on different grids/workspaces may run from
+ *    different host threads; one workspace must not be used by two scans
+ *    at the same time.
+ */
+#ifndef DBTSDF_H
+#define DBTSDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DBT_OK = 0,
+    DBT_EINVAL = 1,    /* bad argument; nothing was enqueued */
+    DBT_ENOMEM = 2,    /* host/device allocation failed, or a buffer is too small */
+    DBT_ECUDA = 3,     /* a CUDA runtime call failed (message in dbt_last_error) */
+    DBT_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    DBT_ESTATE = 5     /* the device latched an error in the workspace */
+} dbt_status;
+
+typedef enum {
+    DBT_BINS_OCTA = 0, /* n x n octahedral cells (bins_a = bins_b = n) */
+    DBT_BINS_AZEL = 1  /* Eq. 2: bins_a = B_az azimuth x bins_b = B_el elevation */
+} dbt_bin_scheme;
+
+/* Kernel and update parameters (Sec. III-B, III-C).
+ *  kernel_size   K, odd, 1..21 (the paper uses 21); neighbourhood [-R, R]^3,
+ *                R = (K - 1) / 2.
+ *  scheme        dbt_bin_scheme.
+ *  bins_a/b      octa: n and n, 1 <= n <= 64; azel: B_az, B_el in 1..256
+ *                (the paper uses 40 x 40).
+ *  shadow_radius r_s in voxels, 0 <= r_s (the shadow is clipped to the
+ *                kernel cube).
+ *  hit_threshold T, 1 <= T <= hit_max (Eq. 6).
+ *  hit_max       H_max, 1 <= H_max <= 65535 (Eq. 5).
+ *  dedup_first   1: only the first return (lowest index) per contact voxel
+ *                and scan is integrated (Sec. IV-B); 0: every return. */
+typedef struct {
+    int32_t kernel_size;
+    int32_t scheme;
+    int32_t bins_a;
+    int32_t bins_b;
+    double shadow_radius;
+    int32_t hit_threshold;
+    int32_t hit_max;
+    int32_t dedup_first;
+    int32_t reserved;  /* must be 0 */
+} dbt_params;
+
+/* A dense grid.  mask/sign/hits are device arrays of pitch_x * ny * nz
+ * elements each (uint32 / uint8 / uint16), 256-byte aligned.  res > 0 is
+ * the voxel edge in metres; origin is the map-frame corner of voxel 0. */
+typedef struct {
+    uint32_t *mask;
+    uint8_t *sign;
+    uint16_t *hits;
+    int32_t nx, ny, nz;
+    int32_t pitch_x;
+    double res;
+    double origin[3];
+} dbt_grid;
+
+/* Opaque directional kernel tables (Eq. 3 distance masks, per-bin shadow
+ * sets, Eq. 2 bin edges), built on the host and uploaded once; shareable by
+ * any number of grids and streams. */
+typedef struct dbt_kernels dbt_kernels;
+
+/* Counters of the last completed scan of a workspace. */
+typedef struct {
+    int64_t n_input;    /* returns handed in */
+    int64_t n_valid;    /* finite and not at the sensor origin */
+    int64_t n_inside;   /* K^3 neighbourhood inside the grid (Sec. III-C) */
+    int64_t n_kept;     /* integrated after the first-return rule */
+    int64_t n_pairs;    /* (return, brick) work items */
+    int64_t n_bricks;   /* bricks touched */
+    uint32_t error;     /* device error bits, 0 = none */
+    uint32_t reserved;
+} dbt_scan_stats;
+
+/* Eq. 1 sizing for the build's layout: pitch_x and bytes of each plane.
+ * Any output pointer may be NULL.  EINVAL for non-positive or too large
+ * dimensions (pitch_x * ny * nz must fit in 2^40 voxels). */
+dbt_status dbt_grid_layout(int32_t nx, int32_t ny, int32_t nz, int32_t *pitch_x,
+                           size_t *mask_bytes, size_t *sign_bytes, size_t *hits_bytes);
+
+/* Sec. III-A initial state on every voxel (padding included): mask all ones,
+ * sign free (1), hits 0.  Asynchronous on stream. */
+dbt_status dbt_grid_init(const dbt_grid *g, void *stream);
+
+/* Builds the kernel tables for p on the host and uploads them (synchronous;
+ * allocates device memory owned by *out).  EINVAL on a bad parameter. */
+dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out);
+
+/* Frees the tables.  The caller must make sure no enqueued work uses them. */
+dbt_status dbt_kernels_destroy(dbt_kernels *k);
+
+/* Host copies of the tables, for checking them against an independent
+ * build.  h_mask: K^3 uint32 Eq. 3 masks, [oz][oy][ox] with o + R as the
+ * index.  h_shadow: bins * K^3 bytes, 1 where offset o is in the shadow of
+ * bin b (Sec. III-B).  Either pointer may be NULL. */
+dbt_status dbt_kernels_export(const dbt_kernels *k, uint32_t *h_mask, uint8_t *h_shadow);
+
+/* The same tables built on the host only (no GPU needed), in the layout of
+ * dbt_kernels_export: h_mask K^3 uint32, h_shadow bins * K^3 bytes. */
+dbt_status dbt_tables_host(const dbt_params *p, uint32_t *h_mask, uint8_t *h_shadow);
+
+/* Bin id of each direction (Eq. 2 or octahedral), computed on the device by
+ * the same routine the integration uses: d_dirs n x 3 float64 map-frame
+ * directions, d_bins n int32 outputs (-1 for a zero direction).  Async. */
+dbt_status dbt_bin_directions(const dbt_kernels *k, const double *d_dirs, int64_t n,
+                              int32_t *d_bins, void *stream);
+
+/* Handle over a caller-owned device scratch buffer used by integration: the
+ * first-return hash table, per-return records, brick counters and the
+ * (return, brick) work lists.  The handle is host memory; the library never
+ * allocates device memory for it.  One workspace serves one grid geometry
+ * and one scan at a time. */
+typedef struct dbt_workspace dbt_workspace;
+
+/* Bytes of device scratch a workspace needs for grid g, tables k and scans
+ * of up to max_points returns (max_points >= 1). */
+dbt_status dbt_workspace_size(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
+                              size_t *bytes);
+
+/* Wraps d_buf (256-byte aligned, >= dbt_workspace_size bytes, owned by the
+ * caller) and zero-fills it asynchronously on stream. */
+dbt_status dbt_workspace_create(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
+                                void *d_buf, size_t bytes, void *stream, dbt_workspace **out);
+
+/* Zero-fills the scratch again (after a device error or an aborted scan). */
+dbt_status dbt_workspace_reset(dbt_workspace *ws, void *stream);
+
+/* Frees the handle (not the caller's device buffer). */
+dbt_status dbt_workspace_destroy(dbt_workspace *ws);
+
+/* Integrates one scan (Sec. III-C).  d_xyz: n returns, float32 xyz
+ * interleaved (12 bytes each, 4-byte aligned), in the sensor frame; NaN,
+ * inf and origin returns are discarded.  pose: row-major 3x4 [R | t]
+ * float64 (host memory, read before return), sensor frame -> map frame; R
+ * must be a rotation (orthonormal to 1e-6, det > 0).  0 <= n <= the
+ * workspace's max_points; g must have the geometry the workspace was made
+ * for.  Asynchronous on stream; leaves the workspace ready for the next
+ * scan. */
+dbt_status dbt_integrate_scan(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
+                              const float *d_xyz, int64_t n, const double pose[12],
+                              void *stream);
+
+/* dbt_integrate_scan from host memory: copies the n returns at h_xyz into
+ * the workspace's staging area (pinned memory keeps the copy asynchronous),
+ * integrates them, and copies the scan's counters into *h_stats, which must
+ * stay valid until the stream reaches that point.  Asynchronous. */
+dbt_status dbt_integrate_scan_host(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
+                                   const float *h_xyz, int64_t n, const double pose[12],
+                                   dbt_scan_stats *h_stats, void *stream);
+
+/* Measurement hooks (not needed for integration).
+ * dbt_workspace_set_timing: when the events are non-NULL, every later scan
+ * on ws records ev_begin just before and ev_end just after its brick
+ * integration kernel (cudaEvent_t passed as void*; NULL to stop).
+ * dbt_scan_footprint: counts, for the scan (same arguments as
+ * dbt_integrate_scan, grid left unchanged), the distinct voxels covered by
+ * the K^3 neighbourhoods of its kept returns (h_counts[0] = U) and by their
+ * shadow sets (h_counts[1] = U_s), i.e. the voxels whose state integration
+ * must read and may write.  d_bits: caller scratch of at least
+ * 2 * ceil(pitch_x * ny * nz / 32) * 4 + 16 bytes.  Synchronous. */
+dbt_status dbt_workspace_set_timing(dbt_workspace *ws, void *ev_begin, void *ev_end);
+dbt_status dbt_scan_footprint(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
+                              const float *d_xyz, int64_t n, const double pose[12], void *d_bits,
+                              size_t bits_bytes, int64_t h_counts[2], void *stream);
+
+/* Synchronises stream and copies the last scan's counters (may be NULL).
+ * Returns DBT_ESTATE when the device latched an error. */
+dbt_status dbt_get_scan_stats(const dbt_workspace *ws, dbt_scan_stats *out, void *stream);
+
+/* Reads voxels: d_idx n x 3 int32 voxel coordinates (x, y, z); writes
+ * d_mask / d_sign / d_hits (any may be NULL).  Coordinates outside the grid
+ * give mask 0xFFFFFFFF, sign 1, hits 0.  Async. */
+dbt_status dbt_read_voxels(const dbt_grid *g, const int32_t *d_idx, int64_t n, uint32_t *d_mask,
+                           uint8_t *d_sign, uint16_t *d_hits, void *stream);
+
+/* Signed distance readout (the paper gives no formula; this library's
+ * reading): sdf = (sign ? +1 : -1) * popcount(mask) * res, in metres, for
+ * voxel coordinates d_idx (n x 3 int32); outside voxels give +32 res. */
+dbt_status dbt_read_distance(const dbt_grid *g, const int32_t *d_idx, int64_t n, float *d_sdf,
+                             void *stream);
+
+/* Synchronises stream and reports a latched device error of the workspace
+ * (ws may be NULL to only synchronise). */
+dbt_status dbt_sync(void *stream, const dbt_workspace *ws);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *dbt_last_error(void);
+
+/* Library version, e.g. "dbtsdf 0.1.0 sm_103a". */
+const char *dbt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBTSDF_H */

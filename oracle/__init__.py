@@ -189,8 +189,9 @@ class Grid:
         return g
 
     def _c(self) -> _Grid:
+        ptr = (lambda a: None if a is None else a.ctypes.data)
         return _Grid(self.nx, self.ny, self.nz, self.res, (ctypes.c_double * 3)(*self.origin),
-                     self.mask.ctypes.data, self.sign.ctypes.data, self.hits.ctypes.data)
+                     ptr(self.mask), ptr(self.sign), ptr(self.hits))
 
     def copy(self):
         return Grid(self.nx, self.ny, self.nz, self.res, self.origin,

@@ -1,0 +1,656 @@
+// C ABI entry points (include/dbtsdf.h): argument checks, the host build of
+// the directional kernel tables, workspace layout, and the launch sequence
+// of one scan.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dbt_internal.cuh"
+
+using namespace dbt;
+
+// pi rounded to the nearest binary64 value
+static const double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string t_err;
+
+static dbt_status fail(dbt_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return st;
+}
+
+static dbt_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(DBT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define DBT_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+static bool aligned256(const void *p) { return ((uintptr_t)p & 255u) == 0; }
+
+// ------------------------------------------------------------------ tables
+struct dbt_kernels {
+    dbt_params params;
+    DevParams dp;
+    DevTables dt;
+    void *d_base = nullptr;
+    std::vector<uint32_t> m2;         // mask by r^2
+    std::vector<uint32_t> sh_off;     // packed shadow offsets by bin
+    std::vector<uint32_t> sh_start;   // nbins + 1
+};
+
+// Smallest k with k * k >= n (exact integer ceil of sqrt).
+static int ceil_isqrt(int n) {
+    int k = 0;
+    while (k * k < n) ++k;
+    return k;
+}
+
+// Eq. 3 as a function of r^2 = |o|^2: 0 at the centre, else ceil(r) low bits.
+static uint32_t eq3_mask_of_r2(int r2) {
+    int k = ceil_isqrt(r2);
+    if (k == 0) return 0u;
+    if (k >= 32) return 0xFFFFFFFFu;
+    return 0xFFFFFFFFu >> (32 - k);
+}
+
+// Octahedral cell centre decoded to a direction, times n (integer vector).
+static void octa_dir_int(int b, int n, long long v[3]) {
+    long long U = 2 * (b % n) + 1 - n;
+    long long V = 2 * (b / n) + 1 - n;
+    long long Z = n - std::llabs(U) - std::llabs(V);
+    if (Z < 0) {
+        long long fu = (n - std::llabs(V)) * (U < 0 ? -1 : 1);
+        long long fv = (n - std::llabs(U)) * (V < 0 ? -1 : 1);
+        U = fu;
+        V = fv;
+    }
+    v[0] = U;
+    v[1] = V;
+    v[2] = Z;
+}
+
+static double az_edge(int k, int baz) { return ((2.0 * kPi) * (double)k) / (double)baz; }
+static double el_edge(int k, int bel) { return (kPi * (double)k) / (double)bel - kPi / 2.0; }
+
+static dbt_status check_params(const dbt_params *p) {
+    if (!p) return fail(DBT_EINVAL, "params is NULL");
+    if (p->kernel_size < 1 || p->kernel_size > MAX_K || (p->kernel_size & 1) == 0)
+        return fail(DBT_EINVAL, "kernel_size must be odd in [1, %d], got %d", MAX_K, p->kernel_size);
+    if (p->scheme == DBT_BINS_OCTA) {
+        if (p->bins_a < 1 || p->bins_a > 64 || p->bins_b != p->bins_a)
+            return fail(DBT_EINVAL, "octahedral bins need bins_a == bins_b in [1, 64]");
+    } else if (p->scheme == DBT_BINS_AZEL) {
+        if (p->bins_a < 1 || p->bins_a > MAX_EDGES || p->bins_b < 1 || p->bins_b > MAX_EDGES)
+            return fail(DBT_EINVAL, "az/el bins must be in [1, %d]", MAX_EDGES);
+    } else {
+        return fail(DBT_EINVAL, "unknown bin scheme %d", p->scheme);
+    }
+    if (!(p->shadow_radius >= 0.0) || !std::isfinite(p->shadow_radius))
+        return fail(DBT_EINVAL, "shadow_radius must be finite and >= 0");
+    if (p->hit_max < 1 || p->hit_max > 65535)
+        return fail(DBT_EINVAL, "hit_max must be in [1, 65535]");
+    if (p->hit_threshold < 1 || p->hit_threshold > p->hit_max)
+        return fail(DBT_EINVAL, "hit_threshold must be in [1, hit_max]");
+    if (p->dedup_first != 0 && p->dedup_first != 1)
+        return fail(DBT_EINVAL, "dedup_first must be 0 or 1");
+    if (p->reserved != 0) return fail(DBT_EINVAL, "reserved must be 0");
+    return DBT_OK;
+}
+
+// Shadow membership of offset o for bin b (Sec. III-B): |o|^2 <= r_s^2 and
+// o . u_b >= 0, the sign decided exactly (octahedral: integer decode).
+static bool in_shadow(const dbt_params *p, const double azel_u[3], const long long octa_v[3],
+                      int ox, int oy, int oz) {
+    double r2 = (double)ox * ox + (double)oy * oy + (double)oz * oz;
+    if (!(r2 <= p->shadow_radius * p->shadow_radius)) return false;
+    if (p->scheme == DBT_BINS_OCTA)
+        return (long long)ox * octa_v[0] + (long long)oy * octa_v[1] + (long long)oz * octa_v[2] >= 0;
+    double dot = ((double)ox * azel_u[0] + (double)oy * azel_u[1]) + (double)oz * azel_u[2];
+    return dot >= 0.0;
+}
+
+// Host tables: Eq. 3 masks by r^2 and the per-bin shadow offset lists.
+static void build_host_tables(const dbt_params *p, std::vector<uint32_t> &m2,
+                              std::vector<uint32_t> &sh_off, std::vector<uint32_t> &sh_start) {
+    const int K = p->kernel_size, R = (K - 1) / 2;
+    const int nbins = p->bins_a * p->bins_b;
+    m2.assign(3 * R * R + 1, 0u);
+    for (int r2 = 0; r2 <= 3 * R * R; ++r2) m2[r2] = eq3_mask_of_r2(r2);
+    sh_off.clear();
+    sh_start.assign(nbins + 1, 0u);
+    for (int b = 0; b < nbins; ++b) {
+        sh_start[b] = (uint32_t)sh_off.size();
+        double u[3] = {0, 0, 0};
+        long long v[3] = {0, 0, 0};
+        if (p->scheme == DBT_BINS_OCTA) {
+            octa_dir_int(b, p->bins_a, v);
+        } else {
+            const int a = b % p->bins_a, e = b / p->bins_a;
+            const double alpha = ((2.0 * kPi) * ((double)a + 0.5)) / (double)p->bins_a;
+            const double eps = (kPi * ((double)e + 0.5)) / (double)p->bins_b - kPi / 2.0;
+            u[0] = std::cos(eps) * std::cos(alpha);
+            u[1] = std::cos(eps) * std::sin(alpha);
+            u[2] = std::sin(eps);
+        }
+        for (int oz = -R; oz <= R; ++oz)
+            for (int oy = -R; oy <= R; ++oy)
+                for (int ox = -R; ox <= R; ++ox)
+                    if (in_shadow(p, u, v, ox, oy, oz)) sh_off.push_back(pack_off(ox, oy, oz));
+    }
+    sh_start[nbins] = (uint32_t)sh_off.size();
+}
+
+// Dense export of host tables: K^3 masks and bins x K^3 shadow bytes.
+static void export_tables(int K, int nbins, const std::vector<uint32_t> &m2,
+                          const std::vector<uint32_t> &sh_off, const std::vector<uint32_t> &sh_start,
+                          uint32_t *h_mask, uint8_t *h_shadow) {
+    const int R = (K - 1) / 2;
+    if (h_mask) {
+        for (int oz = -R; oz <= R; ++oz)
+            for (int oy = -R; oy <= R; ++oy)
+                for (int ox = -R; ox <= R; ++ox)
+                    h_mask[((oz + R) * K + (oy + R)) * K + (ox + R)] = m2[ox * ox + oy * oy + oz * oz];
+    }
+    if (h_shadow) {
+        const size_t kk = (size_t)K * K * K;
+        memset(h_shadow, 0, kk * nbins);
+        for (int b = 0; b < nbins; ++b)
+            for (uint32_t e = sh_start[b]; e < sh_start[b + 1]; ++e) {
+                const uint32_t o = sh_off[e];
+                const int ox = (int)(o & 255u) - 128, oy = (int)((o >> 8) & 255u) - 128,
+                          oz = (int)((o >> 16) & 255u) - 128;
+                h_shadow[b * kk + ((oz + R) * K + (oy + R)) * K + (ox + R)] = 1;
+            }
+    }
+}
+
+extern "C" dbt_status dbt_tables_host(const dbt_params *p, uint32_t *h_mask, uint8_t *h_shadow) {
+    dbt_status st = check_params(p);
+    if (st != DBT_OK) return st;
+    std::vector<uint32_t> m2, sh_off, sh_start;
+    build_host_tables(p, m2, sh_off, sh_start);
+    export_tables(p->kernel_size, p->bins_a * p->bins_b, m2, sh_off, sh_start, h_mask, h_shadow);
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) {
+    if (!out) return fail(DBT_EINVAL, "out is NULL");
+    *out = nullptr;
+    dbt_status st = check_params(p);
+    if (st != DBT_OK) return st;
+    dbt_kernels *k = new (std::nothrow) dbt_kernels();
+    if (!k) return fail(DBT_ENOMEM, "host allocation failed");
+    k->params = *p;
+    const int K = p->kernel_size, R = (K - 1) / 2;
+    const int nbins = p->bins_a * p->bins_b;
+    build_host_tables(p, k->m2, k->sh_off, k->sh_start);
+    // Eq. 2 edge tables
+    std::vector<double> az_c(MAX_EDGES, 0.0), az_s(MAX_EDGES, 0.0), el_s(MAX_EDGES, 0.0);
+    std::vector<int> az_up(MAX_EDGES, 0);
+    if (p->scheme == DBT_BINS_AZEL) {
+        for (int j = 1; j < p->bins_a; ++j) {
+            const double th = az_edge(j, p->bins_a);
+            az_c[j] = std::cos(th);
+            az_s[j] = std::sin(th);
+            az_up[j] = th < kPi;
+        }
+        for (int j = 1; j < p->bins_b; ++j) el_s[j] = std::sin(el_edge(j, p->bins_b));
+    }
+    // one device block for all tables
+    const size_t n_m2 = k->m2.size(), n_off = std::max<size_t>(1, k->sh_off.size());
+    size_t off_m2 = 0;
+    size_t off_sh = off_m2 + ((n_m2 * 4 + 255) & ~size_t(255));
+    size_t off_st = off_sh + ((n_off * 4 + 255) & ~size_t(255));
+    size_t off_azc = off_st + (((nbins + 1) * 4 + 255) & ~size_t(255));
+    size_t off_azs = off_azc + MAX_EDGES * 8;
+    size_t off_els = off_azs + MAX_EDGES * 8;
+    size_t off_up = off_els + MAX_EDGES * 8;
+    size_t total = off_up + MAX_EDGES * 4;
+    cudaError_t e = cudaMalloc(&k->d_base, total);
+    if (e != cudaSuccess) {
+        delete k;
+        return cuda_fail(e, "cudaMalloc(kernel tables)");
+    }
+    char *base = (char *)k->d_base;
+    e = cudaMemcpy(base + off_m2, k->m2.data(), n_m2 * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !k->sh_off.empty())
+        e = cudaMemcpy(base + off_sh, k->sh_off.data(), k->sh_off.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + off_st, k->sh_start.data(), (nbins + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + off_azc, az_c.data(), MAX_EDGES * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + off_azs, az_s.data(), MAX_EDGES * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + off_els, el_s.data(), MAX_EDGES * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + off_up, az_up.data(), MAX_EDGES * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(k->d_base);
+        delete k;
+        return cuda_fail(e, "cudaMemcpy(kernel tables)");
+    }
+    k->dp.K = K;
+    k->dp.R = R;
+    k->dp.scheme = p->scheme;
+    k->dp.na = p->bins_a;
+    k->dp.nb = p->bins_b;
+    k->dp.nbins = nbins;
+    k->dp.T = p->hit_threshold;
+    k->dp.Hmax = p->hit_max;
+    k->dp.dedup = p->dedup_first;
+    k->dp.n_m2 = (int)n_m2;
+    k->dt.m2 = (const uint32_t *)(base + off_m2);
+    k->dt.sh_off = (const uint32_t *)(base + off_sh);
+    k->dt.sh_start = (const uint32_t *)(base + off_st);
+    k->dt.az_c = (const double *)(base + off_azc);
+    k->dt.az_s = (const double *)(base + off_azs);
+    k->dt.el_s = (const double *)(base + off_els);
+    k->dt.az_up = (const int *)(base + off_up);
+    *out = k;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_kernels_destroy(dbt_kernels *k) {
+    if (!k) return DBT_OK;
+    cudaError_t e = k->d_base ? cudaFree(k->d_base) : cudaSuccess;
+    delete k;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFree(kernel tables)");
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_kernels_export(const dbt_kernels *k, uint32_t *h_mask, uint8_t *h_shadow) {
+    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
+    export_tables(k->dp.K, k->dp.nbins, k->m2, k->sh_off, k->sh_start, h_mask, h_shadow);
+    return DBT_OK;
+}
+
+// ------------------------------------------------------------------ grid
+static dbt_status check_grid(const dbt_grid *g) {
+    if (!g) return fail(DBT_EINVAL, "grid is NULL");
+    if (!g->mask || !g->sign || !g->hits) return fail(DBT_EINVAL, "grid arrays must be non-NULL");
+    if (!aligned256(g->mask) || !aligned256(g->sign) || !aligned256(g->hits))
+        return fail(DBT_EINVAL, "grid arrays must be 256-byte aligned");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail(DBT_EINVAL, "grid dims must be >= 1");
+    if (g->pitch_x < g->nx || (g->pitch_x % 32) != 0)
+        return fail(DBT_EINVAL, "pitch_x must be >= nx and a multiple of 32");
+    const double nv = (double)g->pitch_x * g->ny * g->nz;
+    if (nv > 1099511627776.0) return fail(DBT_EINVAL, "grid larger than 2^40 voxels");
+    if (!(g->res > 0.0) || !std::isfinite(g->res)) return fail(DBT_EINVAL, "res must be > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(g->origin[a])) return fail(DBT_EINVAL, "origin must be finite");
+    return DBT_OK;
+}
+
+static DevGrid dev_grid(const dbt_grid *g) {
+    DevGrid d;
+    d.mask = g->mask;
+    d.sign = g->sign;
+    d.hits = g->hits;
+    d.nx = g->nx;
+    d.ny = g->ny;
+    d.nz = g->nz;
+    d.pitch = g->pitch_x;
+    d.nbx = g->pitch_x / BX;
+    d.nby = (g->ny + BY - 1) / BY;
+    d.nbz = (g->nz + BZ - 1) / BZ;
+    d.inv_res = 1.0 / g->res;
+    d.ox = g->origin[0];
+    d.oy = g->origin[1];
+    d.oz = g->origin[2];
+    return d;
+}
+
+extern "C" dbt_status dbt_grid_layout(int32_t nx, int32_t ny, int32_t nz, int32_t *pitch_x,
+                                      size_t *mask_bytes, size_t *sign_bytes, size_t *hits_bytes) {
+    if (nx < 1 || ny < 1 || nz < 1) return fail(DBT_EINVAL, "grid dims must be >= 1");
+    if (nx > 0x7FFFFFE0) return fail(DBT_EINVAL, "nx too large");
+    const long long pitch = ((long long)nx + 31) / 32 * 32;
+    const double nv = (double)pitch * ny * nz;
+    if (nv > 1099511627776.0) return fail(DBT_EINVAL, "grid larger than 2^40 voxels");
+    const size_t n = (size_t)pitch * (size_t)ny * (size_t)nz;
+    if (pitch_x) *pitch_x = (int32_t)pitch;
+    if (mask_bytes) *mask_bytes = n * 4;
+    if (sign_bytes) *sign_bytes = n;
+    if (hits_bytes) *hits_bytes = n * 2;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_grid_init(const dbt_grid *g, void *stream) {
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    const size_t n = (size_t)g->pitch_x * g->ny * g->nz;
+    cudaStream_t s = (cudaStream_t)stream;
+    DBT_CUDA(cudaMemsetAsync(g->mask, 0xFF, n * 4, s));   // all mask bits set
+    DBT_CUDA(cudaMemsetAsync(g->sign, 0x01, n, s));       // free
+    DBT_CUDA(cudaMemsetAsync(g->hits, 0x00, n * 2, s));   // no hits
+    return DBT_OK;
+}
+
+// ------------------------------------------------------------------ workspace
+struct WsLayout {
+    size_t hdr, stage, prec, hkey, hidx, bcnt, boff, touched, pairs, total;
+    uint32_t hcap_alloc, max_touched, nbricks;
+    unsigned long long pairs_cap;
+};
+
+static size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
+
+static int max_pairs_per_return(int K) {
+    const int sx = 1 + (K - 1 + BX - 1) / BX;
+    const int sy = 1 + (K - 1 + BY - 1) / BY;
+    const int sz = 1 + (K - 1 + BZ - 1) / BZ;
+    return sx * sy * sz;
+}
+
+static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long max_points, WsLayout *L) {
+    if (max_points < 1 || max_points > (1ll << 30))
+        return fail(DBT_EINVAL, "max_points must be in [1, 2^30]");
+    const DevGrid d = dev_grid(g);
+    const unsigned long long nb = (unsigned long long)d.nbx * d.nby * d.nbz;
+    if (nb >= (1ull << 32)) return fail(DBT_EINVAL, "too many bricks");
+    L->nbricks = (uint32_t)nb;
+    uint32_t hc = 64;
+    while (hc < 2ull * (unsigned long long)max_points) hc <<= 1;
+    L->hcap_alloc = hc;
+    L->pairs_cap = (unsigned long long)max_points * max_pairs_per_return(k->dp.K);
+    L->max_touched = (uint32_t)std::min<unsigned long long>(nb, L->pairs_cap);
+    size_t o = 0;
+    L->hdr = o;      o += up256(sizeof(WsHeader));
+    L->stage = o;    o += up256((size_t)max_points * 12);
+    L->prec = o;     o += up256((size_t)max_points * 16);
+    L->hkey = o;     o += up256((size_t)hc * 8);
+    L->hidx = o;     o += up256((size_t)hc * 4);
+    L->bcnt = o;     o += up256((size_t)nb * 4);
+    L->boff = o;     o += up256((size_t)nb * 4);
+    L->touched = o;  o += up256((size_t)L->max_touched * 4);
+    L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
+    L->total = o;
+    return DBT_OK;
+}
+
+struct dbt_workspace {
+    WsLayout L;
+    WsDev d;
+    void *buf;
+    long long max_points;
+    int nx, ny, nz, pitch, K;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;   // optional timing of the integrate kernel
+};
+
+extern "C" dbt_status dbt_workspace_size(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
+                                         size_t *bytes) {
+    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
+    if (!bytes) return fail(DBT_EINVAL, "bytes is NULL");
+    if (!g) return fail(DBT_EINVAL, "grid is NULL");
+    // only the geometry of g matters here; its arrays may still be NULL
+    dbt_grid gg = *g;
+    static uint32_t dummy[64] __attribute__((aligned(256)));
+    if (!gg.mask) gg.mask = dummy;
+    if (!gg.sign) gg.sign = (uint8_t *)dummy;
+    if (!gg.hits) gg.hits = (uint16_t *)dummy;
+    dbt_status st = check_grid(&gg);
+    if (st != DBT_OK) return st;
+    WsLayout L;
+    st = ws_layout(&gg, k, max_points, &L);
+    if (st != DBT_OK) return st;
+    *bytes = L.total;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_workspace_create(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
+                                           void *d_buf, size_t bytes, void *stream,
+                                           dbt_workspace **out) {
+    if (!out) return fail(DBT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    if (!d_buf || !aligned256(d_buf)) return fail(DBT_EINVAL, "workspace buffer must be 256-byte aligned");
+    WsLayout L;
+    st = ws_layout(g, k, max_points, &L);
+    if (st != DBT_OK) return st;
+    if (bytes < L.total)
+        return fail(DBT_ENOMEM, "workspace too small: %zu < %zu bytes", bytes, L.total);
+    dbt_workspace *w = new (std::nothrow) dbt_workspace();
+    if (!w) return fail(DBT_ENOMEM, "host allocation failed");
+    char *base = (char *)d_buf;
+    w->L = L;
+    w->buf = d_buf;
+    w->max_points = max_points;
+    w->nx = g->nx;
+    w->ny = g->ny;
+    w->nz = g->nz;
+    w->pitch = g->pitch_x;
+    w->K = k->dp.K;
+    w->d.hdr = (WsHeader *)(base + L.hdr);
+    w->d.stage = (float *)(base + L.stage);
+    w->d.prec = (int4 *)(base + L.prec);
+    w->d.hkey = (unsigned long long *)(base + L.hkey);
+    w->d.hidx = (uint32_t *)(base + L.hidx);
+    w->d.hcap_alloc = L.hcap_alloc;
+    w->d.bcnt = (uint32_t *)(base + L.bcnt);
+    w->d.boff = (uint32_t *)(base + L.boff);
+    w->d.touched = (uint32_t *)(base + L.touched);
+    w->d.max_touched = L.max_touched;
+    w->d.pairs = (uint32_t *)(base + L.pairs);
+    w->d.pairs_cap = L.pairs_cap;
+    cudaError_t e = cudaMemsetAsync(d_buf, 0, L.total, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        delete w;
+        return cuda_fail(e, "cudaMemsetAsync(workspace)");
+    }
+    *out = w;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_workspace_reset(dbt_workspace *ws, void *stream) {
+    if (!ws) return fail(DBT_EINVAL, "workspace is NULL");
+    DBT_CUDA(cudaMemsetAsync(ws->buf, 0, ws->L.total, (cudaStream_t)stream));
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_workspace_destroy(dbt_workspace *ws) {
+    delete ws;
+    return DBT_OK;
+}
+
+// ------------------------------------------------------------------ integration
+static dbt_status check_pose(const double *pose, Pose *out) {
+    if (!pose) return fail(DBT_EINVAL, "pose is NULL");
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(pose[i])) return fail(DBT_EINVAL, "pose has a non-finite entry");
+    double R[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) R[3 * r + c] = pose[4 * r + c];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double dot = 0.0;
+            for (int c = 0; c < 3; ++c) dot += R[3 * i + c] * R[3 * j + c];
+            if (std::fabs(dot - (i == j ? 1.0 : 0.0)) > 1e-6)
+                return fail(DBT_EINVAL, "pose rotation is not orthonormal");
+        }
+    const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                       R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (!(det > 0.0)) return fail(DBT_EINVAL, "pose rotation has det <= 0");
+    for (int i = 0; i < 9; ++i) out->r[i] = R[i];
+    for (int r = 0; r < 3; ++r) out->t[r] = pose[4 * r + 3];
+    return DBT_OK;
+}
+
+static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
+                               const float *d_xyz, int64_t n, const double pose[12],
+                               cudaStream_t s, DevGrid *dg_out, uint32_t *hcap_out);
+
+static dbt_status enqueue_scan(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
+                               const float *d_xyz, int64_t n, const double pose[12],
+                               cudaStream_t s) {
+    DevGrid dg;
+    uint32_t hcap;
+    dbt_status st = enqueue_prep(g, k, ws, d_xyz, n, pose, s, &dg, &hcap);
+    if (st != DBT_OK) return st;
+    const int ni = (int)n;
+    launch_alloc(ws->d, 2 * 152, s);
+    launch_fill(dg, k->dp, ni, ws->d, hcap, s);
+    if (ws->ev_begin) DBT_CUDA(cudaEventRecord(ws->ev_begin, s));
+    launch_integrate(dg, k->dp, k->dt, (long long)n, ws->d, integrate_grid_ctas(k->dp.K), s);
+    if (ws->ev_end) DBT_CUDA(cudaEventRecord(ws->ev_end, s));
+    DBT_CUDA(cudaGetLastError());
+    return DBT_OK;
+}
+
+// Checks the arguments and enqueues the per-return stages that every scan
+// starts with (transform, voxel, bin, first-return rule, brick counts).
+static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
+                               const float *d_xyz, int64_t n, const double pose[12],
+                               cudaStream_t s, DevGrid *dg_out, uint32_t *hcap_out) {
+    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
+    if (!ws) return fail(DBT_EINVAL, "workspace is NULL");
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    if (g->nx != ws->nx || g->ny != ws->ny || g->nz != ws->nz || g->pitch_x != ws->pitch)
+        return fail(DBT_EINVAL, "grid geometry differs from the workspace's");
+    if (k->dp.K != ws->K) return fail(DBT_EINVAL, "kernel size differs from the workspace's");
+    if (n < 0 || n > ws->max_points)
+        return fail(DBT_EINVAL, "n = %lld outside [0, max_points = %lld]", (long long)n, ws->max_points);
+    if (n > 0 && (!d_xyz || ((uintptr_t)d_xyz & 3u)))
+        return fail(DBT_EINVAL, "points must be a non-NULL 4-byte aligned device pointer");
+    Pose P;
+    st = check_pose(pose, &P);
+    if (st != DBT_OK) return st;
+    const DevGrid dg = dev_grid(g);
+    uint32_t hcap = 64;
+    while (hcap < 2ull * (unsigned long long)n) hcap <<= 1;
+    const int ni = (int)n;
+    launch_voxelize(dg, k->dp, k->dt, P, d_xyz, ni, ws->d, hcap, s);
+    launch_count(dg, k->dp, ni, ws->d, hcap, s);
+    *dg_out = dg;
+    *hcap_out = hcap;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_workspace_set_timing(dbt_workspace *ws, void *ev_begin, void *ev_end) {
+    if (!ws) return fail(DBT_EINVAL, "workspace is NULL");
+    ws->ev_begin = (cudaEvent_t)ev_begin;
+    ws->ev_end = (cudaEvent_t)ev_end;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_scan_footprint(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
+                                         const float *d_xyz, int64_t n, const double pose[12],
+                                         void *d_bits, size_t bits_bytes, int64_t h_counts[2],
+                                         void *stream) {
+    if (!h_counts) return fail(DBT_EINVAL, "h_counts is NULL");
+    if (!g) return fail(DBT_EINVAL, "grid is NULL");
+    const size_t words = ((size_t)g->pitch_x * g->ny * g->nz + 31) / 32;
+    if (!d_bits || bits_bytes < 2 * words * 4 + 16)
+        return fail(DBT_EINVAL, "footprint buffer needs %zu bytes", 2 * words * 4 + 16);
+    cudaStream_t s = (cudaStream_t)stream;
+    DevGrid dg;
+    uint32_t hcap;
+    dbt_status st = enqueue_prep(g, k, ws, d_xyz, n, pose, s, &dg, &hcap);
+    if (st != DBT_OK) return st;
+    uint32_t *bits_u = (uint32_t *)d_bits;
+    uint32_t *bits_s = bits_u + words;
+    unsigned long long *counts = (unsigned long long *)(bits_s + words);
+    DBT_CUDA(cudaMemsetAsync(d_bits, 0, 2 * words * 4 + 16, s));
+    launch_footprint(dg, k->dp, k->dt, (int)n, ws->d, hcap, bits_u, bits_s, counts, s);
+    DBT_CUDA(cudaGetLastError());
+    unsigned long long c[2];
+    DBT_CUDA(cudaMemcpyAsync(c, counts, sizeof c, cudaMemcpyDeviceToHost, s));
+    DBT_CUDA(cudaStreamSynchronize(s));
+    h_counts[0] = (int64_t)c[0];
+    h_counts[1] = (int64_t)c[1];
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_integrate_scan(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
+                                         const float *d_xyz, int64_t n, const double pose[12],
+                                         void *stream) {
+    return enqueue_scan(g, k, ws, d_xyz, n, pose, (cudaStream_t)stream);
+}
+
+extern "C" dbt_status dbt_integrate_scan_host(const dbt_grid *g, const dbt_kernels *k,
+                                              dbt_workspace *ws, const float *h_xyz, int64_t n,
+                                              const double pose[12], dbt_scan_stats *h_stats,
+                                              void *stream) {
+    if (!ws) return fail(DBT_EINVAL, "workspace is NULL");
+    if (n < 0 || n > ws->max_points) return fail(DBT_EINVAL, "n outside [0, max_points]");
+    if (n > 0 && !h_xyz) return fail(DBT_EINVAL, "h_xyz is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n > 0) DBT_CUDA(cudaMemcpyAsync(ws->d.stage, h_xyz, (size_t)n * 12, cudaMemcpyHostToDevice, s));
+    dbt_status st = enqueue_scan(g, k, ws, ws->d.stage, n, pose, s);
+    if (st != DBT_OK) return st;
+    if (h_stats)
+        DBT_CUDA(cudaMemcpyAsync(h_stats, &ws->d.hdr->last, sizeof(dbt_scan_stats),
+                                 cudaMemcpyDeviceToHost, s));
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_get_scan_stats(const dbt_workspace *ws, dbt_scan_stats *out, void *stream) {
+    if (!ws) return fail(DBT_EINVAL, "workspace is NULL");
+    DBT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    dbt_scan_stats st;
+    DBT_CUDA(cudaMemcpy(&st, &ws->d.hdr->last, sizeof st, cudaMemcpyDeviceToHost));
+    if (out) *out = st;
+    if (st.error) return fail(DBT_ESTATE, "device error bits 0x%x", st.error);
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_sync(void *stream, const dbt_workspace *ws) {
+    DBT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (ws) {
+        dbt_scan_stats st;
+        DBT_CUDA(cudaMemcpy(&st, &ws->d.hdr->last, sizeof st, cudaMemcpyDeviceToHost));
+        if (st.error) return fail(DBT_ESTATE, "device error bits 0x%x", st.error);
+    }
+    return DBT_OK;
+}
+
+// ------------------------------------------------------------------ readouts
+extern "C" dbt_status dbt_bin_directions(const dbt_kernels *k, const double *d_dirs, int64_t n,
+                                         int32_t *d_bins, void *stream) {
+    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
+    if (n < 0 || n > 0x7FFFFFFF) return fail(DBT_EINVAL, "bad n");
+    if (n > 0 && (!d_dirs || !d_bins)) return fail(DBT_EINVAL, "NULL buffer");
+    launch_bin_dirs(k->dp, k->dt, d_dirs, (int)n, d_bins, (cudaStream_t)stream);
+    DBT_CUDA(cudaGetLastError());
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_read_voxels(const dbt_grid *g, const int32_t *d_idx, int64_t n,
+                                      uint32_t *d_mask, uint8_t *d_sign, uint16_t *d_hits,
+                                      void *stream) {
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    if (n < 0) return fail(DBT_EINVAL, "n < 0");
+    if (n > 0 && !d_idx) return fail(DBT_EINVAL, "d_idx is NULL");
+    launch_read_voxels(dev_grid(g), d_idx, n, d_mask, d_sign, d_hits, (cudaStream_t)stream);
+    DBT_CUDA(cudaGetLastError());
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_read_distance(const dbt_grid *g, const int32_t *d_idx, int64_t n,
+                                        float *d_sdf, void *stream) {
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    if (n < 0) return fail(DBT_EINVAL, "n < 0");
+    if (n > 0 && (!d_idx || !d_sdf)) return fail(DBT_EINVAL, "NULL buffer");
+    launch_read_distance(dev_grid(g), g->res, d_idx, n, d_sdf, (cudaStream_t)stream);
+    DBT_CUDA(cudaGetLastError());
+    return DBT_OK;
+}
+
+extern "C" const char *dbt_last_error(void) { return t_err.c_str(); }
+
+extern "C" const char *dbt_version(void) { return "dbtsdf 0.1.0 sm_103a"; }

@@ -1,0 +1,131 @@
+// Internal declarations shared by the library's translation units (never by
+// the oracle).  Device-side layouts of the kernel tables, the grid view, the
+// pose and the integration workspace.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dbtsdf.h"
+
+namespace dbt {
+
+// Brick = CTA ownership unit of the integration: BX x BY x BZ voxels.  BX = 32
+// makes one brick row a 128-byte mask line; chunks are 4 voxels (16 bytes).
+constexpr int BX = 32, BY = 8, BZ = 8;
+constexpr int BROWS = BY * BZ;              // 64 rows of 32 voxels
+constexpr int BVOX = BX * BY * BZ;          // 2048 voxels
+constexpr int CHUNKS_PER_ROW = BX / 4;      // 8
+constexpr int BCHUNKS = BROWS * CHUNKS_PER_ROW;  // 512
+
+constexpr int MAX_K = 21;
+constexpr int MAX_R = (MAX_K - 1) / 2;
+constexpr int MAX_M2 = 3 * MAX_R * MAX_R + 1;   // r^2 = 0 .. 3 R^2
+constexpr int MAX_EDGES = 256;
+
+// Device error bits latched in the workspace header.
+constexpr uint32_t ERR_HASH_FULL = 1u << 0;
+constexpr uint32_t ERR_PAIRS_OVERFLOW = 1u << 1;
+constexpr uint32_t ERR_TOUCHED_OVERFLOW = 1u << 2;
+constexpr uint32_t ERR_BAD_PAYLOAD = 1u << 3;
+
+// Shadow offsets are packed as (ox + 128) | (oy + 128) << 8 | (oz + 128) << 16.
+__host__ __device__ inline uint32_t pack_off(int ox, int oy, int oz) {
+    return (uint32_t)(ox + 128) | ((uint32_t)(oy + 128) << 8) | ((uint32_t)(oz + 128) << 16);
+}
+
+struct DevParams {
+    int K, R;
+    int scheme;       // DBT_BINS_OCTA / DBT_BINS_AZEL
+    int na, nb;       // bins_a, bins_b
+    int nbins;
+    int T, Hmax;
+    int dedup;
+    int n_m2;         // entries of the mask-by-r^2 table
+};
+
+struct DevTables {
+    const uint32_t *m2;        // Eq. 3 mask as a function of r^2 = |o|^2
+    const uint32_t *sh_off;    // packed shadow offsets, grouped by bin
+    const uint32_t *sh_start;  // nbins + 1 prefix offsets into sh_off
+    const double *az_c;        // azimuth edge k: cos(theta_k), k = 0..B_az-1
+    const double *az_s;        // sin(theta_k)
+    const int *az_up;          // theta_k < pi
+    const double *el_s;        // elevation edge k: sin(phi_k), k = 0..B_el-1
+};
+
+struct DevGrid {
+    uint32_t *mask;
+    uint8_t *sign;
+    uint16_t *hits;
+    int nx, ny, nz, pitch;
+    int nbx, nby, nbz;          // bricks per axis
+    double inv_res;             // 1 / res, rounded once on the host
+    double ox, oy, oz;          // origin
+};
+
+struct Pose {
+    double r[9];                // row-major rotation
+    double t[3];
+};
+
+// Counters of the last completed scan; same layout as dbt_scan_stats.
+struct ScanStats {
+    long long n_input, n_valid, n_inside, n_kept, n_pairs, n_bricks;
+    uint32_t error, reserved;
+};
+static_assert(sizeof(ScanStats) == sizeof(dbt_scan_stats), "stats layout");
+
+struct WsHeader {
+    uint32_t err;               // latched error bits of the current scan
+    uint32_t n_touched;         // bricks touched by the current scan
+    uint32_t pool;              // (return, brick) pairs allocated
+    uint32_t next_work;         // dynamic brick queue of the integrate kernel
+    uint32_t done_ctas;         // integrate CTAs finished
+    uint32_t pad0[3];
+    unsigned long long acc_valid, acc_inside, acc_kept;
+    unsigned long long pad1[5];
+    ScanStats last;             // published by the last integrate CTA
+};
+
+// Device view of a workspace (all pointers into the caller's buffer).
+struct WsDev {
+    WsHeader *hdr;
+    float *stage;               // max_points * 3 floats (host-input staging)
+    int4 *prec;                 // per return: contact (x,y,z) and bin, or x < 0
+    unsigned long long *hkey;   // first-return hash: key = linear voxel + 1
+    uint32_t *hidx;             // ~(lowest return index), 0 = empty
+    uint32_t hcap_alloc;        // allocated slots (power of two)
+    uint32_t *bcnt;             // per brick: pair count / fill cursor (kept 0 between scans)
+    uint32_t *boff;             // per brick: first pair of its segment
+    uint32_t *touched;          // list of touched bricks
+    uint32_t max_touched;
+    uint32_t *pairs;            // pair payloads grouped by brick
+    unsigned long long pairs_cap;
+};
+
+// Return-record flags in prec.w above the 16-bit bin.
+constexpr int PREC_DUP = 1 << 30;
+
+// Launch helpers implemented in the .cu files.
+void launch_voxelize(const DevGrid &g, const DevParams &p, const DevTables &t, const Pose &pose,
+                     const float *xyz, int n, const WsDev &ws, uint32_t hcap, cudaStream_t s);
+void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
+                  cudaStream_t s);
+void launch_alloc(const WsDev &ws, int grid_ctas, cudaStream_t s);
+void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
+                 cudaStream_t s);
+void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, long long n_input,
+                      const WsDev &ws, int grid_ctas, cudaStream_t s);
+int integrate_grid_ctas(int K);
+void launch_footprint(const DevGrid &g, const DevParams &p, const DevTables &t, int n,
+                      const WsDev &ws, uint32_t hcap, uint32_t *bits_u, uint32_t *bits_s,
+                      unsigned long long *counts, cudaStream_t s);
+void launch_bin_dirs(const DevParams &p, const DevTables &t, const double *dirs, int n, int *bins,
+                     cudaStream_t s);
+void launch_read_voxels(const DevGrid &g, const int *idx, long long n, uint32_t *mask,
+                        uint8_t *sign, uint16_t *hits, cudaStream_t s);
+void launch_read_distance(const DevGrid &g, double res, const int *idx, long long n, float *sdf,
+                          cudaStream_t s);
+
+}  // namespace dbt

@@ -1,0 +1,424 @@
+// Per-return stages of one scan (Sec. III-C), before the brick integration:
+//   k_voxelize  map-frame transform, contact voxel, boundary discard,
+//               direction bin, first-return hash insert
+//   k_count     first-return resolve, (return, brick) pair counts
+//   k_alloc     one contiguous pair segment per touched brick
+//   k_fill      pair payloads into the segments; clears the hash table
+// plus the direction-bin and voxel readout kernels.
+//
+// Float -> integer decisions use binary64 with explicit round-to-nearest
+// intrinsics, so that nvcc cannot contract or reorder them:
+//   d = R p, row r = fma(R_r2, z, fma(R_r1, y, R_r0 * x)); w = d + t
+//   c = floor((w - origin) * inv_res)
+//   octahedral: u = d_x * (1/s), v = d_y * (1/s), s = (|x| + |y|) + |z|
+//   Eq. 2: edge comparisons against host-built cos/sin tables.
+#include "dbt_internal.cuh"
+
+namespace dbt {
+
+// ------------------------------------------------------------------ bins
+__device__ __forceinline__ double sgn1(double v) { return v < 0.0 ? -1.0 : 1.0; }
+
+// Octahedral cell of d (the workloads' scheme): projection on |x|+|y|+|z|=1,
+// lower half folded over the diagonals, [-1,1]^2 cut into n x n cells.
+__device__ int bin_octa(double dx, double dy, double dz, int n) {
+    double s = __dadd_rn(__dadd_rn(fabs(dx), fabs(dy)), fabs(dz));
+    if (!(s > 0.0)) return 0;
+    double inv = __drcp_rn(s);
+    double u = __dmul_rn(dx, inv);
+    double v = __dmul_rn(dy, inv);
+    if (dz < 0.0) {
+        double fu = __dmul_rn(__dsub_rn(1.0, fabs(v)), sgn1(u));
+        double fv = __dmul_rn(__dsub_rn(1.0, fabs(u)), sgn1(v));
+        u = fu;
+        v = fv;
+    }
+    double fi = floor(__dmul_rn(__dmul_rn(__dadd_rn(u, 1.0), 0.5), (double)n));
+    double fj = floor(__dmul_rn(__dmul_rn(__dadd_rn(v, 1.0), 0.5), (double)n));
+    int i = (int)fmin(fmax(fi, 0.0), (double)(n - 1));
+    int j = (int)fmin(fmax(fj, 0.0), (double)(n - 1));
+    return j * n + i;
+}
+
+// Eq. 2 azimuth: number of edges theta_k (k >= 1) with theta >= theta_k.
+// Within a half-turn the test is the sign of cos(theta_k) y - sin(theta_k) x;
+// the predicate falls monotonically with k, so a binary search finds the
+// count.
+__device__ __forceinline__ bool az_ge(const DevTables &t, int k, double x, double y, bool upper) {
+    bool eu = t.az_up[k] != 0;
+    if (upper && !eu) return false;
+    if (!upper && eu) return true;
+    return __dsub_rn(__dmul_rn(t.az_c[k], y), __dmul_rn(t.az_s[k], x)) >= 0.0;
+}
+
+__device__ int bin_az(const DevTables &t, int B, double x, double y) {
+    if (x == 0.0 && y == 0.0) return 0;          // atan2(0, 0) = 0
+    bool upper = (y > 0.0) || (y == 0.0 && x >= 0.0);
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (az_ge(t, mid, x, y, upper)) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Eq. 2 elevation: number of edges k >= 1 with z/|d| >= sin(phi_k); the
+// top bin is B_el - 1 (clamped zenith).
+__device__ int bin_el(const DevTables &t, int B, double x, double y, double z) {
+    double nrm = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+    double s = __ddiv_rn(z, nrm);
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s >= t.el_s[mid]) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int bin_of(const DevParams &p, const DevTables &t, double dx, double dy,
+                                      double dz) {
+    if (p.scheme == DBT_BINS_OCTA) return bin_octa(dx, dy, dz, p.na);
+    return bin_el(t, p.nb, dx, dy, dz) * p.na + bin_az(t, p.na, dx, dy);
+}
+
+// ------------------------------------------------------------------ hash
+__device__ __forceinline__ uint32_t hslot(unsigned long long key, uint32_t hcap) {
+    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & (hcap - 1);
+}
+
+// First-return rule (Sec. IV-B): the slot of a contact voxel keeps the
+// bitwise complement of the lowest return index seen, via atomicMax.
+__device__ void hash_insert(const WsDev &ws, uint32_t hcap, unsigned long long key, uint32_t i) {
+    uint32_t s = hslot(key, hcap);
+    for (uint32_t probe = 0; probe < hcap; ++probe) {
+        unsigned long long prev = atomicCAS(&ws.hkey[s], 0ull, key);
+        if (prev == 0ull || prev == key) {
+            atomicMax(&ws.hidx[s], ~i);
+            return;
+        }
+        s = (s + 1) & (hcap - 1);
+    }
+    atomicOr(&ws.hdr->err, ERR_HASH_FULL);
+}
+
+__device__ bool hash_is_first(const WsDev &ws, uint32_t hcap, unsigned long long key, uint32_t i) {
+    uint32_t s = hslot(key, hcap);
+    for (uint32_t probe = 0; probe < hcap; ++probe) {
+        unsigned long long k = ws.hkey[s];
+        if (k == key) return ws.hidx[s] == ~i;
+        if (k == 0ull) break;
+        s = (s + 1) & (hcap - 1);
+    }
+    atomicOr(&ws.hdr->err, ERR_HASH_FULL);
+    return false;
+}
+
+__device__ __forceinline__ unsigned long long voxel_key(const DevGrid &g, int x, int y, int z) {
+    return ((unsigned long long)z * (unsigned long long)g.ny + (unsigned long long)y) *
+               (unsigned long long)g.pitch + (unsigned long long)x + 1ull;
+}
+
+// ------------------------------------------------------------------ K1
+__global__ void __launch_bounds__(256) k_voxelize(DevGrid g, DevParams p, DevTables t, Pose pose,
+                                                  const float *__restrict__ xyz, int n, WsDev ws,
+                                                  uint32_t hcap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = false, inside = false;
+    if (i < n) {
+        const float fx = xyz[3 * i + 0], fy = xyz[3 * i + 1], fz = xyz[3 * i + 2];
+        int4 rec = make_int4(-1, 0, 0, 0);
+        if (isfinite(fx) && isfinite(fy) && isfinite(fz) &&
+            !(fx == 0.0f && fy == 0.0f && fz == 0.0f)) {
+            valid = true;
+            const double px = fx, py = fy, pz = fz;
+            double d[3], q[3];
+            const double org[3] = {g.ox, g.oy, g.oz};
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                d[r] = __fma_rn(pose.r[3 * r + 2], pz,
+                                __fma_rn(pose.r[3 * r + 1], py, __dmul_rn(pose.r[3 * r + 0], px)));
+                const double w = __dadd_rn(d[r], pose.t[r]);
+                q[r] = floor(__dmul_rn(__dsub_rn(w, org[r]), g.inv_res));
+            }
+            const double R = (double)p.R;
+            if (q[0] >= R && q[0] <= (double)(g.nx - 1 - p.R) && q[1] >= R &&
+                q[1] <= (double)(g.ny - 1 - p.R) && q[2] >= R && q[2] <= (double)(g.nz - 1 - p.R)) {
+                inside = true;
+                const int cx = (int)q[0], cy = (int)q[1], cz = (int)q[2];
+                const int b = bin_of(p, t, d[0], d[1], d[2]);
+                rec = make_int4(cx, cy, cz, b);
+                if (p.dedup) hash_insert(ws, hcap, voxel_key(g, cx, cy, cz), (uint32_t)i);
+            }
+        }
+        ws.prec[i] = rec;
+    }
+    const unsigned bv = __ballot_sync(0xffffffffu, valid);
+    const unsigned bi = __ballot_sync(0xffffffffu, inside);
+    if ((threadIdx.x & 31) == 0) {
+        if (bv) atomicAdd(&ws.hdr->acc_valid, (unsigned long long)__popc(bv));
+        if (bi) atomicAdd(&ws.hdr->acc_inside, (unsigned long long)__popc(bi));
+    }
+}
+
+// Brick range of the K^3 neighbourhood of contact c along one axis.
+struct BrickSpan {
+    int x0, x1, y0, y1, z0, z1;
+};
+__device__ __forceinline__ BrickSpan brick_span(int cx, int cy, int cz, int R) {
+    BrickSpan s;
+    s.x0 = (cx - R) / BX;  // contacts are >= R, so these are non-negative
+    s.x1 = (cx + R) / BX;
+    s.y0 = (cy - R) / BY;
+    s.y1 = (cy + R) / BY;
+    s.z0 = (cz - R) / BZ;
+    s.z1 = (cz + R) / BZ;
+    return s;
+}
+
+// ------------------------------------------------------------------ K2
+__global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, WsDev ws,
+                                               uint32_t hcap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool kept = false;
+    if (i < n) {
+        int4 r = ws.prec[i];
+        if (r.x >= 0) {
+            kept = true;
+            if (p.dedup && !hash_is_first(ws, hcap, voxel_key(g, r.x, r.y, r.z), (uint32_t)i)) {
+                kept = false;
+                r.w |= PREC_DUP;
+                ws.prec[i] = r;
+            }
+            if (kept) {
+                const BrickSpan s = brick_span(r.x, r.y, r.z, p.R);
+                for (int bz = s.z0; bz <= s.z1; ++bz)
+                    for (int by = s.y0; by <= s.y1; ++by)
+                        for (int bx = s.x0; bx <= s.x1; ++bx) {
+                            const uint32_t b = ((uint32_t)bz * g.nby + by) * g.nbx + bx;
+                            if (atomicAdd(&ws.bcnt[b], 1u) == 0u) {
+                                const uint32_t tt = atomicAdd(&ws.hdr->n_touched, 1u);
+                                if (tt < ws.max_touched) ws.touched[tt] = b;
+                                else atomicOr(&ws.hdr->err, ERR_TOUCHED_OVERFLOW);
+                            }
+                        }
+            }
+        }
+    }
+    const unsigned bk = __ballot_sync(0xffffffffu, kept);
+    if ((threadIdx.x & 31) == 0 && bk) atomicAdd(&ws.hdr->acc_kept, (unsigned long long)__popc(bk));
+}
+
+// ------------------------------------------------------------------ K3
+// One segment of the pair array per touched brick; warp-aggregated bump of
+// the pool counter.  The per-brick counter is reset to serve as fill cursor.
+__global__ void __launch_bounds__(256) k_alloc(WsDev ws) {
+    const uint32_t nt = min(ws.hdr->n_touched, ws.max_touched);
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < nt; base += gridDim.x * blockDim.x) {
+        const uint32_t t = base + threadIdx.x;
+        uint32_t len = 0, b = 0;
+        if (t < nt) {
+            b = ws.touched[t];
+            len = ws.bcnt[b];
+        }
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        uint32_t wbase = 0;
+        if (lane == 31 && incl) wbase = atomicAdd(&ws.hdr->pool, incl);
+        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+        if (t < nt) {
+            ws.boff[b] = wbase + incl - len;
+            ws.bcnt[b] = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ K4
+// Pair payload: contact relative to the brick corner plus R (x: 6 bits,
+// y, z: 5 bits each) and the bin (16 bits).
+__global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, WsDev ws,
+                                              uint32_t hcap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int4 r = ws.prec[i];
+        if (r.x >= 0 && !(r.w & PREC_DUP)) {
+            const uint32_t bin = (uint32_t)(r.w & 0xFFFF);
+            const BrickSpan s = brick_span(r.x, r.y, r.z, p.R);
+            for (int bz = s.z0; bz <= s.z1; ++bz)
+                for (int by = s.y0; by <= s.y1; ++by)
+                    for (int bx = s.x0; bx <= s.x1; ++bx) {
+                        const uint32_t b = ((uint32_t)bz * g.nby + by) * g.nbx + bx;
+                        const uint32_t slot = atomicAdd(&ws.bcnt[b], 1u);
+                        const unsigned long long pos = (unsigned long long)ws.boff[b] + slot;
+                        const uint32_t rx = (uint32_t)(r.x - bx * BX + p.R);
+                        const uint32_t ry = (uint32_t)(r.y - by * BY + p.R);
+                        const uint32_t rz = (uint32_t)(r.z - bz * BZ + p.R);
+                        if (pos < ws.pairs_cap)
+                            ws.pairs[pos] = rx | (ry << 6) | (rz << 11) | (bin << 16);
+                        else
+                            atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
+                    }
+        }
+    }
+    if (p.dedup) {
+        const uint32_t stride = gridDim.x * blockDim.x;
+        for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < hcap; j += stride) {
+            ws.hkey[j] = 0ull;
+            ws.hidx[j] = 0u;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ footprint
+// Measurement pass (not part of integration): marks, in two caller-owned
+// bitmaps over the padded grid, every voxel of a kept return's K^3
+// neighbourhood and of its shadow set, and counts first-time marks.  The
+// counts U and U_s give the algorithmic bytes of a scan's integration.
+__global__ void __launch_bounds__(256) k_footprint(DevGrid g, DevParams p, DevTables t, int n,
+                                                   WsDev ws, uint32_t *bits_u, uint32_t *bits_s,
+                                                   unsigned long long *counts) {
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const int4 r = ws.prec[i];
+    if (r.x < 0 || (r.w & PREC_DUP)) return;
+    const int R = p.R, K = p.K;
+    unsigned long long nu = 0, ns = 0;
+    for (int e = threadIdx.x; e < K * K * K; e += blockDim.x) {
+        const int ox = e % K - R, oy = (e / K) % K - R, oz = e / (K * K) - R;
+        const unsigned long long v = voxel_key(g, r.x + ox, r.y + oy, r.z + oz) - 1ull;
+        const uint32_t bit = 1u << (v & 31);
+        if (!(atomicOr(&bits_u[v >> 5], bit) & bit)) ++nu;
+    }
+    const uint32_t bin = (uint32_t)(r.w & 0xFFFF);
+    for (uint32_t e = t.sh_start[bin] + threadIdx.x; e < t.sh_start[bin + 1]; e += blockDim.x) {
+        const uint32_t o = t.sh_off[e];
+        const unsigned long long v =
+            voxel_key(g, r.x + (int)(o & 255u) - 128, r.y + (int)((o >> 8) & 255u) - 128,
+                      r.z + (int)((o >> 16) & 255u) - 128) - 1ull;
+        const uint32_t bit = 1u << (v & 31);
+        if (!(atomicOr(&bits_s[v >> 5], bit) & bit)) ++ns;
+    }
+    if (nu) atomicAdd(&counts[0], nu);
+    if (ns) atomicAdd(&counts[1], ns);
+}
+
+// Returns the workspace to its between-scans state after k_voxelize and
+// k_count ran without the rest of the pipeline.
+__global__ void k_ws_rearm(WsDev ws, uint32_t hcap) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t g0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nt = min(ws.hdr->n_touched, ws.max_touched);
+    for (uint32_t j = g0; j < nt; j += stride) ws.bcnt[ws.touched[j]] = 0u;
+    for (uint32_t j = g0; j < hcap; j += stride) {
+        ws.hkey[j] = 0ull;
+        ws.hidx[j] = 0u;
+    }
+}
+
+__global__ void k_ws_rearm_header(WsDev ws) {
+    WsHeader *h = ws.hdr;
+    h->err = 0u;
+    h->n_touched = 0u;
+    h->pool = 0u;
+    h->next_work = 0u;
+    h->done_ctas = 0u;
+    h->acc_valid = 0ull;
+    h->acc_inside = 0ull;
+    h->acc_kept = 0ull;
+}
+
+void launch_footprint(const DevGrid &g, const DevParams &p, const DevTables &t, int n,
+                      const WsDev &ws, uint32_t hcap, uint32_t *bits_u, uint32_t *bits_s,
+                      unsigned long long *counts, cudaStream_t s) {
+    if (n > 0) k_footprint<<<n, 256, 0, s>>>(g, p, t, n, ws, bits_u, bits_s, counts);
+    k_ws_rearm<<<2 * 152, 256, 0, s>>>(ws, hcap);
+    k_ws_rearm_header<<<1, 1, 0, s>>>(ws);
+}
+
+// ------------------------------------------------------------------ readouts
+__global__ void k_bin_dirs(DevParams p, DevTables t, const double *__restrict__ dirs, int n,
+                           int *__restrict__ bins) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = dirs[3 * i], y = dirs[3 * i + 1], z = dirs[3 * i + 2];
+    bins[i] = (x == 0.0 && y == 0.0 && z == 0.0) ? -1 : bin_of(p, t, x, y, z);
+}
+
+__global__ void k_read_voxels(DevGrid g, const int *__restrict__ idx, long long n,
+                              uint32_t *__restrict__ mask, uint8_t *__restrict__ sign,
+                              uint16_t *__restrict__ hits) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = idx[3 * i], y = idx[3 * i + 1], z = idx[3 * i + 2];
+    uint32_t m = 0xFFFFFFFFu;
+    uint8_t s = 1;
+    uint16_t h = 0;
+    if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
+        const size_t v = ((size_t)z * g.ny + y) * g.pitch + x;
+        m = g.mask[v];
+        s = g.sign[v];
+        h = g.hits[v];
+    }
+    if (mask) mask[i] = m;
+    if (sign) sign[i] = s;
+    if (hits) hits[i] = h;
+}
+
+__global__ void k_read_distance(DevGrid g, double res, const int *__restrict__ idx, long long n,
+                                float *__restrict__ sdf) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = idx[3 * i], y = idx[3 * i + 1], z = idx[3 * i + 2];
+    uint32_t m = 0xFFFFFFFFu;
+    uint8_t s = 1;
+    if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
+        const size_t v = ((size_t)z * g.ny + y) * g.pitch + x;
+        m = g.mask[v];
+        s = g.sign[v];
+    }
+    const double d = (double)__popc(m) * res;
+    sdf[i] = (float)(s ? d : -d);
+}
+
+// ------------------------------------------------------------------ launchers
+static inline int blocks_for(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
+
+void launch_voxelize(const DevGrid &g, const DevParams &p, const DevTables &t, const Pose &pose,
+                     const float *xyz, int n, const WsDev &ws, uint32_t hcap, cudaStream_t s) {
+    k_voxelize<<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, t, pose, xyz, n, ws, hcap);
+}
+
+void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
+                  cudaStream_t s) {
+    k_count<<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, n, ws, hcap);
+}
+
+void launch_alloc(const WsDev &ws, int grid_ctas, cudaStream_t s) {
+    k_alloc<<<grid_ctas, 256, 0, s>>>(ws);
+}
+
+void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
+                 cudaStream_t s) {
+    k_fill<<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, n, ws, hcap);
+}
+
+void launch_bin_dirs(const DevParams &p, const DevTables &t, const double *dirs, int n, int *bins,
+                     cudaStream_t s) {
+    if (n > 0) k_bin_dirs<<<blocks_for(n, 256), 256, 0, s>>>(p, t, dirs, n, bins);
+}
+
+void launch_read_voxels(const DevGrid &g, const int *idx, long long n, uint32_t *mask,
+                        uint8_t *sign, uint16_t *hits, cudaStream_t s) {
+    if (n > 0) k_read_voxels<<<blocks_for(n, 256), 256, 0, s>>>(g, idx, n, mask, sign, hits);
+}
+
+void launch_read_distance(const DevGrid &g, double res, const int *idx, long long n, float *sdf,
+                          cudaStream_t s) {
+    if (n > 0) k_read_distance<<<blocks_for(n, 256), 256, 0, s>>>(g, res, idx, n, sdf);
+}
+
+}  // namespace dbt

@@ -1,0 +1,342 @@
+"""Thin ctypes binding of libdbtsdf.so (include/dbtsdf.h).
+
+Functions carry the C names and only marshal arguments; every step of the
+integration runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: if the library is missing or
+the process has no CUDA device, calls fail with an exception.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+DBT_OK, DBT_EINVAL, DBT_ENOMEM, DBT_ECUDA, DBT_ETIMEOUT, DBT_ESTATE = range(6)
+DBT_BINS_OCTA, DBT_BINS_AZEL = 0, 1
+_STATUS = {0: "DBT_OK", 1: "DBT_EINVAL", 2: "DBT_ENOMEM", 3: "DBT_ECUDA",
+           4: "DBT_ETIMEOUT", 5: "DBT_ESTATE"}
+HEADER = os.path.join(_build.INCLUDE, "dbtsdf.h")
+
+
+class DbtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class dbt_params(ctypes.Structure):
+    _fields_ = [("kernel_size", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("bins_a", ctypes.c_int32), ("bins_b", ctypes.c_int32),
+                ("shadow_radius", ctypes.c_double), ("hit_threshold", ctypes.c_int32),
+                ("hit_max", ctypes.c_int32), ("dedup_first", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class dbt_grid(ctypes.Structure):
+    _fields_ = [("mask", ctypes.c_void_p), ("sign", ctypes.c_void_p), ("hits", ctypes.c_void_p),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("pitch_x", ctypes.c_int32), ("res", ctypes.c_double),
+                ("origin", ctypes.c_double * 3)]
+
+
+class dbt_scan_stats(ctypes.Structure):
+    _fields_ = [("n_input", ctypes.c_int64), ("n_valid", ctypes.c_int64),
+                ("n_inside", ctypes.c_int64), ("n_kept", ctypes.c_int64),
+                ("n_pairs", ctypes.c_int64), ("n_bricks", ctypes.c_int64),
+                ("error", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_SIGS = {
+    "dbt_grid_layout": [ctypes.c_int32] * 3 + [_P(ctypes.c_int32)] + [_P(ctypes.c_size_t)] * 3,
+    "dbt_grid_init": [_P(dbt_grid), _vp],
+    "dbt_kernels_build": [_P(dbt_params), _P(_vp)],
+    "dbt_kernels_destroy": [_vp],
+    "dbt_kernels_export": [_vp, _vp, _vp],
+    "dbt_tables_host": [_P(dbt_params), _vp, _vp],
+    "dbt_bin_directions": [_vp, _vp, ctypes.c_int64, _vp, _vp],
+    "dbt_workspace_size": [_P(dbt_grid), _vp, ctypes.c_int64, _P(ctypes.c_size_t)],
+    "dbt_workspace_create": [_P(dbt_grid), _vp, ctypes.c_int64, _vp, ctypes.c_size_t, _vp,
+                             _P(_vp)],
+    "dbt_workspace_reset": [_vp, _vp],
+    "dbt_workspace_destroy": [_vp],
+    "dbt_integrate_scan": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64,
+                           _P(ctypes.c_double), _vp],
+    "dbt_integrate_scan_host": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64,
+                                _P(ctypes.c_double), _P(dbt_scan_stats), _vp],
+    "dbt_get_scan_stats": [_vp, _P(dbt_scan_stats), _vp],
+    "dbt_read_voxels": [_P(dbt_grid), _vp, ctypes.c_int64, _vp, _vp, _vp, _vp],
+    "dbt_read_distance": [_P(dbt_grid), _vp, ctypes.c_int64, _vp, _vp],
+    "dbt_sync": [_vp, _vp],
+    "dbt_workspace_set_timing": [_vp, _vp, _vp],
+    "dbt_scan_footprint": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
+                           _vp, ctypes.c_size_t, _P(ctypes.c_int64), _vp],
+}
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Load libdbtsdf.so (building it in-tree if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        p = path or _build.build()
+        L = ctypes.CDLL(p)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.dbt_last_error.restype = ctypes.c_char_p
+        L.dbt_last_error.argtypes = []
+        L.dbt_version.restype = ctypes.c_char_p
+        L.dbt_version.argtypes = []
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/dbtsdf.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    return re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(dbt_\w+)\s*\(", text, re.M)
+
+
+def _check(status: int):
+    if status != DBT_OK:
+        raise DbtError(status, lib().dbt_last_error().decode())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ C names
+def dbt_version() -> str:
+    return lib().dbt_version().decode()
+
+
+def dbt_grid_layout(nx: int, ny: int, nz: int):
+    pitch = ctypes.c_int32()
+    mb, sb, hb = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().dbt_grid_layout(nx, ny, nz, ctypes.byref(pitch), ctypes.byref(mb),
+                                 ctypes.byref(sb), ctypes.byref(hb)))
+    return pitch.value, mb.value, sb.value, hb.value
+
+
+def dbt_grid_init(grid: "Grid", stream=None):
+    _check(lib().dbt_grid_init(ctypes.byref(grid.c), _stream_ptr(stream)))
+
+
+def make_params(kernel_size=11, scheme=DBT_BINS_OCTA, bins_a=8, bins_b=8, shadow_radius=3.0,
+                hit_threshold=3, hit_max=255, dedup_first=1) -> dbt_params:
+    return dbt_params(kernel_size, scheme, bins_a, bins_b, float(shadow_radius), hit_threshold,
+                      hit_max, dedup_first, 0)
+
+
+def dbt_tables_host(params: dbt_params):
+    """Host-built tables: (K^3 masks [oz][oy][ox], bins x K^3 shadow bytes)."""
+    K = params.kernel_size
+    nb = params.bins_a * params.bins_b
+    m = np.empty(K ** 3, np.uint32)
+    s = np.empty(nb * K ** 3, np.uint8)
+    _check(lib().dbt_tables_host(ctypes.byref(params), m.ctypes.data, s.ctypes.data))
+    return m.reshape(K, K, K), s.reshape(nb, K, K, K)
+
+
+class Kernels:
+    """dbt_kernels_build / dbt_kernels_destroy."""
+
+    def __init__(self, params: dbt_params):
+        self.params = params
+        h = _vp()
+        _check(lib().dbt_kernels_build(ctypes.byref(params), ctypes.byref(h)))
+        self.h = h
+
+    def export(self):
+        K = self.params.kernel_size
+        nb = self.params.bins_a * self.params.bins_b
+        m = np.empty(K ** 3, np.uint32)
+        s = np.empty(nb * K ** 3, np.uint8)
+        _check(lib().dbt_kernels_export(self.h, m.ctypes.data, s.ctypes.data))
+        return m.reshape(K, K, K), s.reshape(nb, K, K, K)
+
+    def close(self):
+        if self.h:
+            _check(lib().dbt_kernels_destroy(self.h))
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dbt_bin_directions(kernels: Kernels, dirs, stream=None):
+    """Device binning of float64 (n, 3) directions (torch tensor on CUDA)."""
+    import torch
+    d = dirs.to(torch.float64).contiguous()
+    out = torch.empty(d.shape[0], dtype=torch.int32, device=d.device)
+    _check(lib().dbt_bin_directions(kernels.h, d.data_ptr(), d.shape[0], out.data_ptr(),
+                                    _stream_ptr(stream)))
+    return out
+
+
+class Grid:
+    """Dense SoA grid in torch device memory: mask u32, sign u8, hits u16,
+    each shaped (nz, ny, pitch_x)."""
+
+    def __init__(self, nx, ny, nz, res, origin=(0.0, 0.0, 0.0), device="cuda", init=True,
+                 stream=None):
+        import torch
+        pitch, mb, sb, hb = dbt_grid_layout(nx, ny, nz)
+        self.nx, self.ny, self.nz, self.pitch = nx, ny, nz, pitch
+        self.res = float(res)
+        self.origin = tuple(float(o) for o in origin)
+        self.mask = torch.empty((nz, ny, pitch), dtype=torch.int32, device=device)
+        self.sign = torch.empty((nz, ny, pitch), dtype=torch.uint8, device=device)
+        self.hits = torch.empty((nz, ny, pitch), dtype=torch.int16, device=device)
+        for t in (self.mask, self.sign, self.hits):
+            if t.data_ptr() % 256:
+                raise DbtError(DBT_EINVAL, "torch returned a non-256-byte-aligned buffer")
+        self.c = dbt_grid(self.mask.data_ptr(), self.sign.data_ptr(), self.hits.data_ptr(),
+                          nx, ny, nz, pitch, self.res, (ctypes.c_double * 3)(*self.origin))
+        if init:
+            dbt_grid_init(self, stream)
+
+    def numpy(self):
+        """Host copies without padding: (mask u32, sign u8, hits u16), (nz, ny, nx)."""
+        m = self.mask[:, :, :self.nx].cpu().numpy().view(np.uint32)
+        s = self.sign[:, :, :self.nx].cpu().numpy()
+        h = self.hits[:, :, :self.nx].cpu().numpy().view(np.uint16)
+        return m, s, h
+
+
+class Workspace:
+    """Caller-owned device scratch (a torch uint8 tensor) + the library handle."""
+
+    def __init__(self, grid: Grid, kernels: Kernels, max_points: int, stream=None):
+        import torch
+        nbytes = ctypes.c_size_t()
+        _check(lib().dbt_workspace_size(ctypes.byref(grid.c), kernels.h, max_points,
+                                        ctypes.byref(nbytes)))
+        self.nbytes = nbytes.value
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=grid.mask.device)
+        off = (-self.buf.data_ptr()) % 256
+        self.ptr = self.buf.data_ptr() + off
+        h = _vp()
+        _check(lib().dbt_workspace_create(ctypes.byref(grid.c), kernels.h, max_points, self.ptr,
+                                          self.nbytes, _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+        self.max_points = max_points
+
+    def reset(self, stream=None):
+        _check(lib().dbt_workspace_reset(self.h, _stream_ptr(stream)))
+
+    def close(self):
+        if self.h:
+            lib().dbt_workspace_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _pose_arg(pose):
+    a = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(12))
+    return a, a.ctypes.data_as(_P(ctypes.c_double))
+
+
+def dbt_integrate_scan(grid: Grid, kernels: Kernels, ws: Workspace, xyz, pose, stream=None):
+    """Integrate one scan; xyz is a CUDA float32 tensor (n, 3), pose (3, 4)."""
+    n = int(xyz.shape[0])
+    if n and (not xyz.is_cuda or not xyz.is_contiguous()):
+        raise DbtError(DBT_EINVAL, "xyz must be a contiguous CUDA float32 tensor")
+    keep, pp = _pose_arg(pose)
+    _check(lib().dbt_integrate_scan(ctypes.byref(grid.c), kernels.h, ws.h,
+                                    xyz.data_ptr() if n else None, n, pp, _stream_ptr(stream)))
+
+
+def dbt_integrate_scan_host(grid: Grid, kernels: Kernels, ws: Workspace, xyz_host, pose,
+                            stats: dbt_scan_stats | None = None, stream=None):
+    """Integrate one scan from host memory (a pinned CPU float32 tensor or a
+    numpy array); the scan counters land in ``stats`` when the stream gets there."""
+    n = int(xyz_host.shape[0])
+    ptr = xyz_host.data_ptr() if hasattr(xyz_host, "data_ptr") else xyz_host.ctypes.data
+    keep, pp = _pose_arg(pose)
+    _check(lib().dbt_integrate_scan_host(ctypes.byref(grid.c), kernels.h, ws.h, ptr if n else None,
+                                         n, pp, ctypes.byref(stats) if stats is not None else None,
+                                         _stream_ptr(stream)))
+
+
+def dbt_get_scan_stats(ws: Workspace, stream=None, check: bool = True) -> dict:
+    st = dbt_scan_stats()
+    r = lib().dbt_get_scan_stats(ws.h, ctypes.byref(st), _stream_ptr(stream))
+    if check:
+        _check(r)
+    return st.as_dict()
+
+
+def dbt_read_voxels(grid: Grid, idx, stream=None):
+    """idx: CUDA int32 (n, 3) voxel coordinates -> (mask, sign, hits) tensors."""
+    import torch
+    i = idx.to(torch.int32).contiguous()
+    n = i.shape[0]
+    m = torch.empty(n, dtype=torch.int32, device=i.device)
+    s = torch.empty(n, dtype=torch.uint8, device=i.device)
+    h = torch.empty(n, dtype=torch.int16, device=i.device)
+    _check(lib().dbt_read_voxels(ctypes.byref(grid.c), i.data_ptr(), n, m.data_ptr(),
+                                 s.data_ptr(), h.data_ptr(), _stream_ptr(stream)))
+    return m, s, h
+
+
+def dbt_read_distance(grid: Grid, idx, stream=None):
+    import torch
+    i = idx.to(torch.int32).contiguous()
+    out = torch.empty(i.shape[0], dtype=torch.float32, device=i.device)
+    _check(lib().dbt_read_distance(ctypes.byref(grid.c), i.data_ptr(), i.shape[0],
+                                   out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
+def dbt_sync(stream=None, ws: Workspace | None = None):
+    _check(lib().dbt_sync(_stream_ptr(stream), ws.h if ws is not None else None))
+
+
+def dbt_workspace_set_timing(ws: Workspace, ev_begin=None, ev_end=None):
+    """Record torch.cuda.Event pair around each later scan's integrate kernel."""
+    _check(lib().dbt_workspace_set_timing(ws.h, ev_begin.cuda_event if ev_begin else None,
+                                          ev_end.cuda_event if ev_end else None))
+
+
+def footprint_bytes(grid: Grid) -> int:
+    words = (grid.pitch * grid.ny * grid.nz + 31) // 32
+    return 2 * words * 4 + 16
+
+
+def dbt_scan_footprint(grid: Grid, kernels: Kernels, ws: Workspace, xyz, pose, bits, stream=None):
+    """(U, U_s) of one scan: distinct voxels under kept returns' kernels and
+    shadows.  ``bits`` is a CUDA uint8 tensor of footprint_bytes(grid)."""
+    n = int(xyz.shape[0])
+    keep, pp = _pose_arg(pose)
+    out = (ctypes.c_int64 * 2)()
+    _check(lib().dbt_scan_footprint(ctypes.byref(grid.c), kernels.h, ws.h,
+                                    xyz.data_ptr() if n else None, n, pp, bits.data_ptr(),
+                                    bits.numel(), out, _stream_ptr(stream)))
+    return int(out[0]), int(out[1])

@@ -159,7 +159,7 @@ def _raycast(scene: Scene, origin: np.ndarray, dirs: np.ndarray) -> np.ndarray:
     best = np.full(n, np.inf)
     ox, oy, oz = origin
     dx, dy, dz = dirs[:, 0], dirs[:, 1], dirs[:, 2]
-    with np.errstate(divide="ignore", invalid="ignore"):
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
         if scene.ground_z is not None:
             t = (scene.ground_z - oz) / dz
             ok = (dz < 0) & (t > 0)
@@ -175,32 +175,65 @@ def _raycast(scene: Scene, origin: np.ndarray, dirs: np.ndarray) -> np.ndarray:
                 if scene.ground_z is not None:
                     ok &= z >= scene.ground_z
                 best = np.where(ok & (t < best), t, best)
-        inv = 1.0 / np.where(dirs == 0.0, 1e-300, dirs)
-        for b in scene.boxes:
-            t1 = (b[0:3] - origin) * inv
-            t2 = (b[3:6] - origin) * inv
-            tn = np.max(np.minimum(t1, t2), axis=1)
-            tf = np.min(np.maximum(t1, t2), axis=1)
-            ok = (tn <= tf) & (tn > 0)
-            best = np.where(ok & (tn < best), tn, best)
+        if scene.boxes.shape[0]:
+            inv = 1.0 / np.where(dirs == 0.0, 1e-300, dirs)           # (n, 3)
+            lo = (scene.boxes[None, :, 0:3] - origin) * inv[:, None, :]  # (n, B, 3)
+            hi = (scene.boxes[None, :, 3:6] - origin) * inv[:, None, :]
+            tn = np.max(np.minimum(lo, hi), axis=2)
+            tf = np.min(np.maximum(lo, hi), axis=2)
+            tn = np.where((tn <= tf) & (tn > 0), tn, np.inf)
+            best = np.minimum(best, tn.min(axis=1))
         if scene.cylinders.shape[0]:
-            a = dx * dx + dy * dy
-            for c in scene.cylinders:
-                cx, cy, r, z0, z1 = c
-                fx, fy = ox - cx, oy - cy
-                bb = 2.0 * (fx * dx + fy * dy)
-                cc = fx * fx + fy * fy - r * r
-                disc = bb * bb - 4.0 * a * cc
-                t = (-bb - np.sqrt(np.maximum(disc, 0.0))) / (2.0 * a)
-                z = oz + t * dz
-                ok = (disc >= 0) & (a > 0) & (t > 0) & (z >= z0) & (z <= z1)
-                best = np.where(ok & (t < best), t, best)
-                # top cap
-                tc = (z1 - oz) / dz
-                hx, hy = ox + tc * dx - cx, oy + tc * dy - cy
-                okc = (dz < 0) & (tc > 0) & (hx * hx + hy * hy <= r * r)
-                best = np.where(okc & (tc < best), tc, best)
+            c = scene.cylinders
+            a = (dx * dx + dy * dy)[:, None]
+            fx = (ox - c[:, 0])[None, :]
+            fy = (oy - c[:, 1])[None, :]
+            bb = 2.0 * (fx * dx[:, None] + fy * dy[:, None])
+            cc = fx * fx + fy * fy - (c[:, 2] * c[:, 2])[None, :]
+            disc = bb * bb - 4.0 * a * cc
+            t = (-bb - np.sqrt(np.maximum(disc, 0.0))) / (2.0 * a)
+            z = oz + t * dz[:, None]
+            ok = (disc >= 0) & (a > 0) & (t > 0) & (z >= c[None, :, 3]) & (z <= c[None, :, 4])
+            best = np.minimum(best, np.where(ok, t, np.inf).min(axis=1))
+            tc = (c[None, :, 4] - oz) / dz[:, None]
+            hx = ox + tc * dx[:, None] - c[None, :, 0]
+            hy = oy + tc * dy[:, None] - c[None, :, 1]
+            okc = (dz[:, None] < 0) & (tc > 0) & (hx * hx + hy * hy <= (c[:, 2] * c[:, 2])[None, :])
+            best = np.minimum(best, np.where(okc, tc, np.inf).min(axis=1))
     return best
+
+
+def _sector_masks(scene: Scene, origin: np.ndarray, nsec: int):
+    """Per azimuth sector, the boxes and cylinders whose bounding circle (seen
+    from the sensor) overlaps the sector, with a one-sector margin."""
+    out = []
+    width = 2.0 * np.pi / nsec
+
+    def spans(cx, cy, rad):
+        dx, dy = cx - origin[0], cy - origin[1]
+        d = np.hypot(dx, dy)
+        ang = np.arctan2(dy, dx) % (2.0 * np.pi)
+        half = np.where(d > rad, np.arcsin(np.minimum(1.0, rad / np.maximum(d, 1e-12))), np.pi)
+        return ang, half + width
+
+    b = scene.boxes
+    if b.shape[0]:
+        bang, bhalf = spans((b[:, 0] + b[:, 3]) / 2, (b[:, 1] + b[:, 4]) / 2,
+                            0.5 * np.hypot(b[:, 3] - b[:, 0], b[:, 4] - b[:, 1]))
+    c = scene.cylinders
+    if c.shape[0]:
+        cang, chalf = spans(c[:, 0], c[:, 1], c[:, 2])
+    for k in range(nsec):
+        mid = (k + 0.5) * width
+
+        def near(ang, half):
+            dd = np.abs((ang - mid + np.pi) % (2.0 * np.pi) - np.pi)
+            return dd <= half + width / 2
+
+        bsel = near(bang, bhalf) if b.shape[0] else np.zeros(0, bool)
+        csel = near(cang, chalf) if c.shape[0] else np.zeros(0, bool)
+        out.append((bsel, csel))
+    return out
 
 
 def rotation_rpy(roll: float, pitch: float, yaw: float) -> np.ndarray:
@@ -224,7 +257,7 @@ def make_pose(R: np.ndarray, t) -> np.ndarray:
 
 def lidar_scan(scene: Scene, pose: np.ndarray, beams: int, width: int, fov_deg: float,
                rmin: float, rmax: float, sigma: float, dropout: float, rng: Rng,
-               chunk: int = 16384) -> np.ndarray:
+               chunk: int = 4096) -> np.ndarray:
     """Spinning LiDAR: ``beams`` elevations in [-fov/2, +fov/2], ``width``
     azimuths k 2 pi / width; returns (beams * width, 3) float32 in the sensor
     frame, beam-major; misses, out-of-range and dropped returns are NaN."""
@@ -236,13 +269,29 @@ def lidar_scan(scene: Scene, pose: np.ndarray, beams: int, width: int, fov_deg: 
     origin = pose[:, 3]
     dw = ds @ R.T
     n = ds.shape[0]
-    t = np.empty(n)
-    for s in range(0, n, chunk):
-        t[s:s + chunk] = _raycast(scene, origin, dw[s:s + chunk])
+    t = np.full(n, np.inf)
+    # cull boxes and poles per world-azimuth sector: each is tested only on
+    # the rays whose azimuth falls within its angular extent seen from the sensor
+    nsec = 64
+    az_w = np.arctan2(dw[:, 1], dw[:, 0]) % (2.0 * np.pi)
+    sec = np.minimum((az_w * (nsec / (2.0 * np.pi))).astype(np.int64), nsec - 1)
+    order = np.argsort(sec, kind="stable")
+    bounds = np.searchsorted(sec[order], np.arange(nsec + 1))
+    prim_sectors = _sector_masks(scene, origin, nsec)
+    for k in range(nsec):
+        idx = order[bounds[k]:bounds[k + 1]]
+        if idx.size == 0:
+            continue
+        bsel, csel = prim_sectors[k]
+        sub = Scene(scene.ground_z, scene.walls, scene.boxes[bsel], scene.cylinders[csel])
+        for c0 in range(0, idx.size, chunk):
+            j = idx[c0:c0 + chunk]
+            t[j] = _raycast(sub, origin, dw[j])
     t = t + rng.normal(n, sigma)
     drop = rng.uniform(n) < dropout
     bad = ~np.isfinite(t) | (t < rmin) | (t > rmax) | drop
-    pts = ds * t[:, None]
+    with np.errstate(invalid="ignore"):
+        pts = ds * t[:, None]
     pts[bad] = np.nan
     return pts.astype(np.float32)
 

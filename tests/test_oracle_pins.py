@@ -9,6 +9,7 @@ the gather form (every voxel: min over returns of ceil |v - c|), which is a
 different formulation from the oracle's per-return scatter of Eqs. 4-6.
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -210,6 +211,11 @@ def test_single_point_worked_example(orc):
 
 
 # ------------------------------------------------------------------ brute force
+def _fma(a, b, c):
+    """Exactly rounded a * b + c via rational arithmetic."""
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
 def _brute_force(orc, p, dims, res, origin, scans):
     """Gather form of Sec. III-C: per voxel, min ceil-distance over kept
     returns in range and the count of returns whose shadow covers it."""
@@ -225,9 +231,10 @@ def _brute_force(orc, p, dims, res, origin, scans):
                 continue
             if px == 0.0 and py == 0.0 and pz == 0.0:
                 continue
-            d = [(pose[r][0] * px + pose[r][1] * py) + pose[r][2] * pz for r in range(3)]
+            d = [_fma(pose[r][2], pz, _fma(pose[r][1], py, pose[r][0] * px)) for r in range(3)]
             w = [d[r] + pose[r][3] for r in range(3)]
-            c = [math.floor((w[a] - origin[a]) / res) for a in range(3)]
+            inv_res = 1.0 / res
+            c = [math.floor((w[a] - origin[a]) * inv_res) for a in range(3)]
             if any(c[a] < R or c[a] > (nx, ny, nz)[a] - 1 - R for a in range(3)):
                 continue
             if p.dedup_first:
@@ -374,8 +381,8 @@ def test_rs0_hits_count_points_per_voxel(orc, room):
     g = orc.Grid.create(128, 128, 128, 0.1)
     st = orc.integrate_scan(g, p, pts, pose)
     ok = np.all(np.isfinite(pts), axis=1)
-    c = np.floor(pts[ok].astype(np.float64) + 0.0)  # identity rotation
-    c = np.floor((pts[ok].astype(np.float64) + pose[:, 3] - 0.0) / 0.1).astype(np.int64)
+    # identity rotation: d = p exactly; c = floor((p + t - 0) * (1 / res))
+    c = np.floor((pts[ok].astype(np.float64) + pose[:, 3] - 0.0) * (1.0 / 0.1)).astype(np.int64)
     inside = np.all((c >= 5) & (c <= 122), axis=1)
     c = c[inside]
     want = np.zeros((128, 128, 128), np.int64)
