@@ -252,6 +252,8 @@ def run_ours(args, rank, world):
     eve = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    for e in evb + eve:          # torch creates the CUDA event on first record
+        e.record(stream)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
