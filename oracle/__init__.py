@@ -70,45 +70,55 @@ class Stats(ctypes.Structure):
 _lib = None
 
 
+def load(path: str):
+    """Load an oracle shared object and declare its signatures."""
+    L = ctypes.CDLL(path)
+    _declare(L)
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        L = _lib
-        P = ctypes.POINTER
-        L.orc_distance_mask.restype = ctypes.c_uint32
-        L.orc_distance_mask.argtypes = [ctypes.c_int] * 3
-        L.orc_bin_octa.restype = ctypes.c_int
-        L.orc_bin_octa.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int]
-        L.orc_bin_azel.restype = ctypes.c_int
-        L.orc_bin_azel.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int] * 2
-        L.orc_bin_az.restype = ctypes.c_int
-        L.orc_bin_az.argtypes = [ctypes.c_double] * 2 + [ctypes.c_int]
-        L.orc_bin_el.restype = ctypes.c_int
-        L.orc_bin_el.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int]
-        L.orc_bin.restype = ctypes.c_int
-        L.orc_bin.argtypes = [P(Params)] + [ctypes.c_double] * 3
-        L.orc_bin_dir.restype = None
-        L.orc_bin_dir.argtypes = [P(Params), ctypes.c_int, P(ctypes.c_double)]
-        L.orc_in_shadow.restype = ctypes.c_int
-        L.orc_in_shadow.argtypes = [P(Params)] + [ctypes.c_int] * 4
-        L.orc_grid_init.restype = None
-        L.orc_grid_init.argtypes = [P(_Grid)]
-        L.orc_grid_bytes_eq1.restype = ctypes.c_int64
-        L.orc_grid_bytes_eq1.argtypes = [ctypes.c_int64] * 3
-        L.orc_integrate_scan.restype = ctypes.c_int64
-        L.orc_integrate_scan.argtypes = [P(_Grid), P(Params), ctypes.c_void_p,
-                                         ctypes.c_int64, ctypes.c_void_p, P(Stats)]
-        L.orc_scan_kept.restype = ctypes.c_int64
-        L.orc_scan_kept.argtypes = [P(Params), P(_Grid), ctypes.c_void_p, ctypes.c_int64,
-                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-        L.orc_query_voxels.restype = None
-        L.orc_query_voxels.argtypes = [P(Params), ctypes.c_int64, ctypes.c_void_p,
-                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
-                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-        L.orc_signed_distance.restype = ctypes.c_double
-        L.orc_signed_distance.argtypes = [ctypes.c_uint32, ctypes.c_uint8, ctypes.c_double]
+        _lib = load(build())
     return _lib
+
+
+def _declare(L):
+    """ctypes signatures of the oracle's C functions."""
+    P = ctypes.POINTER
+    L.orc_distance_mask.restype = ctypes.c_uint32
+    L.orc_distance_mask.argtypes = [ctypes.c_int] * 3
+    L.orc_bin_octa.restype = ctypes.c_int
+    L.orc_bin_octa.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int]
+    L.orc_bin_azel.restype = ctypes.c_int
+    L.orc_bin_azel.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int] * 2
+    L.orc_bin_az.restype = ctypes.c_int
+    L.orc_bin_az.argtypes = [ctypes.c_double] * 2 + [ctypes.c_int]
+    L.orc_bin_el.restype = ctypes.c_int
+    L.orc_bin_el.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int]
+    L.orc_bin.restype = ctypes.c_int
+    L.orc_bin.argtypes = [P(Params)] + [ctypes.c_double] * 3
+    L.orc_bin_dir.restype = None
+    L.orc_bin_dir.argtypes = [P(Params), ctypes.c_int, P(ctypes.c_double)]
+    L.orc_in_shadow.restype = ctypes.c_int
+    L.orc_in_shadow.argtypes = [P(Params)] + [ctypes.c_int] * 4
+    L.orc_grid_init.restype = None
+    L.orc_grid_init.argtypes = [P(_Grid)]
+    L.orc_grid_bytes_eq1.restype = ctypes.c_int64
+    L.orc_grid_bytes_eq1.argtypes = [ctypes.c_int64] * 3
+    L.orc_integrate_scan.restype = ctypes.c_int64
+    L.orc_integrate_scan.argtypes = [P(_Grid), P(Params), ctypes.c_void_p,
+                                     ctypes.c_int64, ctypes.c_void_p, P(Stats)]
+    L.orc_scan_kept.restype = ctypes.c_int64
+    L.orc_scan_kept.argtypes = [P(Params), P(_Grid), ctypes.c_void_p, ctypes.c_int64,
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.orc_query_voxels.restype = None
+    L.orc_query_voxels.argtypes = [P(Params), ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.orc_signed_distance.restype = ctypes.c_double
+    L.orc_signed_distance.argtypes = [ctypes.c_uint32, ctypes.c_uint8, ctypes.c_double]
 
 
 def params(kernel_size=11, scheme=SCHEME_OCTA, bins_a=8, bins_b=8, shadow_radius=3.0,
