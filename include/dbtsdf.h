@@ -200,6 +200,26 @@ dbt_status dbt_scan_footprint(const dbt_grid *g, const dbt_kernels *k, dbt_works
                               const float *d_xyz, int64_t n, const double pose[12], void *d_bits,
                               size_t bits_bytes, int64_t h_counts[2], void *stream);
 
+/* dbt_integrate_scan for callers that cannot allocate device memory (the
+ * paper has no counterpart; this is a deployment convenience).  Some callers
+ * may not call cudaMalloc while they run -- a real-time mapping loop that
+ * forbids allocation after start-up, or a plugin whose host framework owns
+ * every device allocation -- so they cannot provide a workspace.  This entry
+ * point uses a fixed scratch array compiled into the library instead and
+ * allocates nothing (host or device).  Limits: n <= 65,536 returns per scan,
+ * and the grid's integration layout must fit in 18 MiB (true for every grid
+ * of up to 524,288 bricks of 32 x 8 x 8 voxels); larger inputs are rejected
+ * with DBT_EINVAL and a message.  The 18 MiB array occupies device memory on
+ * every GPU that loads the library until the process exits.  All calls share
+ * it: calls whose work overlaps on the GPU race, so issue them on one stream
+ * (or otherwise serialise them).  The first call on a device looks up the
+ * array's device address; make it before capturing a stream into a graph.
+ * Other arguments as dbt_integrate_scan; *h_stats (may be NULL) receives the
+ * scan's counters asynchronously, like dbt_integrate_scan_host. */
+dbt_status dbt_integrate_scan_noalloc(const dbt_grid *g, const dbt_kernels *k, const float *d_xyz,
+                                      int64_t n, const double pose[12], dbt_scan_stats *h_stats,
+                                      void *stream);
+
 /* Synchronises stream and copies the last scan's counters (may be NULL).
  * Returns DBT_ESTATE when the device latched an error. */
 dbt_status dbt_get_scan_stats(const dbt_workspace *ws, dbt_scan_stats *out, void *stream);

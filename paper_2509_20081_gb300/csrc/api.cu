@@ -6,7 +6,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <string>
 #include <vector>
 
 #include "dbt_internal.cuh"
@@ -17,21 +16,22 @@ using namespace dbt;
 static const double kPi = 3.14159265358979323846;
 
 // ------------------------------------------------------------------ errors
-static thread_local std::string t_err;
+// A fixed per-thread buffer: reporting an error never allocates.
+static thread_local char t_err[512];
 
 static dbt_status fail(dbt_status st, const char *fmt, ...) {
-    char buf[512];
     va_list ap;
     va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
+    vsnprintf(t_err, sizeof t_err, fmt, ap);
     va_end(ap);
-    t_err = buf;
     return st;
 }
 
 static dbt_status cuda_fail(cudaError_t e, const char *what) {
     return fail(DBT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+
+dbt_status dbt::report_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
 
 #define DBT_CUDA(call)                                   \
     do {                                                 \
@@ -408,25 +408,12 @@ extern "C" dbt_status dbt_workspace_size(const dbt_grid *g, const dbt_kernels *k
     return DBT_OK;
 }
 
-extern "C" dbt_status dbt_workspace_create(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
-                                           void *d_buf, size_t bytes, void *stream,
-                                           dbt_workspace **out) {
-    if (!out) return fail(DBT_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
-    dbt_status st = check_grid(g);
-    if (st != DBT_OK) return st;
-    if (!d_buf || !aligned256(d_buf)) return fail(DBT_EINVAL, "workspace buffer must be 256-byte aligned");
-    WsLayout L;
-    st = ws_layout(g, k, max_points, &L);
-    if (st != DBT_OK) return st;
-    if (bytes < L.total)
-        return fail(DBT_ENOMEM, "workspace too small: %zu < %zu bytes", bytes, L.total);
-    dbt_workspace *w = new (std::nothrow) dbt_workspace();
-    if (!w) return fail(DBT_ENOMEM, "host allocation failed");
-    char *base = (char *)d_buf;
+// Points a workspace view at the regions of base laid out by L.
+static void ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels *k, long long max_points,
+                    const WsLayout &L, void *base_ptr) {
+    char *base = (char *)base_ptr;
     w->L = L;
-    w->buf = d_buf;
+    w->buf = base_ptr;
     w->max_points = max_points;
     w->nx = g->nx;
     w->ny = g->ny;
@@ -445,6 +432,25 @@ extern "C" dbt_status dbt_workspace_create(const dbt_grid *g, const dbt_kernels 
     w->d.max_touched = L.max_touched;
     w->d.pairs = (uint32_t *)(base + L.pairs);
     w->d.pairs_cap = L.pairs_cap;
+}
+
+extern "C" dbt_status dbt_workspace_create(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
+                                           void *d_buf, size_t bytes, void *stream,
+                                           dbt_workspace **out) {
+    if (!out) return fail(DBT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    if (!d_buf || !aligned256(d_buf)) return fail(DBT_EINVAL, "workspace buffer must be 256-byte aligned");
+    WsLayout L;
+    st = ws_layout(g, k, max_points, &L);
+    if (st != DBT_OK) return st;
+    if (bytes < L.total)
+        return fail(DBT_ENOMEM, "workspace too small: %zu < %zu bytes", bytes, L.total);
+    dbt_workspace *w = new (std::nothrow) dbt_workspace();
+    if (!w) return fail(DBT_ENOMEM, "host allocation failed");
+    ws_bind(w, g, k, max_points, L, d_buf);
     cudaError_t e = cudaMemsetAsync(d_buf, 0, L.total, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         delete w;
@@ -580,6 +586,41 @@ extern "C" dbt_status dbt_integrate_scan(const dbt_grid *g, const dbt_kernels *k
     return enqueue_scan(g, k, ws, d_xyz, n, pose, (cudaStream_t)stream);
 }
 
+// One scan on a scratch buffer owned by the caller of this function (the
+// no-allocation entry point): a workspace view lives on the stack, the
+// regions that must start at zero are cleared on the stream, and nothing is
+// allocated on the host or the device.
+dbt_status dbt::integrate_on_scratch(const dbt_grid *g, const dbt_kernels *k, const float *d_xyz,
+                                     int64_t n, const double pose[12], void *scratch,
+                                     size_t scratch_bytes, long long max_points,
+                                     dbt_scan_stats *h_stats, cudaStream_t s) {
+    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    if (n < 0 || n > max_points)
+        return fail(DBT_EINVAL, "n = %lld exceeds the no-allocation limit of %lld returns per scan",
+                    (long long)n, max_points);
+    WsLayout L;
+    st = ws_layout(g, k, max_points, &L);
+    if (st != DBT_OK) return st;
+    if (L.total > scratch_bytes)
+        return fail(DBT_EINVAL,
+                    "grid too large for the no-allocation scratch: needs %zu bytes, limit %zu "
+                    "(%u bricks of 32x8x8 voxels)", L.total, scratch_bytes, L.nbricks);
+    dbt_workspace w;
+    ws_bind(&w, g, k, max_points, L, scratch);
+    char *base = (char *)scratch;
+    DBT_CUDA(cudaMemsetAsync(base + L.hdr, 0, up256(sizeof(WsHeader)), s));
+    DBT_CUDA(cudaMemsetAsync(base + L.hkey, 0, L.bcnt - L.hkey, s));        // hash keys + indices
+    DBT_CUDA(cudaMemsetAsync(base + L.bcnt, 0, (size_t)L.nbricks * 4, s));  // brick counters
+    st = enqueue_scan(g, k, &w, d_xyz, n, pose, s);
+    if (st != DBT_OK) return st;
+    if (h_stats)
+        DBT_CUDA(cudaMemcpyAsync(h_stats, &w.d.hdr->last, sizeof(dbt_scan_stats),
+                                 cudaMemcpyDeviceToHost, s));
+    return DBT_OK;
+}
+
 extern "C" dbt_status dbt_integrate_scan_host(const dbt_grid *g, const dbt_kernels *k,
                                               dbt_workspace *ws, const float *h_xyz, int64_t n,
                                               const double pose[12], dbt_scan_stats *h_stats,
@@ -651,6 +692,6 @@ extern "C" dbt_status dbt_read_distance(const dbt_grid *g, const int32_t *d_idx,
     return DBT_OK;
 }
 
-extern "C" const char *dbt_last_error(void) { return t_err.c_str(); }
+extern "C" const char *dbt_last_error(void) { return t_err; }
 
 extern "C" const char *dbt_version(void) { return "dbtsdf 0.1.0 sm_103a"; }

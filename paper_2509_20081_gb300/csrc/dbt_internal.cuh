@@ -128,4 +128,13 @@ void launch_read_voxels(const DevGrid &g, const int *idx, long long n, uint32_t 
 void launch_read_distance(const DevGrid &g, double res, const int *idx, long long n, float *sdf,
                           cudaStream_t s);
 
+// Sets the thread's error message for a failed CUDA call; returns DBT_ECUDA.
+dbt_status report_cuda_error(cudaError_t e, const char *what);
+
+// One scan on a caller-provided scratch buffer (see noalloc.cu); defined in api.cu.
+dbt_status integrate_on_scratch(const dbt_grid *g, const dbt_kernels *k, const float *d_xyz,
+                                int64_t n, const double pose[12], void *scratch,
+                                size_t scratch_bytes, long long max_points,
+                                dbt_scan_stats *h_stats, cudaStream_t s);
+
 }  // namespace dbt

@@ -77,6 +77,8 @@ _SIGS = {
     "dbt_read_distance": [_P(dbt_grid), _vp, ctypes.c_int64, _vp, _vp],
     "dbt_sync": [_vp, _vp],
     "dbt_workspace_set_timing": [_vp, _vp, _vp],
+    "dbt_integrate_scan_noalloc": [_P(dbt_grid), _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
+                                   _P(dbt_scan_stats), _vp],
     "dbt_scan_footprint": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
                            _vp, ctypes.c_size_t, _P(ctypes.c_int64), _vp],
 }
@@ -340,3 +342,15 @@ def dbt_scan_footprint(grid: Grid, kernels: Kernels, ws: Workspace, xyz, pose, b
                                     xyz.data_ptr() if n else None, n, pp, bits.data_ptr(),
                                     bits.numel(), out, _stream_ptr(stream)))
     return int(out[0]), int(out[1])
+
+
+def dbt_integrate_scan_noalloc(grid: Grid, kernels: Kernels, xyz, pose,
+                               stats: dbt_scan_stats | None = None, stream=None):
+    """Integrate one scan without any workspace: the library's fixed scratch
+    is used (at most 65,536 returns; see include/dbtsdf.h)."""
+    n = int(xyz.shape[0])
+    keep, pp = _pose_arg(pose)
+    _check(lib().dbt_integrate_scan_noalloc(ctypes.byref(grid.c), kernels.h,
+                                            xyz.data_ptr() if n else None, n, pp,
+                                            ctypes.byref(stats) if stats is not None else None,
+                                            _stream_ptr(stream)))
