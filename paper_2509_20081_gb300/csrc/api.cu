@@ -42,6 +42,8 @@ dbt_status dbt::report_cuda_error(cudaError_t e, const char *what) { return cuda
 static bool aligned256(const void *p) { return ((uintptr_t)p & 255u) == 0; }
 
 // ------------------------------------------------------------------ tables
+static int ceil_isqrt(int n);
+
 struct dbt_kernels {
     dbt_params params;
     DevParams dp;
@@ -50,7 +52,32 @@ struct dbt_kernels {
     std::vector<uint32_t> m2;         // mask by r^2
     std::vector<uint32_t> sh_off;     // packed shadow offsets by bin
     std::vector<uint32_t> sh_start;   // nbins + 1
+    std::vector<uint32_t> prow;       // kernel-row codes for the integration kernel
 };
+
+// Kernel-row codes: for q = oy^2 + oz^2 in [0, 2 R^2] and s in [0, 2R + 4),
+// the four bytes of P[q][s] are the Eq. 3 distance codes ceil(sqrt(ox^2 + q))
+// of the voxels at ox = s - 3 - R + e (e = 0..3), and 32 (no change) where
+// |ox| > R.  A 4-voxel word whose first voxel is at kernel offset ox reads
+// P[q][ox + R + 3].
+static void build_row_codes(int R, std::vector<uint32_t> &prow) {
+    const int W = 2 * R + 4;
+    prow.assign((size_t)(2 * R * R + 1) * W, 0u);
+    for (int q = 0; q <= 2 * R * R; ++q)
+        for (int s = 0; s < W; ++s) {
+            uint32_t word = 0;
+            for (int e = 0; e < 4; ++e) {
+                const int t = s - 3 + e;
+                uint32_t k = 32u;
+                if (t >= 0 && t <= 2 * R) {
+                    const int ox = t - R;
+                    k = (uint32_t)ceil_isqrt(ox * ox + q);
+                }
+                word |= k << (8 * e);
+            }
+            prow[(size_t)q * W + s] = word;
+        }
+}
 
 // Smallest k with k * k >= n (exact integer ceil of sqrt).
 static int ceil_isqrt(int n) {
@@ -198,6 +225,7 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
     const int K = p->kernel_size, R = (K - 1) / 2;
     const int nbins = p->bins_a * p->bins_b;
     build_host_tables(p, k->m2, k->sh_off, k->sh_start);
+    build_row_codes(R, k->prow);
     // Eq. 2 edge tables
     std::vector<double> az_c(MAX_EDGES, 0.0), az_s(MAX_EDGES, 0.0), el_s(MAX_EDGES, 0.0);
     std::vector<int> az_up(MAX_EDGES, 0);
@@ -219,7 +247,8 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
     size_t off_azs = off_azc + MAX_EDGES * 8;
     size_t off_els = off_azs + MAX_EDGES * 8;
     size_t off_up = off_els + MAX_EDGES * 8;
-    size_t total = off_up + MAX_EDGES * 4;
+    size_t off_pr = off_up + MAX_EDGES * 4;
+    size_t total = off_pr + k->prow.size() * 4;
     cudaError_t e = cudaMalloc(&k->d_base, total);
     if (e != cudaSuccess) {
         delete k;
@@ -235,6 +264,8 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
     if (e == cudaSuccess) e = cudaMemcpy(base + off_azs, az_s.data(), MAX_EDGES * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + off_els, el_s.data(), MAX_EDGES * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + off_up, az_up.data(), MAX_EDGES * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + off_pr, k->prow.data(), k->prow.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(k->d_base);
         delete k;
@@ -250,6 +281,7 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
     k->dp.Hmax = p->hit_max;
     k->dp.dedup = p->dedup_first;
     k->dp.n_m2 = (int)n_m2;
+    k->dp.sr = std::min(R, (int)std::floor(p->shadow_radius));
     k->dt.m2 = (const uint32_t *)(base + off_m2);
     k->dt.sh_off = (const uint32_t *)(base + off_sh);
     k->dt.sh_start = (const uint32_t *)(base + off_st);
@@ -257,6 +289,7 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
     k->dt.az_s = (const double *)(base + off_azs);
     k->dt.el_s = (const double *)(base + off_els);
     k->dt.az_up = (const int *)(base + off_up);
+    k->dt.prow = (const uint32_t *)(base + off_pr);
     *out = k;
     return DBT_OK;
 }

@@ -28,6 +28,7 @@ constexpr uint32_t ERR_HASH_FULL = 1u << 0;
 constexpr uint32_t ERR_PAIRS_OVERFLOW = 1u << 1;
 constexpr uint32_t ERR_TOUCHED_OVERFLOW = 1u << 2;
 constexpr uint32_t ERR_BAD_PAYLOAD = 1u << 3;
+constexpr uint32_t ERR_MASK_FORM = 1u << 4;      // a grid mask was not of the form 2^k - 1
 
 // Shadow offsets are packed as (ox + 128) | (oy + 128) << 8 | (oz + 128) << 16.
 __host__ __device__ inline uint32_t pack_off(int ox, int oy, int oz) {
@@ -42,6 +43,7 @@ struct DevParams {
     int T, Hmax;
     int dedup;
     int n_m2;         // entries of the mask-by-r^2 table
+    int sr;           // min(R, floor(r_s)): no shadow offset exceeds it on any axis
 };
 
 struct DevTables {
@@ -52,6 +54,7 @@ struct DevTables {
     const double *az_s;        // sin(theta_k)
     const int *az_up;          // theta_k < pi
     const double *el_s;        // elevation edge k: sin(phi_k), k = 0..B_el-1
+    const uint32_t *prow;      // kernel-row codes P[q * (2R + 4) + s], q = 0 .. 2 R^2
 };
 
 struct DevGrid {
