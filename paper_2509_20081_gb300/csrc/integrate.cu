@@ -49,12 +49,8 @@ static_assert(sizeof(WarpArea) % 16 == 0, "warp area alignment");
 // plane so that the 8-row x 4-word lane pattern of phase C is conflict-free.
 __device__ __forceinline__ int kword(int row, int w) { return row * 8 + (w ^ (row & 4)); }
 
-// Byte-wise minimum of four 7-bit values.
-__device__ __forceinline__ uint32_t vmin4(uint32_t a, uint32_t b) {
-    const uint32_t d = (a | 0x80808080u) - b;       // byte: a - b + 128, never borrows
-    const uint32_t ge = __byte_perm(d, 0, 0xBA98);  // byte 0xFF where a >= b
-    return (b & ge) | (a & ~ge);
-}
+// Byte-wise unsigned minimum of four codes.
+__device__ __forceinline__ uint32_t vmin4(uint32_t a, uint32_t b) { return __vminu4(a, b); }
 
 __device__ __forceinline__ uint32_t code_to_mask(uint32_t k) {
     return k == 0u ? 0u : (0xFFFFFFFFu >> (32u - k));
