@@ -272,11 +272,20 @@ struct IntegrateCfg {
 };
 static IntegrateCfg g_cfg;
 
+// Occupancy-based persistent grid for one kernel size; the shared-memory
+// limit of each template instance is raised once per device to what its
+// largest kernel size needs (the attribute belongs to the function, so it
+// must not be lowered for a smaller K).
 template <int WL>
-static int configure(size_t smem) {
-    cudaFuncSetAttribute(k_integrate<WL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static int configure(size_t smem, size_t smem_max) {
+    static int limit_set_on = -1;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
+    if (limit_set_on != dev) {
+        cudaFuncSetAttribute(k_integrate<WL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_max);
+        limit_set_on = dev;
+    }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<WL>, WPC * 32, smem);
     return max(1, sms * max(1, per_sm));
@@ -292,7 +301,8 @@ int integrate_grid_ctas(int K) {
     }
     if (!g_cfg.ctas[K]) {
         const size_t smem = integrate_smem(K);
-        g_cfg.ctas[K] = K <= 13 ? configure<4>(smem) : configure<8>(smem);
+        g_cfg.ctas[K] = K <= 13 ? configure<4>(smem, integrate_smem(13))
+                                : configure<8>(smem, integrate_smem(MAX_K));
     }
     return g_cfg.ctas[K];
 }
