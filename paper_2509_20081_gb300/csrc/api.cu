@@ -372,7 +372,7 @@ extern "C" dbt_status dbt_grid_init(const dbt_grid *g, void *stream) {
 
 // ------------------------------------------------------------------ workspace
 struct WsLayout {
-    size_t hdr, stage, prec, hkey, hidx, bcnt, boff, touched, pairs, total;
+    size_t hdr, stage, prec, hkey, hidx, bcnt, boff, touched, order, pairs, total;
     uint32_t hcap_alloc, max_touched, nbricks;
     unsigned long long pairs_cap;
 };
@@ -407,6 +407,7 @@ static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long m
     L->bcnt = o;     o += up256((size_t)nb * 4);
     L->boff = o;     o += up256((size_t)nb * 4);
     L->touched = o;  o += up256((size_t)L->max_touched * 4);
+    L->order = o;    o += up256((size_t)L->max_touched * 4);
     L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
     L->total = o;
     return DBT_OK;
@@ -462,6 +463,7 @@ static void ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels *k, l
     w->d.bcnt = (uint32_t *)(base + L.bcnt);
     w->d.boff = (uint32_t *)(base + L.boff);
     w->d.touched = (uint32_t *)(base + L.touched);
+    w->d.order = (uint32_t *)(base + L.order);
     w->d.max_touched = L.max_touched;
     w->d.pairs = (uint32_t *)(base + L.pairs);
     w->d.pairs_cap = L.pairs_cap;

@@ -83,9 +83,11 @@ struct WsHeader {
     uint32_t err;               // latched error bits of the current scan
     uint32_t n_touched;         // bricks touched by the current scan
     uint32_t pool;              // (return, brick) pairs allocated
-    uint32_t next_work;         // dynamic brick queue of the integrate kernel
-    uint32_t done_ctas;         // integrate CTAs finished
-    uint32_t pad0[3];
+    uint32_t next_work;         // dynamic queue of light bricks (one warp each)
+    uint32_t done_ctas;         // integrate warps finished
+    uint32_t n_heavy;           // bricks with more than HEAVY_PAIRS pairs (one CTA each)
+    uint32_t n_light;
+    uint32_t next_heavy;        // dynamic queue of heavy bricks
     unsigned long long acc_valid, acc_inside, acc_kept;
     unsigned long long pad1[5];
     ScanStats last;             // published by the last integrate CTA
@@ -101,11 +103,16 @@ struct WsDev {
     uint32_t hcap_alloc;        // allocated slots (power of two)
     uint32_t *bcnt;             // per brick: pair count / fill cursor (kept 0 between scans)
     uint32_t *boff;             // per brick: first pair of its segment
-    uint32_t *touched;          // list of touched bricks
+    uint32_t *touched;          // list of touched bricks (first-touch order)
+    uint32_t *order;            // touched bricks, heavy ones first
     uint32_t max_touched;
     uint32_t *pairs;            // pair payloads grouped by brick
     unsigned long long pairs_cap;
 };
+
+// Bricks with more (return, brick) pairs than this are integrated by a whole
+// CTA (its warps split the pairs); the others by a single warp.
+constexpr uint32_t HEAVY_PAIRS = 48;
 
 // Return-record flags in prec.w above the 16-bit bin.
 constexpr int PREC_DUP = 1 << 30;

@@ -1,32 +1,34 @@
 // Brick integration of one scan (Sec. III-C, Eqs. 4-6).
 //
-// Persistent CTAs of WPC warps; each warp takes touched bricks (32 x 8 x 8
-// voxels) from a dynamic queue and owns its brick alone, so no two threads
-// of different warps ever touch the same voxel and no atomics are needed.
-//
 // Distance codes.  A mask of the form 2^k - 1 is stored as k = popcount; the
 // Eq. 4 AND of two such masks is the mask of min(k).  Grid masks start all
 // ones (Sec. III-A) and only ever meet Eq. 3 masks, so they keep this form
-// (checked on load; a violation latches ERR_MASK_FORM).  Staged bricks hold
-// 8-bit codes, four voxels per 32-bit word, and the AND of four voxels is
-// one byte-wise minimum.
+// (checked on load; a violation latches ERR_MASK_FORM).  A staged brick holds
+// 8-bit codes, four voxels per 32-bit word, and the AND of four voxels is one
+// byte-wise minimum.
 //
 // Kernel rows.  For a row of the K^3 kernel at squared lateral offset
-// q = oy^2 + oz^2, the codes along x are ceil(sqrt(ox^2 + q)).  The host
-// builds P[q][s]: the four codes a 4-voxel word receives when its first
-// voxel sits at ox = s - 3 - R (32 = no change outside the kernel).  One
-// word update is then a table load, a load of the staged word, a byte-wise
-// min and a conditional store.
+// q = oy^2 + oz^2 the codes along x are ceil(sqrt(ox^2 + q)).  The host builds
+// P[q][s]: the four codes a 4-voxel word receives when its first voxel sits
+// at ox = s - 3 - R (32, no change, outside the kernel).  A word update is a
+// table load, a staged-word load, a byte-wise min and a conditional store.
 //
-// Per brick the warp
-//   A. ORs, per brick row, the 16-byte chunks any return's kernel covers,
-//   B. stages those chunks as codes (and zeroes per-voxel shadow counts),
-//   C. applies every (return, brick) pair: one warp iteration per kernel
-//      plane (lanes = 8 rows x 4 words), then the bin's shadow offsets
-//      that fall in the brick (counts, Eq. 5),
-//   D. writes back the chunks whose codes changed as masks, and for chunks
-//      with shadow counts c updates h' = min(h + c, H_max), sign 0 when
-//      h < T <= h' (Eq. 6).
+// Work split.  Persistent CTAs of WPC warps.  Bricks (32 x 8 x 8 voxels)
+// with more than HEAVY_PAIRS (return, brick) pairs are taken first, one per
+// CTA: each warp applies a share of the pairs to its own staged copy and the
+// copies are merged (byte-wise min of codes, sum of counts).  The other
+// bricks are taken one per warp.  A brick is only ever written by the CTA or
+// warp that took it, so no atomics touch the grid.
+//
+// Per brick:
+//   A. the 16-byte chunks of each brick row that any pair's kernel covers
+//      (lanes take one pair each and OR-reduce 64-bit row masks per chunk),
+//   B. those chunks staged as codes; shadow counts zeroed,
+//   C. every pair applied (lanes = 8 rows x 4 planes, each lane updating the
+//      up to NW words of its kernel row), then the bin's shadow offsets that
+//      fall in the brick counted (Eq. 5),
+//   D. chunks whose codes changed written back as masks; for chunks with
+//      shadow counts c: h' = min(h + c, H_max), sign 0 when h < T <= h' (Eq. 6).
 // AND is commutative and the saturating count with a threshold crossing
 // depends only on the total count, so D gives exactly the state of applying
 // the returns one by one in scan order (the first-return rule is resolved
@@ -35,201 +37,334 @@
 
 namespace dbt {
 
-constexpr int WPC = 8;  // warps per CTA
+constexpr int WPC = 8;            // warps per CTA
+constexpr int NTHR = WPC * 32;
 
 struct WarpArea {
-    uint32_t kst[BROWS * 8];  // codes: word kword(row, w) holds voxels x = 4w .. 4w+3 of a row
-    uint16_t cnt[BVOX];       // shadow counts, index row * 32 + x
-    uint8_t dirty[BROWS * 8]; // word changed (same index as kst)
-    uint8_t need[BROWS];      // covered chunks of each row (bit w)
+    uint32_t kst[BROWS * 8];      // codes: word kword(row, w) = voxels 4w .. 4w+3 of a row
+    uint16_t cnt[BVOX];           // shadow counts, index row * 32 + x
+    uint8_t dirty[BROWS * 8];     // word changed (index as kst)
+    uint32_t need[BROWS];         // covered chunks of each row (bit w)
 };
 static_assert(sizeof(WarpArea) % 16 == 0, "warp area alignment");
 
-// Word w of brick row `row`, with bit 2 of w flipped on rows 4-7 of each
-// plane so that the 8-row x 4-word lane pattern of phase C is conflict-free.
-__device__ __forceinline__ int kword(int row, int w) { return row * 8 + (w ^ (row & 4)); }
+// Word w of brick row `row` (row = z * 8 + y).  The XOR with bits 2..4 of the
+// row spreads both access patterns over all 32 banks: phase C (8 rows x 4
+// consecutive planes, same w) and phases B/D (4 consecutive rows x 8 words).
+__device__ __forceinline__ int kword(int row, int w) { return row * 8 + (w ^ ((row >> 2) & 7)); }
 
-// Byte-wise unsigned minimum of four codes.
 __device__ __forceinline__ uint32_t vmin4(uint32_t a, uint32_t b) { return __vminu4(a, b); }
 
 __device__ __forceinline__ uint32_t code_to_mask(uint32_t k) {
     return k == 0u ? 0u : (0xFFFFFFFFu >> (32u - k));
 }
 
-template <int WL>
-__global__ void __launch_bounds__(WPC * 32) k_integrate(DevGrid g, DevParams p, DevTables t,
-                                                        long long n_input, WsDev ws) {
+struct PairBox {
+    int cx, cy, cz;               // contact relative to the brick corner
+    int x0, x1, y0, y1, z0, z1;   // kernel box clipped to the brick
+};
+
+__device__ __forceinline__ PairBox decode_pair(uint32_t pl, int R) {
+    PairBox b;
+    b.cx = (int)(pl & 63u) - R;
+    b.cy = (int)((pl >> 6) & 31u) - R;
+    b.cz = (int)((pl >> 11) & 31u) - R;
+    b.x0 = max(b.cx - R, 0);
+    b.x1 = min(b.cx + R, BX - 1);
+    b.y0 = max(b.cy - R, 0);
+    b.y1 = min(b.cy + R, BY - 1);
+    b.z0 = max(b.cz - R, 0);
+    b.z1 = min(b.cz + R, BZ - 1);
+    return b;
+}
+
+// Phase A for pairs[j] with j = first + lane + step k, j < len: cr[c] gets
+// bit `row` set when some pair's kernel covers chunk c of that brick row.
+__device__ __forceinline__ void coverage(const uint32_t *pairs, uint32_t first, uint32_t len,
+                                         uint32_t step, int R, int lane,
+                                         unsigned long long cr[CHUNKS_PER_ROW]) {
+    for (uint32_t base = first; base < len; base += step) {
+        const uint32_t j = base + lane;
+        unsigned long long rows = 0ull;
+        uint32_t cm = 0;
+        if (j < len) {
+            const PairBox b = decode_pair(__ldg(pairs + j), R);
+            const unsigned long long ybits =
+                (unsigned long long)((0xFFu >> (7 - (b.y1 - b.y0))) << b.y0);
+            const unsigned long long zspread =
+                (0x0101010101010101ull >> (8 * (7 - (b.z1 - b.z0)))) << (8 * b.z0);
+            rows = ybits * zspread;
+            cm = (0xFFu >> (7 - (b.x1 >> 2))) & (0xFFu << (b.x0 >> 2));
+        }
+#pragma unroll
+        for (int c = 0; c < CHUNKS_PER_ROW; ++c) {
+            const unsigned long long v = ((cm >> c) & 1u) ? rows : 0ull;
+            const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)v);
+            const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(v >> 32));
+            cr[c] |= ((unsigned long long)hi << 32) | lo;
+        }
+    }
+}
+
+// Phase C for one pair on a warp's staged copy.
+template <int NW>
+__device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint32_t *P,
+                                           const DevTables &t, int R, int W, int SR, int lane) {
+    const PairBox b = decode_pair(pl, R);
+    const int ry = lane & 7, zs = lane >> 3;
+    const int w0 = b.x0 >> 2;
+    const int nw = (b.x1 >> 2) - w0;
+    const int s0 = 4 * w0 - b.cx + R + 3;
+    const bool iny = ry >= b.y0 && ry <= b.y1;
+    const int oy = ry - b.cy;
+    const int oysq = oy * oy;
+    for (int rzb = b.z0; rzb <= b.z1; rzb += 4) {
+        const int rz = rzb + zs;
+        if (iny && rz <= b.z1) {
+            const int oz = rz - b.cz;
+            const int pb = (oysq + oz * oz) * W + s0;
+            const int row = rz * BY + ry;
+            const int rbase = row * 8, f = (row >> 2) & 7;
+#pragma unroll
+            for (int j = 0; j < NW; ++j) {
+                if (j <= nw) {
+                    const uint32_t kwd = P[pb + 4 * j];
+                    const int addr = rbase + ((w0 + j) ^ f);
+                    const uint32_t a = wa->kst[addr];
+                    const uint32_t nv = vmin4(a, kwd);
+                    if (nv != a) {
+                        wa->kst[addr] = nv;
+                        wa->dirty[addr] = 1;
+                    }
+                }
+            }
+        }
+    }
+    if (b.cx >= -SR && b.cx <= BX - 1 + SR && b.cy >= -SR && b.cy <= BY - 1 + SR &&
+        b.cz >= -SR && b.cz <= BZ - 1 + SR) {
+        const uint32_t bin = pl >> 16;
+        const uint32_t s1 = __ldg(&t.sh_start[bin + 1]);
+        for (uint32_t e = __ldg(&t.sh_start[bin]) + lane; e < s1; e += 32) {
+            const uint32_t o = __ldg(&t.sh_off[e]);
+            const int vx = b.cx + (int)(o & 255u) - 128;
+            const int vy = b.cy + (int)((o >> 8) & 255u) - 128;
+            const int vz = b.cz + (int)((o >> 16) & 255u) - 128;
+            if ((unsigned)vx < (unsigned)BX && (unsigned)vy < (unsigned)BY &&
+                (unsigned)vz < (unsigned)BZ)
+                wa->cnt[(vz * BY + vy) * BX + vx] += 1;   // distinct voxels within one pair
+        }
+    }
+}
+
+__device__ __forceinline__ size_t chunk_index(const DevGrid &g, int bx, int by, int bz, int row,
+                                              int ch) {
+    const int gy = by * BY + (row & (BY - 1)), gz = bz * BZ + row / BY;
+    return ((size_t)gz * g.ny + gy) * g.pitch + (size_t)bx * BX + ch * 4;
+}
+
+__device__ __forceinline__ uint32_t load_codes(const DevGrid &g, size_t gi, uint32_t &form_bad) {
+    const uint4 m = __ldcg(reinterpret_cast<const uint4 *>(g.mask + gi));
+    form_bad |= (m.x & (m.x + 1u)) | (m.y & (m.y + 1u)) | (m.z & (m.z + 1u)) | (m.w & (m.w + 1u));
+    return (uint32_t)__popc(m.x) | ((uint32_t)__popc(m.y) << 8) | ((uint32_t)__popc(m.z) << 16) |
+           ((uint32_t)__popc(m.w) << 24);
+}
+
+// Phase D for one chunk: codes k (changed when dirty) and packed counts c.
+__device__ __forceinline__ void store_chunk(const DevGrid &g, size_t gi, uint32_t k, bool dirty,
+                                            uint2 c, uint32_t T, uint32_t Hmax) {
+    if (dirty) {
+        const uint4 m = make_uint4(code_to_mask(k & 255u), code_to_mask((k >> 8) & 255u),
+                                   code_to_mask((k >> 16) & 255u), code_to_mask(k >> 24));
+        __stcg(reinterpret_cast<uint4 *>(g.mask + gi), m);
+    }
+    if (c.x | c.y) {
+        uint2 hv = __ldcg(reinterpret_cast<const uint2 *>(g.hits + gi));
+        uint32_t sv = __ldcg(reinterpret_cast<const unsigned int *>(g.sign + gi));
+        const uint32_t cnt4[4] = {c.x & 0xFFFFu, c.x >> 16, c.y & 0xFFFFu, c.y >> 16};
+        uint32_t h[4] = {hv.x & 0xFFFFu, hv.x >> 16, hv.y & 0xFFFFu, hv.y >> 16};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t hn = min(h[e] + cnt4[e], Hmax);
+            if (cnt4[e] && h[e] < T && hn >= T) sv &= ~(0xFFu << (8 * e));
+            if (cnt4[e]) h[e] = hn;
+        }
+        hv.x = h[0] | (h[1] << 16);
+        hv.y = h[2] | (h[3] << 16);
+        __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv);
+        __stcg(reinterpret_cast<unsigned int *>(g.sign + gi), sv);
+    }
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g, DevParams p, DevTables t,
+                                                    long long n_input, WsDev ws) {
     extern __shared__ __align__(16) uint32_t smem[];
-    constexpr int LY = 32 / WL;  // rows per lane group
+    __shared__ uint32_t s_item;
+    __shared__ unsigned long long s_cr[CHUNKS_PER_ROW];
     const int R = p.R;
     const int W = 2 * R + 4;
     const int np = (2 * R * R + 1) * W;
     uint32_t *P = smem;
-    for (int j = threadIdx.x; j < np; j += blockDim.x) P[j] = t.prow[j];
-    WarpArea *wa = reinterpret_cast<WarpArea *>(smem + ((np + 3) & ~3)) + (threadIdx.x >> 5);
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31;
+    for (int j = threadIdx.x; j < np; j += NTHR) P[j] = t.prow[j];
+    WarpArea *areas = reinterpret_cast<WarpArea *>(smem + ((np + 3) & ~3));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    WarpArea *wa = areas + warp;
     const uint32_t nt = min(*(volatile uint32_t *)&ws.hdr->n_touched, ws.max_touched);
+    const uint32_t nheavy = min(*(volatile uint32_t *)&ws.hdr->n_heavy, nt);
     const int SR = p.sr;
     const uint32_t T = (uint32_t)p.T, Hmax = (uint32_t)p.Hmax;
+    uint32_t form_bad = 0;
 
+    // ---------------- heavy bricks: one CTA each
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(&ws.hdr->next_heavy, 1u);
+        if (tid < CHUNKS_PER_ROW) s_cr[tid] = 0ull;
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= nheavy) break;
+        const uint32_t b = ws.order[it];
+        const uint32_t start = ws.boff[b];
+        uint32_t len = ws.bcnt[b];
+        if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing
+        const int bx = (int)(b % (uint32_t)g.nbx);
+        const uint32_t byz = b / (uint32_t)g.nbx;
+        const int by = (int)(byz % (uint32_t)g.nby), bz = (int)(byz / (uint32_t)g.nby);
+        const uint32_t *pairs = ws.pairs + start;
+
+        // A
+        unsigned long long cr[CHUNKS_PER_ROW];
+#pragma unroll
+        for (int c = 0; c < CHUNKS_PER_ROW; ++c) cr[c] = 0ull;
+        coverage(pairs, 32u * warp, len, 32u * WPC, R, lane, cr);
+        if (lane < CHUNKS_PER_ROW) {
+            unsigned long long mine = 0ull;
+#pragma unroll
+            for (int c = 0; c < CHUNKS_PER_ROW; ++c)
+                if (c == lane) mine = cr[c];
+            atomicOr(&s_cr[lane], mine);
+        }
+        __syncthreads();
+        uint32_t *need = areas[0].need;
+        if (tid < BROWS) {
+            uint32_t nb = 0;
+#pragma unroll
+            for (int c = 0; c < CHUNKS_PER_ROW; ++c) nb |= (uint32_t)((s_cr[c] >> tid) & 1ull) << c;
+            need[tid] = nb;
+        }
+        __syncthreads();
+        // B: stage into every warp's copy
+        for (int c = tid; c < BCHUNKS; c += NTHR) {
+            const int row = c >> 3, ch = c & 7;
+            if ((need[row] >> ch) & 1u) {
+                const uint32_t k = load_codes(g, chunk_index(g, bx, by, bz, row, ch), form_bad);
+                const int wd = kword(row, ch);
+#pragma unroll
+                for (int v = 0; v < WPC; ++v) {
+                    areas[v].kst[wd] = k;
+                    areas[v].dirty[wd] = 0;
+                    *reinterpret_cast<uint2 *>(&areas[v].cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
+                }
+            }
+        }
+        __syncthreads();
+        // C: warp w applies pairs w * 32 + 256 k + lane-broadcast order
+        for (uint32_t base = 32u * warp; base < len; base += 32u * WPC) {
+            const uint32_t mine = base + lane < len ? __ldg(pairs + base + lane) : 0u;
+            const int cnt = (int)min(32u, len - base);
+            for (int j = 0; j < cnt; ++j) {
+                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, t, R, W, SR, lane);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // D: merge the copies and write back
+        for (int c = tid; c < BCHUNKS; c += NTHR) {
+            const int row = c >> 3, ch = c & 7;
+            if ((need[row] >> ch) & 1u) {
+                const int wd = kword(row, ch);
+                uint32_t k = areas[0].kst[wd];
+                uint32_t dirty = areas[0].dirty[wd];
+                uint2 cs = *reinterpret_cast<const uint2 *>(&areas[0].cnt[row * 32 + ch * 4]);
+#pragma unroll
+                for (int v = 1; v < WPC; ++v) {
+                    k = vmin4(k, areas[v].kst[wd]);
+                    dirty |= areas[v].dirty[wd];
+                    const uint2 cv = *reinterpret_cast<const uint2 *>(&areas[v].cnt[row * 32 + ch * 4]);
+                    cs.x += cv.x;   // packed 16-bit counts: a voxel's total fits 16 bits
+                    cs.y += cv.y;
+                }
+                store_chunk(g, chunk_index(g, bx, by, bz, row, ch), k, dirty != 0, cs, T, Hmax);
+            }
+        }
+        if (tid == 0) ws.bcnt[b] = 0u;
+    }
+
+    // ---------------- light bricks: one warp each
     for (;;) {
         uint32_t w = 0;
         if (lane == 0) w = atomicAdd(&ws.hdr->next_work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        if (w >= nt) break;
-        const uint32_t b = ws.touched[w];
+        if (nheavy + w >= nt) break;
+        const uint32_t b = ws.order[nheavy + w];
         const uint32_t start = ws.boff[b];
         uint32_t len = ws.bcnt[b];
-        if ((unsigned long long)start + len > ws.pairs_cap) {  // cannot happen by sizing
-            if (lane == 0) atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
-            len = 0;
-        }
+        if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing
         const int bx = (int)(b % (uint32_t)g.nbx);
         const uint32_t byz = b / (uint32_t)g.nbx;
-        const int by = (int)(byz % (uint32_t)g.nby);
-        const int bz = (int)(byz / (uint32_t)g.nby);
+        const int by = (int)(byz % (uint32_t)g.nby), bz = (int)(byz / (uint32_t)g.nby);
         const uint32_t *pairs = ws.pairs + start;
 
-        // ---- A: covered chunks; lane owns rows `lane` and `lane + 32`
+        // A
+        unsigned long long cr[CHUNKS_PER_ROW];
+#pragma unroll
+        for (int c = 0; c < CHUNKS_PER_ROW; ++c) cr[c] = 0ull;
+        coverage(pairs, 0u, len, 32u, R, lane, cr);
         {
-            uint32_t need0 = 0, need1 = 0;
-            const int ry = lane & 7, rz0 = lane >> 3, rz1 = rz0 + 4;
-            for (uint32_t base = 0; base < len; base += 32) {
-                const uint32_t mine = base + lane < len ? __ldg(pairs + base + lane) : 0u;
-                const int cnt = (int)min(32u, len - base);
-                for (int j = 0; j < cnt; ++j) {
-                    const uint32_t pl = __shfl_sync(0xffffffffu, mine, j);
-                    const int cx = (int)(pl & 63u) - R;
-                    const int cy = (int)((pl >> 6) & 31u) - R;
-                    const int cz = (int)((pl >> 11) & 31u) - R;
-                    const int x0 = max(cx - R, 0), x1 = min(cx + R, BX - 1);
-                    const uint32_t cm = (0xFFu >> (7 - (x1 >> 2))) & (0xFFu << (x0 >> 2));
-                    const bool iny = ry >= cy - R && ry <= cy + R;
-                    if (iny && rz0 >= cz - R && rz0 <= cz + R) need0 |= cm;
-                    if (iny && rz1 >= cz - R && rz1 <= cz + R) need1 |= cm;
-                }
+            uint32_t n0 = 0, n1 = 0;
+#pragma unroll
+            for (int c = 0; c < CHUNKS_PER_ROW; ++c) {
+                n0 |= (uint32_t)((cr[c] >> lane) & 1ull) << c;
+                n1 |= (uint32_t)((cr[c] >> (lane + 32)) & 1ull) << c;
             }
-            wa->need[lane] = (uint8_t)need0;
-            wa->need[lane + 32] = (uint8_t)need1;
+            wa->need[lane] = n0;
+            wa->need[lane + 32] = n1;
         }
         __syncwarp();
-
-        // ---- B: stage covered chunks as codes; lanes = 4 rows x 8 chunks
+        // B: lanes = 4 rows x 8 chunks
         const int rs = lane >> 3, ch = lane & 7;
-        uint32_t form_bad = 0;
-#pragma unroll 4
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < BROWS / 4; ++i) {
             const int row = rs + 4 * i;
             if ((wa->need[row] >> ch) & 1u) {
-                const int gy = by * BY + (row & 7), gz = bz * BZ + (row >> 3);
-                const size_t gi = ((size_t)gz * g.ny + gy) * g.pitch + (size_t)bx * BX + ch * 4;
-                const uint4 m = __ldcg(reinterpret_cast<const uint4 *>(g.mask + gi));
-                form_bad |= (m.x & (m.x + 1u)) | (m.y & (m.y + 1u)) | (m.z & (m.z + 1u)) |
-                            (m.w & (m.w + 1u));
-                const uint32_t k = (uint32_t)__popc(m.x) | ((uint32_t)__popc(m.y) << 8) |
-                                   ((uint32_t)__popc(m.z) << 16) | ((uint32_t)__popc(m.w) << 24);
-                wa->kst[kword(row, ch)] = k;
-                wa->dirty[kword(row, ch)] = 0;
+                const int wd = kword(row, ch);
+                wa->kst[wd] = load_codes(g, chunk_index(g, bx, by, bz, row, ch), form_bad);
+                wa->dirty[wd] = 0;
                 *reinterpret_cast<uint2 *>(&wa->cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
             }
         }
-        if (form_bad) atomicOr(&ws.hdr->err, ERR_MASK_FORM);
         __syncwarp();
-
-        // ---- C: Eqs. 4-5 on the staged brick
-        const int ly = lane / WL, lw = lane % WL;
+        // C
         for (uint32_t base = 0; base < len; base += 32) {
             const uint32_t mine = base + lane < len ? __ldg(pairs + base + lane) : 0u;
             const int cnt = (int)min(32u, len - base);
             for (int j = 0; j < cnt; ++j) {
-                const uint32_t pl = __shfl_sync(0xffffffffu, mine, j);
-                const int cx = (int)(pl & 63u) - R;
-                const int cy = (int)((pl >> 6) & 31u) - R;
-                const int cz = (int)((pl >> 11) & 31u) - R;
-                const int x0 = max(cx - R, 0), x1 = min(cx + R, BX - 1);
-                const int y0 = max(cy - R, 0), y1 = min(cy + R, BY - 1);
-                const int z0 = max(cz - R, 0), z1 = min(cz + R, BZ - 1);
-                const int wv = (x0 >> 2) + lw;
-                const bool actw = wv <= (x1 >> 2);
-                const int s = 4 * wv - cx + R + 3;
-                for (int yb = y0; yb <= y1; yb += LY) {
-                    const int ry = yb + ly;
-                    const bool act = actw && ry <= y1;
-                    const int oy = ry - cy;
-                    const int pidx = oy * oy * W + s;
-                    const int addr = ry * 8 + (wv ^ (ry & 4));
-                    for (int rz = z0; rz <= z1; ++rz) {
-                        const int oz = rz - cz;
-                        if (act) {
-                            const uint32_t kw = P[pidx + oz * oz * W];
-                            uint32_t *cell = &wa->kst[rz * 64 + addr];
-                            const uint32_t a = *cell;
-                            const uint32_t nv = vmin4(a, kw);
-                            if (nv != a) {
-                                *cell = nv;
-                                wa->dirty[rz * 64 + addr] = 1;
-                            }
-                        }
-                    }
-                }
-                if (cx >= -SR && cx <= BX - 1 + SR && cy >= -SR && cy <= BY - 1 + SR &&
-                    cz >= -SR && cz <= BZ - 1 + SR) {
-                    const uint32_t bin = pl >> 16;
-                    const uint32_t s1 = __ldg(&t.sh_start[bin + 1]);
-                    for (uint32_t e = __ldg(&t.sh_start[bin]) + lane; e < s1; e += 32) {
-                        const uint32_t o = __ldg(&t.sh_off[e]);
-                        const int vx = cx + (int)(o & 255u) - 128;
-                        const int vy = cy + (int)((o >> 8) & 255u) - 128;
-                        const int vz = cz + (int)((o >> 16) & 255u) - 128;
-                        if ((unsigned)vx < (unsigned)BX && (unsigned)vy < (unsigned)BY &&
-                            (unsigned)vz < (unsigned)BZ)
-                            wa->cnt[(vz * BY + vy) * BX + vx] += 1;
-                    }
-                }
+                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, t, R, W, SR, lane);
                 __syncwarp();
             }
         }
-
-        // ---- D: write back
-#pragma unroll 4
-        for (int i = 0; i < 16; ++i) {
+        // D
+        for (int i = 0; i < BROWS / 4; ++i) {
             const int row = rs + 4 * i;
             if ((wa->need[row] >> ch) & 1u) {
-                const int gy = by * BY + (row & 7), gz = bz * BZ + (row >> 3);
-                const size_t gi = ((size_t)gz * g.ny + gy) * g.pitch + (size_t)bx * BX + ch * 4;
-                if (wa->dirty[kword(row, ch)]) {
-                    const uint32_t k = wa->kst[kword(row, ch)];
-                    const uint4 m = make_uint4(code_to_mask(k & 255u), code_to_mask((k >> 8) & 255u),
-                                               code_to_mask((k >> 16) & 255u), code_to_mask(k >> 24));
-                    __stcg(reinterpret_cast<uint4 *>(g.mask + gi), m);
-                }
-                const uint2 c = *reinterpret_cast<const uint2 *>(&wa->cnt[row * 32 + ch * 4]);
-                if (c.x | c.y) {
-                    uint2 hv = __ldcg(reinterpret_cast<const uint2 *>(g.hits + gi));
-                    uint32_t sv = __ldcg(reinterpret_cast<const unsigned int *>(g.sign + gi));
-                    const uint32_t cnt4[4] = {c.x & 0xFFFFu, c.x >> 16, c.y & 0xFFFFu, c.y >> 16};
-                    uint32_t h[4] = {hv.x & 0xFFFFu, hv.x >> 16, hv.y & 0xFFFFu, hv.y >> 16};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (cnt4[e]) {
-                            const uint32_t ho = h[e];
-                            const uint32_t hn = min(ho + cnt4[e], Hmax);
-                            if (ho < T && hn >= T) sv &= ~(0xFFu << (8 * e));
-                            h[e] = hn;
-                        }
-                    }
-                    hv.x = h[0] | (h[1] << 16);
-                    hv.y = h[2] | (h[3] << 16);
-                    __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv);
-                    __stcg(reinterpret_cast<unsigned int *>(g.sign + gi), sv);
-                }
+                const int wd = kword(row, ch);
+                store_chunk(g, chunk_index(g, bx, by, bz, row, ch), wa->kst[wd], wa->dirty[wd] != 0,
+                            *reinterpret_cast<const uint2 *>(&wa->cnt[row * 32 + ch * 4]), T, Hmax);
             }
         }
         if (lane == 0) ws.bcnt[b] = 0u;
         __syncwarp();
     }
+    if (form_bad) atomicOr(&ws.hdr->err, ERR_MASK_FORM);
 
     // Last warp out publishes the scan's counters and re-arms the workspace.
     if (lane == 0) {
@@ -250,6 +385,9 @@ __global__ void __launch_bounds__(WPC * 32) k_integrate(DevGrid g, DevParams p, 
             h->n_touched = 0u;
             h->pool = 0u;
             h->next_work = 0u;
+            h->n_heavy = 0u;
+            h->n_light = 0u;
+            h->next_heavy = 0u;
             h->acc_valid = 0ull;
             h->acc_inside = 0ull;
             h->acc_kept = 0ull;
@@ -276,20 +414,23 @@ static IntegrateCfg g_cfg;
 // limit of each template instance is raised once per device to what its
 // largest kernel size needs (the attribute belongs to the function, so it
 // must not be lowered for a smaller K).
-template <int WL>
+template <int NW>
 static int configure(size_t smem, size_t smem_max) {
     static int limit_set_on = -1;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     if (limit_set_on != dev) {
-        cudaFuncSetAttribute(k_integrate<WL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_integrate<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_max);
         limit_set_on = dev;
     }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<WL>, WPC * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<NW>, NTHR, smem);
     return max(1, sms * max(1, per_sm));
 }
+
+// Words of a kernel row: an x-extent of K voxels starting anywhere in a word.
+static int words_per_row(int K) { return K <= 13 ? 4 : 6; }
 
 // Persistent grid for kernel size K: every SM filled to its occupancy limit.
 int integrate_grid_ctas(int K) {
@@ -301,8 +442,8 @@ int integrate_grid_ctas(int K) {
     }
     if (!g_cfg.ctas[K]) {
         const size_t smem = integrate_smem(K);
-        g_cfg.ctas[K] = K <= 13 ? configure<4>(smem, integrate_smem(13))
-                                : configure<8>(smem, integrate_smem(MAX_K));
+        g_cfg.ctas[K] = words_per_row(K) == 4 ? configure<4>(smem, integrate_smem(13))
+                                              : configure<6>(smem, integrate_smem(MAX_K));
     }
     return g_cfg.ctas[K];
 }
@@ -310,10 +451,10 @@ int integrate_grid_ctas(int K) {
 void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, long long n_input,
                       const WsDev &ws, int grid_ctas, cudaStream_t s) {
     const size_t smem = integrate_smem(p.K);
-    if (p.K <= 13)
-        k_integrate<4><<<grid_ctas, WPC * 32, smem, s>>>(g, p, t, n_input, ws);
+    if (words_per_row(p.K) == 4)
+        k_integrate<4><<<grid_ctas, NTHR, smem, s>>>(g, p, t, n_input, ws);
     else
-        k_integrate<8><<<grid_ctas, WPC * 32, smem, s>>>(g, p, t, n_input, ws);
+        k_integrate<6><<<grid_ctas, NTHR, smem, s>>>(g, p, t, n_input, ws);
 }
 
 }  // namespace dbt
