@@ -268,10 +268,11 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g, DevParams p, DevT
             }
         }
         __syncthreads();
-        // C: warp w applies pairs w * 32 + 256 k + lane-broadcast order
-        for (uint32_t base = 32u * warp; base < len; base += 32u * WPC) {
-            const uint32_t mine = base + lane < len ? __ldg(pairs + base + lane) : 0u;
-            const int cnt = (int)min(32u, len - base);
+        // C: warp w applies pairs w, w + WPC, w + 2 WPC, ...
+        for (uint32_t base = 0; base * WPC + warp < len; base += 32) {
+            const uint32_t jj = (base + lane) * WPC + warp;
+            const uint32_t mine = jj < len ? __ldg(pairs + jj) : 0u;
+            const int cnt = (int)min(32u, (len - warp + WPC - 1) / WPC - base);
             for (int j = 0; j < cnt; ++j) {
                 apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, t, R, W, SR, lane);
                 __syncwarp();
