@@ -282,6 +282,8 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
     k->dp.dedup = p->dedup_first;
     k->dp.n_m2 = (int)n_m2;
     k->dp.sr = std::min(R, (int)std::floor(p->shadow_radius));
+    k->dp.n_sh = (int)k->sh_off.size();
+    k->dp.sh_smem = shadow_in_smem(nbins, k->dp.n_sh) ? 1 : 0;
     k->dt.m2 = (const uint32_t *)(base + off_m2);
     k->dt.sh_off = (const uint32_t *)(base + off_sh);
     k->dt.sh_start = (const uint32_t *)(base + off_st);
@@ -544,7 +546,7 @@ static dbt_status enqueue_scan(const dbt_grid *g, const dbt_kernels *k, dbt_work
     launch_alloc(ws->d, 2 * 152, s);
     launch_fill(dg, k->dp, ni, ws->d, hcap, s);
     if (ws->ev_begin) DBT_CUDA(cudaEventRecord(ws->ev_begin, s));
-    launch_integrate(dg, k->dp, k->dt, (long long)n, ws->d, integrate_grid_ctas(k->dp.K), s);
+    launch_integrate(dg, k->dp, k->dt, (long long)n, ws->d, integrate_grid_ctas(k->dp), s);
     if (ws->ev_end) DBT_CUDA(cudaEventRecord(ws->ev_end, s));
     DBT_CUDA(cudaGetLastError());
     return DBT_OK;

@@ -44,7 +44,16 @@ struct DevParams {
     int dedup;
     int n_m2;         // entries of the mask-by-r^2 table
     int sr;           // min(R, floor(r_s)): no shadow offset exceeds it on any axis
+    int n_sh;         // shadow offsets over all bins
+    int sh_smem;      // 1: the integrate kernel stages the shadow table in shared memory
 };
+
+// Shadow tables up to this many words (offsets + starts) are staged in
+// shared memory by the integrate kernel.
+constexpr int SHADOW_SMEM_WORDS = 4608;
+__host__ __device__ inline bool shadow_in_smem(int nbins, int n_sh) {
+    return ((nbins + 1 + 3) & ~3) + n_sh <= SHADOW_SMEM_WORDS;
+}
 
 struct DevTables {
     const uint32_t *m2;        // Eq. 3 mask as a function of r^2 = |o|^2
@@ -127,7 +136,7 @@ void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, u
                  cudaStream_t s);
 void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, long long n_input,
                       const WsDev &ws, int grid_ctas, cudaStream_t s);
-int integrate_grid_ctas(int K);
+int integrate_grid_ctas(const DevParams &p);
 void launch_footprint(const DevGrid &g, const DevParams &p, const DevTables &t, int n,
                       const WsDev &ws, uint32_t hcap, uint32_t *bits_u, uint32_t *bits_s,
                       unsigned long long *counts, cudaStream_t s);

@@ -106,36 +106,39 @@ __device__ __forceinline__ void coverage(const uint32_t *pairs, uint32_t first, 
     }
 }
 
-// Phase C for one pair on a warp's staged copy.
+// Phase C for one pair on a warp's staged copy.  The box's wy x wz kernel
+// rows are spread over the lanes (row r -> z = r / wy, y = r % wy, the
+// division by wy <= 8 done exactly as (r * ceil(256 / wy)) >> 8 for r < 64);
+// each lane updates the up to NW words of its row.  sh / shs: the per-bin
+// shadow offsets and their starts (shared or global memory).
 template <int NW>
 __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint32_t *P,
-                                           const DevTables &t, int R, int W, int SR, int lane) {
+                                           const uint32_t *sh, const uint32_t *shs, int R, int W,
+                                           int SR, int lane) {
     const PairBox b = decode_pair(pl, R);
-    const int ry = lane & 7, zs = lane >> 3;
+    const int wy = b.y1 - b.y0 + 1;
+    const int nrows = wy * (b.z1 - b.z0 + 1);
+    const int magic = (256 + wy - 1) / wy;
     const int w0 = b.x0 >> 2;
     const int nw = (b.x1 >> 2) - w0;
     const int s0 = 4 * w0 - b.cx + R + 3;
-    const bool iny = ry >= b.y0 && ry <= b.y1;
-    const int oy = ry - b.cy;
-    const int oysq = oy * oy;
-    for (int rzb = b.z0; rzb <= b.z1; rzb += 4) {
-        const int rz = rzb + zs;
-        if (iny && rz <= b.z1) {
-            const int oz = rz - b.cz;
-            const int pb = (oysq + oz * oz) * W + s0;
-            const int row = rz * BY + ry;
-            const int rbase = row * 8, f = (row >> 2) & 7;
+    for (int r = lane; r < nrows; r += 32) {
+        const int qz = (r * magic) >> 8;
+        const int ry = b.y0 + (r - qz * wy), rz = b.z0 + qz;
+        const int oy = ry - b.cy, oz = rz - b.cz;
+        const int pb = (oy * oy + oz * oz) * W + s0;
+        const int row = rz * BY + ry;
+        const int rbase = row * 8, f = (row >> 2) & 7;
 #pragma unroll
-            for (int j = 0; j < NW; ++j) {
-                if (j <= nw) {
-                    const uint32_t kwd = P[pb + 4 * j];
-                    const int addr = rbase + ((w0 + j) ^ f);
-                    const uint32_t a = wa->kst[addr];
-                    const uint32_t nv = vmin4(a, kwd);
-                    if (nv != a) {
-                        wa->kst[addr] = nv;
-                        wa->dirty[addr] = 1;
-                    }
+        for (int j = 0; j < NW; ++j) {
+            if (j <= nw) {
+                const uint32_t kwd = P[pb + 4 * j];
+                const int addr = rbase + ((w0 + j) ^ f);
+                const uint32_t a = wa->kst[addr];
+                const uint32_t nv = vmin4(a, kwd);
+                if (nv != a) {
+                    wa->kst[addr] = nv;
+                    wa->dirty[addr] = 1;
                 }
             }
         }
@@ -143,15 +146,23 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
     if (b.cx >= -SR && b.cx <= BX - 1 + SR && b.cy >= -SR && b.cy <= BY - 1 + SR &&
         b.cz >= -SR && b.cz <= BZ - 1 + SR) {
         const uint32_t bin = pl >> 16;
-        const uint32_t s1 = __ldg(&t.sh_start[bin + 1]);
-        for (uint32_t e = __ldg(&t.sh_start[bin]) + lane; e < s1; e += 32) {
-            const uint32_t o = __ldg(&t.sh_off[e]);
-            const int vx = b.cx + (int)(o & 255u) - 128;
-            const int vy = b.cy + (int)((o >> 8) & 255u) - 128;
-            const int vz = b.cz + (int)((o >> 16) & 255u) - 128;
-            if ((unsigned)vx < (unsigned)BX && (unsigned)vy < (unsigned)BY &&
-                (unsigned)vz < (unsigned)BZ)
-                wa->cnt[(vz * BY + vy) * BX + vx] += 1;   // distinct voxels within one pair
+        const uint32_t e0 = shs[bin], e1 = shs[bin + 1];
+        for (uint32_t e = e0; e < e1; e += 64) {
+            // both halves fetched before use
+            const uint32_t o0 = e + lane < e1 ? sh[e + lane] : 0u;
+            const uint32_t o1 = e + 32 + lane < e1 ? sh[e + 32 + lane] : 0u;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t o = h ? o1 : o0;
+                if (o) {   // packed offsets are never 0 (each byte is biased by 128)
+                    const int vx = b.cx + (int)(o & 255u) - 128;
+                    const int vy = b.cy + (int)((o >> 8) & 255u) - 128;
+                    const int vz = b.cz + (int)((o >> 16) & 255u) - 128;
+                    if ((unsigned)vx < (unsigned)BX && (unsigned)vy < (unsigned)BY &&
+                        (unsigned)vz < (unsigned)BZ)
+                        wa->cnt[(vz * BY + vy) * BX + vx] += 1;   // distinct voxels per pair
+                }
+            }
         }
     }
 }
@@ -207,6 +218,16 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g, DevParams p, DevT
     uint32_t *P = smem;
     for (int j = threadIdx.x; j < np; j += NTHR) P[j] = t.prow[j];
     WarpArea *areas = reinterpret_cast<WarpArea *>(smem + ((np + 3) & ~3));
+    // shadow offsets: in shared memory after the warp areas when they fit
+    const uint32_t *sh = t.sh_off, *shs = t.sh_start;
+    if (p.sh_smem) {
+        uint32_t *s_shs = reinterpret_cast<uint32_t *>(areas + WPC);
+        uint32_t *s_sh = s_shs + ((p.nbins + 1 + 3) & ~3);
+        for (int j = threadIdx.x; j <= p.nbins; j += NTHR) s_shs[j] = t.sh_start[j];
+        for (int j = threadIdx.x; j < p.n_sh; j += NTHR) s_sh[j] = t.sh_off[j];
+        sh = s_sh;
+        shs = s_shs;
+    }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     WarpArea *wa = areas + warp;
     const uint32_t nt = min(*(volatile uint32_t *)&ws.hdr->n_touched, ws.max_touched);
@@ -274,7 +295,7 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g, DevParams p, DevT
             const uint32_t mine = jj < len ? __ldg(pairs + jj) : 0u;
             const int cnt = (int)min(32u, (len - warp + WPC - 1) / WPC - base);
             for (int j = 0; j < cnt; ++j) {
-                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, t, R, W, SR, lane);
+                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, sh, shs, R, W, SR, lane);
                 __syncwarp();
             }
         }
@@ -349,7 +370,7 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g, DevParams p, DevT
             const uint32_t mine = base + lane < len ? __ldg(pairs + base + lane) : 0u;
             const int cnt = (int)min(32u, len - base);
             for (int j = 0; j < cnt; ++j) {
-                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, t, R, W, SR, lane);
+                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, sh, shs, R, W, SR, lane);
                 __syncwarp();
             }
         }
@@ -398,16 +419,19 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g, DevParams p, DevT
     }
 }
 
-// Dynamic shared memory of one CTA for kernel size K.
-static size_t integrate_smem(int K) {
+// Dynamic shared memory of one CTA: row codes, warp areas, and (when they
+// fit in SHADOW_SMEM_WORDS) the shadow offset table.
+static size_t integrate_smem(int K, int nbins, int n_sh) {
     const int R = (K - 1) / 2;
     const size_t np = (size_t)(2 * R * R + 1) * (2 * R + 4);
-    return ((np + 3) & ~size_t(3)) * 4 + WPC * sizeof(WarpArea);
+    size_t bytes = ((np + 3) & ~size_t(3)) * 4 + WPC * sizeof(WarpArea);
+    if (shadow_in_smem(nbins, n_sh)) bytes += (size_t)(((nbins + 1 + 3) & ~3) + n_sh) * 4;
+    return bytes;
 }
 
 struct IntegrateCfg {
     int device = -1;
-    int ctas[MAX_K + 1] = {};
+    int ctas[MAX_K + 1][2] = {};
 };
 static IntegrateCfg g_cfg;
 
@@ -433,25 +457,29 @@ static int configure(size_t smem, size_t smem_max) {
 // Words of a kernel row: an x-extent of K voxels starting anywhere in a word.
 static int words_per_row(int K) { return K <= 13 ? 4 : 6; }
 
-// Persistent grid for kernel size K: every SM filled to its occupancy limit.
-int integrate_grid_ctas(int K) {
+// Persistent grid for these parameters: every SM filled to its occupancy limit.
+int integrate_grid_ctas(const DevParams &p) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (g_cfg.device != dev) {
         g_cfg = IntegrateCfg();
         g_cfg.device = dev;
     }
-    if (!g_cfg.ctas[K]) {
-        const size_t smem = integrate_smem(K);
-        g_cfg.ctas[K] = words_per_row(K) == 4 ? configure<4>(smem, integrate_smem(13))
-                                              : configure<6>(smem, integrate_smem(MAX_K));
+    const int inb = p.sh_smem ? 1 : 0;
+    if (!g_cfg.ctas[p.K][inb]) {
+        const size_t smem = integrate_smem(p.K, p.nbins, p.n_sh);
+        const size_t smax = words_per_row(p.K) == 4
+                                ? integrate_smem(13, 0, 0) + SHADOW_SMEM_WORDS * 4
+                                : integrate_smem(MAX_K, 0, 0) + SHADOW_SMEM_WORDS * 4;
+        g_cfg.ctas[p.K][inb] = words_per_row(p.K) == 4 ? configure<4>(smem, smax)
+                                                      : configure<6>(smem, smax);
     }
-    return g_cfg.ctas[K];
+    return g_cfg.ctas[p.K][inb];
 }
 
 void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, long long n_input,
                       const WsDev &ws, int grid_ctas, cudaStream_t s) {
-    const size_t smem = integrate_smem(p.K);
+    const size_t smem = integrate_smem(p.K, p.nbins, p.n_sh);
     if (words_per_row(p.K) == 4)
         k_integrate<4><<<grid_ctas, NTHR, smem, s>>>(g, p, t, n_input, ws);
     else
