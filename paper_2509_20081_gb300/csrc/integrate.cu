@@ -24,10 +24,9 @@
 //   A. the 16-byte chunks of each brick row that any pair's kernel covers
 //      (lanes take one pair each and OR-reduce 64-bit row masks per chunk),
 //   B. those chunks staged as codes; shadow counts zeroed,
-//   C. every pair applied (one pair at a time, lanes = the kernel rows in the
-//      brick, each lane updating the up to NW words of its row), then the
-//      shadow offsets counted (Eq. 5; lanes = pairs, each walking its bin's
-//      offsets and adding the ones inside the brick atomically),
+//   C. every pair applied (lanes = 8 rows x 4 planes, each lane updating the
+//      up to NW words of its kernel row), then the bin's shadow offsets that
+//      fall in the brick counted (Eq. 5),
 //   D. chunks whose codes changed written back as masks; for chunks with
 //      shadow counts c: h' = min(h + c, H_max), sign 0 when h < T <= h' (Eq. 6).
 // AND is commutative and the saturating count with a threshold crossing
@@ -107,13 +106,15 @@ __device__ __forceinline__ void coverage(const uint32_t *pairs, uint32_t first, 
     }
 }
 
-// Phase C (Eq. 4) for one pair on a warp's staged copy.  The box's wy x wz
-// kernel rows are spread over the lanes (row r -> z = r / wy, y = r % wy, the
+// Phase C for one pair on a warp's staged copy.  The box's wy x wz kernel
+// rows are spread over the lanes (row r -> z = r / wy, y = r % wy, the
 // division by wy <= 8 done exactly as (r * ceil(256 / wy)) >> 8 for r < 64);
-// each lane updates the up to NW words of its row.
+// each lane updates the up to NW words of its row.  sh / shs: the per-bin
+// shadow offsets and their starts (shared or global memory).
 template <int NW>
-__device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint32_t *P, int R,
-                                           int W, int lane) {
+__device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint32_t *P,
+                                           const uint32_t *sh, const uint32_t *shs, int R, int W,
+                                           int SR, int lane) {
     const PairBox b = decode_pair(pl, R);
     const int wy = b.y1 - b.y0 + 1;
     const int nrows = wy * (b.z1 - b.z0 + 1);
@@ -142,42 +143,25 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
             }
         }
     }
-}
-
-// Phase C (Eq. 5 counts) for pairs[j], j = first + stride (base + lane):
-// each lane walks its own pair's shadow offsets (sh / shs, per bin, in shared
-// or global memory) and counts those inside the brick.  Two lanes may hit
-// one voxel, so counts are added atomically to their packed 16-bit halves.
-__device__ __forceinline__ void shadow_counts(const uint32_t *pairs, uint32_t first,
-                                              uint32_t stride, uint32_t len, WarpArea *wa,
-                                              const uint32_t *sh, const uint32_t *shs, int R,
-                                              int SR, int lane) {
-    uint32_t *cnt32 = reinterpret_cast<uint32_t *>(wa->cnt);
-    for (uint32_t base = 0; first + stride * base < len; base += 32) {
-        const uint32_t j = first + stride * (base + lane);
-        uint32_t e = 0, e1 = 0;
-        int cx = 0, cy = 0, cz = 0;
-        if (j < len) {
-            const uint32_t pl = __ldg(pairs + j);
-            cx = (int)(pl & 63u) - R;
-            cy = (int)((pl >> 6) & 31u) - R;
-            cz = (int)((pl >> 11) & 31u) - R;
-            if (cx >= -SR && cx <= BX - 1 + SR && cy >= -SR && cy <= BY - 1 + SR &&
-                cz >= -SR && cz <= BZ - 1 + SR) {
-                const uint32_t bin = pl >> 16;
-                e = shs[bin];
-                e1 = shs[bin + 1];
-            }
-        }
-        for (; e < e1; ++e) {
-            const uint32_t o = sh[e];
-            const int vx = cx + (int)(o & 255u) - 128;
-            const int vy = cy + (int)((o >> 8) & 255u) - 128;
-            const int vz = cz + (int)((o >> 16) & 255u) - 128;
-            if ((unsigned)vx < (unsigned)BX && (unsigned)vy < (unsigned)BY &&
-                (unsigned)vz < (unsigned)BZ) {
-                const int v = (vz * BY + vy) * BX + vx;
-                atomicAdd(&cnt32[v >> 1], 1u << (16 * (v & 1)));
+    if (b.cx >= -SR && b.cx <= BX - 1 + SR && b.cy >= -SR && b.cy <= BY - 1 + SR &&
+        b.cz >= -SR && b.cz <= BZ - 1 + SR) {
+        const uint32_t bin = pl >> 16;
+        const uint32_t e0 = shs[bin], e1 = shs[bin + 1];
+        for (uint32_t e = e0; e < e1; e += 64) {
+            // both halves fetched before use
+            const uint32_t o0 = e + lane < e1 ? sh[e + lane] : 0u;
+            const uint32_t o1 = e + 32 + lane < e1 ? sh[e + 32 + lane] : 0u;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t o = h ? o1 : o0;
+                if (o) {   // packed offsets are never 0 (each byte is biased by 128)
+                    const int vx = b.cx + (int)(o & 255u) - 128;
+                    const int vy = b.cy + (int)((o >> 8) & 255u) - 128;
+                    const int vz = b.cz + (int)((o >> 16) & 255u) - 128;
+                    if ((unsigned)vx < (unsigned)BX && (unsigned)vy < (unsigned)BY &&
+                        (unsigned)vz < (unsigned)BZ)
+                        wa->cnt[(vz * BY + vy) * BX + vx] += 1;   // distinct voxels per pair
+                }
             }
         }
     }
@@ -311,11 +295,10 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g, DevParams p, DevT
             const uint32_t mine = jj < len ? __ldg(pairs + jj) : 0u;
             const int cnt = (int)min(32u, (len - warp + WPC - 1) / WPC - base);
             for (int j = 0; j < cnt; ++j) {
-                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, R, W, lane);
+                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, sh, shs, R, W, SR, lane);
                 __syncwarp();
             }
         }
-        shadow_counts(pairs, warp, WPC, len, wa, sh, shs, R, SR, lane);
         __syncthreads();
         // D: merge the copies and write back
         for (int c = tid; c < BCHUNKS; c += NTHR) {
@@ -387,12 +370,10 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g, DevParams p, DevT
             const uint32_t mine = base + lane < len ? __ldg(pairs + base + lane) : 0u;
             const int cnt = (int)min(32u, len - base);
             for (int j = 0; j < cnt; ++j) {
-                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, R, W, lane);
+                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, sh, shs, R, W, SR, lane);
                 __syncwarp();
             }
         }
-        shadow_counts(pairs, 0u, 1u, len, wa, sh, shs, R, SR, lane);
-        __syncwarp();
         // D
         for (int i = 0; i < BROWS / 4; ++i) {
             const int row = rs + 4 * i;
