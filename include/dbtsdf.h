@@ -200,6 +200,54 @@ dbt_status dbt_scan_footprint(const dbt_grid *g, const dbt_kernels *k, dbt_works
                               const float *d_xyz, int64_t n, const double pose[12], void *d_bits,
                               size_t bits_bytes, int64_t h_counts[2], void *stream);
 
+/* Batches: many scans of many grids (maps of any size) integrated by one
+ * launch sequence.  The result on every grid equals integrating its scans
+ * one by one with dbt_integrate_scan, in any order: a scan's effect depends
+ * only on its kept returns (Eq. 4 is an AND; Eqs. 5-6 depend only on the
+ * total count), and the first-return rule applies per scan.  Each brick
+ * touched by several scans is staged once.  The grids are fixed when the
+ * batch is created; each set of items names a grid by index.  dbt_batch_run
+ * only enqueues kernels and memsets, so it can be captured in a CUDA graph
+ * and replayed while the items are unchanged. */
+typedef struct dbt_batch dbt_batch;
+
+typedef struct {
+    int32_t grid;           /* index into the batch's grids */
+    int32_t reserved;       /* must be 0 */
+    int64_t n;              /* returns */
+    const float *d_xyz;     /* device, n x 3 float32, sensor frame */
+    double pose[12];        /* row-major [R | t], sensor -> map */
+} dbt_batch_item;
+
+/* Bytes of device scratch for a batch over n_grids grids (<= 256), up to
+ * max_points returns in total and max_items scans per run. */
+dbt_status dbt_batch_size(const dbt_grid *grids, int32_t n_grids, const dbt_kernels *k,
+                          int64_t max_points, int32_t max_items, size_t *bytes);
+
+/* Wraps caller-owned device scratch d_buf (256-byte aligned) for the given
+ * grids (copied; their arrays must stay valid) and uploads the grid table
+ * (synchronous on stream). */
+dbt_status dbt_batch_create(const dbt_grid *grids, int32_t n_grids, const dbt_kernels *k,
+                            int64_t max_points, int32_t max_items, void *d_buf, size_t bytes,
+                            void *stream, dbt_batch **out);
+
+/* Checks and uploads the scans of the next run (the copy first waits for
+ * earlier work on stream).  Items of one grid may appear in any number. */
+dbt_status dbt_batch_set_items(dbt_batch *b, const dbt_batch_item *items, int32_t n_items,
+                               void *stream);
+
+/* Enqueues the integration of the current items (asynchronous). */
+dbt_status dbt_batch_run(dbt_batch *b, void *stream);
+
+/* Synchronises stream; per-scan counters of the last run for the first n
+ * items (n_pairs / n_bricks are 0 per scan) and the run's totals (either
+ * pointer may be NULL).  DBT_ESTATE when the device latched an error. */
+dbt_status dbt_batch_stats(const dbt_batch *b, dbt_scan_stats *per_item, int32_t n,
+                           dbt_scan_stats *total, void *stream);
+
+/* Frees the handle (not the caller's buffer). */
+dbt_status dbt_batch_destroy(dbt_batch *b);
+
 /* dbt_integrate_scan for callers that cannot allocate device memory (the
  * paper has no counterpart; this is a deployment convenience).  Some callers
  * may not call cudaMalloc while they run -- a real-time mapping loop that

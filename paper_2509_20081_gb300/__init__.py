@@ -5,7 +5,7 @@ include/dbtsdf.h); ``dbtsdf`` is its thin ctypes binding.
 """
 from . import build  # noqa: F401
 from .dbtsdf import (  # noqa: F401
-    DBT_BINS_AZEL, DBT_BINS_OCTA, DbtError, Grid, Kernels, Workspace, dbt_bin_directions,
+    Batch, DBT_BINS_AZEL, DBT_BINS_OCTA, DbtError, Grid, Kernels, Workspace, dbt_bin_directions,
     dbt_get_scan_stats, dbt_grid_init, dbt_grid_layout, dbt_integrate_scan,
     dbt_integrate_scan_host, dbt_read_distance, dbt_read_voxels, dbt_sync, dbt_tables_host,
     dbt_version, lib, make_params)

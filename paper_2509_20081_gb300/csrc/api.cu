@@ -658,6 +658,247 @@ dbt_status dbt::integrate_on_scratch(const dbt_grid *g, const dbt_kernels *k, co
     return DBT_OK;
 }
 
+// ------------------------------------------------------------------ batches
+struct dbt_batch {
+    const dbt_kernels *k = nullptr;
+    int n_grids = 0;
+    std::vector<DevGrid> grids;          // host copies
+    std::vector<dbt_grid> cgrids;
+    std::vector<uint32_t> bbase;         // n_grids + 1
+    long long max_points = 0;
+    int max_items = 0;
+    WsLayout L;                          // integration scratch (bricks of all grids)
+    WsDev d;
+    void *buf = nullptr;
+    size_t off_grids = 0, off_bbase = 0, off_items = 0, off_istart = 0, off_icnt = 0, total = 0;
+    std::vector<ItemDev> items;          // staged descriptors of the current set
+    std::vector<long long> istart;
+    int n_items = 0;
+    long long n_total = 0;
+    BatchDev bd;
+};
+
+static dbt_status batch_layout(const dbt_grid *grids, int n_grids, const dbt_kernels *k,
+                               long long max_points, int max_items, WsLayout *L,
+                               std::vector<uint32_t> *bbase, size_t *tail_offs /* 5 + total */) {
+    if (!grids || n_grids < 1 || n_grids > MAX_BATCH_GRIDS)
+        return fail(DBT_EINVAL, "n_grids must be in [1, %d]", MAX_BATCH_GRIDS);
+    if (max_items < 1 || max_items > MAX_BATCH_ITEMS)
+        return fail(DBT_EINVAL, "max_items must be in [1, %d]", MAX_BATCH_ITEMS);
+    if (max_points < 1 || max_points > (1ll << 31) - 1)
+        return fail(DBT_EINVAL, "max_points must be in [1, 2^31 - 1]");
+    bbase->assign(n_grids + 1, 0u);
+    unsigned long long nb = 0;
+    for (int m = 0; m < n_grids; ++m) {
+        dbt_status st = check_grid(&grids[m]);
+        if (st != DBT_OK) return fail(st, "grid %d: %s", m, dbt_last_error());
+        const DevGrid d = dev_grid(&grids[m]);
+        (*bbase)[m] = (uint32_t)nb;
+        nb += (unsigned long long)d.nbx * d.nby * d.nbz;
+        if (nb >= (1ull << 32)) return fail(DBT_EINVAL, "too many bricks over the batch's grids");
+    }
+    (*bbase)[n_grids] = (uint32_t)nb;
+    // the single-grid layout with the batch's total brick count
+    uint32_t hc = 64;
+    while (hc < 2ull * (unsigned long long)max_points) hc <<= 1;
+    L->nbricks = (uint32_t)nb;
+    L->hcap_alloc = hc;
+    L->pairs_cap = (unsigned long long)max_points * max_pairs_per_return(k->dp.K);
+    L->max_touched = (uint32_t)std::min<unsigned long long>(nb, L->pairs_cap);
+    size_t o = 0;
+    L->hdr = o;      o += up256(sizeof(WsHeader));
+    L->stage = o;    o += up256(16);
+    L->prec = o;     o += up256((size_t)max_points * 16);
+    L->hkey = o;     o += up256((size_t)hc * 8);
+    L->hidx = o;     o += up256((size_t)hc * 4);
+    L->bcnt = o;     o += up256((size_t)nb * 4);
+    L->boff = o;     o += up256((size_t)nb * 4);
+    L->touched = o;  o += up256((size_t)L->max_touched * 4);
+    L->order = o;    o += up256((size_t)L->max_touched * 4);
+    L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
+    L->total = o;
+    tail_offs[0] = o;  o += up256((size_t)n_grids * sizeof(DevGrid));
+    tail_offs[1] = o;  o += up256((size_t)(n_grids + 1) * 4);
+    tail_offs[2] = o;  o += up256((size_t)max_items * sizeof(ItemDev));
+    tail_offs[3] = o;  o += up256((size_t)(max_items + 1) * 8);
+    tail_offs[4] = o;  o += up256((size_t)max_items * sizeof(ItemCounters));
+    tail_offs[5] = o;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_batch_size(const dbt_grid *grids, int32_t n_grids, const dbt_kernels *k,
+                                     int64_t max_points, int32_t max_items, size_t *bytes) {
+    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
+    if (!bytes) return fail(DBT_EINVAL, "bytes is NULL");
+    WsLayout L;
+    std::vector<uint32_t> bb;
+    size_t offs[6];
+    dbt_status st = batch_layout(grids, n_grids, k, max_points, max_items, &L, &bb, offs);
+    if (st != DBT_OK) return st;
+    *bytes = offs[5];
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_batch_create(const dbt_grid *grids, int32_t n_grids, const dbt_kernels *k,
+                                       int64_t max_points, int32_t max_items, void *d_buf,
+                                       size_t bytes, void *stream, dbt_batch **out) {
+    if (!out) return fail(DBT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
+    if (!d_buf || !aligned256(d_buf)) return fail(DBT_EINVAL, "batch buffer must be 256-byte aligned");
+    dbt_batch *b = new (std::nothrow) dbt_batch();
+    if (!b) return fail(DBT_ENOMEM, "host allocation failed");
+    size_t offs[6];
+    dbt_status st = batch_layout(grids, n_grids, k, max_points, max_items, &b->L, &b->bbase, offs);
+    if (st != DBT_OK) {
+        delete b;
+        return st;
+    }
+    if (bytes < offs[5]) {
+        delete b;
+        return fail(DBT_ENOMEM, "batch buffer too small: %zu < %zu bytes", bytes, offs[5]);
+    }
+    b->k = k;
+    b->n_grids = n_grids;
+    b->max_points = max_points;
+    b->max_items = max_items;
+    b->buf = d_buf;
+    b->off_grids = offs[0];
+    b->off_bbase = offs[1];
+    b->off_items = offs[2];
+    b->off_istart = offs[3];
+    b->off_icnt = offs[4];
+    b->total = offs[5];
+    for (int m = 0; m < n_grids; ++m) {
+        b->grids.push_back(dev_grid(&grids[m]));
+        b->cgrids.push_back(grids[m]);
+    }
+    char *base = (char *)d_buf;
+    dbt_workspace w;
+    ws_bind(&w, &grids[0], k, max_points, b->L, d_buf);
+    b->d = w.d;
+    b->bd.grids = (const DevGrid *)(base + b->off_grids);
+    b->bd.bbase = (const uint32_t *)(base + b->off_bbase);
+    b->bd.items = (const ItemDev *)(base + b->off_items);
+    b->bd.istart = (const long long *)(base + b->off_istart);
+    b->bd.icnt = (ItemCounters *)(base + b->off_icnt);
+    b->bd.n_grids = n_grids;
+    b->bd.n_items = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_buf, 0, b->total, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + b->off_grids, b->grids.data(), n_grids * sizeof(DevGrid),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + b->off_bbase, b->bbase.data(), (n_grids + 1) * 4,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "batch set-up");
+    }
+    *out = b;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_batch_set_items(dbt_batch *b, const dbt_batch_item *items, int32_t n_items,
+                                          void *stream) {
+    if (!b) return fail(DBT_EINVAL, "batch is NULL");
+    if (n_items < 0 || n_items > b->max_items)
+        return fail(DBT_EINVAL, "n_items = %d outside [0, %d]", n_items, b->max_items);
+    if (n_items > 0 && !items) return fail(DBT_EINVAL, "items is NULL");
+    b->items.resize(std::max(1, n_items));
+    b->istart.assign(n_items + 1, 0ll);
+    long long total = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const dbt_batch_item &it = items[i];
+        if (it.grid < 0 || it.grid >= b->n_grids)
+            return fail(DBT_EINVAL, "item %d: grid %d outside [0, %d)", i, it.grid, b->n_grids);
+        if (it.n < 0) return fail(DBT_EINVAL, "item %d: n < 0", i);
+        if (it.n > 0 && (!it.d_xyz || ((uintptr_t)it.d_xyz & 3u)))
+            return fail(DBT_EINVAL, "item %d: points must be a 4-byte aligned device pointer", i);
+        Pose P;
+        dbt_status st = check_pose(it.pose, &P);
+        if (st != DBT_OK) return fail(st, "item %d: %s", i, dbt_last_error());
+        ItemDev &d = b->items[i];
+        d.xyz = it.d_xyz;
+        d.n = it.n;
+        d.grid = it.grid;
+        d.pad = 0;
+        d.pose = P;
+        b->istart[i] = total;
+        total += it.n;
+        if (total > b->max_points)
+            return fail(DBT_EINVAL, "the items hold more than max_points = %lld returns", b->max_points);
+    }
+    b->istart[n_items] = total;
+    char *base = (char *)b->buf;
+    cudaStream_t s = (cudaStream_t)stream;
+    // pageable sources: each copy waits for earlier work on the stream, so a
+    // running batch never sees its descriptors change
+    if (n_items > 0)
+        DBT_CUDA(cudaMemcpyAsync(base + b->off_items, b->items.data(), n_items * sizeof(ItemDev),
+                                 cudaMemcpyHostToDevice, s));
+    DBT_CUDA(cudaMemcpyAsync(base + b->off_istart, b->istart.data(), (n_items + 1) * 8,
+                             cudaMemcpyHostToDevice, s));
+    b->n_items = n_items;
+    b->n_total = total;
+    b->bd.n_items = n_items;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_batch_run(dbt_batch *b, void *stream) {
+    if (!b) return fail(DBT_EINVAL, "batch is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const dbt_kernels *k = b->k;
+    uint32_t hcap = 64;
+    while (hcap < 2ull * (unsigned long long)b->n_total) hcap <<= 1;
+    if (b->n_items > 0)
+        DBT_CUDA(cudaMemsetAsync((char *)b->buf + b->off_icnt, 0, b->n_items * sizeof(ItemCounters), s));
+    if (b->n_items > 0) {
+        launch_voxelize_batch(b->bd, k->dp, k->dt, b->n_total, b->d, hcap, s);
+        launch_count_batch(b->bd, k->dp, b->n_total, b->d, hcap, s);
+    }
+    launch_alloc(b->d, 2 * 152, s);
+    if (b->n_items > 0) launch_fill_batch(b->bd, k->dp, b->n_total, b->d, hcap, s);
+    launch_integrate_batch(b->bd, k->dp, k->dt, b->n_total, b->d, integrate_grid_ctas(k->dp), s);
+    DBT_CUDA(cudaGetLastError());
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_batch_stats(const dbt_batch *b, dbt_scan_stats *per_item, int32_t n,
+                                      dbt_scan_stats *total, void *stream) {
+    if (!b) return fail(DBT_EINVAL, "batch is NULL");
+    if (n < 0 || n > b->n_items) return fail(DBT_EINVAL, "n outside [0, n_items]");
+    DBT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    dbt_scan_stats tot;
+    DBT_CUDA(cudaMemcpy(&tot, &b->d.hdr->last, sizeof tot, cudaMemcpyDeviceToHost));
+    if (total) *total = tot;
+    if (per_item && n > 0) {
+        std::vector<ItemCounters> c(n);
+        DBT_CUDA(cudaMemcpy(c.data(), (char *)b->buf + b->off_icnt, n * sizeof(ItemCounters),
+                            cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n; ++i) {
+            dbt_scan_stats &o = per_item[i];
+            o.n_input = b->istart[i + 1] - b->istart[i];
+            o.n_valid = (long long)c[i].valid;
+            o.n_inside = (long long)c[i].inside;
+            o.n_kept = (long long)c[i].kept;
+            o.n_pairs = 0;
+            o.n_bricks = 0;
+            o.error = tot.error;
+            o.reserved = 0;
+        }
+    }
+    if (tot.error) return fail(DBT_ESTATE, "device error bits 0x%x", tot.error);
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_batch_destroy(dbt_batch *b) {
+    delete b;
+    return DBT_OK;
+}
+
 extern "C" dbt_status dbt_integrate_scan_host(const dbt_grid *g, const dbt_kernels *k,
                                               dbt_workspace *ws, const float *h_xyz, int64_t n,
                                               const double pose[12], dbt_scan_stats *h_stats,

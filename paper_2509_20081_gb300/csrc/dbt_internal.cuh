@@ -81,6 +81,35 @@ struct Pose {
     double t[3];
 };
 
+// One scan of a batch: its returns, the grid (index into the batch's grid
+// table) and the pose.
+struct ItemDev {
+    const float *xyz;
+    long long n;
+    int grid;
+    int pad;
+    Pose pose;
+};
+
+// Per-scan counters of a batch.
+struct ItemCounters {
+    unsigned long long valid, inside, kept, pad;
+};
+
+// Device tables of a batch: grids with the first global brick of each
+// (bricks of all grids are numbered in one space), scans with the first
+// return of each (returns of all scans in one index space).
+struct BatchDev {
+    const DevGrid *grids;      // n_grids
+    const uint32_t *bbase;     // n_grids + 1
+    const ItemDev *items;      // n_items
+    const long long *istart;   // n_items + 1
+    ItemCounters *icnt;        // n_items
+    int n_grids, n_items;
+};
+constexpr int MAX_BATCH_GRIDS = 256;   // grid index lives in 8 bits of a return record
+constexpr int MAX_BATCH_ITEMS = 1 << 20;
+
 // Counters of the last completed scan; same layout as dbt_scan_stats.
 struct ScanStats {
     long long n_input, n_valid, n_inside, n_kept, n_pairs, n_bricks;
@@ -123,7 +152,8 @@ struct WsDev {
 // CTA (its warps split the pairs); the others by a single warp.
 constexpr uint32_t HEAVY_PAIRS = 48;
 
-// Return-record flags in prec.w above the 16-bit bin.
+// Return record prec.w: bin in bits 0-15, batch grid index in bits 16-23,
+// PREC_DUP when the first-return rule drops the return.
 constexpr int PREC_DUP = 1 << 30;
 
 // Launch helpers implemented in the .cu files.
@@ -136,6 +166,15 @@ void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, u
                  cudaStream_t s);
 void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, long long n_input,
                       const WsDev &ws, int grid_ctas, cudaStream_t s);
+// Batched forms: every scan of bd at once (one brick pass over all grids).
+void launch_voxelize_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
+                           long long n, const WsDev &ws, uint32_t hcap, cudaStream_t s);
+void launch_count_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
+                        uint32_t hcap, cudaStream_t s);
+void launch_fill_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
+                       uint32_t hcap, cudaStream_t s);
+void launch_integrate_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
+                            long long n_input, const WsDev &ws, int grid_ctas, cudaStream_t s);
 int integrate_grid_ctas(const DevParams &p);
 void launch_footprint(const DevGrid &g, const DevParams &p, const DevTables &t, int n,
                       const WsDev &ws, uint32_t hcap, uint32_t *bits_u, uint32_t *bits_s,

@@ -147,17 +147,17 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
         b.cz >= -SR && b.cz <= BZ - 1 + SR) {
         const uint32_t bin = pl >> 16;
         const uint32_t e0 = shs[bin], e1 = shs[bin + 1];
-        for (uint32_t e = e0; e < e1; e += 64) {
-            // both halves fetched before use
-            const uint32_t o0 = e + lane < e1 ? sh[e + lane] : 0u;
-            const uint32_t o1 = e + 32 + lane < e1 ? sh[e + 32 + lane] : 0u;
+        for (uint32_t e = e0; e < e1; e += 96) {
+            // three batches of 32 fetched before use (a 3-voxel shadow has <= 96 offsets)
+            uint32_t o[3];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t o = h ? o1 : o0;
-                if (o) {   // packed offsets are never 0 (each byte is biased by 128)
-                    const int vx = b.cx + (int)(o & 255u) - 128;
-                    const int vy = b.cy + (int)((o >> 8) & 255u) - 128;
-                    const int vz = b.cz + (int)((o >> 16) & 255u) - 128;
+            for (int h = 0; h < 3; ++h) o[h] = e + 32 * h + lane < e1 ? sh[e + 32 * h + lane] : 0u;
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+                if (o[h]) {   // packed offsets are never 0 (each byte is biased by 128)
+                    const int vx = b.cx + (int)(o[h] & 255u) - 128;
+                    const int vy = b.cy + (int)((o[h] >> 8) & 255u) - 128;
+                    const int vz = b.cz + (int)((o[h] >> 16) & 255u) - 128;
                     if ((unsigned)vx < (unsigned)BX && (unsigned)vy < (unsigned)BY &&
                         (unsigned)vz < (unsigned)BZ)
                         wa->cnt[(vz * BY + vy) * BX + vx] += 1;   // distinct voxels per pair
@@ -206,9 +206,32 @@ __device__ __forceinline__ void store_chunk(const DevGrid &g, size_t gi, uint32_
     }
 }
 
-template <int NW>
-__global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g, DevParams p, DevTables t,
-                                                    long long n_input, WsDev ws) {
+// Grid of global brick b in a batch (bricks of grid m are [bbase[m], bbase[m+1])).
+__device__ __forceinline__ int grid_of_brick(const BatchDev &bd, uint32_t b) {
+    int lo = 0, hi = bd.n_grids - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bd.bbase[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Grid view and local brick index of touched brick b.
+template <bool BATCH>
+__device__ __forceinline__ uint32_t brick_grid(const DevGrid &g, const BatchDev &bd, uint32_t b,
+                                               DevGrid &gg) {
+    if (!BATCH) {
+        gg = g;
+        return b;
+    }
+    const int gi = grid_of_brick(bd, b);
+    gg = bd.grids[gi];
+    return b - bd.bbase[gi];
+}
+
+template <int NW, bool BATCH>
+__global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, DevParams p,
+                                                    DevTables t, long long n_input, WsDev ws) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t s_item;
     __shared__ unsigned long long s_cr[CHUNKS_PER_ROW];
@@ -248,8 +271,10 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g, DevParams p, DevT
         const uint32_t start = ws.boff[b];
         uint32_t len = ws.bcnt[b];
         if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing
-        const int bx = (int)(b % (uint32_t)g.nbx);
-        const uint32_t byz = b / (uint32_t)g.nbx;
+        DevGrid g;
+        const uint32_t lb = brick_grid<BATCH>(g0, bd, b, g);
+        const int bx = (int)(lb % (uint32_t)g.nbx);
+        const uint32_t byz = lb / (uint32_t)g.nbx;
         const int by = (int)(byz % (uint32_t)g.nby), bz = (int)(byz / (uint32_t)g.nby);
         const uint32_t *pairs = ws.pairs + start;
 
@@ -332,8 +357,10 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g, DevParams p, DevT
         const uint32_t start = ws.boff[b];
         uint32_t len = ws.bcnt[b];
         if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing
-        const int bx = (int)(b % (uint32_t)g.nbx);
-        const uint32_t byz = b / (uint32_t)g.nbx;
+        DevGrid g;
+        const uint32_t lb = brick_grid<BATCH>(g0, bd, b, g);
+        const int bx = (int)(lb % (uint32_t)g.nbx);
+        const uint32_t byz = lb / (uint32_t)g.nbx;
         const int by = (int)(byz % (uint32_t)g.nby), bz = (int)(byz / (uint32_t)g.nby);
         const uint32_t *pairs = ws.pairs + start;
 
@@ -445,12 +472,14 @@ static int configure(size_t smem, size_t smem_max) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     if (limit_set_on != dev) {
-        cudaFuncSetAttribute(k_integrate<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_integrate<NW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_max);
+        cudaFuncSetAttribute(k_integrate<NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_max);
         limit_set_on = dev;
     }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<NW>, NTHR, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<NW, true>, NTHR, smem);
     return max(1, sms * max(1, per_sm));
 }
 
@@ -480,10 +509,21 @@ int integrate_grid_ctas(const DevParams &p) {
 void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, long long n_input,
                       const WsDev &ws, int grid_ctas, cudaStream_t s) {
     const size_t smem = integrate_smem(p.K, p.nbins, p.n_sh);
+    const BatchDev none = {};
     if (words_per_row(p.K) == 4)
-        k_integrate<4><<<grid_ctas, NTHR, smem, s>>>(g, p, t, n_input, ws);
+        k_integrate<4, false><<<grid_ctas, NTHR, smem, s>>>(g, none, p, t, n_input, ws);
     else
-        k_integrate<6><<<grid_ctas, NTHR, smem, s>>>(g, p, t, n_input, ws);
+        k_integrate<6, false><<<grid_ctas, NTHR, smem, s>>>(g, none, p, t, n_input, ws);
+}
+
+void launch_integrate_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
+                            long long n_input, const WsDev &ws, int grid_ctas, cudaStream_t s) {
+    const size_t smem = integrate_smem(p.K, p.nbins, p.n_sh);
+    const DevGrid none = {};
+    if (words_per_row(p.K) == 4)
+        k_integrate<4, true><<<grid_ctas, NTHR, smem, s>>>(none, bd, p, t, n_input, ws);
+    else
+        k_integrate<6, true><<<grid_ctas, NTHR, smem, s>>>(none, bd, p, t, n_input, ws);
 }
 
 }  // namespace dbt

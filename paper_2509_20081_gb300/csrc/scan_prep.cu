@@ -119,37 +119,43 @@ __device__ __forceinline__ unsigned long long voxel_key(const DevGrid &g, int x,
 }
 
 // ------------------------------------------------------------------ K1
+// Sec. III-C for one return: discard non-finite and origin returns, map-frame
+// transform, contact voxel, boundary discard, bin.  Returns 0 (not valid),
+// 1 (valid, outside) or 2 (inside, rec filled with contact and bin).
+__device__ __forceinline__ int contact_of(const DevGrid &g, const DevParams &p, const DevTables &t,
+                                          const Pose &pose, float fx, float fy, float fz,
+                                          int4 &rec) {
+    if (!(isfinite(fx) && isfinite(fy) && isfinite(fz)) || (fx == 0.0f && fy == 0.0f && fz == 0.0f))
+        return 0;
+    const double px = fx, py = fy, pz = fz;
+    double d[3], q[3];
+    const double org[3] = {g.ox, g.oy, g.oz};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        d[r] = __fma_rn(pose.r[3 * r + 2], pz,
+                        __fma_rn(pose.r[3 * r + 1], py, __dmul_rn(pose.r[3 * r + 0], px)));
+        const double w = __dadd_rn(d[r], pose.t[r]);
+        q[r] = floor(__dmul_rn(__dsub_rn(w, org[r]), g.inv_res));
+    }
+    const double R = (double)p.R;
+    if (!(q[0] >= R && q[0] <= (double)(g.nx - 1 - p.R) && q[1] >= R &&
+          q[1] <= (double)(g.ny - 1 - p.R) && q[2] >= R && q[2] <= (double)(g.nz - 1 - p.R)))
+        return 1;
+    rec = make_int4((int)q[0], (int)q[1], (int)q[2], bin_of(p, t, d[0], d[1], d[2]));
+    return 2;
+}
+
 __global__ void __launch_bounds__(256) k_voxelize(DevGrid g, DevParams p, DevTables t, Pose pose,
                                                   const float *__restrict__ xyz, int n, WsDev ws,
                                                   uint32_t hcap) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false, inside = false;
     if (i < n) {
-        const float fx = xyz[3 * i + 0], fy = xyz[3 * i + 1], fz = xyz[3 * i + 2];
         int4 rec = make_int4(-1, 0, 0, 0);
-        if (isfinite(fx) && isfinite(fy) && isfinite(fz) &&
-            !(fx == 0.0f && fy == 0.0f && fz == 0.0f)) {
-            valid = true;
-            const double px = fx, py = fy, pz = fz;
-            double d[3], q[3];
-            const double org[3] = {g.ox, g.oy, g.oz};
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                d[r] = __fma_rn(pose.r[3 * r + 2], pz,
-                                __fma_rn(pose.r[3 * r + 1], py, __dmul_rn(pose.r[3 * r + 0], px)));
-                const double w = __dadd_rn(d[r], pose.t[r]);
-                q[r] = floor(__dmul_rn(__dsub_rn(w, org[r]), g.inv_res));
-            }
-            const double R = (double)p.R;
-            if (q[0] >= R && q[0] <= (double)(g.nx - 1 - p.R) && q[1] >= R &&
-                q[1] <= (double)(g.ny - 1 - p.R) && q[2] >= R && q[2] <= (double)(g.nz - 1 - p.R)) {
-                inside = true;
-                const int cx = (int)q[0], cy = (int)q[1], cz = (int)q[2];
-                const int b = bin_of(p, t, d[0], d[1], d[2]);
-                rec = make_int4(cx, cy, cz, b);
-                if (p.dedup) hash_insert(ws, hcap, voxel_key(g, cx, cy, cz), (uint32_t)i);
-            }
-        }
+        const int c = contact_of(g, p, t, pose, xyz[3 * i + 0], xyz[3 * i + 1], xyz[3 * i + 2], rec);
+        valid = c > 0;
+        inside = c == 2;
+        if (inside && p.dedup) hash_insert(ws, hcap, voxel_key(g, rec.x, rec.y, rec.z), (uint32_t)i);
         ws.prec[i] = rec;
     }
     const unsigned bv = __ballot_sync(0xffffffffu, valid);
@@ -283,6 +289,146 @@ __global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, WsD
     if (p.dedup) {
         const uint32_t stride = gridDim.x * blockDim.x;
         for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < hcap; j += stride) {
+            ws.hkey[j] = 0ull;
+            ws.hidx[j] = 0u;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ batches
+// The same stages for every scan of a batch at once.  Returns of all scans
+// share one index space (scan k owns [istart[k], istart[k+1])); the
+// first-return hash key carries the scan, so the rule stays per scan; bricks
+// of all grids share one index space (grid m owns [bbase[m], bbase[m+1])).
+
+__device__ __forceinline__ int item_of(const BatchDev &bd, long long i) {
+    int lo = 0, hi = bd.n_items - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bd.istart[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ unsigned long long batch_key(const DevGrid &g, int item, int x, int y,
+                                                        int z) {
+    return ((unsigned long long)item << 40) + voxel_key(g, x, y, z);
+}
+
+// Adds per-scan counts of a warp: lanes with the same item are summed by
+// their leader.
+__device__ __forceinline__ void add_item_counts(const BatchDev &bd, int item, bool a, bool b,
+                                                unsigned long long ItemCounters::*fa,
+                                                unsigned long long ItemCounters::*fb) {
+    const unsigned peers = __match_any_sync(0xffffffffu, item);
+    const unsigned ba = __ballot_sync(0xffffffffu, a) & peers;
+    const unsigned bb = __ballot_sync(0xffffffffu, b) & peers;
+    const int lane = threadIdx.x & 31;
+    if (item >= 0 && lane == __ffs(peers) - 1) {
+        if (ba) atomicAdd(&(bd.icnt[item].*fa), (unsigned long long)__popc(ba));
+        if (fb && bb) atomicAdd(&(bd.icnt[item].*fb), (unsigned long long)__popc(bb));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_voxelize_b(BatchDev bd, DevParams p, DevTables t,
+                                                    long long n, WsDev ws, uint32_t hcap) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = false, inside = false;
+    int item = -1;
+    if (i < n) {
+        item = item_of(bd, i);
+        const ItemDev &it = bd.items[item];
+        const DevGrid g = bd.grids[it.grid];
+        const long long j = i - bd.istart[item];
+        int4 rec = make_int4(-1, 0, 0, 0);
+        const int c = contact_of(g, p, t, it.pose, it.xyz[3 * j + 0], it.xyz[3 * j + 1],
+                                 it.xyz[3 * j + 2], rec);
+        valid = c > 0;
+        inside = c == 2;
+        if (inside) {
+            rec.w |= it.grid << 16;
+            if (p.dedup) hash_insert(ws, hcap, batch_key(g, item, rec.x, rec.y, rec.z), (uint32_t)i);
+        }
+        ws.prec[i] = rec;
+    }
+    const unsigned bv = __ballot_sync(0xffffffffu, valid);
+    const unsigned bi = __ballot_sync(0xffffffffu, inside);
+    if ((threadIdx.x & 31) == 0) {
+        if (bv) atomicAdd(&ws.hdr->acc_valid, (unsigned long long)__popc(bv));
+        if (bi) atomicAdd(&ws.hdr->acc_inside, (unsigned long long)__popc(bi));
+    }
+    add_item_counts(bd, item, valid, inside, &ItemCounters::valid, &ItemCounters::inside);
+}
+
+__global__ void __launch_bounds__(256) k_count_b(BatchDev bd, DevParams p, long long n, WsDev ws,
+                                                 uint32_t hcap) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool kept = false;
+    int item = -1;
+    if (i < n) {
+        item = item_of(bd, i);
+        int4 r = ws.prec[i];
+        if (r.x >= 0) {
+            const int gi = (r.w >> 16) & 0xFF;
+            const DevGrid g = bd.grids[gi];
+            kept = true;
+            if (p.dedup && !hash_is_first(ws, hcap, batch_key(g, item, r.x, r.y, r.z), (uint32_t)i)) {
+                kept = false;
+                r.w |= PREC_DUP;
+                ws.prec[i] = r;
+            }
+            if (kept) {
+                const uint32_t b0 = bd.bbase[gi];
+                const BrickSpan s = brick_span(r.x, r.y, r.z, p.R);
+                for (int bz = s.z0; bz <= s.z1; ++bz)
+                    for (int by = s.y0; by <= s.y1; ++by)
+                        for (int bx = s.x0; bx <= s.x1; ++bx) {
+                            const uint32_t b = b0 + ((uint32_t)bz * g.nby + by) * g.nbx + bx;
+                            if (atomicAdd(&ws.bcnt[b], 1u) == 0u) {
+                                const uint32_t tt = atomicAdd(&ws.hdr->n_touched, 1u);
+                                if (tt < ws.max_touched) ws.touched[tt] = b;
+                                else atomicOr(&ws.hdr->err, ERR_TOUCHED_OVERFLOW);
+                            }
+                        }
+            }
+        }
+    }
+    const unsigned bk = __ballot_sync(0xffffffffu, kept);
+    if ((threadIdx.x & 31) == 0 && bk) atomicAdd(&ws.hdr->acc_kept, (unsigned long long)__popc(bk));
+    add_item_counts(bd, item, kept, false, &ItemCounters::kept, nullptr);
+}
+
+__global__ void __launch_bounds__(256) k_fill_b(BatchDev bd, DevParams p, long long n, WsDev ws,
+                                                uint32_t hcap) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int4 r = ws.prec[i];
+        if (r.x >= 0 && !(r.w & PREC_DUP)) {
+            const int gi = (r.w >> 16) & 0xFF;
+            const DevGrid g = bd.grids[gi];
+            const uint32_t b0 = bd.bbase[gi];
+            const uint32_t bin = (uint32_t)(r.w & 0xFFFF);
+            const BrickSpan s = brick_span(r.x, r.y, r.z, p.R);
+            for (int bz = s.z0; bz <= s.z1; ++bz)
+                for (int by = s.y0; by <= s.y1; ++by)
+                    for (int bx = s.x0; bx <= s.x1; ++bx) {
+                        const uint32_t b = b0 + ((uint32_t)bz * g.nby + by) * g.nbx + bx;
+                        const uint32_t slot = atomicAdd(&ws.bcnt[b], 1u);
+                        const unsigned long long pos = (unsigned long long)ws.boff[b] + slot;
+                        const uint32_t rx = (uint32_t)(r.x - bx * BX + p.R);
+                        const uint32_t ry = (uint32_t)(r.y - by * BY + p.R);
+                        const uint32_t rz = (uint32_t)(r.z - bz * BZ + p.R);
+                        if (pos < ws.pairs_cap)
+                            ws.pairs[pos] = rx | (ry << 6) | (rz << 11) | (bin << 16);
+                        else
+                            atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
+                    }
+        }
+    }
+    if (p.dedup) {
+        const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+        for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+             j < hcap; j += stride) {
             ws.hkey[j] = 0ull;
             ws.hidx[j] = 0u;
         }
@@ -423,6 +569,23 @@ void launch_alloc(const WsDev &ws, int grid_ctas, cudaStream_t s) {
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                  cudaStream_t s) {
     k_fill<<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, n, ws, hcap);
+}
+
+static inline unsigned batch_blocks(long long n) { return (unsigned)max(1ll, (n + 255) / 256); }
+
+void launch_voxelize_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
+                           long long n, const WsDev &ws, uint32_t hcap, cudaStream_t s) {
+    k_voxelize_b<<<batch_blocks(n), 256, 0, s>>>(bd, p, t, n, ws, hcap);
+}
+
+void launch_count_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
+                        uint32_t hcap, cudaStream_t s) {
+    k_count_b<<<batch_blocks(n), 256, 0, s>>>(bd, p, n, ws, hcap);
+}
+
+void launch_fill_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
+                       uint32_t hcap, cudaStream_t s) {
+    k_fill_b<<<batch_blocks(n), 256, 0, s>>>(bd, p, n, ws, hcap);
 }
 
 void launch_bin_dirs(const DevParams &p, const DevTables &t, const double *dirs, int n, int *bins,

@@ -53,6 +53,11 @@ class dbt_scan_stats(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class dbt_batch_item(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("d_xyz", ctypes.c_void_p), ("pose", ctypes.c_double * 12)]
+
+
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
 _SIGS = {
@@ -77,6 +82,14 @@ _SIGS = {
     "dbt_read_distance": [_P(dbt_grid), _vp, ctypes.c_int64, _vp, _vp],
     "dbt_sync": [_vp, _vp],
     "dbt_workspace_set_timing": [_vp, _vp, _vp],
+    "dbt_batch_size": [_P(dbt_grid), ctypes.c_int32, _vp, ctypes.c_int64, ctypes.c_int32,
+                       _P(ctypes.c_size_t)],
+    "dbt_batch_create": [_P(dbt_grid), ctypes.c_int32, _vp, ctypes.c_int64, ctypes.c_int32, _vp,
+                         ctypes.c_size_t, _vp, _P(_vp)],
+    "dbt_batch_set_items": [_vp, _P(dbt_batch_item), ctypes.c_int32, _vp],
+    "dbt_batch_run": [_vp, _vp],
+    "dbt_batch_stats": [_vp, _P(dbt_scan_stats), ctypes.c_int32, _P(dbt_scan_stats), _vp],
+    "dbt_batch_destroy": [_vp],
     "dbt_integrate_scan_noalloc": [_P(dbt_grid), _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
                                    _P(dbt_scan_stats), _vp],
     "dbt_scan_footprint": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
@@ -354,3 +367,66 @@ def dbt_integrate_scan_noalloc(grid: Grid, kernels: Kernels, xyz, pose,
                                             xyz.data_ptr() if n else None, n, pp,
                                             ctypes.byref(stats) if stats is not None else None,
                                             _stream_ptr(stream)))
+
+
+class Batch:
+    """dbt_batch_*: many scans of several grids integrated by one launch
+    sequence (dbt_batch_run), which is also capturable in a CUDA graph."""
+
+    def __init__(self, grids: list, kernels: Kernels, max_points: int, max_items: int, stream=None):
+        import torch
+        self.grids = list(grids)
+        arr = (dbt_grid * len(grids))(*[g.c for g in grids])
+        self._arr = arr
+        nbytes = ctypes.c_size_t()
+        _check(lib().dbt_batch_size(arr, len(grids), kernels.h, max_points, max_items,
+                                    ctypes.byref(nbytes)))
+        self.nbytes = nbytes.value
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=grids[0].mask.device)
+        ptr = self.buf.data_ptr() + (-self.buf.data_ptr()) % 256
+        h = _vp()
+        _check(lib().dbt_batch_create(arr, len(grids), kernels.h, max_points, max_items, ptr,
+                                      self.nbytes, _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+        self.kernels = kernels
+        self.n_items = 0
+        self._keep = []
+
+    def set_items(self, items, stream=None):
+        """items: list of (grid index, CUDA float32 (n, 3) tensor, pose (3, 4))."""
+        arr = (dbt_batch_item * max(1, len(items)))()
+        keep = []
+        for i, (gi, xyz, pose) in enumerate(items):
+            n = int(xyz.shape[0])
+            p = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(12))
+            arr[i].grid = gi
+            arr[i].reserved = 0
+            arr[i].n = n
+            arr[i].d_xyz = xyz.data_ptr() if n else None
+            arr[i].pose[:] = p.tolist()
+            keep.append(xyz)
+        _check(lib().dbt_batch_set_items(self.h, arr, len(items), _stream_ptr(stream)))
+        self._keep = keep
+        self.n_items = len(items)
+
+    def run(self, stream=None):
+        _check(lib().dbt_batch_run(self.h, _stream_ptr(stream)))
+
+    def stats(self, stream=None, check=True):
+        per = (dbt_scan_stats * max(1, self.n_items))()
+        tot = dbt_scan_stats()
+        r = lib().dbt_batch_stats(self.h, per, self.n_items, ctypes.byref(tot), _stream_ptr(stream))
+        if check:
+            _check(r)
+        return [per[i].as_dict() for i in range(self.n_items)], tot.as_dict()
+
+    def close(self):
+        if self.h:
+            lib().dbt_batch_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
