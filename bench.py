@@ -258,10 +258,13 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(dev.index) if rank == 0 else None
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     t0.record(stream)
     for s in range(args.steps):
+        evs[s].record(stream)
         B.dbt_workspace_set_timing(ws, evb[s], eve[s])
         dbt.dbt_integrate_scan(g, k, ws, d_scans[s % nsc], poses[s % nsc])
+    evs[args.steps].record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -272,6 +275,8 @@ def run_ours(args, rank, world):
     st = dbt.dbt_get_scan_stats(ws)
     assert st["error"] == 0, st
     t_int = [evb[s].elapsed_time(eve[s]) for s in range(args.steps)]
+    t_scan = sorted(evs[s].elapsed_time(evs[s + 1]) for s in range(args.steps))
+    batched = run_batched(args, w, k, g, d_scans, poses, stream, world)
     bytes_alg = sum(alg[s % nsc] for s in range(args.steps))
     kept_timed = sum(kept[s % nsc] for s in range(args.steps))
 
@@ -317,6 +322,9 @@ def run_ours(args, rank, world):
         "e2e": {"value": world * args.steps * npts / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": npts * 12, "d2h_bytes_per_step": 64,
                 "ms_per_step": ms_e2e / args.steps},
+        "latency_ms": {"p50": pct(t_scan, 50), "p99": pct(t_scan, 99), "max": t_scan[-1],
+                       "what": "device time per scan, plain per-scan launches"},
+        "batched": batched,
         "gpu_launches": 5 * args.steps,
         "roofline": {"bound": "hbm", "kernel": "k_integrate", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
@@ -335,15 +343,154 @@ def run_ours(args, rank, world):
     return 0
 
 
+def pct(sorted_vals, q):
+    i = min(len(sorted_vals) - 1, max(0, int(round(q / 100.0 * (len(sorted_vals) - 1)))))
+    return sorted_vals[i]
+
+
+def run_batched(args, w, k, g, d_scans, poses, stream, world):
+    """The same K scans as graph-replayed batches of args.batch consecutive
+    scans (one dbt_batch_run per batch, captured once, replayed in order)."""
+    import torch
+
+    import paper_2509_20081_gb300 as dbt
+    S = max(1, args.batch)
+    nsc = len(w.scans)
+    groups = [list(range(i, min(i + S, args.steps))) for i in range(0, args.steps, S)]
+    batches, graphs = [], []
+    cap = torch.cuda.Stream()
+    for grp in groups:
+        items = [(0, d_scans[s % nsc], poses[s % nsc]) for s in grp]
+        b = dbt.Batch([g], k, sum(int(x.shape[0]) for _, x, _ in items), len(items))
+        b.set_items(items)
+        batches.append(b)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(cap):
+        batches[0].run(stream=cap)                  # configures the kernels before capture
+    torch.cuda.synchronize()
+    for b in batches:
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=cap):
+            b.run(stream=cap)
+        graphs.append(gr)
+    for _ in range(max(1, args.warmup // S)):
+        graphs[0].replay()
+    dbt.dbt_grid_init(g)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(graphs) + 1)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i, gr in enumerate(graphs):
+        gr.replay()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(len(graphs)))
+    ms = ev[0].elapsed_time(ev[-1])
+    _, tot = batches[-1].stats()
+    npts = sum(int(d_scans[s % nsc].shape[0]) for s in range(args.steps))
+    out = {"value": world * npts / (ms * 1e-3), "unit": UNIT, "scans_per_batch": S,
+           "ms_per_scan": ms / args.steps, "batch_ms_p50": pct(per, 50), "batch_ms_p99": pct(per, 99),
+           "launch": "one CUDA graph per batch (dbt_batch_run captured), replayed in order"}
+    for b in batches:
+        b.close()
+    return out
+
+
+def run_maps(args, rank, world):
+    """Uneven independent maps (side 64-512 voxels at 0.05-0.2 m), 8 scans
+    of 4,096-131,072 returns each: a step integrates all scans of all maps,
+    either as one graph-replayed batch (value) or as one plain launch sequence
+    per scan (plain)."""
+    import torch
+
+    import paper_2509_20081_gb300 as dbt
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    maps = synth.batched_maps(n_maps=args.maps, scans_per_map=8)
+    k = dbt.Kernels(dbt.make_params(**maps[0].params))
+    grids = [dbt.Grid(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.res) for w in maps]
+    items = [(m, torch.from_numpy(pts).to(dev), pose) for m, w in enumerate(maps)
+             for pts, pose in w.scans]
+    npts = sum(int(x.shape[0]) for _, x, _ in items)
+    stream = torch.cuda.current_stream()
+    # plain: one workspace per map, one dbt_integrate_scan per scan
+    wss = [dbt.Workspace(grids[m], k, max(int(x.shape[0]) for mm, x, _ in items if mm == m))
+           for m in range(len(maps))]
+
+    def plain_pass():
+        for m, x, pose in items:
+            dbt.dbt_integrate_scan(grids[m], k, wss[m], x, pose)
+
+    b = dbt.Batch(grids, k, npts, len(items))
+    b.set_items(items)
+    cap = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(cap):
+        b.run(stream=cap)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap):
+        b.run(stream=cap)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        for g in grids:
+            dbt.dbt_grid_init(g)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return e0.elapsed_time(e1) / steps
+
+    ms_batch = timed(graph.replay, args.steps)
+    ms_plain = timed(plain_pass, args.steps)
+    t = torch.tensor([ms_batch, ms_plain], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_batch, ms_plain = float(t[0]), float(t[1])
+    if rank != 0:
+        return 0
+    vox = sum(w.grid.nx * w.grid.ny * w.grid.nz for w in maps)
+    line = {"metric": METRIC, "value": world * npts / (ms_batch * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": f"maps: {len(maps)} maps ({vox / 1e6:.0f} M voxels), "
+                                   f"{len(items)} scans, {npts} returns per step",
+                       "parallelism": f"replicas x{args.gpus}",
+                       "l2": "grids larger than L2 in total; no flush"},
+            "batched": {"value": world * npts / (ms_batch * 1e-3), "ms_per_step": ms_batch,
+                        "launch": "one CUDA graph of dbt_batch_run over all scans"},
+            "plain": {"value": world * npts / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                      "launch": f"{len(items)} dbt_integrate_scan calls (5 kernels each)"},
+            "gpu_launches": 5 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["urban", "urban_half", "highres"], default="urban")
+    ap.add_argument("--workload", choices=["urban", "urban_half", "highres", "maps"], default="urban")
+    ap.add_argument("--maps", type=int, default=32, help="maps workload: number of maps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--batch", type=int, default=10, help="scans per batch in the batched leg")
     ap.add_argument("--ref-stride", type=int, default=16,
                     help="reference arm: integrate every n-th return of each scan")
     args = ap.parse_args()
@@ -359,6 +506,8 @@ def main():
     try:
         if args.impl == "reference":
             return run_reference(args, rank, world)
+        if args.workload == "maps":
+            return run_maps(args, rank, world)
         return run_ours(args, rank, world)
     finally:
         if world > 1:
