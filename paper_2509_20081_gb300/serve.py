@@ -227,6 +227,16 @@ class Server:
     def map_state(self, rid):
         return self.grids[rid]
 
+    def reset(self):
+        """Fresh maps (Sec. III-A state) and empty statistics; no round may be in flight."""
+        self.torch.cuda.synchronize()
+        for g in self.grids.values():
+            B.dbt_grid_init(g)
+        for rid in self.pending:
+            self.pending[rid] = []
+        self.completed, self.rounds, self.round_sizes = [], 0, []
+        self.torch.cuda.synchronize()
+
     def drain(self, clock):
         while not self.idle():
             self.poll(clock())

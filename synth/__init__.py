@@ -415,3 +415,42 @@ def random_rotation(rng: Rng) -> np.ndarray:
     """Uniform-ish random rotation from three angles."""
     a = rng.uniform(3, -math.pi, math.pi)
     return rotation_rpy(float(a[0]), float(a[1]) / 2.0, float(a[2]))
+
+
+def serving_robots(n_robots: int = 16, scans_per_robot: int = 4, duration: float = 60.0,
+                   seed_offset: int = 4, side_lo: int = 400, side_hi: int = 1200,
+                   z_lo: int = 100, z_hi: int = 200, res: float = 0.05):
+    """Robots with resident maps at res (x = y side log-uniform in [side_lo,
+    side_hi], z in [z_lo, z_hi]), each with a pool of scans (beams from
+    {16, 32, 64, 128} x widths from {900, 1024, 2048}, 14k-262k returns) from
+    the urban generator scaled to its map, and Poisson arrival times at a rate
+    uniform in [10, 20] Hz over `duration` seconds (scan k of the trace uses
+    pool entry k mod scans_per_robot).  Returns (maps, arrivals) with
+    arrivals = [(robot, time, pool index)] sorted by time."""
+    rng = Rng(BASE_SEED + seed_offset)
+    maps, arrivals = [], []
+    beams_set, widths = (16, 32, 64, 128), (900, 1024, 2048)
+    for r in range(n_robots):
+        side = int(round(float(rng.log_uniform(1, side_lo, side_hi)[0])))
+        nz = int(rng.integers(1, z_lo, z_hi + 1)[0])
+        scale = side * res / 80.0
+        while True:
+            beams = beams_set[int(rng.integers(1, 0, 4)[0])]
+            width = widths[int(rng.integers(1, 0, 3)[0])]
+            if 14000 <= beams * width <= 262144:
+                break
+        w = urban_sequence(n_scans=scans_per_robot, seed_offset=100 + 17 * r + seed_offset,
+                           scale=scale, res=res, beams=beams, width=width,
+                           rmax=max(10.0, 60.0 * scale))
+        w.grid = GridSpec(w.grid.nx, w.grid.ny, min(w.grid.nz, nz) if nz >= 64 else w.grid.nz, res)
+        maps.append(w)
+        rate = float(rng.uniform(1, 10.0, 20.0)[0])
+        t, k = 0.0, 0
+        while True:
+            t += -math.log(1.0 - float(rng.uniform(1)[0])) / rate
+            if t >= duration:
+                break
+            arrivals.append((r, t, k % scans_per_robot))
+            k += 1
+    arrivals.sort(key=lambda a: a[1])
+    return maps, arrivals
