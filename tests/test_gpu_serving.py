@@ -18,13 +18,11 @@ def _need_cuda():
 def _robots(n=4, scans=6):
     maps = synth.batched_maps(n_maps=n, scans_per_map=scans, side_lo=64, side_hi=160,
                               n_lo=3000, n_hi=30000, seed_offset=7)
-    rng = synth.Rng(99)
     arrivals = []
     for rid, w in enumerate(maps):
-        t = 0.0
-        for pts, pose in w.scans:
-            t += float(rng.uniform(1, 0.0005, 0.003)[0])      # bursts: rounds must mix robots
-            arrivals.append((rid, t, pts, pose))
+        for k, (pts, pose) in enumerate(w.scans):
+            # every robot's k-th scan arrives at the same instant, so rounds mix robots
+            arrivals.append((rid, 0.004 * k, pts, pose))
     return maps, arrivals
 
 
