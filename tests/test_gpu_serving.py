@@ -68,7 +68,7 @@ def test_serving_admission_and_retire():
               for rid, w in enumerate(maps)}
     need0 = serve.grid_bytes(*robots[0][:3])
     need1 = serve.grid_bytes(*robots[1][:3])
-    srv = serve.Server(k, {0: robots[0]}, budget_bytes=1 << 40, n_streams=1,
+    srv = serve.Server(k, robots, budget_bytes=1 << 40, n_streams=1,
                        max_round_points=100000, max_round_items=16)
     scr = max(srv._scratch_bytes([0]), srv._scratch_bytes([1]))
     # both maps never fit at once; either one alone does
