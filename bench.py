@@ -301,10 +301,7 @@ def run_ours(args, rank, world):
     ms_e2e = e0.elapsed_time(e1)
     assert all(sp.error == 0 for sp in st_ptrs)
 
-    tmax = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-    ms, ms_e2e = float(tmax[0]), float(tmax[1])
+    ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev, world)
     if rank != 0:
         return 0
 
@@ -341,6 +338,16 @@ def run_ours(args, rank, world):
                                           f"{secs:.1f} s of single-thread CPU"}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def max_over_ranks(vals, dev, world):
+    """Element-wise maximum of per-rank timings (every rank gets the result)."""
+    if world <= 1:
+        return [float(v) for v in vals]
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
 
 
 def pct(sorted_vals, q):
@@ -456,10 +463,7 @@ def run_maps(args, rank, world):
 
     ms_batch = timed(graph.replay, args.steps)
     ms_plain = timed(plain_pass, args.steps)
-    t = torch.tensor([ms_batch, ms_plain], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_batch, ms_plain = float(t[0]), float(t[1])
+    ms_batch, ms_plain = max_over_ranks([ms_batch, ms_plain], dev, world)
     if rank != 0:
         return 0
     vox = sum(w.grid.nx * w.grid.ny * w.grid.nz for w in maps)
