@@ -53,7 +53,9 @@ INTEGRATE_SRC = os.path.join(ROOT, "paper_2509_20081_gb300", "csrc", "integrate.
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_integrate, per kept
 # return, from the capture summarised under profiles/ (valid only for the
 # integrate.cu source with this sha256 prefix; otherwise traffic is null).
-NCU_TRAFFIC = {"integrate_sha": None, "bytes_per_kept_return": None}
+NCU_TRAFFIC = {"integrate_sha": "ac7ebba84dea7e33", "bytes_per_kept_return": 1073.8,
+               "source": "profiles/k_integrate_urban_half.md (urban_half, 39.9 k kept returns "
+                         "per scan, 42.9 MB DRAM read+write per launch), scaled by kept returns"}
 
 WORKLOADS = {
     "urban": dict(n_scans=100, scale=1.0, res=0.05, beams=64, width=1024, seed_offset=1),
@@ -310,6 +312,9 @@ def run_ours(args, rank, world):
     traffic = None
     if NCU_TRAFFIC["integrate_sha"] == integrate_sha() and NCU_TRAFFIC["bytes_per_kept_return"]:
         traffic = NCU_TRAFFIC["bytes_per_kept_return"] * kept_timed / args.steps
+        traffic_note = NCU_TRAFFIC["source"]
+    else:
+        traffic_note = "no ncu capture of this integrate.cu yet"
     line = {
         "metric": METRIC, "value": world * args.steps * npts / (ms * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -325,6 +330,7 @@ def run_ours(args, rank, world):
         "gpu_launches": 5 * args.steps,
         "roofline": {"bound": "hbm", "kernel": "k_integrate", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": traffic_note,
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "alg_bytes_per_launch": bytes_alg / args.steps,
                      "ms_per_launch": statistics.mean(t_int),
