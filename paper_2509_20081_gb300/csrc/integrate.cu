@@ -106,15 +106,13 @@ __device__ __forceinline__ void coverage(const uint32_t *pairs, uint32_t first, 
     }
 }
 
-// Phase C for one pair on a warp's staged copy.  The box's wy x wz kernel
-// rows are spread over the lanes (row r -> z = r / wy, y = r % wy, the
+// Phase C (Eq. 4) for one pair on a warp's staged copy.  The box's wy x wz
+// kernel rows are spread over the lanes (row r -> z = r / wy, y = r % wy, the
 // division by wy <= 8 done exactly as (r * ceil(256 / wy)) >> 8 for r < 64);
-// each lane updates the up to NW words of its row.  sh / shs: the per-bin
-// shadow offsets and their starts (shared or global memory).
+// each lane updates the up to NW words of its row.
 template <int NW>
-__device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint32_t *P,
-                                           const uint32_t *sh, const uint32_t *shs, int R, int W,
-                                           int SR, int lane) {
+__device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint32_t *P, int R,
+                                           int W, int lane) {
     const PairBox b = decode_pair(pl, R);
     const int wy = b.y1 - b.y0 + 1;
     const int nrows = wy * (b.z1 - b.z0 + 1);
@@ -143,24 +141,42 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
             }
         }
     }
-    if (b.cx >= -SR && b.cx <= BX - 1 + SR && b.cy >= -SR && b.cy <= BY - 1 + SR &&
-        b.cz >= -SR && b.cz <= BZ - 1 + SR) {
-        const uint32_t bin = pl >> 16;
-        const uint32_t e0 = shs[bin], e1 = shs[bin + 1];
-        for (uint32_t e = e0; e < e1; e += 96) {
-            // three batches of 32 fetched before use (a 3-voxel shadow has <= 96 offsets)
-            uint32_t o[3];
+}
+
+// Eq. 5 counts of one pair: lanes walk the bin's shadow offsets (sh / shs,
+// in shared or global memory) and count those inside the brick.  ATOMIC:
+// several warps count into one array, so counts are added atomically to
+// their packed 16-bit halves (a voxel's total never reaches 2^16: it is at
+// most the number of lattice points within r_s).
+template <bool ATOMIC>
+__device__ __forceinline__ void shadow_pair(uint32_t pl, uint16_t *cnt, const uint32_t *sh,
+                                            const uint32_t *shs, int R, int SR, int lane) {
+    const int cx = (int)(pl & 63u) - R;
+    const int cy = (int)((pl >> 6) & 31u) - R;
+    const int cz = (int)((pl >> 11) & 31u) - R;
+    if (!(cx >= -SR && cx <= BX - 1 + SR && cy >= -SR && cy <= BY - 1 + SR && cz >= -SR &&
+          cz <= BZ - 1 + SR))
+        return;
+    const uint32_t bin = pl >> 16;
+    const uint32_t e0 = shs[bin], e1 = shs[bin + 1];
+    for (uint32_t e = e0; e < e1; e += 96) {
+        // three batches of 32 fetched before use (a 3-voxel shadow has <= 96 offsets)
+        uint32_t o[3];
 #pragma unroll
-            for (int h = 0; h < 3; ++h) o[h] = e + 32 * h + lane < e1 ? sh[e + 32 * h + lane] : 0u;
+        for (int h = 0; h < 3; ++h) o[h] = e + 32 * h + lane < e1 ? sh[e + 32 * h + lane] : 0u;
 #pragma unroll
-            for (int h = 0; h < 3; ++h) {
-                if (o[h]) {   // packed offsets are never 0 (each byte is biased by 128)
-                    const int vx = b.cx + (int)(o[h] & 255u) - 128;
-                    const int vy = b.cy + (int)((o[h] >> 8) & 255u) - 128;
-                    const int vz = b.cz + (int)((o[h] >> 16) & 255u) - 128;
-                    if ((unsigned)vx < (unsigned)BX && (unsigned)vy < (unsigned)BY &&
-                        (unsigned)vz < (unsigned)BZ)
-                        wa->cnt[(vz * BY + vy) * BX + vx] += 1;   // distinct voxels per pair
+        for (int h = 0; h < 3; ++h) {
+            if (o[h]) {   // packed offsets are never 0 (each byte is biased by 128)
+                const int vx = cx + (int)(o[h] & 255u) - 128;
+                const int vy = cy + (int)((o[h] >> 8) & 255u) - 128;
+                const int vz = cz + (int)((o[h] >> 16) & 255u) - 128;
+                if ((unsigned)vx < (unsigned)BX && (unsigned)vy < (unsigned)BY &&
+                    (unsigned)vz < (unsigned)BZ) {
+                    const int v = (vz * BY + vy) * BX + vx;
+                    if (ATOMIC)
+                        atomicAdd(reinterpret_cast<uint32_t *>(cnt) + (v >> 1), 1u << (16 * (v & 1)));
+                    else
+                        cnt[v] += 1;   // distinct voxels within one pair
                 }
             }
         }
@@ -206,6 +222,110 @@ __device__ __forceinline__ void store_chunk(const DevGrid &g, size_t gi, uint32_
     }
 }
 
+// ---------------------------------------------------------------- dense bricks
+// For a brick with many pairs, the Eq. 4 result is computed once per voxel
+// instead of once per pair: the mask left by AND-ing the kernels of all
+// contacts c whose K^3 window holds voxel v is the mask of code
+// ceil(sqrt(f(v))) with f(v) = min |v - c|^2 over those contacts, and this
+// windowed minimum separates along the axes:
+//   f = min_{|dz|<=R} [dz^2 + min_{|dy|<=R} [dy^2 + min_{|dx|<=R} dx^2]]
+// where the innermost minimum runs over the contacts of one row.  Rows of the
+// brick dilated by R hold 64-bit contact occupancy masks; pass x finds the
+// nearest contact within +-R of each voxel by bit scans, passes y and z are
+// 2R+1-tap min-plus sweeps on bytes, four voxels per word.  With R <= 6 every
+// finite sum is at most 3 R^2 = 108, and the no-contact value DENSE_INF = 127
+// plus a tap stays below 256, so bytes never carry into each other.
+constexpr uint32_t DENSE_INF = 127u;
+
+__device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const uint32_t *pairs,
+                                uint32_t len, WarpArea *areas, const uint8_t *ctab,
+                                const uint32_t *sh, const uint32_t *shs, int R, int SR,
+                                uint32_t T, uint32_t Hmax, uint32_t &form_bad) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int D = BY + 2 * R;                                   // dilated y / z extent
+    unsigned char *scr = reinterpret_cast<unsigned char *>(areas + 1);
+    unsigned long long *occ = reinterpret_cast<unsigned long long *>(scr);   // D * D rows
+    uint32_t *g1 = reinterpret_cast<uint32_t *>(scr + D * D * 8);          // D * D rows x 8 words
+    uint32_t *g2 = g1 + D * D * 8;                                          // D x 8 rows x 8 words
+    WarpArea *a0 = areas;
+    const uint32_t *need = a0->need;
+    const uint32_t inf4 = DENSE_INF * 0x01010101u;
+    // B: stage the covered chunks once; clear the occupancy
+    for (int c = tid; c < BCHUNKS; c += NTHR) {
+        const int row = c >> 3, ch = c & 7;
+        if ((need[row] >> ch) & 1u) {
+            const int wd = kword(row, ch);
+            a0->kst[wd] = load_codes(g, chunk_index(g, bx, by, bz, row, ch), form_bad);
+            a0->dirty[wd] = 0;
+            *reinterpret_cast<uint2 *>(&a0->cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
+        }
+    }
+    for (int r = tid; r < D * D; r += NTHR) occ[r] = 0ull;
+    __syncthreads();
+    // contacts: payload coordinates are brick-relative + R, i.e. dilated indices
+    for (uint32_t j = tid; j < len; j += NTHR) {
+        const uint32_t pl = __ldg(pairs + j);
+        atomicOr(&occ[((pl >> 11) & 31u) * D + ((pl >> 6) & 31u)], 1ull << (pl & 63u));
+    }
+    __syncthreads();
+    // pass x: squared distance to the nearest contact of the row within +-R
+    const uint32_t win = (1u << (2 * R + 1)) - 1u, lmask = (1u << (R + 1)) - 1u;
+    for (int r = warp; r < D * D; r += WPC) {
+        const unsigned long long o = occ[r];
+        uint32_t v = DENSE_INF;
+        if (o) {
+            const uint32_t wv = (uint32_t)(o >> lane) & win;   // bit j: contact at x - R + j
+            const uint32_t left = wv & lmask, right = wv >> R;
+            int d = 2 * R + 2;
+            if (left) d = R - (31 - __clz(left));
+            if (right) d = min(d, __ffs(right) - 1);
+            if (d <= R) v = (uint32_t)(d * d);
+        }
+        reinterpret_cast<unsigned char *>(g1)[r * 32 + lane] = (unsigned char)v;
+    }
+    __syncthreads();
+    // pass y
+    for (int idx = tid; idx < D * 64; idx += NTHR) {
+        const int w = idx & 7, y = (idx >> 3) & 7, zp = idx >> 6;
+        uint32_t acc = inf4;
+        for (int dy = -R; dy <= R; ++dy)
+            acc = vmin4(acc, g1[(zp * D + (y + dy + R)) * 8 + w] + (uint32_t)(dy * dy) * 0x01010101u);
+        g2[(zp * 8 + y) * 8 + w] = vmin4(acc, inf4);
+    }
+    __syncthreads();
+    // pass z, codes, and Eq. 4 on the staged brick
+    for (int idx = tid; idx < BROWS * 8; idx += NTHR) {
+        const int w = idx & 7, row = idx >> 3, y = row & 7, z = row >> 3;
+        if (!((need[row] >> w) & 1u)) continue;
+        uint32_t acc = inf4;
+        for (int dz = -R; dz <= R; ++dz)
+            acc = vmin4(acc, g2[((z + dz + R) * 8 + y) * 8 + w] + (uint32_t)(dz * dz) * 0x01010101u);
+        const uint32_t code = (uint32_t)ctab[acc & 255u] | ((uint32_t)ctab[(acc >> 8) & 255u] << 8) |
+                              ((uint32_t)ctab[(acc >> 16) & 255u] << 16) |
+                              ((uint32_t)ctab[acc >> 24] << 24);
+        const int wd = kword(row, w);
+        const uint32_t old = a0->kst[wd];
+        const uint32_t nv = vmin4(old, code);
+        if (nv != old) {
+            a0->kst[wd] = nv;
+            a0->dirty[wd] = 1;
+        }
+    }
+    // Eq. 5 counts: pairs spread over the warps, counted into one array
+    for (uint32_t j = warp; j < len; j += WPC)
+        shadow_pair<true>(__ldg(pairs + j), a0->cnt, sh, shs, R, SR, lane);
+    __syncthreads();
+    // D
+    for (int c = tid; c < BCHUNKS; c += NTHR) {
+        const int row = c >> 3, ch = c & 7;
+        if ((need[row] >> ch) & 1u) {
+            const int wd = kword(row, ch);
+            store_chunk(g, chunk_index(g, bx, by, bz, row, ch), a0->kst[wd], a0->dirty[wd] != 0,
+                        *reinterpret_cast<const uint2 *>(&a0->cnt[row * 32 + ch * 4]), T, Hmax);
+        }
+    }
+}
+
 // Grid of global brick b in a batch (bricks of grid m are [bbase[m], bbase[m+1])).
 __device__ __forceinline__ int grid_of_brick(const BatchDev &bd, uint32_t b) {
     int lo = 0, hi = bd.n_grids - 1;
@@ -235,6 +355,12 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t s_item;
     __shared__ unsigned long long s_cr[CHUNKS_PER_ROW];
+    __shared__ uint8_t s_ctab[256];
+    for (int j = threadIdx.x; j < 256; j += NTHR) {
+        int kk = 0;
+        while (kk * kk < j && kk < 16) ++kk;
+        s_ctab[j] = (uint8_t)(j < (int)DENSE_INF ? kk : 32);   // ceil(sqrt(f)); 32 = no change
+    }
     const int R = p.R;
     const int W = 2 * R + 4;
     const int np = (2 * R * R + 1) * W;
@@ -299,6 +425,12 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
             need[tid] = nb;
         }
         __syncthreads();
+        if constexpr (NW == 4) {
+            integrate_dense(g, bx, by, bz, pairs, len, areas, s_ctab, sh, shs, R, SR, T, Hmax,
+                            form_bad);
+            if (tid == 0) ws.bcnt[b] = 0u;
+            continue;
+        }
         // B: stage into every warp's copy
         for (int c = tid; c < BCHUNKS; c += NTHR) {
             const int row = c >> 3, ch = c & 7;
@@ -320,7 +452,9 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
             const uint32_t mine = jj < len ? __ldg(pairs + jj) : 0u;
             const int cnt = (int)min(32u, (len - warp + WPC - 1) / WPC - base);
             for (int j = 0; j < cnt; ++j) {
-                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, sh, shs, R, W, SR, lane);
+                const uint32_t pl = __shfl_sync(0xffffffffu, mine, j);
+                apply_pair<NW>(pl, wa, P, R, W, lane);
+                shadow_pair<false>(pl, wa->cnt, sh, shs, R, SR, lane);
                 __syncwarp();
             }
         }
@@ -397,7 +531,9 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
             const uint32_t mine = base + lane < len ? __ldg(pairs + base + lane) : 0u;
             const int cnt = (int)min(32u, len - base);
             for (int j = 0; j < cnt; ++j) {
-                apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, sh, shs, R, W, SR, lane);
+                const uint32_t pl = __shfl_sync(0xffffffffu, mine, j);
+                apply_pair<NW>(pl, wa, P, R, W, lane);
+                shadow_pair<false>(pl, wa->cnt, sh, shs, R, SR, lane);
                 __syncwarp();
             }
         }
