@@ -66,7 +66,13 @@ typedef enum {
  *  hit_threshold T, 1 <= T <= hit_max (Eq. 6).
  *  hit_max       H_max, 1 <= H_max <= 65535 (Eq. 5).
  *  dedup_first   1: only the first return (lowest index) per contact voxel
- *                and scan is integrated (Sec. IV-B); 0: every return. */
+ *                and scan is integrated (Sec. IV-B); 0: every return.
+ *  shadow_cos    shape of the shadow (Sec. III-B): offset o of the ball
+ *                |o| <= r_s is in the shadow of bin b when
+ *                o . v_b >= shadow_cos * sqrt(|o|^2 |v_b|^2), v_b the bin's
+ *                direction.  0 gives the paper's hemisphere; c in (0, 1] a
+ *                cone of half-angle acos(c) around the ray (the conical
+ *                model the paper compares against).  Finite, in [0, 1]. */
 typedef struct {
     int32_t kernel_size;
     int32_t scheme;
@@ -77,6 +83,7 @@ typedef struct {
     int32_t hit_max;
     int32_t dedup_first;
     int32_t reserved;  /* must be 0 */
+    double shadow_cos;
 } dbt_params;
 
 /* A dense grid.  mask/sign/hits are device arrays of pitch_x * ny * nz

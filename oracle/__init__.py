@@ -48,7 +48,8 @@ class Params(ctypes.Structure):
                 ("shadow_radius", ctypes.c_double),
                 ("hit_threshold", ctypes.c_int),
                 ("hit_max", ctypes.c_int),
-                ("dedup_first", ctypes.c_int)]
+                ("dedup_first", ctypes.c_int),
+                ("shadow_cos", ctypes.c_double)]
 
 
 class _Grid(ctypes.Structure):
@@ -119,12 +120,19 @@ def _declare(L):
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.orc_signed_distance.restype = ctypes.c_double
     L.orc_signed_distance.argtypes = [ctypes.c_uint32, ctypes.c_uint8, ctypes.c_double]
+    L.orc_mc_config.restype = ctypes.c_int
+    L.orc_mc_config.argtypes = [ctypes.c_int, ctypes.c_void_p]
+    L.orc_sdf_field.restype = None
+    L.orc_sdf_field.argtypes = [P(_Grid), ctypes.c_void_p, ctypes.c_void_p]
+    L.orc_mesh.restype = ctypes.c_int64
+    L.orc_mesh.argtypes = [P(_Grid), ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                           ctypes.c_int64, ctypes.c_void_p]
 
 
 def params(kernel_size=11, scheme=SCHEME_OCTA, bins_a=8, bins_b=8, shadow_radius=3.0,
-           hit_threshold=3, hit_max=255, dedup_first=1) -> Params:
+           hit_threshold=3, hit_max=255, dedup_first=1, shadow_cos=0.0) -> Params:
     return Params(kernel_size, scheme, bins_a, bins_b, float(shadow_radius),
-                  hit_threshold, hit_max, dedup_first)
+                  hit_threshold, hit_max, dedup_first, float(shadow_cos))
 
 
 # ---------------------------------------------------------------- tables
@@ -272,3 +280,49 @@ def signed_distance(mask: int, sign: int, res: float) -> float:
 def grid_bytes_eq1(nx, ny, nz) -> int:
     """Eq. 1 with S_voxel = 8 bytes."""
     return int(lib().orc_grid_bytes_eq1(nx, ny, nz))
+
+
+# ---------------------------------------------------------------- export
+MC_EDGE_CORNERS = ((0, 1), (2, 3), (4, 5), (6, 7), (0, 2), (1, 3), (4, 6), (5, 7),
+                   (0, 4), (1, 5), (2, 6), (3, 7))
+
+
+def mc_config(cfg: int) -> np.ndarray:
+    """Triangles (as edge ids, shape (t, 3)) of Marching-Cubes configuration
+    cfg, bit q = corner q inside (Fig. 3 export; table derived in the C)."""
+    buf = np.zeros(3 * 12, np.int32)
+    n = int(lib().orc_mc_config(int(cfg), buf.ctypes.data))
+    return buf[:3 * n].reshape(n, 3).copy()
+
+
+def _box(g: Grid, box) -> np.ndarray:
+    if box is None:
+        box = (0, 0, 0, g.nx, g.ny, g.nz)
+    b = np.ascontiguousarray(np.asarray(box, dtype=np.int64).reshape(6))
+    if (b[:3] < 0).any() or (b[3:] < 0).any() or (b[:3] + b[3:] > (g.nx, g.ny, g.nz)).any():
+        raise ValueError("box outside the grid")
+    return b
+
+
+def sdf_field(g: Grid, box=None) -> np.ndarray:
+    """Signed distance (proposed readout) of every voxel of the box
+    (x0, y0, z0, bx, by, bz), shaped (bz, by, bx), float32."""
+    b = _box(g, box)
+    out = np.empty((int(b[5]), int(b[4]), int(b[3])), np.float32)
+    lib().orc_sdf_field(ctypes.byref(g._c()), b.ctypes.data, out.ctypes.data)
+    return out
+
+
+def mesh(g: Grid, box=None, iso: float = 0.0):
+    """Marching Cubes at iso over the box's cells (Fig. 3: export as a mesh
+    at iso = 0).  Returns (triangles (t, 3, 3) float32 map-frame vertices,
+    cell number of each triangle (t,) int64), cells x-fastest."""
+    b = _box(g, box)
+    gc = g._c()
+    n = int(lib().orc_mesh(ctypes.byref(gc), b.ctypes.data, float(iso), None, 0, None))
+    tri = np.empty((n, 3, 3), np.float32)
+    cell = np.empty(n, np.int64)
+    if n:
+        lib().orc_mesh(ctypes.byref(gc), b.ctypes.data, float(iso), tri.ctypes.data, n,
+                       cell.ctypes.data)
+    return tri, cell

@@ -54,6 +54,7 @@ typedef struct {
     int hit_threshold;    /* T */
     int hit_max;          /* H_max */
     int dedup_first;      /* 1: only the first return per contact voxel */
+    double shadow_cos;    /* 0: hemispherical shadow; c > 0: cone, cos(half-angle) = c */
 } orc_params;
 
 typedef struct {
@@ -243,9 +244,13 @@ void orc_bin_dir(const orc_params *p, int b, double out[3])
 }
 
 /* ------------------------------------------------------------------ */
-/* Sec. III-B: hemispherical shadow set.  Offset o is in the shadow of bin b
- * when its centre lies in the Euclidean ball of radius r_s around the
- * contact voxel and not in the half facing the sensor: o . u_b >= 0.    */
+/* Sec. III-B: shadow set.  Offset o is in the shadow of bin b when its
+ * centre lies in the Euclidean ball of radius r_s around the contact voxel
+ * and not in the half facing the sensor, o . u_b >= 0 (the hemisphere).
+ * The conical model of the same section (shadow_cos = c > 0) keeps, of that
+ * ball, the offsets within the half-angle acos(c) of the bin direction:
+ * o . u_b >= c |o| |u_b|.  u_b as returned by orc_bin_dir (not normalised
+ * for the octahedral scheme, so the hemisphere test is exact there).     */
 int orc_in_shadow(const orc_params *p, int b, int ox, int oy, int oz)
 {
     double r2 = (double)ox * ox + (double)oy * oy + (double)oz * oz;
@@ -254,7 +259,10 @@ int orc_in_shadow(const orc_params *p, int b, int ox, int oy, int oz)
     double u[3];
     orc_bin_dir(p, b, u);
     double dot = ((double)ox * u[0] + (double)oy * u[1]) + (double)oz * u[2];
-    return dot >= 0.0;
+    if (p->shadow_cos == 0.0)
+        return dot >= 0.0;
+    double uu = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
+    return dot >= p->shadow_cos * sqrt(r2 * uu);
 }
 
 /* ------------------------------------------------------------------ */
@@ -478,4 +486,183 @@ double orc_signed_distance(uint32_t mask, uint8_t sign, double res)
     for (int i = 0; i < 32; i++)
         bits += (mask >> i) & 1u;
     return (sign ? 1.0 : -1.0) * (double)bits * res;
+}
+
+/* ------------------------------------------------------------------ */
+/* Map export (Sec. III-C, Fig. 3): a triangle mesh of the iso-surface
+ * sdf = iso by Marching Cubes, the paper's export at iso = 0.
+ *
+ * Readings (the paper names the method only):
+ *   - the field is orc_signed_distance at the voxel centres; a cell is the
+ *     cube between 2 x 2 x 2 neighbouring centres, corner q (bit 0: +x,
+ *     bit 1: +y, bit 2: +z); a corner is inside when sdf < iso.
+ *   - the vertex on a crossed edge is linearly interpolated from its lower
+ *     corner a to its upper corner b: t = (iso - f_a) / (f_b - f_a),
+ *     coordinate = origin + res * ((index of a + 0.5) + t) along the edge's
+ *     axis, origin + res * (index + 0.5) on the other two, in binary64,
+ *     then rounded to float.
+ *   - the configuration table is derived from the cube: on each face, every
+ *     inside corner region (boundary walked counter-clockwise seen from
+ *     outside) is closed by a segment from the crossing where the walk
+ *     leaves it to the crossing where it entered it, so on a face with two
+ *     diagonal inside corners the inside corners stay apart; the same rule on
+ *     both cells sharing a face makes the surface closed.  The segments form
+ *     loops, walked from the lowest-numbered edge; a loop (e_0 .. e_m-1)
+ *     becomes the fan (e_0, e_i+1, e_i), i = 1 .. m-2, whose right-hand
+ *     normal points to the outside (sdf > iso).
+ *   - triangles are listed by cell in x-fastest order over the box, then in
+ *     table order.                                                       */
+
+#define ORC_MC_MAXT 12
+
+static int orc_mc_ntri[256];
+static int orc_mc_tri[256][ORC_MC_MAXT][3];
+static int orc_mc_built = 0;
+
+/* the 12 edges as (lower corner, upper corner): 4 along x, 4 along y, 4 along z */
+static const int orc_mc_edge_corner[12][2] = {
+    {0, 1}, {2, 3}, {4, 5}, {6, 7},
+    {0, 2}, {1, 3}, {4, 6}, {5, 7},
+    {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+
+/* faces -x, +x, -y, +y, -z, +z; corners counter-clockwise seen from outside */
+static const int orc_mc_face[6][4] = {
+    {0, 4, 6, 2}, {1, 3, 7, 5}, {0, 1, 5, 4}, {2, 6, 7, 3}, {0, 2, 3, 1}, {4, 5, 7, 6}};
+
+static int orc_mc_edge_of(int a, int b)
+{
+    for (int e = 0; e < 12; e++)
+        if ((orc_mc_edge_corner[e][0] == a && orc_mc_edge_corner[e][1] == b) ||
+            (orc_mc_edge_corner[e][0] == b && orc_mc_edge_corner[e][1] == a))
+            return e;
+    return -1;
+}
+
+static void orc_mc_build(void)
+{
+    for (int cfg = 0; cfg < 256; cfg++) {
+        int next[12];
+        for (int e = 0; e < 12; e++)
+            next[e] = -1;
+        for (int f = 0; f < 6; f++) {
+            int in[4], edge[4];
+            for (int k = 0; k < 4; k++) {
+                in[k] = (cfg >> orc_mc_face[f][k]) & 1;
+                edge[k] = orc_mc_edge_of(orc_mc_face[f][k], orc_mc_face[f][(k + 1) % 4]);
+            }
+            /* side k runs from corner k to corner k+1: it leaves an inside
+             * region when in[k] && !in[k+1], enters one when the reverse */
+            for (int k = 0; k < 4; k++) {
+                if (!(in[k] && !in[(k + 1) % 4]))
+                    continue;
+                for (int back = 1; back <= 4; back++) {
+                    int j = (k - back + 4) % 4;
+                    if (!in[j] && in[(j + 1) % 4]) {
+                        next[edge[k]] = edge[j];
+                        break;
+                    }
+                }
+            }
+        }
+        int used[12] = {0};
+        int nt = 0;
+        for (int e0 = 0; e0 < 12; e0++) {
+            if (next[e0] < 0 || used[e0])
+                continue;
+            int loop[12], m = 0;
+            int e = e0;
+            while (!used[e]) {
+                used[e] = 1;
+                loop[m++] = e;
+                e = next[e];
+            }
+            for (int i = 1; i + 1 < m; i++) {
+                orc_mc_tri[cfg][nt][0] = loop[0];
+                orc_mc_tri[cfg][nt][1] = loop[i + 1];
+                orc_mc_tri[cfg][nt][2] = loop[i];
+                nt++;
+            }
+        }
+        orc_mc_ntri[cfg] = nt;
+    }
+    orc_mc_built = 1;
+}
+
+/* Triangles of configuration cfg (bit q set: corner q inside) as edge ids;
+ * returns their number.  tri may be NULL.                                 */
+int orc_mc_config(int cfg, int *tri)
+{
+    if (!orc_mc_built)
+        orc_mc_build();
+    if (tri)
+        for (int t = 0; t < orc_mc_ntri[cfg]; t++)
+            for (int v = 0; v < 3; v++)
+                tri[3 * t + v] = orc_mc_tri[cfg][t][v];
+    return orc_mc_ntri[cfg];
+}
+
+static double orc_sdf_at(const orc_grid *g, int64_t x, int64_t y, int64_t z)
+{
+    int64_t v = (z * g->ny + y) * g->nx + x;
+    return orc_signed_distance(g->mask[v], g->sign[v], g->res);
+}
+
+/* Signed distance of every voxel of the box [x0, x0+bx) x [y0, y0+by) x
+ * [z0, z0+bz) into out[(z * by + y) * bx + x] (float).                    */
+void orc_sdf_field(const orc_grid *g, const int64_t box[6], float *out)
+{
+    for (int64_t z = 0; z < box[5]; z++)
+        for (int64_t y = 0; y < box[4]; y++)
+            for (int64_t x = 0; x < box[3]; x++)
+                out[(z * box[4] + y) * box[3] + x] =
+                    (float)orc_sdf_at(g, box[0] + x, box[1] + y, box[2] + z);
+}
+
+/* Marching Cubes over the cells of the voxel box (x0, y0, z0, bx, by, bz):
+ * cells (i, j, k) with corners inside the box, numbered
+ * L = (k (by - 1) + j) (bx - 1) + i.  Writes up to max_tri triangles (9
+ * floats each: three xyz vertices in the map frame) to tri and, if cell is
+ * not NULL, the cell number L of each; returns the total number of
+ * triangles of the box.                                                   */
+int64_t orc_mesh(const orc_grid *g, const int64_t box[6], double iso, float *tri,
+                 int64_t max_tri, int64_t *cell)
+{
+    if (!orc_mc_built)
+        orc_mc_build();
+    int64_t cx = box[3] - 1, cy = box[4] - 1, cz = box[5] - 1;
+    if (cx < 1 || cy < 1 || cz < 1)
+        return 0;
+    int64_t n = 0;
+    for (int64_t k = 0; k < cz; k++)
+        for (int64_t j = 0; j < cy; j++)
+            for (int64_t i = 0; i < cx; i++) {
+                int64_t base[3] = {box[0] + i, box[1] + j, box[2] + k};
+                double f[8];
+                int cfg = 0;
+                for (int q = 0; q < 8; q++) {
+                    f[q] = orc_sdf_at(g, base[0] + (q & 1), base[1] + ((q >> 1) & 1),
+                                      base[2] + ((q >> 2) & 1));
+                    if (f[q] < iso)
+                        cfg |= 1 << q;
+                }
+                for (int t = 0; t < orc_mc_ntri[cfg]; t++, n++) {
+                    if (n >= max_tri)
+                        continue;
+                    for (int v = 0; v < 3; v++) {
+                        int e = orc_mc_tri[cfg][t][v];
+                        int a = orc_mc_edge_corner[e][0], b = orc_mc_edge_corner[e][1];
+                        int axis = e / 4;
+                        double tt = (iso - f[a]) / (f[b] - f[a]);
+                        for (int d = 0; d < 3; d++) {
+                            double idx = (double)(base[d] + ((a >> d) & 1)) + 0.5;
+                            if (d == axis)
+                                idx = idx + tt;
+                            tri[9 * n + 3 * v + d] = (float)(g->origin[d] + g->res * idx);
+                        }
+                    }
+                    if (cell)
+                        cell[n] = (k * cy + j) * cx + i;
+                }
+            }
+    return n;
 }

@@ -135,19 +135,26 @@ static dbt_status check_params(const dbt_params *p) {
     if (p->dedup_first != 0 && p->dedup_first != 1)
         return fail(DBT_EINVAL, "dedup_first must be 0 or 1");
     if (p->reserved != 0) return fail(DBT_EINVAL, "reserved must be 0");
+    if (!(p->shadow_cos >= 0.0 && p->shadow_cos <= 1.0))
+        return fail(DBT_EINVAL, "shadow_cos must be in [0, 1]");
     return DBT_OK;
 }
 
 // Shadow membership of offset o for bin b (Sec. III-B): |o|^2 <= r_s^2 and
-// o . u_b >= 0, the sign decided exactly (octahedral: integer decode).
+// o . v_b >= c sqrt(|o|^2 |v_b|^2), c = shadow_cos (0: the hemisphere).
+// Octahedral v_b is the integer decode of the cell centre (n times u_b), so
+// the hemisphere's sign test is exact; the cone compares in binary64.
 static bool in_shadow(const dbt_params *p, const double azel_u[3], const long long octa_v[3],
                       int ox, int oy, int oz) {
     double r2 = (double)ox * ox + (double)oy * oy + (double)oz * oz;
     if (!(r2 <= p->shadow_radius * p->shadow_radius)) return false;
-    if (p->scheme == DBT_BINS_OCTA)
-        return (long long)ox * octa_v[0] + (long long)oy * octa_v[1] + (long long)oz * octa_v[2] >= 0;
-    double dot = ((double)ox * azel_u[0] + (double)oy * azel_u[1]) + (double)oz * azel_u[2];
-    return dot >= 0.0;
+    double v[3];
+    for (int i = 0; i < 3; ++i)
+        v[i] = p->scheme == DBT_BINS_OCTA ? (double)octa_v[i] : azel_u[i];
+    const double dot = ((double)ox * v[0] + (double)oy * v[1]) + (double)oz * v[2];
+    if (p->shadow_cos == 0.0) return dot >= 0.0;
+    const double vv = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
+    return dot >= p->shadow_cos * std::sqrt(r2 * vv);
 }
 
 // Host tables: Eq. 3 masks by r^2 and the per-bin shadow offset lists.

@@ -181,13 +181,84 @@ __device__ __forceinline__ BrickSpan brick_span(int cx, int cy, int cz, int R) {
     return s;
 }
 
+// Bump of a per-brick counter; returns the counter's previous value, first:
+// this increment took it from 0.  AGG (batches, where many lanes of a warp
+// name one brick): lanes naming the same brick form one group whose lowest
+// lane adds the group size, each lane getting its rank in the group; all 32
+// lanes must call it together.  Without AGG (one scan: fewer collisions, and
+// the grid is too small to hide the extra latency) a plain atomic per lane.
+template <bool AGG>
+__device__ __forceinline__ uint32_t brick_add(uint32_t *ctr, uint32_t b, bool valid, bool &first) {
+    if constexpr (!AGG) {
+        const uint32_t old = valid ? atomicAdd(&ctr[b], 1u) : 1u;
+        first = valid && old == 0u;
+        return old;
+    } else {
+        const uint32_t key = valid ? b : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (valid && lane == leader) base = atomicAdd(&ctr[b], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        const uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+        first = valid && base == 0u && rank == 0u;
+        return base + rank;
+    }
+}
+
+// The (up to 2 x 4 x 4) bricks of each lane's pair span; f(valid, brick,
+// bx, by, bz) per brick.  AGG: enumerated in lock-step over the warp (steps
+// past a lane's own span call f with valid = false) so that brick_add sees
+// all lanes.
+template <bool AGG, typename F>
+__device__ __forceinline__ void for_pair_bricks(bool has, const BrickSpan &s, const DevGrid &g,
+                                                uint32_t b0, F f) {
+    const int sx = s.x1 - s.x0 + 1, sy = s.y1 - s.y0 + 1, sz = s.z1 - s.z0 + 1;
+    const int np = has ? sx * sy * sz : 0;
+    const int nsteps = AGG ? __reduce_max_sync(0xffffffffu, np) : np;
+    int ix = 0, iy = 0, iz = 0;
+    for (int j = 0; j < nsteps; ++j) {
+        const bool v = j < np;
+        const uint32_t b = v ? b0 + ((uint32_t)(s.z0 + iz) * g.nby + (s.y0 + iy)) * g.nbx + (s.x0 + ix)
+                             : 0u;
+        f(v, b, s.x0 + ix, s.y0 + iy, s.z0 + iz);
+        if (++ix == sx) {
+            ix = 0;
+            if (++iy == sy) {
+                iy = 0;
+                ++iz;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ K2
+// Pair counts per brick; a brick's first pair appends it to the touched list.
+template <bool AGG>
+__device__ __forceinline__ void count_pairs(const WsDev &ws, const DevGrid &g, uint32_t b0,
+                                            bool kept, const BrickSpan &s) {
+    for_pair_bricks<AGG>(kept, s, g, b0, [&](bool v, uint32_t b, int, int, int) {
+        bool first;
+        brick_add<AGG>(ws.bcnt, b, v, first);
+        if (first) {
+            const uint32_t tt = atomicAdd(&ws.hdr->n_touched, 1u);
+            if (tt < ws.max_touched) ws.touched[tt] = b;
+            else atomicOr(&ws.hdr->err, ERR_TOUCHED_OVERFLOW);
+        }
+    });
+}
+
 __global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, WsDev ws,
                                                uint32_t hcap) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool kept = false;
+    int rx = 0, ry = 0, rz = 0;
     if (i < n) {
         int4 r = ws.prec[i];
+        rx = r.x;
+        ry = r.y;
+        rz = r.z;
         if (r.x >= 0) {
             kept = true;
             if (p.dedup && !hash_is_first(ws, hcap, voxel_key(g, r.x, r.y, r.z), (uint32_t)i)) {
@@ -195,21 +266,9 @@ __global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, Ws
                 r.w |= PREC_DUP;
                 ws.prec[i] = r;
             }
-            if (kept) {
-                const BrickSpan s = brick_span(r.x, r.y, r.z, p.R);
-                for (int bz = s.z0; bz <= s.z1; ++bz)
-                    for (int by = s.y0; by <= s.y1; ++by)
-                        for (int bx = s.x0; bx <= s.x1; ++bx) {
-                            const uint32_t b = ((uint32_t)bz * g.nby + by) * g.nbx + bx;
-                            if (atomicAdd(&ws.bcnt[b], 1u) == 0u) {
-                                const uint32_t tt = atomicAdd(&ws.hdr->n_touched, 1u);
-                                if (tt < ws.max_touched) ws.touched[tt] = b;
-                                else atomicOr(&ws.hdr->err, ERR_TOUCHED_OVERFLOW);
-                            }
-                        }
-            }
         }
     }
+    count_pairs<false>(ws, g, 0u, kept, kept ? brick_span(rx, ry, rz, p.R) : BrickSpan{});
     const unsigned bk = __ballot_sync(0xffffffffu, kept);
     if ((threadIdx.x & 31) == 0 && bk) atomicAdd(&ws.hdr->acc_kept, (unsigned long long)__popc(bk));
 }
@@ -262,30 +321,34 @@ __global__ void __launch_bounds__(256) k_alloc(WsDev ws) {
 // ------------------------------------------------------------------ K4
 // Pair payload: contact relative to the brick corner plus R (x: 6 bits,
 // y, z: 5 bits each) and the bin (16 bits).
+// Pair payloads into the segments, slots from the per-brick cursors.
+template <bool AGG>
+__device__ __forceinline__ void fill_pairs(const WsDev &ws, const DevGrid &g, uint32_t b0,
+                                           const DevParams &p, bool has, int4 r) {
+    const uint32_t bin = (uint32_t)(r.w & 0xFFFF);
+    for_pair_bricks<AGG>(has, has ? brick_span(r.x, r.y, r.z, p.R) : BrickSpan{}, g, b0,
+                    [&](bool v, uint32_t b, int bx, int by, int bz) {
+        bool first;
+        const uint32_t slot = brick_add<AGG>(ws.bcnt, b, v, first);
+        if (v) {
+            const unsigned long long pos = (unsigned long long)ws.boff[b] + slot;
+            const uint32_t rx = (uint32_t)(r.x - bx * BX + p.R);
+            const uint32_t ry = (uint32_t)(r.y - by * BY + p.R);
+            const uint32_t rz = (uint32_t)(r.z - bz * BZ + p.R);
+            if (pos < ws.pairs_cap)
+                ws.pairs[pos] = rx | (ry << 6) | (rz << 11) | (bin << 16);
+            else
+                atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
+        }
+    });
+}
+
 __global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, WsDev ws,
                                               uint32_t hcap) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        const int4 r = ws.prec[i];
-        if (r.x >= 0 && !(r.w & PREC_DUP)) {
-            const uint32_t bin = (uint32_t)(r.w & 0xFFFF);
-            const BrickSpan s = brick_span(r.x, r.y, r.z, p.R);
-            for (int bz = s.z0; bz <= s.z1; ++bz)
-                for (int by = s.y0; by <= s.y1; ++by)
-                    for (int bx = s.x0; bx <= s.x1; ++bx) {
-                        const uint32_t b = ((uint32_t)bz * g.nby + by) * g.nbx + bx;
-                        const uint32_t slot = atomicAdd(&ws.bcnt[b], 1u);
-                        const unsigned long long pos = (unsigned long long)ws.boff[b] + slot;
-                        const uint32_t rx = (uint32_t)(r.x - bx * BX + p.R);
-                        const uint32_t ry = (uint32_t)(r.y - by * BY + p.R);
-                        const uint32_t rz = (uint32_t)(r.z - bz * BZ + p.R);
-                        if (pos < ws.pairs_cap)
-                            ws.pairs[pos] = rx | (ry << 6) | (rz << 11) | (bin << 16);
-                        else
-                            atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
-                    }
-        }
-    }
+    int4 r = make_int4(-1, 0, 0, 0);
+    if (i < n) r = ws.prec[i];
+    fill_pairs<false>(ws, g, 0u, p, r.x >= 0 && !(r.w & PREC_DUP), r);
     if (p.dedup) {
         const uint32_t stride = gridDim.x * blockDim.x;
         for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < hcap; j += stride) {
@@ -365,6 +428,9 @@ __global__ void __launch_bounds__(256) k_count_b(BatchDev bd, DevParams p, long 
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool kept = false;
     int item = -1;
+    DevGrid gk = {};
+    uint32_t b0k = 0;
+    BrickSpan sk = {};
     if (i < n) {
         item = item_of(bd, i);
         int4 r = ws.prec[i];
@@ -378,21 +444,13 @@ __global__ void __launch_bounds__(256) k_count_b(BatchDev bd, DevParams p, long 
                 ws.prec[i] = r;
             }
             if (kept) {
-                const uint32_t b0 = bd.bbase[gi];
-                const BrickSpan s = brick_span(r.x, r.y, r.z, p.R);
-                for (int bz = s.z0; bz <= s.z1; ++bz)
-                    for (int by = s.y0; by <= s.y1; ++by)
-                        for (int bx = s.x0; bx <= s.x1; ++bx) {
-                            const uint32_t b = b0 + ((uint32_t)bz * g.nby + by) * g.nbx + bx;
-                            if (atomicAdd(&ws.bcnt[b], 1u) == 0u) {
-                                const uint32_t tt = atomicAdd(&ws.hdr->n_touched, 1u);
-                                if (tt < ws.max_touched) ws.touched[tt] = b;
-                                else atomicOr(&ws.hdr->err, ERR_TOUCHED_OVERFLOW);
-                            }
-                        }
+                gk = g;
+                b0k = bd.bbase[gi];
+                sk = brick_span(r.x, r.y, r.z, p.R);
             }
         }
     }
+    count_pairs<true>(ws, gk, b0k, kept, sk);
     const unsigned bk = __ballot_sync(0xffffffffu, kept);
     if ((threadIdx.x & 31) == 0 && bk) atomicAdd(&ws.hdr->acc_kept, (unsigned long long)__popc(bk));
     add_item_counts(bd, item, kept, false, &ItemCounters::kept, nullptr);
@@ -401,30 +459,17 @@ __global__ void __launch_bounds__(256) k_count_b(BatchDev bd, DevParams p, long 
 __global__ void __launch_bounds__(256) k_fill_b(BatchDev bd, DevParams p, long long n, WsDev ws,
                                                 uint32_t hcap) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        const int4 r = ws.prec[i];
-        if (r.x >= 0 && !(r.w & PREC_DUP)) {
-            const int gi = (r.w >> 16) & 0xFF;
-            const DevGrid g = bd.grids[gi];
-            const uint32_t b0 = bd.bbase[gi];
-            const uint32_t bin = (uint32_t)(r.w & 0xFFFF);
-            const BrickSpan s = brick_span(r.x, r.y, r.z, p.R);
-            for (int bz = s.z0; bz <= s.z1; ++bz)
-                for (int by = s.y0; by <= s.y1; ++by)
-                    for (int bx = s.x0; bx <= s.x1; ++bx) {
-                        const uint32_t b = b0 + ((uint32_t)bz * g.nby + by) * g.nbx + bx;
-                        const uint32_t slot = atomicAdd(&ws.bcnt[b], 1u);
-                        const unsigned long long pos = (unsigned long long)ws.boff[b] + slot;
-                        const uint32_t rx = (uint32_t)(r.x - bx * BX + p.R);
-                        const uint32_t ry = (uint32_t)(r.y - by * BY + p.R);
-                        const uint32_t rz = (uint32_t)(r.z - bz * BZ + p.R);
-                        if (pos < ws.pairs_cap)
-                            ws.pairs[pos] = rx | (ry << 6) | (rz << 11) | (bin << 16);
-                        else
-                            atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
-                    }
-        }
+    int4 r = make_int4(-1, 0, 0, 0);
+    if (i < n) r = ws.prec[i];
+    const bool has = r.x >= 0 && !(r.w & PREC_DUP);
+    DevGrid g = {};
+    uint32_t b0 = 0;
+    if (has) {
+        const int gi = (r.w >> 16) & 0xFF;
+        g = bd.grids[gi];
+        b0 = bd.bbase[gi];
     }
+    fill_pairs<true>(ws, g, b0, p, has, r);
     if (p.dedup) {
         const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
         for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;

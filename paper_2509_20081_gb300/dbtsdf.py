@@ -33,7 +33,7 @@ class dbt_params(ctypes.Structure):
                 ("bins_a", ctypes.c_int32), ("bins_b", ctypes.c_int32),
                 ("shadow_radius", ctypes.c_double), ("hit_threshold", ctypes.c_int32),
                 ("hit_max", ctypes.c_int32), ("dedup_first", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("shadow_cos", ctypes.c_double)]
 
 
 class dbt_grid(ctypes.Structure):
@@ -156,9 +156,9 @@ def dbt_grid_init(grid: "Grid", stream=None):
 
 
 def make_params(kernel_size=11, scheme=DBT_BINS_OCTA, bins_a=8, bins_b=8, shadow_radius=3.0,
-                hit_threshold=3, hit_max=255, dedup_first=1) -> dbt_params:
+                hit_threshold=3, hit_max=255, dedup_first=1, shadow_cos=0.0) -> dbt_params:
     return dbt_params(kernel_size, scheme, bins_a, bins_b, float(shadow_radius), hit_threshold,
-                      hit_max, dedup_first, 0)
+                      hit_max, dedup_first, 0, float(shadow_cos))
 
 
 def dbt_tables_host(params: dbt_params):

@@ -32,6 +32,9 @@ TABLE_CASES = [
     dict(kernel_size=21, scheme=1, bins_a=40, bins_b=40, shadow_radius=3.0),
     dict(kernel_size=11, scheme=1, bins_a=36, bins_b=18, shadow_radius=4.0),
     dict(kernel_size=5, scheme=1, bins_a=7, bins_b=5, shadow_radius=2.0),
+    dict(kernel_size=11, scheme=0, bins_a=8, bins_b=8, shadow_radius=5.0, shadow_cos=0.5),
+    dict(kernel_size=21, scheme=1, bins_a=40, bins_b=40, shadow_radius=8.0, shadow_cos=0.9),
+    dict(kernel_size=15, scheme=0, bins_a=16, bins_b=16, shadow_radius=7.0, shadow_cos=1.0),
 ]
 
 
@@ -51,7 +54,8 @@ def test_tables_equal_oracle(orc, case):
     dict(kernel_size=4), dict(kernel_size=23), dict(kernel_size=0),
     dict(bins_a=8, bins_b=4), dict(scheme=7), dict(shadow_radius=-1.0),
     dict(shadow_radius=float("nan")), dict(hit_threshold=0), dict(hit_threshold=300),
-    dict(hit_max=70000), dict(dedup_first=2),
+    dict(hit_max=70000), dict(dedup_first=2), dict(shadow_cos=-0.1), dict(shadow_cos=1.5),
+    dict(shadow_cos=float("nan")),
 ])
 def test_bad_params_refused(bad):
     p = dbt.make_params(**bad)

@@ -112,6 +112,8 @@ def test_host_entry_point_matches(orc, room3):
     dict(kernel_size=21, scheme=1, bins_a=40, bins_b=40, shadow_radius=3.0),   # the paper's
     dict(kernel_size=15, scheme=1, bins_a=36, bins_b=18, shadow_radius=6.5),
     dict(kernel_size=17, scheme=0, bins_a=16, bins_b=16, shadow_radius=4.0),
+    dict(shadow_radius=5.0, shadow_cos=0.7),                                    # conical shadow
+    dict(kernel_size=21, scheme=1, bins_a=40, bins_b=40, shadow_radius=6.0, shadow_cos=0.5),
 ])
 def test_room_variants(orc, room3, variant):
     pd = params(**variant)

@@ -17,8 +17,14 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "dbtsdf_oracle.c")
 MUTATIONS = {
     "eq3_floor_not_ceil": ("int c = (int)ceil(r);", "int c = (int)floor(r);"),
     "eq3_shift_off_by_one": ("return 0xFFFFFFFFu >> (32 - c);", "return 0xFFFFFFFFu >> (31 - c);"),
-    "shadow_plane_excluded": ("    return dot >= 0.0;\n}", "    return dot > 0.0;\n}"),
-    "shadow_front_half": ("    return dot >= 0.0;\n}", "    return dot <= 0.0;\n}"),
+    "shadow_plane_excluded": ("return dot >= 0.0;\n    double uu", "return dot > 0.0;\n    double uu"),
+    "shadow_front_half": ("return dot >= 0.0;\n    double uu", "return dot <= 0.0;\n    double uu"),
+    "cone_squared_norm": ("return dot >= p->shadow_cos * sqrt(r2 * uu);",
+                          "return dot >= p->shadow_cos * (r2 * uu);"),
+    "cone_dir_norm_dropped": ("return dot >= p->shadow_cos * sqrt(r2 * uu);",
+                              "return dot >= p->shadow_cos * sqrt(r2);"),
+    "cone_ignored": ("    if (p->shadow_cos == 0.0)\n        return dot >= 0.0;",
+                     "    if (1)\n        return dot >= 0.0;"),
     "shadow_radius_strict": ("if (!(r2 <= p->shadow_radius * p->shadow_radius))",
                              "if (!(r2 < p->shadow_radius * p->shadow_radius))"),
     "eq6_strict_threshold": ("if (h_old < p->hit_threshold && h_new >= p->hit_threshold)\n"
@@ -63,6 +69,8 @@ def _battery(room):
         lambda: pins.test_ball_counts_oeis(orc),
         lambda: pins.test_shadow_radius_one(orc),
         lambda: pins.test_shadow_lies_behind_surface(orc),
+        lambda: pins.test_cone_exact_integer_form(orc, 1, 2),
+        lambda: pins.test_cone_narrows_to_the_ray(orc),
         lambda: pins.test_single_point_worked_example(orc),
         lambda: pins.test_brute_force_tiny_grids(orc, pins.CASES[0]),
         lambda: pins.test_brute_force_tiny_grids(orc, pins.CASES[1]),

@@ -190,6 +190,64 @@ def test_shadow_radius_zero(orc):
     assert S.sum() == 64 and all(S[b, 3, 3, 3] for b in range(64))
 
 
+def test_cone_zero_is_hemisphere(orc):
+    """shadow_cos = 0 is the hemisphere itself (half-angle 90 degrees)."""
+    for scheme, a, b in ((orc.SCHEME_OCTA, 8, 8), (orc.SCHEME_AZEL, 40, 40)):
+        h = orc.shadow_table(orc.params(kernel_size=11, scheme=scheme, bins_a=a, bins_b=b,
+                                        shadow_radius=4.0))
+        c = orc.shadow_table(orc.params(kernel_size=11, scheme=scheme, bins_a=a, bins_b=b,
+                                        shadow_radius=4.0, shadow_cos=0.0))
+        np.testing.assert_array_equal(h, c)
+
+
+@pytest.mark.parametrize("num,den", [(1, 2), (3, 4), (1, 1)])
+def test_cone_exact_integer_form(orc, num, den):
+    """Octahedral bins: the cone o.v >= c |o| |v| with rational c = num/den is
+    o.v >= 0 and den^2 (o.v)^2 >= num^2 |o|^2 |v|^2 in integers; brute force
+    over every offset and bin (v = the integer cell-centre decode, whose
+    direction is pinned by test_octa_centre_round_trip)."""
+    K, n, rs = 11, 8, 5.0
+    p = orc.params(kernel_size=K, shadow_radius=rs, shadow_cos=num / den)
+    S = orc.shadow_table(p)
+    R = K // 2
+    for b in range(n * n):
+        v = np.round(orc.bin_dir(p, b)).astype(np.int64)
+        vv = int((v * v).sum())
+        for oz in range(-R, R + 1):
+            for oy in range(-R, R + 1):
+                for ox in range(-R, R + 1):
+                    r2 = ox * ox + oy * oy + oz * oz
+                    dot = int(ox * v[0] + oy * v[1] + oz * v[2])
+                    want = (r2 <= rs * rs and dot >= 0
+                            and den * den * dot * dot >= num * num * r2 * vv)
+                    assert bool(S[b, oz + R, oy + R, ox + R]) == want, (b, ox, oy, oz)
+
+
+def test_cone_narrows_to_the_ray(orc):
+    """c = 1 keeps only offsets parallel to the bin direction (Cauchy-Schwarz
+    equality): at n = 2 the cell of (1, 1, 1) decodes to v = (1, 1, 0), so
+    exactly the offsets t v, t >= 0, inside the ball.  The sets shrink as c
+    grows and all hold the contact voxel: the conical model concentrates the
+    hits on the central voxel (Sec. III-B)."""
+    p1 = orc.params(kernel_size=11, bins_a=2, bins_b=2, shadow_radius=5.0, shadow_cos=1.0)
+    b = orc.bin_of(p1, (1, 1, 1))
+    assert list(np.round(orc.bin_dir(p1, b)).astype(int)) == [1, 1, 0]
+    S1 = orc.shadow_table(p1)
+    R = 5
+    v = np.round(orc.bin_dir(p1, b)).astype(np.int64)
+    got = {(ox - R, oy - R, oz - R) for oz, oy, ox in np.argwhere(S1[b])}
+    want = {tuple(int(t) * v) for t in range(0, 6)
+            if (t * v * t * v).sum() <= 25 and all(abs(t * v) <= R)}
+    assert got == want
+    prev = None
+    for c in (0.0, 0.3, 0.6, 0.9, 1.0):
+        S = orc.shadow_table(orc.params(kernel_size=11, shadow_radius=5.0, shadow_cos=c))
+        assert all(S[bb, R, R, R] for bb in range(64))
+        if prev is not None:
+            assert not (S & ~prev).any() and S.sum() < prev.sum()
+        prev = S
+
+
 # ------------------------------------------------------------------ worked example
 def test_single_point_worked_example(orc):
     g = orc.Grid.create(5, 5, 5, 1.0)
