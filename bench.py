@@ -53,7 +53,7 @@ INTEGRATE_SRC = os.path.join(ROOT, "paper_2509_20081_gb300", "csrc", "integrate.
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_integrate, per kept
 # return, from the capture summarised under profiles/ (valid only for the
 # integrate.cu source with this sha256 prefix; otherwise traffic is null).
-NCU_TRAFFIC = {"integrate_sha": "ac7ebba84dea7e33", "bytes_per_kept_return": 1073.8,
+NCU_TRAFFIC = {"integrate_sha": "11885f291e10ebe7", "bytes_per_kept_return": 1074.5,
                "source": "profiles/k_integrate_urban_half.md (urban_half, 39.9 k kept returns "
                          "per scan, 42.9 MB DRAM read+write per launch), scaled by kept returns"}
 
@@ -490,6 +490,106 @@ def run_maps(args, rank, world):
     return 0
 
 
+def run_mesh(args, rank, world):
+    """Map export (Fig. 3: Marching Cubes at iso = 0) at the urban map's size:
+    a 1600 x 1600 x 320 stepped-terrain map state (819 M cells).  A step is
+    one dbt_mesh_extract of the whole map (count pass, scan, emit pass);
+    value = cells meshed per second.  Roofline: the count pass, 5 bytes read
+    per voxel (mask + sign)."""
+    import torch
+
+    import paper_2509_20081_gb300 as dbt
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    nx, ny, nz, res = 1600, 1600, 320, 0.05
+    m, s, _ = synth.terrain_state(nx, ny, nz, 21)
+    g = dbt.Grid(nx, ny, nz, res)
+    g.load(m, s)
+    B = dbt.dbtsdf
+    box = (B.ctypes.c_int32 * 6)(0, 0, 0, nx, ny, nz)
+    need = dbt.dbt_mesh_scratch_size(g)
+    scratch = torch.empty(need, dtype=torch.uint8, device=dev)
+    n = B.ctypes.c_int64()
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def extract(tri_ptr, cap):
+        B._check(B.lib().dbt_mesh_extract(B.ctypes.byref(g.c), box, 0.0, scratch.data_ptr(), need,
+                                          tri_ptr, None, cap, B.ctypes.byref(n), sp))
+    extract(None, 0)
+    ntri = int(n.value)
+    tri = torch.empty((ntri, 3, 3), dtype=torch.float32, device=dev)
+    host = torch.empty((ntri, 3, 3), dtype=torch.float32).pin_memory()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return sum(a.elapsed_time(b) for a, b in ev) / args.steps
+
+    clk = ClockSampler(dev.index or 0)
+    ms_count = timed(lambda: extract(None, 0))
+    ms_full = timed(lambda: extract(tri.data_ptr(), ntri))
+    sample = clk.stop()
+
+    def e2e():
+        extract(tri.data_ptr(), ntri)
+        host.copy_(tri, non_blocking=True)
+    ms_e2e = timed(e2e)
+    ms_full, ms_count, ms_e2e = max_over_ranks([ms_full, ms_count, ms_e2e], dev, world)
+    if rank != 0:
+        return 0
+    cells = (nx - 1) * (ny - 1) * (nz - 1)
+    vox = nx * ny * nz
+    peak, src = measured_peaks()
+    achieved = 5.0 * vox / (ms_count * 1e-3) / 1e9
+    line = {"metric": "map cells meshed/sec (Marching Cubes, iso = 0)",
+            "value": world * cells / (ms_full * 1e-3), "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_full,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"mesh: stepped terrain map {nx}x{ny}x{nz} at {res} m "
+                                   f"({cells / 1e6:.0f} M cells, {ntri} triangles)",
+                       "parallelism": f"replicas x{args.gpus}",
+                       "l2": "map (5.7 GB) larger than L2; no flush"},
+            "count_ms": ms_count, "emit_ms": ms_full - ms_count, "triangles": ntri,
+            "e2e": {"value": world * cells / (ms_e2e * 1e-3), "unit": "cells/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 36 * ntri + 8,
+                    "what": "extract + copy of the triangles to pinned host memory"},
+            "gpu_launches": 6 * args.steps,
+            "roofline": {"bound": "hbm", "kernel": "count pass (k_mc_count + scans)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "alg_bytes_per_launch": 5.0 * vox, "peak_source": src},
+            "clocks": sample}
+    if not args.no_cpu_baseline:
+        import oracle
+        og = oracle.Grid(nx, ny, nz, res, (0.0, 0.0, 0.0), m, s, None)
+        t0 = time.perf_counter()
+        done = 0
+        z0 = 0
+        while time.perf_counter() - t0 < args.cpu_budget and z0 + 2 <= nz:
+            oracle.mesh(og, box=(0, 0, z0, nx, ny, 2))
+            done += (nx - 1) * (ny - 1)
+            z0 += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / dt, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {z0} cell layers of the map, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(args, rank, world):
     """16 robots with resident maps, Poisson scan arrivals (10-20 Hz each),
     replayed at several speed-ups: continuous batching (2 streams, rounds of
@@ -560,7 +660,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["urban", "urban_half", "highres", "maps", "serving"],
+    ap.add_argument("--workload",
+                    choices=["urban", "urban_half", "highres", "maps", "serving", "mesh"],
                     default="urban")
     ap.add_argument("--maps", type=int, default=32, help="maps workload: number of maps")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: simulated seconds")
@@ -589,6 +690,8 @@ def main():
             return run_maps(args, rank, world)
         if args.workload == "serving":
             return run_serving(args, rank, world)
+        if args.workload == "mesh":
+            return run_mesh(args, rank, world)
         return run_ours(args, rank, world)
     finally:
         if world > 1:

@@ -291,6 +291,47 @@ dbt_status dbt_read_voxels(const dbt_grid *g, const int32_t *d_idx, int64_t n, u
 dbt_status dbt_read_distance(const dbt_grid *g, const int32_t *d_idx, int64_t n, float *d_sdf,
                              void *stream);
 
+/* ---- Map export (Sec. III-C, Fig. 3: the map is exported as a mesh by
+ * Marching Cubes at iso = 0) ----
+ *
+ * A box is int32 {x0, y0, z0, bx, by, bz}: the voxels [x0, x0+bx) x
+ * [y0, y0+by) x [z0, z0+bz), inside the grid (EINVAL otherwise). */
+
+/* Signed distance (the readout of dbt_read_distance) of every voxel of the
+ * box into d_out[(z * by + y) * bx + x], float32, caller-owned.  Async. */
+dbt_status dbt_sdf_field(const dbt_grid *g, const int32_t box[6], float *d_out, void *stream);
+
+/* Bytes of device scratch dbt_mesh_extract needs for this box. */
+dbt_status dbt_mesh_scratch_size(const dbt_grid *g, const int32_t box[6], size_t *bytes);
+
+/* Marching Cubes over the cells of the box (the (bx-1)(by-1)(bz-1) cubes
+ * between voxel centres, numbered L = (k (by-1) + j) (bx-1) + i).  A corner
+ * is inside when its sdf < iso; the vertex on a crossed edge from lower
+ * corner a to upper corner b is at t = (iso - f_a) / (f_b - f_a) (binary64,
+ * rounded to float); vertices are in the map frame (origin + res * (index +
+ * 0.5) at voxel centres).  Triangles are ordered by cell, then by the
+ * configuration table (dbt_mesh_table); each is 9 floats (three xyz
+ * vertices) whose right-hand normal points to sdf > iso, and the surface of
+ * the box is closed except where it meets the box's faces.
+ *   d_scratch   >= dbt_mesh_scratch_size bytes, 256-byte aligned.
+ *   d_tri       room for max_tri triangles (9 floats each); may be NULL when
+ *               max_tri == 0 (count only).
+ *   d_cell      NULL, or room for max_tri int64 cell numbers L.
+ *   h_ntri      (host) the box's total triangle count; when it exceeds
+ *               max_tri only the first max_tri are written.
+ * Blocks until the count is known (the triangles are written asynchronously
+ * afterwards on stream). */
+dbt_status dbt_mesh_extract(const dbt_grid *g, const int32_t box[6], double iso, void *d_scratch,
+                            size_t scratch_bytes, float *d_tri, int64_t *d_cell, int64_t max_tri,
+                            int64_t *h_ntri, void *stream);
+
+/* The Marching Cubes configuration table: h_ntri[256] triangles per
+ * configuration (bit q set = corner q inside, q = x | 2y | 4z) and
+ * h_edges[256 * 15] their edge ids, 3 per triangle.  Edge 4 a + j runs along
+ * axis a from corner lo to lo + 2^a, lo = (j&1)<<1 | (j>>1)<<2 (a = 0),
+ * (j&1) | (j>>1)<<2 (a = 1), j (a = 2). */
+dbt_status dbt_mesh_table(uint8_t *h_ntri, uint8_t *h_edges);
+
 /* Synchronises stream and reports a latched device error of the workspace
  * (ws may be NULL to only synchronise). */
 dbt_status dbt_sync(void *stream, const dbt_workspace *ws);

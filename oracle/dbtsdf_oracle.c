@@ -507,9 +507,12 @@ double orc_signed_distance(uint32_t mask, uint8_t sign, double res)
  *     leaves it to the crossing where it entered it, so on a face with two
  *     diagonal inside corners the inside corners stay apart; the same rule on
  *     both cells sharing a face makes the surface closed.  The segments form
- *     loops, walked from the lowest-numbered edge; a loop (e_0 .. e_m-1)
- *     becomes the fan (e_0, e_i+1, e_i), i = 1 .. m-2, whose right-hand
- *     normal points to the outside (sdf > iso).
+ *     loops, walked from the lowest-numbered edge.  A loop is cut into a fan
+ *     from its first vertex whose diagonals all avoid joining two edges of
+ *     one face (such a diagonal would lie in the face, where the neighbouring
+ *     cell's surface meets it); with that apex first, (e_0 .. e_m-1) becomes
+ *     (e_0, e_i+1, e_i), i = 1 .. m-2, whose right-hand normal points to the
+ *     outside (sdf > iso).
  *   - triangles are listed by cell in x-fastest order over the box, then in
  *     table order.                                                       */
 
@@ -536,6 +539,22 @@ static int orc_mc_edge_of(int a, int b)
             (orc_mc_edge_corner[e][0] == b && orc_mc_edge_corner[e][1] == a))
             return e;
     return -1;
+}
+
+/* 1 when edges e and f lie on a common face of the cube */
+static int orc_mc_share_face(int e, int f)
+{
+    for (int k = 0; k < 6; k++) {
+        int ne = 0, nf = 0;
+        for (int c = 0; c < 4; c++) {
+            int q = orc_mc_face[k][c];
+            ne += q == orc_mc_edge_corner[e][0] || q == orc_mc_edge_corner[e][1];
+            nf += q == orc_mc_edge_corner[f][0] || q == orc_mc_edge_corner[f][1];
+        }
+        if (ne == 2 && nf == 2)
+            return 1;
+    }
+    return 0;
 }
 
 static void orc_mc_build(void)
@@ -576,10 +595,24 @@ static void orc_mc_build(void)
                 loop[m++] = e;
                 e = next[e];
             }
+            int apex = 0;
+            for (int a = 0; a < m; a++) {
+                int ok = 1;
+                for (int k = 2; k + 1 < m; k++)
+                    if (orc_mc_share_face(loop[a], loop[(a + k) % m]))
+                        ok = 0;
+                if (ok) {
+                    apex = a;
+                    break;
+                }
+            }
+            int r[12];
+            for (int i = 0; i < m; i++)
+                r[i] = loop[(apex + i) % m];
             for (int i = 1; i + 1 < m; i++) {
-                orc_mc_tri[cfg][nt][0] = loop[0];
-                orc_mc_tri[cfg][nt][1] = loop[i + 1];
-                orc_mc_tri[cfg][nt][2] = loop[i];
+                orc_mc_tri[cfg][nt][0] = r[0];
+                orc_mc_tri[cfg][nt][1] = r[i + 1];
+                orc_mc_tri[cfg][nt][2] = r[i];
                 nt++;
             }
         }

@@ -977,6 +977,103 @@ extern "C" dbt_status dbt_read_distance(const dbt_grid *g, const int32_t *d_idx,
     return DBT_OK;
 }
 
+// ------------------------------------------------------------------ export
+static dbt_status export_box(const dbt_grid *g, const int32_t box[6], ExportBox *b) {
+    if (!box) return fail(DBT_EINVAL, "box is NULL");
+    for (int a = 0; a < 3; ++a) {
+        const int n = a == 0 ? g->nx : a == 1 ? g->ny : g->nz;
+        if (box[a] < 0 || box[a + 3] < 0 || (long long)box[a] + box[a + 3] > n)
+            return fail(DBT_EINVAL, "box axis %d outside the grid", a);
+    }
+    b->x0 = box[0];
+    b->y0 = box[1];
+    b->z0 = box[2];
+    b->bx = box[3];
+    b->by = box[4];
+    b->bz = box[5];
+    b->cx = std::max(0, box[3] - 1);
+    b->cy = std::max(0, box[4] - 1);
+    b->cz = std::max(0, box[5] - 1);
+    b->ncell = b->cx * b->cy * b->cz;
+    return DBT_OK;
+}
+
+// Inside bits over (sign, popcount): bit s * 33 + p is (s ? p : -p) * res < iso.
+static void inside_lut(double res, double iso, uint64_t *lut0, uint64_t *lut1) {
+    *lut0 = 0;
+    *lut1 = 0;
+    for (int s = 0; s < 2; ++s)
+        for (int p = 0; p <= 32; ++p) {
+            const double f = (s ? 1.0 : -1.0) * (double)p * res;
+            if (f < iso) {
+                const int idx = s * 33 + p;
+                if (idx < 64) *lut0 |= 1ull << idx;
+                else *lut1 |= 1ull << (idx - 64);
+            }
+        }
+}
+
+extern "C" dbt_status dbt_sdf_field(const dbt_grid *g, const int32_t box[6], float *d_out,
+                                    void *stream) {
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    ExportBox b;
+    if ((st = export_box(g, box, &b)) != DBT_OK) return st;
+    if ((long long)b.bx * b.by * b.bz > 0 && !d_out) return fail(DBT_EINVAL, "d_out is NULL");
+    launch_sdf_field(dev_grid(g), g->res, b, d_out, (cudaStream_t)stream);
+    DBT_CUDA(cudaGetLastError());
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_mesh_scratch_size(const dbt_grid *g, const int32_t box[6],
+                                            size_t *bytes) {
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    ExportBox b;
+    if ((st = export_box(g, box, &b)) != DBT_OK) return st;
+    if (!bytes) return fail(DBT_EINVAL, "bytes is NULL");
+    *bytes = mc_scratch_bytes(b);
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_mesh_extract(const dbt_grid *g, const int32_t box[6], double iso,
+                                       void *d_scratch, size_t scratch_bytes, float *d_tri,
+                                       int64_t *d_cell, int64_t max_tri, int64_t *h_ntri,
+                                       void *stream) {
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    ExportBox b;
+    if ((st = export_box(g, box, &b)) != DBT_OK) return st;
+    if (!std::isfinite(iso)) return fail(DBT_EINVAL, "iso must be finite");
+    if (!h_ntri) return fail(DBT_EINVAL, "h_ntri is NULL");
+    if (max_tri < 0) return fail(DBT_EINVAL, "max_tri < 0");
+    if (max_tri > 0 && !d_tri) return fail(DBT_EINVAL, "d_tri is NULL with max_tri > 0");
+    if (!d_scratch || !aligned256(d_scratch)) return fail(DBT_EINVAL, "scratch must be 256-byte aligned");
+    if (scratch_bytes < mc_scratch_bytes(b)) return fail(DBT_EINVAL, "scratch too small");
+    const cudaStream_t s = (cudaStream_t)stream;
+    const DevGrid dg = dev_grid(g);
+    uint64_t lut0, lut1;
+    inside_lut(g->res, iso, &lut0, &lut1);
+    launch_mc_count(dg, b, lut0, lut1, d_scratch, s);
+    DBT_CUDA(cudaGetLastError());
+    unsigned long long total = 0;
+    DBT_CUDA(cudaMemcpyAsync(&total, mc_total_ptr(d_scratch), sizeof(total), cudaMemcpyDeviceToHost, s));
+    DBT_CUDA(cudaStreamSynchronize(s));
+    *h_ntri = (int64_t)total;
+    if (max_tri > 0 && total > 0) {
+        launch_mc_emit(dg, b, g->res, iso, lut0, lut1, d_scratch, d_tri, (long long *)d_cell,
+                       (long long)max_tri, s);
+        DBT_CUDA(cudaGetLastError());
+    }
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_mesh_table(uint8_t *h_ntri, uint8_t *h_edges) {
+    if (!h_ntri || !h_edges) return fail(DBT_EINVAL, "NULL output");
+    mc_table_host(h_ntri, h_edges);
+    return DBT_OK;
+}
+
 extern "C" const char *dbt_last_error(void) { return t_err; }
 
-extern "C" const char *dbt_version(void) { return "dbtsdf 0.1.0 sm_103a"; }
+extern "C" const char *dbt_version(void) { return "dbtsdf 0.2.0 sm_103a"; }

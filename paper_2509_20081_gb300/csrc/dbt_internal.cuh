@@ -3,6 +3,7 @@
 // pose and the integration workspace.
 #pragma once
 
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -185,6 +186,22 @@ void launch_read_voxels(const DevGrid &g, const int *idx, long long n, uint32_t 
                         uint8_t *sign, uint16_t *hits, cudaStream_t s);
 void launch_read_distance(const DevGrid &g, double res, const int *idx, long long n, float *sdf,
                           cudaStream_t s);
+
+// Map export (export.cu).  A box of voxels [x0, x0+bx) x ...; its cells are
+// the cx x cy x cz = (bx-1)(by-1)(bz-1) cubes between voxel centres.
+struct ExportBox {
+    int x0, y0, z0, bx, by, bz;
+    long long cx, cy, cz, ncell;
+};
+void launch_sdf_field(const DevGrid &g, double res, const ExportBox &b, float *out, cudaStream_t s);
+size_t mc_scratch_bytes(const ExportBox &b);
+void launch_mc_count(const DevGrid &g, const ExportBox &b, uint64_t lut0, uint64_t lut1,
+                     void *scratch, cudaStream_t s);
+void launch_mc_emit(const DevGrid &g, const ExportBox &b, double res, double iso, uint64_t lut0,
+                    uint64_t lut1, void *scratch, float *tri, long long *cell, long long max_tri,
+                    cudaStream_t s);
+const unsigned long long *mc_total_ptr(void *scratch);
+void mc_table_host(uint8_t *ntri, uint8_t *edges);
 
 // Sets the thread's error message for a failed CUDA call; returns DBT_ECUDA.
 dbt_status report_cuda_error(cudaError_t e, const char *what);

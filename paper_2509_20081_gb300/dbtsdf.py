@@ -94,6 +94,11 @@ _SIGS = {
                                    _P(dbt_scan_stats), _vp],
     "dbt_scan_footprint": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
                            _vp, ctypes.c_size_t, _P(ctypes.c_int64), _vp],
+    "dbt_sdf_field": [_P(dbt_grid), _P(ctypes.c_int32), _vp, _vp],
+    "dbt_mesh_scratch_size": [_P(dbt_grid), _P(ctypes.c_int32), _P(ctypes.c_size_t)],
+    "dbt_mesh_extract": [_P(dbt_grid), _P(ctypes.c_int32), ctypes.c_double, _vp, ctypes.c_size_t,
+                         _vp, _vp, ctypes.c_int64, _P(ctypes.c_int64), _vp],
+    "dbt_mesh_table": [_vp, _vp],
 }
 
 _lib = None
@@ -210,6 +215,14 @@ def dbt_bin_directions(kernels: Kernels, dirs, stream=None):
     return out
 
 
+class _nullctx:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
 class Grid:
     """Dense SoA grid in torch device memory: mask u32, sign u8, hits u16,
     each shaped (nz, ny, pitch_x)."""
@@ -231,6 +244,24 @@ class Grid:
                           nx, ny, nz, pitch, self.res, (ctypes.c_double * 3)(*self.origin))
         if init:
             dbt_grid_init(self, stream)
+
+    def load(self, mask, sign, hits=None, stream=None):
+        """Sets the state from host arrays shaped (nz, ny, nx) (mask u32, sign
+        u8, hits u16; hits None = 0), e.g. a map saved with numpy()."""
+        import torch
+        shp = (self.nz, self.ny, self.nx)
+        for a in (mask, sign) + (() if hits is None else (hits,)):
+            if tuple(np.shape(a)) != shp:
+                raise ValueError(f"state arrays must be shaped {shp}")
+        with torch.cuda.stream(stream) if stream is not None else _nullctx():
+            self.mask[:, :, :self.nx].copy_(
+                torch.from_numpy(np.ascontiguousarray(mask, np.uint32).view(np.int32)))
+            self.sign[:, :, :self.nx].copy_(torch.from_numpy(np.ascontiguousarray(sign, np.uint8)))
+            if hits is None:
+                self.hits[:, :, :self.nx].zero_()
+            else:
+                self.hits[:, :, :self.nx].copy_(
+                    torch.from_numpy(np.ascontiguousarray(hits, np.uint16).view(np.int16)))
 
     def numpy(self):
         """Host copies without padding: (mask u32, sign u8, hits u16), (nz, ny, nx)."""
@@ -328,6 +359,67 @@ def dbt_read_distance(grid: Grid, idx, stream=None):
     _check(lib().dbt_read_distance(ctypes.byref(grid.c), i.data_ptr(), i.shape[0],
                                    out.data_ptr(), _stream_ptr(stream)))
     return out
+
+
+def _box(grid: Grid, box):
+    b = (0, 0, 0, grid.nx, grid.ny, grid.nz) if box is None else tuple(int(v) for v in box)
+    if len(b) != 6:
+        raise ValueError("box is (x0, y0, z0, bx, by, bz)")
+    return (ctypes.c_int32 * 6)(*b)
+
+
+def dbt_sdf_field(grid: Grid, box=None, stream=None):
+    """Signed distance of every voxel of the box, a (bz, by, bx) float32
+    tensor on the grid's device."""
+    import torch
+    b = _box(grid, box)
+    out = torch.empty((b[5], b[4], b[3]), dtype=torch.float32, device=grid.mask.device)
+    _check(lib().dbt_sdf_field(ctypes.byref(grid.c), b, out.data_ptr() if out.numel() else None,
+                               _stream_ptr(stream)))
+    return out
+
+
+def dbt_mesh_scratch_size(grid: Grid, box=None) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().dbt_mesh_scratch_size(ctypes.byref(grid.c), _box(grid, box), ctypes.byref(n)))
+    return int(n.value)
+
+
+def dbt_mesh_extract(grid: Grid, box=None, iso: float = 0.0, with_cells: bool = False,
+                     scratch=None, stream=None):
+    """Marching Cubes at iso over the box (two passes: count, then emit into
+    a buffer of exactly that size).  Returns (triangles (t, 3, 3) float32,
+    cell numbers (t,) int64 or None) on the grid's device."""
+    import torch
+    dev = grid.mask.device
+    b = _box(grid, box)
+    need = dbt_mesh_scratch_size(grid, box)
+    if scratch is None or scratch.numel() < need:
+        scratch = torch.empty(need, dtype=torch.uint8, device=dev)
+    n = ctypes.c_int64()
+    sp = _stream_ptr(stream)
+    _check(lib().dbt_mesh_extract(ctypes.byref(grid.c), b, float(iso), scratch.data_ptr(), need,
+                                  None, None, 0, ctypes.byref(n), sp))
+    t = int(n.value)
+    tri = torch.empty((t, 3, 3), dtype=torch.float32, device=dev)
+    cell = torch.empty(t, dtype=torch.int64, device=dev) if with_cells else None
+    if t:
+        m = ctypes.c_int64()
+        _check(lib().dbt_mesh_extract(ctypes.byref(grid.c), b, float(iso), scratch.data_ptr(),
+                                      need, tri.data_ptr(),
+                                      cell.data_ptr() if cell is not None else None, t,
+                                      ctypes.byref(m), sp))
+        if int(m.value) != t:
+            raise RuntimeError("grid changed between the mesh passes")
+    return tri, cell
+
+
+def dbt_mesh_table():
+    """(ntri (256,) uint8, edges (256, 5, 3) uint8) of the library's table."""
+    nt = np.zeros(256, np.uint8)
+    ed = np.zeros(256 * 15, np.uint8)
+    _check(lib().dbt_mesh_table(nt.ctypes.data, ed.ctypes.data))
+    return nt, ed.reshape(256, 5, 3)
 
 
 def dbt_sync(stream=None, ws: Workspace | None = None):

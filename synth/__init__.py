@@ -17,6 +17,11 @@ which are not available here):
   * ``urban_sequence`` urban block (ground, 40 buildings, 200 poles),
                        64 x 1024 scans, +-22.5 deg, 1-60 m, 1 m per scan
   * ``batched_maps``   uneven maps each with a few room scans
+
+Map states for the export path (signed-distance field, Marching Cubes) are
+given directly, voxel by voxel, as a distance in whole voxels and an
+occupancy flag (``map_state``): a sphere, a stepped terrain with boxes, and
+random states.
 """
 from __future__ import annotations
 
@@ -454,3 +459,61 @@ def serving_robots(n_robots: int = 16, scans_per_robot: int = 4, duration: float
             k += 1
     arrivals.sort(key=lambda a: a[1])
     return maps, arrivals
+
+
+# ---------------------------------------------------------------- map states
+def map_state(dist, occupied):
+    """A map state as the export path reads it: per voxel a distance mask
+    whose `dist` (0..32) low bits are set, sign 0 where `occupied` (else
+    1), hits 0.  Returns (mask u32, sign u8, hits u16) of dist's shape."""
+    d = np.clip(np.asarray(dist, np.int64), 0, 32).astype(np.uint64)
+    mask = ((np.uint64(1) << d) - np.uint64(1)).astype(np.uint32)
+    sign = np.where(np.asarray(occupied, bool), 0, 1).astype(np.uint8)
+    return mask, sign, np.zeros(mask.shape, np.uint16)
+
+
+def sphere_state(n: int, centre, radius: float):
+    """n^3 voxels; a ball of `radius` voxels around `centre` (voxel units)
+    is occupied; distance = | |p - c| - radius | rounded, at least 1."""
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(np.float64)
+    r = np.sqrt((x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2)
+    return map_state(np.maximum(1, np.rint(np.abs(r - radius))), r < radius)
+
+
+def random_state(shape, seed: int, p_occupied: float = 0.5, min_dist: int = 0, max_dist: int = 32):
+    """Independent random voxels: distance uniform in [min_dist, max_dist],
+    occupied with probability p_occupied (a stress case: every cell
+    configuration, ambiguous faces included)."""
+    rng = Rng(BASE_SEED + seed)
+    n = int(np.prod(shape))
+    dist = rng.integers(n, min_dist, max_dist + 1).reshape(shape)
+    occ = (rng.uniform(n) < p_occupied).reshape(shape)
+    return map_state(dist, occ)
+
+
+def terrain_state(nx: int, ny: int, nz: int, seed: int, block: int = 40, n_boxes: int = 60):
+    """A stepped terrain: the ground height is constant over block x block
+    columns, uniform in [nz/8, nz/2], with n_boxes boxes (sides 8-80 voxels,
+    heights up to nz/3) standing on it; occupied = at or below the surface,
+    distance = |z - surface| along z (+1 below), capped at 32.  Built slice by
+    slice, so full-size maps (1600 x 1600 x 320) take a few seconds."""
+    rng = Rng(BASE_SEED + seed)
+    gy, gx = -(-ny // block), -(-nx // block)
+    h = rng.integers(gy * gx, nz // 8, nz // 2 + 1).reshape(gy, gx)
+    top = np.repeat(np.repeat(h, block, 0), block, 1)[:ny, :nx].astype(np.int64)
+    for _ in range(n_boxes):
+        sx, sy = (int(v) for v in rng.integers(2, 8, 81))
+        x0 = int(rng.integers(1, 0, max(1, nx - sx))[0])
+        y0 = int(rng.integers(1, 0, max(1, ny - sy))[0])
+        hz = int(rng.integers(1, 4, max(5, nz // 3))[0])
+        top[y0:y0 + sy, x0:x0 + sx] += hz
+    top = np.minimum(top, nz - 2)
+    mask = np.empty((nz, ny, nx), np.uint32)
+    sign = np.empty((nz, ny, nx), np.uint8)
+    for z in range(nz):
+        s = z - top
+        occ = s <= 0
+        m, sg, _ = map_state(np.where(occ, 1 - s, s), occ)
+        mask[z] = m
+        sign[z] = sg
+    return mask, sign, np.zeros((nz, ny, nx), np.uint16)

@@ -102,3 +102,13 @@ def test_grid_checks_refuse_misaligned():
     assert L.dbt_grid_init(ctypes.byref(g), None) == B.DBT_EINVAL
     g = _fake_grid(res=0.0)
     assert L.dbt_grid_init(ctypes.byref(g), None) == B.DBT_EINVAL
+
+
+def test_mesh_table_equals_oracle(orc):
+    """The library's compile-time Marching Cubes table and the oracle's own
+    derivation agree on every configuration."""
+    nt, ed = dbt.dbt_mesh_table()
+    for c in range(256):
+        t = orc.mc_config(c)
+        assert nt[c] == len(t), c
+        np.testing.assert_array_equal(ed[c, :len(t)], t)
