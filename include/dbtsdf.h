@@ -184,6 +184,51 @@ dbt_status dbt_integrate_scan(const dbt_grid *g, const dbt_kernels *k, dbt_works
                               const float *d_xyz, int64_t n, const double pose[12],
                               void *stream);
 
+/* ---- Update pre-steps (Sec. III-C, Sec. IV-B) ---- */
+
+/* Options of dbt_integrate_scan_ex.
+ *  downsample  DS >= 1: sequential downsampling, only returns whose index is
+ *              a multiple of DS are handed to the update (Sec. IV-B; the
+ *              others count as not handed in: neither valid nor kept).
+ *  n_poses     0: one pose for the scan (the pose argument).  1..256:
+ *              motion compensation (Sec. III-C): return i is transformed
+ *              with poses[m(i)], m(i) = ((i mod period) * n_poses) / period
+ *              (integer division): the sweep's time runs with the index
+ *              modulo period and is cut into n_poses equal slices.  For a
+ *              beam-major spinning scan of W azimuths per beam, period = W;
+ *              for returns stored in acquisition order, period = n.
+ *  period      >= 1 when n_poses > 0.
+ *  poses       host, n_poses x 12 (row-major 3x4 [R | t] each, checked like
+ *              pose), read before the call returns (copied into the
+ *              workspace on stream from pageable memory, so a call with
+ *              n_poses > 0 cannot be captured into a CUDA graph). */
+typedef struct {
+    int32_t downsample;
+    int32_t n_poses;
+    int64_t period;
+    const double *poses;
+} dbt_scan_options;
+
+/* dbt_integrate_scan with the options above (opt == NULL: the plain call;
+ * pose may be NULL when opt->n_poses > 0).  Bit-identical to the plain
+ * update of the downsampled returns, each under its slice's pose. */
+dbt_status dbt_integrate_scan_ex(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
+                                 const float *d_xyz, int64_t n, const double pose[12],
+                                 const dbt_scan_options *opt, void *stream);
+
+typedef enum {
+    DBT_MOTION_FULL = 0, /* R(tau) = R0 Exp(tau Log(R0^T R1)): constant angular velocity */
+    DBT_MOTION_YAW = 1   /* R(tau) = Rz(tau dpsi) R0, dpsi = wrapped yaw(R1) - yaw(R0) */
+} dbt_motion_mode;
+
+/* Motion-compensation poses for a sweep from pose start to pose end (the
+ * paper's "yaw-only or full SE(3)" compensation; its formula is not given,
+ * these are this library's readings): out[12 m ..] = the pose at
+ * tau_m = (m + 0.5) / n_poses, m < n_poses <= 256, rotation per mode and
+ * translation t0 + tau (t1 - t0).  Host only. */
+dbt_status dbt_pose_ramp(const double start[12], const double end[12], int32_t n_poses,
+                         int32_t mode, double *out);
+
 /* dbt_integrate_scan from host memory: copies the n returns at h_xyz into
  * the workspace's staging area (pinned memory keeps the copy asynchronous),
  * integrates them, and copies the scan's counters into *h_stats, which must
@@ -263,7 +308,8 @@ dbt_status dbt_batch_destroy(dbt_batch *b);
  * point uses a fixed scratch array compiled into the library instead and
  * allocates nothing (host or device).  Limits: n <= 65,536 returns per scan,
  * and the grid's integration layout must fit in 18 MiB (true for every grid
- * of up to 524,288 bricks of 32 x 8 x 8 voxels); larger inputs are rejected
+ * of up to 524,288 bricks of 32 x 8 x 8 voxels at K <= 17, ~440,000 bricks
+ * at K = 19 or 21); larger inputs are rejected
  * with DBT_EINVAL and a message.  The 18 MiB array occupies device memory on
  * every GPU that loads the library until the process exits.  All calls share
  * it: calls whose work overlaps on the GPU race, so issue them on one stream

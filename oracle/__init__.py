@@ -111,6 +111,13 @@ def _declare(L):
     L.orc_integrate_scan.restype = ctypes.c_int64
     L.orc_integrate_scan.argtypes = [P(_Grid), P(Params), ctypes.c_void_p,
                                      ctypes.c_int64, ctypes.c_void_p, P(Stats)]
+    L.orc_integrate_scan_ex.restype = ctypes.c_int64
+    L.orc_integrate_scan_ex.argtypes = [P(_Grid), P(Params), ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                        P(Stats)]
+    L.orc_pose_interp.restype = None
+    L.orc_pose_interp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_void_p]
     L.orc_scan_kept.restype = ctypes.c_int64
     L.orc_scan_kept.argtypes = [P(Params), P(_Grid), ctypes.c_void_p, ctypes.c_int64,
                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -214,6 +221,41 @@ class Grid:
     def copy(self):
         return Grid(self.nx, self.ny, self.nz, self.res, self.origin,
                     self.mask.copy(), self.sign.copy(), self.hits.copy())
+
+
+def integrate_scan_ex(g: Grid, p: Params, xyz, poses, period: int | None = None,
+                      downsample: int = 1) -> dict:
+    """Sec. III-C update with sequential downsampling (every downsample-th
+    return) and motion compensation: return i uses poses[m(i)],
+    m(i) = ((i mod period) * len(poses)) // period (period defaults to n)."""
+    pts = _as_points(xyz)
+    ps = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 12))
+    per = int(period) if period else max(1, pts.shape[0])
+    st = Stats()
+    r = lib().orc_integrate_scan_ex(ctypes.byref(g._c()), ctypes.byref(p), pts.ctypes.data,
+                                    pts.shape[0], ps.ctypes.data, ps.shape[0], per,
+                                    int(downsample), ctypes.byref(st))
+    if r < 0:
+        raise RuntimeError("oracle integrate_scan_ex failed")
+    return st.as_dict()
+
+
+POSE_FULL = 0
+POSE_YAW = 1
+
+
+def pose_interp(T0, T1, tau: float, mode: int = POSE_FULL) -> np.ndarray:
+    """Motion-compensation pose at time fraction tau (3 x 4)."""
+    a = _as_pose(T0)
+    b = _as_pose(T1)
+    out = np.empty(12, np.float64)
+    lib().orc_pose_interp(a.ctypes.data, b.ctypes.data, float(tau), int(mode), out.ctypes.data)
+    return out.reshape(3, 4)
+
+
+def pose_ramp(T0, T1, n_poses: int, mode: int = POSE_FULL) -> np.ndarray:
+    """Poses at the slice centres tau_m = (m + 0.5) / n_poses, (n_poses, 3, 4)."""
+    return np.stack([pose_interp(T0, T1, (m + 0.5) / n_poses, mode) for m in range(n_poses)])
 
 
 def _as_points(xyz) -> np.ndarray:

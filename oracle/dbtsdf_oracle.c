@@ -332,12 +332,22 @@ static void orc_apply_kernel(orc_grid *g, const orc_params *p, const int64_t c[3
 /* One scan, returns in array order (Sec. III-C with the first-return rule
  * of Sec. IV-B).  Returns the number of kept returns, or -1 on a bad
  * argument or an allocation failure.                                   */
-int64_t orc_integrate_scan(orc_grid *g, const orc_params *p, const float *xyz, int64_t n,
-                           const double pose[12], orc_stats *st_out)
+/* Sec. III-C with the update's optional pre-steps:
+ *   - sequential downsampling (Sec. IV-B, "DS"): only returns whose index is
+ *     a multiple of ds are handed to the update (ds = 1: all);
+ *   - motion compensation (Sec. III-C, Fig. 3): return i is transformed with
+ *     its own pose poses[m(i)], m(i) = ((i mod period) * n_poses) / period,
+ *     i.e. the sweep's time runs with the index modulo period (period = the
+ *     returns per beam of a beam-major spinning scan, or n for returns in
+ *     acquisition order) and is cut into n_poses equal slices.
+ * n_poses = 1 is the single-pose update.  Returns the kept count or -1.    */
+int64_t orc_integrate_scan_ex(orc_grid *g, const orc_params *p, const float *xyz, int64_t n,
+                              const double *poses, int n_poses, int64_t period, int ds,
+                              orc_stats *st_out)
 {
     orc_stats st;
     memset(&st, 0, sizeof st);
-    if (p->kernel_size < 1 || (p->kernel_size & 1) == 0)
+    if (p->kernel_size < 1 || (p->kernel_size & 1) == 0 || n_poses < 1 || period < 1 || ds < 1)
         return -1;
     int64_t nv = g->nx * g->ny * g->nz;
     uint8_t *seen = NULL;
@@ -348,9 +358,12 @@ int64_t orc_integrate_scan(orc_grid *g, const orc_params *p, const float *xyz, i
     }
     st.n_input = n;
     for (int64_t i = 0; i < n; i++) {
+        if (i % ds != 0)
+            continue;
+        int64_t m = ((i % period) * (int64_t)n_poses) / period;
         int64_t c[3];
         int b, valid;
-        int inside = orc_contact(p, g, xyz + 3 * i, pose, c, &b, &valid);
+        int inside = orc_contact(p, g, xyz + 3 * i, poses + 12 * m, c, &b, &valid);
         st.n_valid += valid;
         if (!inside)
             continue;
@@ -368,6 +381,104 @@ int64_t orc_integrate_scan(orc_grid *g, const orc_params *p, const float *xyz, i
     if (st_out)
         *st_out = st;
     return st.n_kept;
+}
+
+int64_t orc_integrate_scan(orc_grid *g, const orc_params *p, const float *xyz, int64_t n,
+                           const double pose[12], orc_stats *st_out)
+{
+    return orc_integrate_scan_ex(g, p, xyz, n, pose, 1, 1, 1, st_out);
+}
+
+/* Pose at time fraction tau in [0, 1] of a sweep that starts at T0 and ends
+ * at T1 (row-major 3x4 [R | t]), for the motion compensation of Sec. III-C
+ * ("yaw-only or full SE(3)"; the paper gives no formula, this is a reading):
+ *   mode 0, full: R(tau) = R0 Exp(tau Log(R0^T R1)) -- rotation at constant
+ *     angular velocity about a fixed axis (Rodrigues' formula) -- and
+ *     t(tau) = t0 + tau (t1 - t0);
+ *   mode 1, yaw-only: R(tau) = Rz(tau dpsi) R0 with dpsi = yaw(R1) - yaw(R0)
+ *     wrapped into (-pi, pi], yaw(R) = atan2(R_10, R_00); t(tau) as above.  */
+void orc_pose_interp(const double T0[12], const double T1[12], double tau, int mode,
+                     double out[12])
+{
+    double R0[3][3], R1[3][3], Q[3][3];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) {
+            R0[r][c] = T0[4 * r + c];
+            R1[r][c] = T1[4 * r + c];
+        }
+    double K[3][3] = {{0}};
+    double phi = 0.0;
+    if (mode == 1) {
+        double dpsi = atan2(R1[1][0], R1[0][0]) - atan2(R0[1][0], R0[0][0]);
+        while (dpsi > ORC_PI)
+            dpsi -= 2.0 * ORC_PI;
+        while (dpsi <= -ORC_PI)
+            dpsi += 2.0 * ORC_PI;
+        phi = tau * dpsi;
+        /* Rz(phi) R0: the axis is the map's z, applied on the left */
+        double cz = cos(phi), sz = sin(phi);
+        for (int c = 0; c < 3; c++) {
+            Q[0][c] = cz * R0[0][c] - sz * R0[1][c];
+            Q[1][c] = sz * R0[0][c] + cz * R0[1][c];
+            Q[2][c] = R0[2][c];
+        }
+    } else {
+        /* D = R0^T R1, its angle and unit axis */
+        double D[3][3];
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++)
+                D[r][c] = R0[0][r] * R1[0][c] + R0[1][r] * R1[1][c] + R0[2][r] * R1[2][c];
+        double cth = (D[0][0] + D[1][1] + D[2][2] - 1.0) / 2.0;
+        if (cth > 1.0)
+            cth = 1.0;
+        if (cth < -1.0)
+            cth = -1.0;
+        double th = acos(cth);
+        double w[3] = {0.0, 0.0, 0.0};
+        if (th > 1e-12) {
+            if (th < ORC_PI - 1e-6) {
+                double k = 1.0 / (2.0 * sin(th));
+                w[0] = (D[2][1] - D[1][2]) * k;
+                w[1] = (D[0][2] - D[2][0]) * k;
+                w[2] = (D[1][0] - D[0][1]) * k;
+            } else {
+                /* near a half turn: D ~ 2 w w^T - I, take the largest column */
+                int j = 0;
+                for (int a = 1; a < 3; a++)
+                    if (D[a][a] > D[j][j])
+                        j = a;
+                for (int a = 0; a < 3; a++)
+                    w[a] = (D[a][j] + (a == j ? 1.0 : 0.0));
+                double sgn = (D[(j + 2) % 3][(j + 1) % 3] - D[(j + 1) % 3][(j + 2) % 3]) < 0.0 ? -1.0 : 1.0;
+                double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+                for (int a = 0; a < 3; a++)
+                    w[a] = sgn * w[a] / nw;
+            }
+        }
+        phi = tau * th;
+        K[0][1] = -w[2];
+        K[0][2] = w[1];
+        K[1][0] = w[2];
+        K[1][2] = -w[0];
+        K[2][0] = -w[1];
+        K[2][1] = w[0];
+        /* Exp = I + sin(phi) K + (1 - cos(phi)) K^2, then Q = R0 Exp */
+        double E[3][3];
+        double s = sin(phi), c1 = 1.0 - cos(phi);
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) {
+                double kk = K[r][0] * K[0][c] + K[r][1] * K[1][c] + K[r][2] * K[2][c];
+                E[r][c] = (r == c ? 1.0 : 0.0) + s * K[r][c] + c1 * kk;
+            }
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++)
+                Q[r][c] = R0[r][0] * E[0][c] + R0[r][1] * E[1][c] + R0[r][2] * E[2][c];
+    }
+    for (int r = 0; r < 3; r++) {
+        for (int c = 0; c < 3; c++)
+            out[4 * r + c] = Q[r][c];
+        out[4 * r + 3] = T0[4 * r + 3] + tau * (T1[4 * r + 3] - T0[4 * r + 3]);
+    }
 }
 
 /* ------------------------------------------------------------------ */

@@ -381,7 +381,7 @@ extern "C" dbt_status dbt_grid_init(const dbt_grid *g, void *stream) {
 
 // ------------------------------------------------------------------ workspace
 struct WsLayout {
-    size_t hdr, stage, prec, hkey, hidx, bcnt, boff, touched, order, pairs, total;
+    size_t hdr, stage, prec, hkey, hidx, bcnt, boff, touched, order, pairs, poses, total;
     uint32_t hcap_alloc, max_touched, nbricks;
     unsigned long long pairs_cap;
 };
@@ -418,6 +418,7 @@ static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long m
     L->touched = o;  o += up256((size_t)L->max_touched * 4);
     L->order = o;    o += up256((size_t)L->max_touched * 4);
     L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
+    L->poses = o;    o += up256((size_t)MAX_SCAN_POSES * sizeof(Pose));
     L->total = o;
     return DBT_OK;
 }
@@ -476,6 +477,7 @@ static void ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels *k, l
     w->d.max_touched = L.max_touched;
     w->d.pairs = (uint32_t *)(base + L.pairs);
     w->d.pairs_cap = L.pairs_cap;
+    w->d.poses = (Pose *)(base + L.poses);
 }
 
 extern "C" dbt_status dbt_workspace_create(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
@@ -540,14 +542,15 @@ static dbt_status check_pose(const double *pose, Pose *out) {
 
 static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
                                const float *d_xyz, int64_t n, const double pose[12],
-                               cudaStream_t s, DevGrid *dg_out, uint32_t *hcap_out);
+                               cudaStream_t s, DevGrid *dg_out, uint32_t *hcap_out,
+                               const dbt_scan_options *opt = nullptr);
 
 static dbt_status enqueue_scan(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
                                const float *d_xyz, int64_t n, const double pose[12],
-                               cudaStream_t s) {
+                               cudaStream_t s, const dbt_scan_options *opt = nullptr) {
     DevGrid dg;
     uint32_t hcap;
-    dbt_status st = enqueue_prep(g, k, ws, d_xyz, n, pose, s, &dg, &hcap);
+    dbt_status st = enqueue_prep(g, k, ws, d_xyz, n, pose, s, &dg, &hcap, opt);
     if (st != DBT_OK) return st;
     const int ni = (int)n;
     launch_alloc(ws->d, 2 * 152, s);
@@ -563,7 +566,8 @@ static dbt_status enqueue_scan(const dbt_grid *g, const dbt_kernels *k, dbt_work
 // starts with (transform, voxel, bin, first-return rule, brick counts).
 static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
                                const float *d_xyz, int64_t n, const double pose[12],
-                               cudaStream_t s, DevGrid *dg_out, uint32_t *hcap_out) {
+                               cudaStream_t s, DevGrid *dg_out, uint32_t *hcap_out,
+                               const dbt_scan_options *opt) {
     if (!k) return fail(DBT_EINVAL, "kernels is NULL");
     if (!ws) return fail(DBT_EINVAL, "workspace is NULL");
     dbt_status st = check_grid(g);
@@ -575,14 +579,39 @@ static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_work
         return fail(DBT_EINVAL, "n = %lld outside [0, max_points = %lld]", (long long)n, ws->max_points);
     if (n > 0 && (!d_xyz || ((uintptr_t)d_xyz & 3u)))
         return fail(DBT_EINVAL, "points must be a non-NULL 4-byte aligned device pointer");
-    Pose P;
-    st = check_pose(pose, &P);
-    if (st != DBT_OK) return st;
+    Pose P{};
+    ScanEx ex{1, 0, 1};
+    const bool use_ex = opt != nullptr;
+    if (use_ex) {
+        if (opt->downsample < 1) return fail(DBT_EINVAL, "downsample must be >= 1");
+        if (opt->n_poses < 0 || opt->n_poses > MAX_SCAN_POSES)
+            return fail(DBT_EINVAL, "n_poses must be in [0, %d]", MAX_SCAN_POSES);
+        if (opt->n_poses > 0 && (!opt->poses || opt->period < 1))
+            return fail(DBT_EINVAL, "motion compensation needs poses and period >= 1");
+        ex.ds = opt->downsample;
+        ex.n_poses = opt->n_poses;
+        ex.period = opt->n_poses > 0 ? opt->period : 1;
+        if (opt->n_poses > 0) {
+            Pose table[MAX_SCAN_POSES];
+            for (int m = 0; m < opt->n_poses; ++m) {
+                st = check_pose(opt->poses + 12 * m, &table[m]);
+                if (st != DBT_OK) return st;
+            }
+            DBT_CUDA(cudaMemcpyAsync(ws->d.poses, table, sizeof(Pose) * opt->n_poses,
+                                     cudaMemcpyHostToDevice, s));
+        } else {
+            st = check_pose(pose, &P);
+            if (st != DBT_OK) return st;
+        }
+    } else {
+        st = check_pose(pose, &P);
+        if (st != DBT_OK) return st;
+    }
     const DevGrid dg = dev_grid(g);
     uint32_t hcap = 64;
     while (hcap < 2ull * (unsigned long long)n) hcap <<= 1;
     const int ni = (int)n;
-    launch_voxelize(dg, k->dp, k->dt, P, d_xyz, ni, ws->d, hcap, s);
+    launch_voxelize(dg, k->dp, k->dt, P, d_xyz, ni, ws->d, hcap, s, use_ex ? &ex : nullptr);
     launch_count(dg, k->dp, ni, ws->d, hcap, s);
     *dg_out = dg;
     *hcap_out = hcap;
@@ -628,6 +657,92 @@ extern "C" dbt_status dbt_integrate_scan(const dbt_grid *g, const dbt_kernels *k
                                          const float *d_xyz, int64_t n, const double pose[12],
                                          void *stream) {
     return enqueue_scan(g, k, ws, d_xyz, n, pose, (cudaStream_t)stream);
+}
+
+extern "C" dbt_status dbt_integrate_scan_ex(const dbt_grid *g, const dbt_kernels *k,
+                                            dbt_workspace *ws, const float *d_xyz, int64_t n,
+                                            const double pose[12], const dbt_scan_options *opt,
+                                            void *stream) {
+    if (!opt) return enqueue_scan(g, k, ws, d_xyz, n, pose, (cudaStream_t)stream);
+    return enqueue_scan(g, k, ws, d_xyz, n, pose, (cudaStream_t)stream, opt);
+}
+
+// Motion-compensation pose at time fraction tau between T0 and T1.  Full:
+// R0 Exp(tau Log(R0^T R1)) (Rodrigues), yaw-only: Rz(tau dpsi) R0 with the
+// yaw difference wrapped into (-pi, pi]; translation linear in both.
+static void pose_at(const double *T0, const double *T1, double tau, int mode, double *out) {
+    double R0[9], R1[9], Q[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            R0[3 * r + c] = T0[4 * r + c];
+            R1[3 * r + c] = T1[4 * r + c];
+        }
+    if (mode == DBT_MOTION_YAW) {
+        double dpsi = std::atan2(R1[3], R1[0]) - std::atan2(R0[3], R0[0]);
+        while (dpsi > kPi) dpsi -= 2.0 * kPi;
+        while (dpsi <= -kPi) dpsi += 2.0 * kPi;
+        const double a = tau * dpsi, ca = std::cos(a), sa = std::sin(a);
+        for (int c = 0; c < 3; ++c) {
+            Q[c] = ca * R0[c] - sa * R0[3 + c];
+            Q[3 + c] = sa * R0[c] + ca * R0[3 + c];
+            Q[6 + c] = R0[6 + c];
+        }
+    } else {
+        double D[9];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                D[3 * r + c] = R0[r] * R1[c] + R0[3 + r] * R1[3 + c] + R0[6 + r] * R1[6 + c];
+        const double cth = std::min(1.0, std::max(-1.0, (D[0] + D[4] + D[8] - 1.0) / 2.0));
+        const double th = std::acos(cth);
+        double w[3] = {0.0, 0.0, 0.0};
+        if (th > 1e-12) {
+            if (th < kPi - 1e-6) {
+                const double f = 1.0 / (2.0 * std::sin(th));
+                w[0] = (D[7] - D[5]) * f;
+                w[1] = (D[2] - D[6]) * f;
+                w[2] = (D[3] - D[1]) * f;
+            } else {   // half turn: D ~ 2 w w^T - I
+                int j = 0;
+                for (int a = 1; a < 3; ++a)
+                    if (D[4 * a] > D[4 * j]) j = a;
+                for (int a = 0; a < 3; ++a) w[a] = D[3 * a + j] + (a == j ? 1.0 : 0.0);
+                const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+                const double sg = (D[3 * j2 + j1] - D[3 * j1 + j2]) < 0.0 ? -1.0 : 1.0;
+                const double nw = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+                for (int a = 0; a < 3; ++a) w[a] = sg * w[a] / nw;
+            }
+        }
+        const double phi = tau * th, s = std::sin(phi), c1 = 1.0 - std::cos(phi);
+        const double K[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+        double E[9];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                const double kk = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+                E[3 * r + c] = (r == c ? 1.0 : 0.0) + s * K[3 * r + c] + c1 * kk;
+            }
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                Q[3 * r + c] = R0[3 * r] * E[c] + R0[3 * r + 1] * E[3 + c] + R0[3 * r + 2] * E[6 + c];
+    }
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) out[4 * r + c] = Q[3 * r + c];
+        out[4 * r + 3] = T0[4 * r + 3] + tau * (T1[4 * r + 3] - T0[4 * r + 3]);
+    }
+}
+
+extern "C" dbt_status dbt_pose_ramp(const double start[12], const double end[12], int32_t n_poses,
+                                    int32_t mode, double *out) {
+    if (!start || !end || !out) return fail(DBT_EINVAL, "NULL argument");
+    if (n_poses < 1 || n_poses > MAX_SCAN_POSES)
+        return fail(DBT_EINVAL, "n_poses must be in [1, %d]", MAX_SCAN_POSES);
+    if (mode != DBT_MOTION_FULL && mode != DBT_MOTION_YAW) return fail(DBT_EINVAL, "unknown mode");
+    Pose tmp;
+    dbt_status st = check_pose(start, &tmp);
+    if (st == DBT_OK) st = check_pose(end, &tmp);
+    if (st != DBT_OK) return st;
+    for (int m = 0; m < n_poses; ++m)
+        pose_at(start, end, ((double)m + 0.5) / (double)n_poses, mode, out + 12 * m);
+    return DBT_OK;
 }
 
 // One scan on a scratch buffer owned by the caller of this function (the

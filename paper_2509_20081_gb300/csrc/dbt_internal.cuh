@@ -147,7 +147,18 @@ struct WsDev {
     uint32_t max_touched;
     uint32_t *pairs;            // pair payloads grouped by brick
     unsigned long long pairs_cap;
+    Pose *poses;                // motion compensation: MAX_SCAN_POSES per-slice poses
 };
+
+// Update pre-steps of dbt_integrate_scan_ex: sequential downsampling (every
+// ds-th return) and motion compensation (return i uses ws.poses[m(i)],
+// m(i) = ((i mod period) * n_poses) / period).
+struct ScanEx {
+    int ds;
+    int n_poses;
+    long long period;
+};
+constexpr int MAX_SCAN_POSES = 256;
 
 // Bricks with more (return, brick) pairs than this are integrated by a whole
 // CTA (its warps split the pairs); the others by a single warp.
@@ -159,7 +170,8 @@ constexpr int PREC_DUP = 1 << 30;
 
 // Launch helpers implemented in the .cu files.
 void launch_voxelize(const DevGrid &g, const DevParams &p, const DevTables &t, const Pose &pose,
-                     const float *xyz, int n, const WsDev &ws, uint32_t hcap, cudaStream_t s);
+                     const float *xyz, int n, const WsDev &ws, uint32_t hcap, cudaStream_t s,
+                     const ScanEx *ex = nullptr);
 void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                   cudaStream_t s);
 void launch_alloc(const WsDev &ws, int grid_ctas, cudaStream_t s);

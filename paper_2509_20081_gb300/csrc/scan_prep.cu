@@ -145,14 +145,30 @@ __device__ __forceinline__ int contact_of(const DevGrid &g, const DevParams &p, 
     return 2;
 }
 
+// EX: the update's pre-steps (ScanEx): returns off the downsampling stride
+// are not handed in at all, the others use the pose of their time slice.
+template <bool EX>
 __global__ void __launch_bounds__(256) k_voxelize(DevGrid g, DevParams p, DevTables t, Pose pose,
                                                   const float *__restrict__ xyz, int n, WsDev ws,
-                                                  uint32_t hcap) {
+                                                  uint32_t hcap, ScanEx ex) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false, inside = false;
     if (i < n) {
         int4 rec = make_int4(-1, 0, 0, 0);
-        const int c = contact_of(g, p, t, pose, xyz[3 * i + 0], xyz[3 * i + 1], xyz[3 * i + 2], rec);
+        int c = 0;
+        if constexpr (EX) {
+            if (i % ex.ds == 0) {
+                if (ex.n_poses > 0) {
+                    const long long m = ((long long)i % ex.period) * ex.n_poses / ex.period;
+                    const Pose pm = ws.poses[m];
+                    c = contact_of(g, p, t, pm, xyz[3 * i + 0], xyz[3 * i + 1], xyz[3 * i + 2], rec);
+                } else {
+                    c = contact_of(g, p, t, pose, xyz[3 * i + 0], xyz[3 * i + 1], xyz[3 * i + 2], rec);
+                }
+            }
+        } else {
+            c = contact_of(g, p, t, pose, xyz[3 * i + 0], xyz[3 * i + 1], xyz[3 * i + 2], rec);
+        }
         valid = c > 0;
         inside = c == 2;
         if (inside && p.dedup) hash_insert(ws, hcap, voxel_key(g, rec.x, rec.y, rec.z), (uint32_t)i);
@@ -598,8 +614,13 @@ __global__ void k_read_distance(DevGrid g, double res, const int *__restrict__ i
 static inline int blocks_for(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 
 void launch_voxelize(const DevGrid &g, const DevParams &p, const DevTables &t, const Pose &pose,
-                     const float *xyz, int n, const WsDev &ws, uint32_t hcap, cudaStream_t s) {
-    k_voxelize<<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, t, pose, xyz, n, ws, hcap);
+                     const float *xyz, int n, const WsDev &ws, uint32_t hcap, cudaStream_t s,
+                     const ScanEx *ex) {
+    if (ex)
+        k_voxelize<true><<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, t, pose, xyz, n, ws, hcap, *ex);
+    else
+        k_voxelize<false><<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, t, pose, xyz, n, ws, hcap,
+                                                                    ScanEx{1, 0, 1});
 }
 
 void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,

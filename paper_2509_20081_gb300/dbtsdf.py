@@ -36,6 +36,15 @@ class dbt_params(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("shadow_cos", ctypes.c_double)]
 
 
+class dbt_scan_options(ctypes.Structure):
+    _fields_ = [("downsample", ctypes.c_int32), ("n_poses", ctypes.c_int32),
+                ("period", ctypes.c_int64), ("poses", ctypes.c_void_p)]
+
+
+DBT_MOTION_FULL = 0
+DBT_MOTION_YAW = 1
+
+
 class dbt_grid(ctypes.Structure):
     _fields_ = [("mask", ctypes.c_void_p), ("sign", ctypes.c_void_p), ("hits", ctypes.c_void_p),
                 ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
@@ -94,6 +103,10 @@ _SIGS = {
                                    _P(dbt_scan_stats), _vp],
     "dbt_scan_footprint": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
                            _vp, ctypes.c_size_t, _P(ctypes.c_int64), _vp],
+    "dbt_integrate_scan_ex": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
+                              _P(dbt_scan_options), _vp],
+    "dbt_pose_ramp": [_P(ctypes.c_double), _P(ctypes.c_double), ctypes.c_int32, ctypes.c_int32,
+                      _P(ctypes.c_double)],
     "dbt_sdf_field": [_P(dbt_grid), _P(ctypes.c_int32), _vp, _vp],
     "dbt_mesh_scratch_size": [_P(dbt_grid), _P(ctypes.c_int32), _P(ctypes.c_size_t)],
     "dbt_mesh_extract": [_P(dbt_grid), _P(ctypes.c_int32), ctypes.c_double, _vp, ctypes.c_size_t,
@@ -317,6 +330,41 @@ def dbt_integrate_scan(grid: Grid, kernels: Kernels, ws: Workspace, xyz, pose, s
     keep, pp = _pose_arg(pose)
     _check(lib().dbt_integrate_scan(ctypes.byref(grid.c), kernels.h, ws.h,
                                     xyz.data_ptr() if n else None, n, pp, _stream_ptr(stream)))
+
+
+def dbt_integrate_scan_ex(grid: Grid, kernels: Kernels, ws: Workspace, xyz, pose=None,
+                          downsample: int = 1, poses=None, period: int | None = None,
+                          stream=None):
+    """Integrate one scan with sequential downsampling (every downsample-th
+    return) and/or motion compensation (poses: (M, 3, 4), return i uses
+    poses[((i mod period) * M) // period]; period defaults to n)."""
+    n = int(xyz.shape[0])
+    if n and (not xyz.is_cuda or not xyz.is_contiguous()):
+        raise DbtError(DBT_EINVAL, "xyz must be a contiguous CUDA float32 tensor")
+    opt = dbt_scan_options(int(downsample), 0, 1, None)
+    keep_p = None
+    if poses is not None:
+        keep_p = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 12))
+        opt.n_poses = keep_p.shape[0]
+        opt.period = int(period) if period else max(1, n)
+        opt.poses = keep_p.ctypes.data
+        pp = None
+    else:
+        keep, pp = _pose_arg(pose)
+    _check(lib().dbt_integrate_scan_ex(ctypes.byref(grid.c), kernels.h, ws.h,
+                                       xyz.data_ptr() if n else None, n, pp, ctypes.byref(opt),
+                                       _stream_ptr(stream)))
+
+
+def dbt_pose_ramp(start, end, n_poses: int, mode: int = DBT_MOTION_FULL) -> np.ndarray:
+    """Motion-compensation poses at tau_m = (m + 0.5) / n_poses, (n_poses, 3, 4)."""
+    a = np.ascontiguousarray(np.asarray(start, np.float64).reshape(12))
+    b = np.ascontiguousarray(np.asarray(end, np.float64).reshape(12))
+    out = np.empty(12 * int(n_poses), np.float64)
+    P = ctypes.POINTER(ctypes.c_double)
+    _check(lib().dbt_pose_ramp(a.ctypes.data_as(P), b.ctypes.data_as(P), int(n_poses), int(mode),
+                               out.ctypes.data_as(P)))
+    return out.reshape(-1, 3, 4)
 
 
 def dbt_integrate_scan_host(grid: Grid, kernels: Kernels, ws: Workspace, xyz_host, pose,

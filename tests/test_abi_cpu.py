@@ -112,3 +112,26 @@ def test_mesh_table_equals_oracle(orc):
         t = orc.mc_config(c)
         assert nt[c] == len(t), c
         np.testing.assert_array_equal(ed[c, :len(t)], t)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_pose_ramp_matches_oracle(orc, mode):
+    """The library's motion-compensation poses (host code) agree with the
+    oracle's own interpolation at the slice centres."""
+    import synth
+    T0 = synth.make_pose(synth.rotation_rpy(0.1, -0.05, 2.9), (1.0, 2.0, 0.3))
+    T1 = synth.make_pose(synth.rotation_rpy(0.14, -0.02, -3.1), (1.6, 2.1, 0.35))
+    got = dbt.dbt_pose_ramp(T0, T1, 17, mode)
+    want = orc.pose_ramp(T0, T1, 17, mode)
+    np.testing.assert_allclose(got, want, atol=1e-13)
+
+
+def test_pose_ramp_refuses_bad_arguments():
+    import synth
+    T = synth.make_pose(np.eye(3), (0, 0, 0))
+    bad = T.copy()
+    bad[0, 0] = 2.0
+    for args in [(T, T, 0, 0), (T, T, 257, 0), (T, T, 4, 2), (bad, T, 4, 0)]:
+        with pytest.raises(B.DbtError) as e:
+            dbt.dbt_pose_ramp(*args)
+        assert e.value.status == B.DBT_EINVAL

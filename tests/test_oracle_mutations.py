@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import synth
+import test_oracle_deskew as deskew
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "dbtsdf_oracle.c")
@@ -40,10 +41,8 @@ MUTATIONS = {
     "translation_dropped": ("w[r] = d[r] + pose[4 * r + 3];", "w[r] = d[r];"),
     "boundary_off_by_one": ("if (!(q >= (double)R && q <= (double)(n[a] - 1 - R)))",
                             "if (!(q >= (double)R && q <= (double)(n[a] - R)))"),
-    "last_return_kept": ("    for (int64_t i = 0; i < n; i++) {\n        int64_t c[3];\n        int b, valid;\n"
-                         "        int inside = orc_contact(",
-                         "    for (int64_t i = n - 1; i >= 0; i--) {\n        int64_t c[3];\n        int b, valid;\n"
-                         "        int inside = orc_contact("),
+    "last_return_kept": ("    for (int64_t i = 0; i < n; i++) {\n        if (i % ds != 0)",
+                         "    for (int64_t i = n - 1; i >= 0; i--) {\n        if (i % ds != 0)"),
     "octa_fold_swapped": ("double fu = (1.0 - fabs(v)) * orc_sgn(u);", "double fu = (1.0 - fabs(u)) * orc_sgn(u);"),
     "el_edge_sign": ("return (ORC_PI * (double)k) / (double)bel - ORC_PI / 2.0;",
                      "return (ORC_PI * (double)k) / (double)bel + ORC_PI / 2.0;"),
@@ -51,6 +50,15 @@ MUTATIONS = {
     "kernel_index_transposed": ("int64_t v = ((c[2] + oz) * g->ny + (c[1] + oy)) * g->nx + (c[0] + ox);",
                                 "int64_t v = ((c[2] + oz) * g->ny + (c[1] + ox)) * g->nx + (c[0] + oy);"),
     "bin_from_sensor_frame": ("*bin = orc_bin(p, d[0], d[1], d[2]);", "*bin = orc_bin(p, px, py, pz);"),
+    "slice_index_not_periodic": ("int64_t m = ((i % period) * (int64_t)n_poses) / period;",
+                                 "int64_t m = (i * (int64_t)n_poses) / period;\n"
+                                 "        if (m >= n_poses) m = n_poses - 1;"),
+    "downsample_offset": ("if (i % ds != 0)\n            continue;",
+                          "if (i % ds != ds - 1)\n            continue;"),
+    "yaw_not_wrapped": ("        while (dpsi <= -ORC_PI)\n            dpsi += 2.0 * ORC_PI;",
+                        "        while (0)\n            dpsi += 2.0 * ORC_PI;"),
+    "full_interp_wrong_side": ("Q[r][c] = R0[r][0] * E[0][c] + R0[r][1] * E[1][c] + R0[r][2] * E[2][c];",
+                               "Q[r][c] = E[r][0] * R0[0][c] + E[r][1] * R0[1][c] + E[r][2] * R0[2][c];"),
     "octa_dir_not_folded": ("    if (Z < 0.0) {\n        double fu = ((double)n - fabs(V)) * orc_sgn(U);",
                             "    if (Z < -1e300) {\n        double fu = ((double)n - fabs(V)) * orc_sgn(U);"),
 }
@@ -78,6 +86,10 @@ def _battery(room):
         lambda: pins.test_first_return_rule_uses_first_bin(orc),
         lambda: pins.test_border_returns_change_nothing(orc),
         lambda: pins.test_rs0_hits_count_points_per_voxel(orc, room),
+        lambda: deskew.test_downsampling_is_every_ds_th_return(orc, 3),
+        lambda: deskew.test_one_pose_per_slice_equals_returns_one_by_one(orc),
+        lambda: [deskew.test_interp_endpoints_and_rotations(orc, k, m) for k in range(4) for m in (0, 1)],
+        lambda: [deskew.test_yaw_interp_turns_about_map_z_only(orc, k) for k in range(3)],
     ]
     failed = []
     for i, c in enumerate(checks):
