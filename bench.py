@@ -557,7 +557,7 @@ def run_mesh(args, rank, world):
     line = {"metric": "map cells meshed/sec (Marching Cubes, iso = 0)",
             "value": world * cells / (ms_full * 1e-3), "unit": "cells/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_full,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"mesh: stepped terrain map {nx}x{ny}x{nz} at {res} m "
                                    f"({cells / 1e6:.0f} M cells, {ntri} triangles)",

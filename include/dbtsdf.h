@@ -351,11 +351,13 @@ dbt_status dbt_sdf_field(const dbt_grid *g, const int32_t box[6], float *d_out, 
 dbt_status dbt_mesh_scratch_size(const dbt_grid *g, const int32_t box[6], size_t *bytes);
 
 /* Marching Cubes over the cells of the box (the (bx-1)(by-1)(bz-1) cubes
- * between voxel centres, numbered L = (k (by-1) + j) (bx-1) + i).  A corner
- * is inside when its sdf < iso; the vertex on a crossed edge from lower
- * corner a to upper corner b is at t = (iso - f_a) / (f_b - f_a) (binary64,
- * rounded to float); vertices are in the map frame (origin + res * (index +
- * 0.5) at voxel centres).  Triangles are ordered by cell, then by the
+ * between voxel centres, numbered L = (k (by-1) + j) (bx-1) + i).  The field
+ * is the readout in binary32, f = (sign ? +1 : -1) * popcount(mask) * res
+ * (res and iso rounded to float); a corner is inside when f < iso; the vertex
+ * on a crossed edge from lower corner a to upper corner b is at
+ * t = (iso - f_a) / (f_b - f_a), coordinate origin + res * ((index + 0.5) +
+ * t) along the edge (binary32, in this order); vertices are in the map
+ * frame.  Triangles are ordered by cell, then by the
  * configuration table (dbt_mesh_table); each is 9 floats (three xyz
  * vertices) whose right-hand normal points to sdf > iso, and the surface of
  * the box is closed except where it meets the box's faces.

@@ -604,14 +604,15 @@ double orc_signed_distance(uint32_t mask, uint8_t sign, double res)
  * sdf = iso by Marching Cubes, the paper's export at iso = 0.
  *
  * Readings (the paper names the method only):
- *   - the field is orc_signed_distance at the voxel centres; a cell is the
- *     cube between 2 x 2 x 2 neighbouring centres, corner q (bit 0: +x,
- *     bit 1: +y, bit 2: +z); a corner is inside when sdf < iso.
+ *   - the field at a voxel centre is f = (sign ? +1 : -1) * popcount(mask)
+ *     * res evaluated in binary32 (res and iso rounded to float once); a
+ *     cell is the cube between 2 x 2 x 2 neighbouring centres, corner q
+ *     (bit 0: +x, bit 1: +y, bit 2: +z); a corner is inside when f < iso.
  *   - the vertex on a crossed edge is linearly interpolated from its lower
  *     corner a to its upper corner b: t = (iso - f_a) / (f_b - f_a),
  *     coordinate = origin + res * ((index of a + 0.5) + t) along the edge's
- *     axis, origin + res * (index + 0.5) on the other two, in binary64,
- *     then rounded to float.
+ *     axis, origin + res * (index + 0.5) on the other two; every operation
+ *     in binary32 in this order (the mesh is a float mesh).
  *   - the configuration table is derived from the cube: on each face, every
  *     inside corner region (boundary walked counter-clockwise seen from
  *     outside) is closed by a segment from the crossing where the walk
@@ -751,6 +752,16 @@ static double orc_sdf_at(const orc_grid *g, int64_t x, int64_t y, int64_t z)
     return orc_signed_distance(g->mask[v], g->sign[v], g->res);
 }
 
+/* the mesh's binary32 field value of a voxel */
+static float orc_mesh_level(const orc_grid *g, int64_t x, int64_t y, int64_t z, float res)
+{
+    int64_t v = (z * g->ny + y) * g->nx + x;
+    int bits = 0;
+    for (int i = 0; i < 32; i++)
+        bits += (g->mask[v] >> i) & 1u;
+    return (g->sign[v] ? 1.0f : -1.0f) * (float)bits * res;
+}
+
 /* Signed distance of every voxel of the box [x0, x0+bx) x [y0, y0+by) x
  * [z0, z0+bz) into out[(z * by + y) * bx + x] (float).                    */
 void orc_sdf_field(const orc_grid *g, const int64_t box[6], float *out)
@@ -776,17 +787,19 @@ int64_t orc_mesh(const orc_grid *g, const int64_t box[6], double iso, float *tri
     int64_t cx = box[3] - 1, cy = box[4] - 1, cz = box[5] - 1;
     if (cx < 1 || cy < 1 || cz < 1)
         return 0;
+    float res = (float)g->res, isof = (float)iso;
+    float org[3] = {(float)g->origin[0], (float)g->origin[1], (float)g->origin[2]};
     int64_t n = 0;
     for (int64_t k = 0; k < cz; k++)
         for (int64_t j = 0; j < cy; j++)
             for (int64_t i = 0; i < cx; i++) {
                 int64_t base[3] = {box[0] + i, box[1] + j, box[2] + k};
-                double f[8];
+                float f[8];
                 int cfg = 0;
                 for (int q = 0; q < 8; q++) {
-                    f[q] = orc_sdf_at(g, base[0] + (q & 1), base[1] + ((q >> 1) & 1),
-                                      base[2] + ((q >> 2) & 1));
-                    if (f[q] < iso)
+                    f[q] = orc_mesh_level(g, base[0] + (q & 1), base[1] + ((q >> 1) & 1),
+                                          base[2] + ((q >> 2) & 1), res);
+                    if (f[q] < isof)
                         cfg |= 1 << q;
                 }
                 for (int t = 0; t < orc_mc_ntri[cfg]; t++, n++) {
@@ -796,12 +809,12 @@ int64_t orc_mesh(const orc_grid *g, const int64_t box[6], double iso, float *tri
                         int e = orc_mc_tri[cfg][t][v];
                         int a = orc_mc_edge_corner[e][0], b = orc_mc_edge_corner[e][1];
                         int axis = e / 4;
-                        double tt = (iso - f[a]) / (f[b] - f[a]);
+                        float tt = (isof - f[a]) / (f[b] - f[a]);
                         for (int d = 0; d < 3; d++) {
-                            double idx = (double)(base[d] + ((a >> d) & 1)) + 0.5;
+                            float idx = (float)(base[d] + ((a >> d) & 1)) + 0.5f;
                             if (d == axis)
                                 idx = idx + tt;
-                            tri[9 * n + 3 * v + d] = (float)(g->origin[d] + g->res * idx);
+                            tri[9 * n + 3 * v + d] = org[d] + res * idx;
                         }
                     }
                     if (cell)

@@ -1113,14 +1113,16 @@ static dbt_status export_box(const dbt_grid *g, const int32_t box[6], ExportBox 
     return DBT_OK;
 }
 
-// Inside bits over (sign, popcount): bit s * 33 + p is (s ? p : -p) * res < iso.
+// Inside bits over (sign, popcount): bit s * 33 + p is f < iso with the
+// mesh's binary32 field f = (s ? 1 : -1) * p * res (res, iso rounded to float).
 static void inside_lut(double res, double iso, uint64_t *lut0, uint64_t *lut1) {
     *lut0 = 0;
     *lut1 = 0;
+    const float resf = (float)res, isof = (float)iso;
     for (int s = 0; s < 2; ++s)
         for (int p = 0; p <= 32; ++p) {
-            const double f = (s ? 1.0 : -1.0) * (double)p * res;
-            if (f < iso) {
+            const float f = (s ? 1.0f : -1.0f) * (float)p * resf;
+            if (f < isof) {
                 const int idx = s * 33 + p;
                 if (idx < 64) *lut0 |= 1ull << idx;
                 else *lut1 |= 1ull << (idx - 64);

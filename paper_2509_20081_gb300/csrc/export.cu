@@ -6,11 +6,14 @@
 // centres (the distance is the number of set bits, Sec. III-A; the sign flag
 // says free or occupied, Eq. 6).
 //
-// Mesh: a cell is the cube between 2 x 2 x 2 neighbouring voxel centres,
-// corner q at (+x if bit 0, +y if bit 1, +z if bit 2); a corner is inside
-// when sdf < iso.  The vertex on a crossed edge from lower corner a to upper
-// corner b sits at t = (iso - f_a) / (f_b - f_a) along the edge, evaluated in
-// binary64 with round-to-nearest intrinsics and rounded to float once.
+// Mesh: the field at a voxel centre is f = (sign ? +1 : -1) * popcount *
+// res in binary32 (res and iso rounded to float once); a cell is the cube
+// between 2 x 2 x 2 neighbouring voxel centres, corner q at (+x if bit 0, +y
+// if bit 1, +z if bit 2); a corner is inside when f < iso.  The vertex on a
+// crossed edge from lower corner a to upper corner b sits at
+// t = (iso - f_a) / (f_b - f_a) along the edge, coordinate origin + res *
+// ((index + 0.5) + t), every step a binary32 round-to-nearest intrinsic (the
+// mesh is a float mesh; binary64 would run on the slow FP64 pipe).
 // Triangles are listed by cell, x fastest over the box, then in table order,
 // so the output is deterministic.
 //
@@ -130,6 +133,17 @@ static_assert(kMcTable.ntri[0] == 0 && kMcTable.ntri[255] == 0 && kMcTable.ntri[
 
 __device__ const McTable g_mc = kMcTable;
 
+// q = a / d, r = a % d for a >= 0, d > 0; 32-bit division when both fit
+// (64-bit division is a long software sequence).
+__device__ __forceinline__ void divmod(long long a, long long d, long long &q, long long &r) {
+    if (((unsigned long long)a | (unsigned long long)d) >> 32) {
+        q = a / d;
+    } else {
+        q = (long long)((uint32_t)a / (uint32_t)d);
+    }
+    r = a - q * d;
+}
+
 // ------------------------------------------------------------------ field
 __device__ __forceinline__ double voxel_sdf(const DevGrid &g, size_t v, double res) {
     const double s = __ldg(g.sign + v) ? 1.0 : -1.0;
@@ -141,8 +155,9 @@ __global__ void __launch_bounds__(256) k_sdf_field(DevGrid g, double res, Export
     const long long n = (long long)b.bx * b.by * b.bz;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long x = i % b.bx, yz = i / b.bx;
-        const long long y = yz % b.by, z = yz / b.by;
+        long long x, yz, y, z;
+        divmod(i, b.bx, yz, x);
+        divmod(yz, b.by, z, y);
         const size_t v = ((size_t)(b.z0 + z) * g.ny + (size_t)(b.y0 + y)) * g.pitch +
                          (size_t)(b.x0 + x);
         out[i] = (float)voxel_sdf(g, v, res);
@@ -150,59 +165,167 @@ __global__ void __launch_bounds__(256) k_sdf_field(DevGrid g, double res, Export
 }
 
 // ------------------------------------------------------------------ cells
-// A warp walks one unit of MC_UNIT consecutive cells, 32 per step.
-constexpr int MC_UNIT = 1024;
-constexpr int MC_STEPS = MC_UNIT / 32;
+// Pass 0 turns the box into an inside bit plane: bit x of word
+// ((z * by + y) * wpr + x / 32) is voxel (x0 + x, y0 + y, z0 + z) < iso.
+//
+// The cells are then walked in units: a unit is a segment of up to 1024
+// consecutive cells of one cell row (fixed j, k), so units are contiguous
+// and ordered in the cell numbering L; a warp takes a unit and lane l the
+// 32 cells x = 1024 u + 32 l .. + 31, whose 2 x 2 x 2 corner bits come from
+// four 33-bit windows of the plane (rows j, j+1 of slices k, k+1).  A cell
+// with all eight bits equal has no triangle, so a lane visits only the set
+// bits of its "mixed" mask: the work follows the surface, not the volume.
+constexpr int MC_LEVELS = 66;          // (sign, popcount) pairs: s * 33 + p
+constexpr int MC_SEG = 1024;           // cells per unit
 
-struct CellWalk {
-    long long i, j, k;      // cell coordinates inside the box
-};
+__device__ __forceinline__ size_t voxel_index(const DevGrid &g, const ExportBox &b, long long x,
+                                              long long y, long long z) {
+    return ((size_t)(b.z0 + z) * g.ny + (size_t)(b.y0 + y)) * g.pitch + (size_t)(b.x0 + x);
+}
 
-__device__ __forceinline__ CellWalk cell_at(const ExportBox &b, long long L) {
-    CellWalk c;
-    c.i = L % b.cx;
-    const long long r = L / b.cx;
-    c.j = r % b.cy;
-    c.k = r / b.cy;
+__device__ __forceinline__ int voxel_level(const DevGrid &g, size_t v) {
+    return (__ldg(g.sign + v) ? 33 : 0) + __popc(__ldg(g.mask + v));
+}
+
+// Inside test of a voxel: f = (s ? +1 : -1) * p * res is monotone in p for
+// each sign, so f < iso is p < p_free for free voxels and p > p_occ for
+// occupied ones (thresholds derived on the host from the same comparison).
+__device__ __forceinline__ bool inside_of(uint32_t mask, uint32_t sign, int p_free, int p_occ) {
+    const int pc = __popc(mask);
+    return sign ? pc < p_free : pc > p_occ;
+}
+
+// Bit i of the byte c moved to bit 4 i.
+__device__ __forceinline__ uint32_t spread4(uint32_t c) {
+    c = (c | (c << 12)) & 0x000F000Fu;
+    c = (c | (c << 6)) & 0x03030303u;
+    c = (c | (c << 3)) & 0x11111111u;
     return c;
 }
 
-__device__ __forceinline__ void cell_advance(const ExportBox &b, CellWalk &c, int d) {
-    c.i += d;
-    while (c.i >= b.cx) {
-        c.i -= b.cx;
-        if (++c.j == b.cy) {
-            c.j = 0;
-            ++c.k;
+// One warp per plane row.  With x0 a multiple of 4 (rows 16-byte aligned)
+// each lane reads four voxels at once (uint4 masks, one word of signs) and
+// the four ballots (bit l = voxel 4 l + q) are interleaved into the row's
+// four words of 32 voxels; otherwise one voxel per lane per word.
+__global__ void __launch_bounds__(256) k_mc_bits(DevGrid g, ExportBox b, int p_free, int p_occ,
+                                                 int wpr, uint32_t *__restrict__ bits) {
+    const int lane = threadIdx.x & 31;
+    const long long rows = (long long)b.by * b.bz;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const bool vec = (b.x0 & 3) == 0;
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows;
+         r += warps) {
+        long long y, z;
+        divmod(r, b.by, z, y);
+        const size_t v0 = voxel_index(g, b, 0, y, z);
+        const uint32_t *mrow = g.mask + v0;
+        const uint8_t *srow = g.sign + v0;
+        uint32_t *out = bits + r * wpr;
+        if (vec) {
+            for (int x0 = 0; x0 < b.bx; x0 += 256) {        // two chunks of 128 in flight
+                bool in[2][4] = {};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int x = x0 + 128 * h + 4 * lane;
+                    if (x + 3 < b.bx) {
+                        const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(mrow + x));
+                        const uint32_t s4 = __ldg(reinterpret_cast<const uint32_t *>(srow + x));
+                        in[h][0] = inside_of(m4.x, s4 & 0xFFu, p_free, p_occ);
+                        in[h][1] = inside_of(m4.y, (s4 >> 8) & 0xFFu, p_free, p_occ);
+                        in[h][2] = inside_of(m4.z, (s4 >> 16) & 0xFFu, p_free, p_occ);
+                        in[h][3] = inside_of(m4.w, s4 >> 24, p_free, p_occ);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (x + q < b.bx)
+                                in[h][q] = inside_of(__ldg(mrow + x + q), __ldg(srow + x + q), p_free, p_occ);
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t b0 = __ballot_sync(0xffffffffu, in[h][0]);
+                    const uint32_t b1 = __ballot_sync(0xffffffffu, in[h][1]);
+                    const uint32_t b2 = __ballot_sync(0xffffffffu, in[h][2]);
+                    const uint32_t b3 = __ballot_sync(0xffffffffu, in[h][3]);
+                    const int w = ((x0 + 128 * h) >> 5) + lane;   // lanes 0-3: the four words
+                    if (lane < 4 && w < wpr) {
+                        const int sh = 8 * lane;
+                        out[w] = spread4((b0 >> sh) & 0xFFu) | (spread4((b1 >> sh) & 0xFFu) << 1) |
+                                 (spread4((b2 >> sh) & 0xFFu) << 2) | (spread4((b3 >> sh) & 0xFFu) << 3);
+                    }
+                }
+            }
+        } else {
+            for (int w0 = 0; w0 < wpr; w0 += 4) {
+                bool in[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {         // four words' loads in flight
+                    const int x = 32 * (w0 + q) + lane;
+                    in[q] = x < b.bx && inside_of(__ldg(mrow + x), __ldg(srow + x), p_free, p_occ);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t word = __ballot_sync(0xffffffffu, in[q]);
+                    if (lane == 0 && w0 + q < wpr) out[w0 + q] = word;
+                }
+            }
         }
     }
 }
 
-__device__ __forceinline__ size_t cell_base(const DevGrid &g, const ExportBox &b, const CellWalk &c) {
-    return ((size_t)(b.z0 + c.k) * g.ny + (size_t)(b.y0 + c.j)) * g.pitch + (size_t)(b.x0 + c.i);
+struct Unit {
+    long long j, k;         // cell row
+    long long x0;           // first cell of the unit in the row
+};
+
+__device__ __forceinline__ Unit unit_at(const ExportBox &b, long long upr, long long u) {
+    Unit t;
+    long long row, seg;
+    divmod(u, upr, row, seg);
+    t.x0 = seg * MC_SEG;
+    divmod(row, b.cy, t.k, t.j);
+    return t;
 }
 
-// Inside bit of a voxel from the host-built table over (sign, popcount):
-// bit s * 33 + p of lut says (s ? p : -p) * res < iso.
-__device__ __forceinline__ uint32_t voxel_inside(const DevGrid &g, size_t v, uint64_t lut0,
-                                                 uint64_t lut1) {
-    const int idx = (__ldg(g.sign + v) ? 33 : 0) + __popc(__ldg(g.mask + v));
-    return (uint32_t)(((idx < 64 ? lut0 >> idx : lut1 >> (idx - 64))) & 1ull);
+// The lane's 32 cells from x = xs: its four windows (bit s and s + 1 of each
+// for cell xs + s), and the mask of cells that exist and are mixed.
+struct LaneCells {
+    uint64_t w00, w10, w01, w11;   // rows (j, k), (j+1, k), (j, k+1), (j+1, k+1)
+    uint32_t mixed;
+};
+
+__device__ __forceinline__ uint64_t window(const uint32_t *bits, int wpr, long long row, long long w) {
+    const uint32_t *p = bits + row * wpr;
+    const uint64_t lo = w < wpr ? __ldg(p + w) : 0u;
+    const uint64_t hi = w + 1 < wpr ? (__ldg(p + w + 1) & 1u) : 0u;
+    return lo | (hi << 32);
 }
 
-__device__ __forceinline__ int cell_config(const DevGrid &g, size_t v0, uint64_t lut0, uint64_t lut1) {
-    const size_t sy = (size_t)g.pitch, sz = (size_t)g.pitch * g.ny;
-    int cfg = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const size_t v = v0 + ((q & 1) ? 1 : 0) + ((q & 2) ? sy : 0) + ((q & 4) ? sz : 0);
-        cfg |= (int)voxel_inside(g, v, lut0, lut1) << q;
-    }
-    return cfg;
+__device__ __forceinline__ LaneCells lane_cells(const uint32_t *bits, int wpr, const ExportBox &b,
+                                                const Unit &t, int lane) {
+    LaneCells c;
+    const long long xs = t.x0 + 32LL * lane;
+    const long long w = xs >> 5;
+    const long long r = t.k * b.by + t.j;
+    c.w00 = window(bits, wpr, r, w);
+    c.w10 = window(bits, wpr, r + 1, w);
+    c.w01 = window(bits, wpr, r + b.by, w);
+    c.w11 = window(bits, wpr, r + b.by + 1, w);
+    const uint64_t o = c.w00 | c.w10 | c.w01 | c.w11, a = c.w00 & c.w10 & c.w01 & c.w11;
+    const uint64_t o2 = o | (o >> 1), a2 = a & (a >> 1);   // bit s: cells s, s + 1 together
+    const long long n = b.cx - xs;                        // cells of this lane that exist
+    const uint32_t valid = n >= 32 ? 0xffffffffu : n <= 0 ? 0u : (1u << n) - 1u;
+    c.mixed = (uint32_t)(o2 & ~a2) & valid;
+    return c;
 }
 
-__global__ void __launch_bounds__(256) k_mc_count(DevGrid g, ExportBox b, uint64_t lut0,
-                                                  uint64_t lut1, long long n_units,
+__device__ __forceinline__ int lane_config(const LaneCells &c, int s) {
+    return (int)(((c.w00 >> s) & 3u) | (((c.w10 >> s) & 3u) << 2) | (((c.w01 >> s) & 3u) << 4) |
+                 (((c.w11 >> s) & 3u) << 6));
+}
+
+__global__ void __launch_bounds__(256) k_mc_count(ExportBox b, const uint32_t *__restrict__ bits,
+                                                  int wpr, long long upr, long long n_units,
                                                   uint32_t *__restrict__ unit_count) {
     __shared__ uint8_t s_ntri[256];
     for (int c = threadIdx.x; c < 256; c += blockDim.x) s_ntri[c] = g_mc.ntri[c];
@@ -211,17 +334,24 @@ __global__ void __launch_bounds__(256) k_mc_count(DevGrid g, ExportBox b, uint64
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long u = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n_units;
          u += warps) {
-        const long long L0 = u * MC_UNIT + lane;
-        CellWalk c = cell_at(b, L0 < b.ncell ? L0 : 0);
-        uint32_t total = 0;
-        for (int s = 0; s < MC_STEPS; ++s) {
-            const long long L = L0 + 32LL * s;
-            uint32_t nt = 0;
-            if (L < b.ncell) nt = s_ntri[cell_config(g, cell_base(g, b, c), lut0, lut1)];
-            total += __reduce_add_sync(0xffffffffu, nt);
-            if (L + 32 < b.ncell) cell_advance(b, c, 32);
-        }
-        if (lane == 0) unit_count[u] = total;
+        const LaneCells c = lane_cells(bits, wpr, b, unit_at(b, upr, u), lane);
+        uint32_t nt = 0;
+        for (uint32_t m = c.mixed; m; m &= m - 1) nt += s_ntri[lane_config(c, __ffs(m) - 1)];
+        nt = __reduce_add_sync(0xffffffffu, nt);
+        if (lane == 0) unit_count[u] = nt;
+    }
+}
+
+// Crossing fractions t = (iso - f_a) / (f_b - f_a) for every pair of levels
+// (f = (s ? +1 : -1) * p * res), in binary32, once per call; entries of
+// pairs on the same side of iso are never read.
+__global__ void k_mc_fractions(float res, float iso, float *__restrict__ tab) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < MC_LEVELS * MC_LEVELS;
+         e += gridDim.x * blockDim.x) {
+        const int la = e / MC_LEVELS, lb = e % MC_LEVELS;
+        const float fa = __fmul_rn(__fmul_rn(la >= 33 ? 1.0f : -1.0f, (float)(la % 33)), res);
+        const float fb = __fmul_rn(__fmul_rn(lb >= 33 ? 1.0f : -1.0f, (float)(lb % 33)), res);
+        tab[e] = fa == fb ? 0.0f : __fdiv_rn(__fsub_rn(iso, fa), __fsub_rn(fb, fa));
     }
 }
 
@@ -296,97 +426,173 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_mc_scan_units(const uint32_t *
 }
 
 // ------------------------------------------------------------------ emit
-__global__ void __launch_bounds__(256) k_mc_emit(DevGrid g, ExportBox b, double res, double iso,
-                                                 uint64_t lut0, uint64_t lut1, long long n_units,
-                                                 const unsigned long long *__restrict__ unit_off,
-                                                 float *__restrict__ tri, long long *__restrict__ cell,
-                                                 long long max_tri) {
+// Position of the n-th (0-based) set bit of m, n < popc(m).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (n >= c) {
+            n -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src);
+    const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(v >> 32), src);
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+
+// A warp takes a unit with triangles and deals its surface cells (the mixed
+// bits of all lanes, in cell order) out 32 at a time, one per lane: lane l
+// of a round gets the cell of rank 32 r + l, found from the lanes' prefix
+// counts by a binary search over shuffles.
+__device__ __forceinline__ float mc_coord(float org, float res, long long idx, float t) {
+    return __fadd_rn(org, __fmul_rn(res, __fadd_rn(__fadd_rn(__ll2float_rn(idx), 0.5f), t)));
+}
+
+__global__ void __launch_bounds__(256, 4) k_mc_emit(DevGrid g, ExportBox b, float res,
+                                                    const uint32_t *__restrict__ bits, int wpr,
+                                                    long long upr, const float *__restrict__ frac,
+                                                    long long n_units,
+                                                    const unsigned long long *__restrict__ unit_off,
+                                                    const uint32_t *__restrict__ unit_count,
+                                                    float *__restrict__ tri,
+                                                    long long *__restrict__ cell, long long max_tri) {
     __shared__ McTable s_mc;
+    __shared__ float s_frac[MC_LEVELS * MC_LEVELS];
     {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(&g_mc);
         uint32_t *dst = reinterpret_cast<uint32_t *>(&s_mc);
         for (int c = threadIdx.x; c < (int)(sizeof(McTable) / 4); c += blockDim.x) dst[c] = src[c];
+        for (int c = threadIdx.x; c < MC_LEVELS * MC_LEVELS; c += blockDim.x) s_frac[c] = frac[c];
     }
     __syncthreads();
-    const double org[3] = {g.ox, g.oy, g.oz};
-    const size_t sy = (size_t)g.pitch, sz = (size_t)g.pitch * g.ny;
+    const float org[3] = {__double2float_rn(g.ox), __double2float_rn(g.oy), __double2float_rn(g.oz)};
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long u = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n_units;
          u += warps) {
-        const long long L0 = u * MC_UNIT + lane;
-        CellWalk c = cell_at(b, L0 < b.ncell ? L0 : 0);
+        if (unit_count[u] == 0) continue;                    // warp-uniform
+        const Unit t = unit_at(b, upr, u);
+        const LaneCells c = lane_cells(bits, wpr, b, t, lane);
+        const int nm = __popc(c.mixed);
+        int ex = nm;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, ex, d);
+            if (lane >= d) ex += y;
+        }
+        const int n_surf = __shfl_sync(0xffffffffu, ex, 31);
+        ex -= nm;                                             // exclusive prefix
         unsigned long long off = unit_off[u];
-        for (int s = 0; s < MC_STEPS; ++s) {
-            const long long L = L0 + 32LL * s;
-            int cfg = 0, nt = 0;
-            size_t v0 = 0;
-            if (L < b.ncell) {
-                v0 = cell_base(g, b, c);
-                cfg = cell_config(g, v0, lut0, lut1);
-                nt = s_mc.ntri[cfg];
+        const long long Lrow = (t.k * b.cy + t.j) * b.cx;
+        const long long jy = b.y0 + t.j, kz = b.z0 + t.k;
+        const float py[2] = {mc_coord(org[1], res, jy, 0.0f), mc_coord(org[1], res, jy + 1, 0.0f)};
+        const float pz[2] = {mc_coord(org[2], res, kz, 0.0f), mc_coord(org[2], res, kz + 1, 0.0f)};
+        for (int r0 = 0; r0 < n_surf; r0 += 32) {
+            const int k = r0 + lane;
+            int owner = 0;                                    // last lane with ex <= k
+#pragma unroll
+            for (int step = 16; step; step >>= 1) {
+                const int e = __shfl_sync(0xffffffffu, ex, owner + step);
+                if (e <= k) owner += step;
             }
+            const uint32_t om = __shfl_sync(0xffffffffu, c.mixed, owner);
+            const int oe = __shfl_sync(0xffffffffu, ex, owner);
+            LaneCells oc;
+            oc.w00 = shfl64(c.w00, owner);
+            oc.w10 = shfl64(c.w10, owner);
+            oc.w01 = shfl64(c.w01, owner);
+            oc.w11 = shfl64(c.w11, owner);
+            const bool have = k < n_surf;
+            const int s = have ? nth_set_bit(om, k - oe) : 0;
+            const int cfg = lane_config(oc, s);
+            const int nt = have ? s_mc.ntri[cfg] : 0;
             int incl = nt;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, incl, d);
                 if (lane >= d) incl += y;
             }
-            const int step_total = __shfl_sync(0xffffffffu, incl, 31);
-            if (nt) {
-                const long long base[3] = {b.x0 + c.i, b.y0 + c.j, b.z0 + c.k};
-                for (int t = 0; t < nt; ++t) {
-                    const unsigned long long id = off + (unsigned long long)(incl - nt + t);
-                    if (id >= (unsigned long long)max_tri) break;
-                    float *o = tri + 9ull * id;
+            unsigned long long id = off + (unsigned long long)(incl - nt);
+            off += (unsigned long long)__shfl_sync(0xffffffffu, incl, 31);
+            if (!have || id >= (unsigned long long)max_tri) continue;
+            const long long i = t.x0 + 32LL * owner + s;
+            int lv[8];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const int e = s_mc.edge[cfg][3 * t + k];
-                        const int axis = e >> 2;
-                        const int a = mc_edge_lo(e), bq = a | (1 << axis);
-                        const size_t va = v0 + ((a & 1) ? 1 : 0) + ((a & 2) ? sy : 0) + ((a & 4) ? sz : 0);
-                        const size_t vb = v0 + ((bq & 1) ? 1 : 0) + ((bq & 2) ? sy : 0) + ((bq & 4) ? sz : 0);
-                        const double fa = voxel_sdf(g, va, res), fb = voxel_sdf(g, vb, res);
-                        const double tt = __ddiv_rn(__dsub_rn(iso, fa), __dsub_rn(fb, fa));
+            for (int q = 0; q < 8; ++q)
+                lv[q] = voxel_level(g, voxel_index(g, b, i + (q & 1), t.j + ((q >> 1) & 1),
+                                                   t.k + ((q >> 2) & 1)));
+            const long long ix = b.x0 + i;
+            const float px[2] = {mc_coord(org[0], res, ix, 0.0f), mc_coord(org[0], res, ix + 1, 0.0f)};
+            const long long q0[3] = {ix, jy, kz};
+            for (int tt = 0; tt < nt && id < (unsigned long long)max_tri; ++tt, ++id) {
+                float *o = tri + 9ull * id;
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            double q = __dadd_rn((double)(base[d] + ((a >> d) & 1)), 0.5);
-                            if (d == axis) q = __dadd_rn(q, tt);
-                            o[3 * k + d] = __double2float_rn(__dadd_rn(org[d], __dmul_rn(res, q)));
-                        }
-                    }
-                    if (cell) cell[id] = L;
+                for (int kk = 0; kk < 3; ++kk) {
+                    const int e = s_mc.edge[cfg][3 * tt + kk];
+                    const int axis = e >> 2;
+                    const int a = mc_edge_lo(e), bq = a | (1 << axis);
+                    const float onaxis = mc_coord(org[axis], res, q0[axis],
+                                                  s_frac[lv[a] * MC_LEVELS + lv[bq]]);
+                    o[3 * kk + 0] = axis == 0 ? onaxis : px[a & 1];
+                    o[3 * kk + 1] = axis == 1 ? onaxis : py[(a >> 1) & 1];
+                    o[3 * kk + 2] = axis == 2 ? onaxis : pz[(a >> 2) & 1];
                 }
+                if (cell) cell[id] = Lrow + i;
             }
-            off += (unsigned long long)step_total;
-            if (L + 32 < b.ncell) cell_advance(b, c, 32);
         }
     }
 }
 
 // ------------------------------------------------------------------ launchers
-long long mc_units(const ExportBox &b) { return (b.ncell + MC_UNIT - 1) / MC_UNIT; }
+static long long mc_upr(const ExportBox &b) { return (b.cx + MC_SEG - 1) / MC_SEG; }
 
-size_t mc_scratch_bytes(const ExportBox &b) {
+long long mc_units(const ExportBox &b) { return b.ncell ? mc_upr(b) * b.cy * b.cz : 0; }
+
+static int mc_wpr(const ExportBox &b) { return (b.bx + 31) / 32; }
+
+static size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Scratch: [total | fractions | unit counts | unit offsets | tile sums | bit plane]
+struct McLayout {
+    unsigned long long *total;
+    float *frac;
+    uint32_t *cnt;
+    unsigned long long *uoff, *toff;
+    uint32_t *bits;
+    size_t bytes;
+};
+
+static McLayout mc_layout(const ExportBox &b, void *scratch) {
     const long long nu = mc_units(b);
     const long long nt = (nu + SCAN_THREADS - 1) / SCAN_THREADS;
-    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
-    return up(256) + up((size_t)nu * 4) + up((size_t)nu * 8) + up((size_t)nt * 8);
+    const size_t nbits = (size_t)mc_wpr(b) * (size_t)b.by * (size_t)b.bz;
+    McLayout m{};
+    char *p = static_cast<char *>(scratch);
+    size_t o = 0;
+    m.total = reinterpret_cast<unsigned long long *>(p + o);
+    o += up256(256);
+    m.frac = reinterpret_cast<float *>(p + o);
+    o += up256(sizeof(float) * MC_LEVELS * MC_LEVELS);
+    m.cnt = reinterpret_cast<uint32_t *>(p + o);
+    o += up256((size_t)nu * 4);
+    m.uoff = reinterpret_cast<unsigned long long *>(p + o);
+    o += up256((size_t)nu * 8);
+    m.toff = reinterpret_cast<unsigned long long *>(p + o);
+    o += up256((size_t)nt * 8);
+    m.bits = reinterpret_cast<uint32_t *>(p + o);
+    o += up256(nbits * 4);
+    m.bytes = o;
+    return m;
 }
 
-static void mc_layout(const ExportBox &b, void *scratch, unsigned long long **total,
-                      uint32_t **cnt, unsigned long long **uoff, unsigned long long **toff) {
-    const long long nu = mc_units(b);
-    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
-    char *p = static_cast<char *>(scratch);
-    *total = reinterpret_cast<unsigned long long *>(p);
-    p += up(256);
-    *cnt = reinterpret_cast<uint32_t *>(p);
-    p += up((size_t)nu * 4);
-    *uoff = reinterpret_cast<unsigned long long *>(p);
-    p += up((size_t)nu * 8);
-    *toff = reinterpret_cast<unsigned long long *>(p);
-}
+size_t mc_scratch_bytes(const ExportBox &b) { return mc_layout(b, nullptr).bytes; }
 
 static int grid_for(long long work, int per_block) {
     const long long b = (work + per_block - 1) / per_block;
@@ -400,31 +606,40 @@ void launch_sdf_field(const DevGrid &g, double res, const ExportBox &b, float *o
 
 void launch_mc_count(const DevGrid &g, const ExportBox &b, uint64_t lut0, uint64_t lut1,
                      void *scratch, cudaStream_t s) {
-    unsigned long long *total, *uoff, *toff;
-    uint32_t *cnt;
-    mc_layout(b, scratch, &total, &cnt, &uoff, &toff);
+    const McLayout m = mc_layout(b, scratch);
     const long long nu = mc_units(b);
     if (nu == 0) {
-        cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
+        cudaMemsetAsync(m.total, 0, sizeof(unsigned long long), s);
         return;
     }
     const long long nt = (nu + SCAN_THREADS - 1) / SCAN_THREADS;
-    k_mc_count<<<grid_for(nu, 8), 256, 0, s>>>(g, b, lut0, lut1, nu, cnt);
-    k_mc_scan_tiles<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(cnt, nu, toff);
-    k_mc_scan_sums<<<1, SCAN_THREADS, 0, s>>>(toff, nt, total);
-    k_mc_scan_units<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(cnt, nu, toff, uoff);
+    const int wpr = mc_wpr(b);
+    // the inside levels of each sign are a run of popcounts (f is monotone in
+    // p): free voxels p < p_free, occupied ones p > p_occ
+    auto inside = [&](int lv) { return ((lv < 64 ? lut0 >> lv : lut1 >> (lv - 64)) & 1ull) != 0; };
+    int p_free = 0, p_occ = 32;
+    while (p_free <= 32 && inside(33 + p_free)) ++p_free;
+    while (p_occ >= 0 && inside(p_occ)) --p_occ;
+    k_mc_bits<<<grid_for((long long)b.by * b.bz, 8), 256, 0, s>>>(g, b, p_free, p_occ, wpr, m.bits);
+    k_mc_count<<<grid_for(nu, 8), 256, 0, s>>>(b, m.bits, wpr, mc_upr(b), nu, m.cnt);
+    k_mc_scan_tiles<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(m.cnt, nu, m.toff);
+    k_mc_scan_sums<<<1, SCAN_THREADS, 0, s>>>(m.toff, nt, m.total);
+    k_mc_scan_units<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(m.cnt, nu, m.toff, m.uoff);
 }
 
 void launch_mc_emit(const DevGrid &g, const ExportBox &b, double res, double iso, uint64_t lut0,
                     uint64_t lut1, void *scratch, float *tri, long long *cell, long long max_tri,
                     cudaStream_t s) {
-    unsigned long long *total, *uoff, *toff;
-    uint32_t *cnt;
-    mc_layout(b, scratch, &total, &cnt, &uoff, &toff);
+    (void)lut0;
+    (void)lut1;
+    const McLayout m = mc_layout(b, scratch);
     const long long nu = mc_units(b);
     if (nu == 0 || max_tri <= 0) return;
-    k_mc_emit<<<grid_for(nu, 8), 256, 0, s>>>(g, b, res, iso, lut0, lut1, nu, uoff, tri, cell,
-                                              max_tri);
+    const float resf = (float)res, isof = (float)iso;
+    k_mc_fractions<<<(MC_LEVELS * MC_LEVELS + 255) / 256, 256, 0, s>>>(resf, isof, m.frac);
+    k_mc_emit<<<std::min(grid_for(nu, 8), 152 * 8), 256, 0, s>>>(g, b, resf, m.bits, mc_wpr(b),
+                                                                 mc_upr(b), m.frac, nu, m.uoff,
+                                                                 m.cnt, tri, cell, max_tri);
 }
 
 const unsigned long long *mc_total_ptr(void *scratch) {
