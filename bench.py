@@ -53,7 +53,7 @@ INTEGRATE_SRC = os.path.join(ROOT, "paper_2509_20081_gb300", "csrc", "integrate.
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_integrate, per kept
 # return, from the capture summarised under profiles/ (valid only for the
 # integrate.cu source with this sha256 prefix; otherwise traffic is null).
-NCU_TRAFFIC = {"integrate_sha": "11885f291e10ebe7", "bytes_per_kept_return": 1074.5,
+NCU_TRAFFIC = {"integrate_sha": "0fd2d45b444c0bce", "bytes_per_kept_return": 1074.5,
                "source": "profiles/k_integrate_urban_half.md (urban_half, 39.9 k kept returns "
                          "per scan, 42.9 MB DRAM read+write per launch), scaled by kept returns"}
 
@@ -245,6 +245,14 @@ def run_ours(args, rank, world):
     del bits
     torch.cuda.empty_cache()
 
+    # the library's autotuner picks the launch tuning on the first scan (the
+    # map is a scratch here: it is re-initialised below); results do not
+    # depend on the tuning
+    if args.no_autotune:
+        tuning = ws.tuning()
+    else:
+        tuning = B.dbt_workspace_autotune(g, k, ws, d_scans[0], poses[0], n_trials=3)
+
     # warm-up, then a fresh map
     for s in range(args.warmup):
         dbt.dbt_integrate_scan(g, k, ws, d_scans[s % nsc], poses[s % nsc])
@@ -327,6 +335,7 @@ def run_ours(args, rank, world):
         "latency_ms": {"p50": pct(t_scan, 50), "p99": pct(t_scan, 99), "max": t_scan[-1],
                        "what": "device time per scan, plain per-scan launches"},
         "batched": batched,
+        "tuning": tuning,
         "gpu_launches": 5 * args.steps,
         "roofline": {"bound": "hbm", "kernel": "k_integrate", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
@@ -380,6 +389,10 @@ def run_batched(args, w, k, g, d_scans, poses, stream, world):
     torch.cuda.synchronize()
     with torch.cuda.stream(cap):
         batches[0].run(stream=cap)                  # configures the kernels before capture
+        tuning = (batches[0].tuning() if args.no_autotune
+                  else batches[0].autotune(n_trials=2, stream=cap))   # g is re-initialised below
+    for b in batches:
+        b.set_tuning(**tuning)
     torch.cuda.synchronize()
     for b in batches:
         gr = torch.cuda.CUDAGraph()
@@ -407,7 +420,8 @@ def run_batched(args, w, k, g, d_scans, poses, stream, world):
     npts = sum(int(d_scans[s % nsc].shape[0]) for s in range(args.steps))
     out = {"value": world * npts / (ms * 1e-3), "unit": UNIT, "scans_per_batch": S,
            "ms_per_scan": ms / args.steps, "batch_ms_p50": pct(per, 50), "batch_ms_p99": pct(per, 99),
-           "launch": "one CUDA graph per batch (dbt_batch_run captured), replayed in order"}
+           "launch": "one CUDA graph per batch (dbt_batch_run captured), replayed in order",
+           "tuning": tuning}
     for b in batches:
         b.close()
     return out
@@ -444,6 +458,8 @@ def run_maps(args, rank, world):
     torch.cuda.synchronize()
     with torch.cuda.stream(cap):
         b.run(stream=cap)
+        tuning = (b.tuning() if args.no_autotune
+                  else b.autotune(n_trials=2, stream=cap))   # the maps are re-initialised before timing
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=cap):
@@ -482,7 +498,8 @@ def run_maps(args, rank, world):
                        "parallelism": f"replicas x{args.gpus}",
                        "l2": "grids larger than L2 in total; no flush"},
             "batched": {"value": world * npts / (ms_batch * 1e-3), "ms_per_step": ms_batch,
-                        "launch": "one CUDA graph of dbt_batch_run over all scans"},
+                        "launch": "one CUDA graph of dbt_batch_run over all scans",
+                        "tuning": tuning},
             "plain": {"value": world * npts / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                       "launch": f"{len(items)} dbt_integrate_scan calls (5 kernels each)"},
             "gpu_launches": 5 * args.steps}
@@ -665,10 +682,13 @@ def main():
                     default="urban")
     ap.add_argument("--maps", type=int, default=32, help="maps workload: number of maps")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: simulated seconds")
-    ap.add_argument("--speeds", default="1,8,16,24,32", help="serving: replay speed-ups")
+    ap.add_argument("--speeds", default="1,8,16,24,32,48,64",
+                    help="serving: replay speed-ups")
     ap.add_argument("--slo-ms", type=float, default=100.0, help="serving: p99 latency bound")
     ap.add_argument("--hbm-budget-gb", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch tuning (short runs, profiler captures)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--batch", type=int, default=10, help="scans per batch in the batched leg")
     ap.add_argument("--ref-stride", type=int, default=16,

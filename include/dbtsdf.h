@@ -300,6 +300,40 @@ dbt_status dbt_batch_stats(const dbt_batch *b, dbt_scan_stats *per_item, int32_t
 /* Frees the handle (not the caller's buffer). */
 dbt_status dbt_batch_destroy(dbt_batch *b);
 
+/* ---- Tuning and autotuning (no counterpart in the paper: launch choices of
+ * this implementation; every setting gives bit-identical maps) ----
+ *  heavy_pairs     bricks with more (return, brick) pairs than this are
+ *                  integrated by a whole CTA, the others by one warp
+ *                  (default 48; >= 0).
+ *  integrate_ctas  CTAs of the persistent integrate kernel; 0 = every SM
+ *                  filled to its occupancy limit (the default); at most 4x
+ *                  that. */
+typedef struct {
+    int32_t heavy_pairs;
+    int32_t integrate_ctas;
+} dbt_tuning;
+
+dbt_status dbt_workspace_set_tuning(dbt_workspace *ws, const dbt_kernels *k, const dbt_tuning *t);
+dbt_status dbt_workspace_get_tuning(const dbt_workspace *ws, dbt_tuning *t);
+dbt_status dbt_batch_set_tuning(dbt_batch *b, const dbt_tuning *t);
+dbt_status dbt_batch_get_tuning(const dbt_batch *b, dbt_tuning *t);
+
+/* Times every candidate tuning (heavy_pairs 16..256 x one, two or the
+ * maximum CTAs per SM) over n_trials runs of the batch's current items (one
+ * warm-up run each) with CUDA events on stream, keeps the fastest in *best
+ * and sets it on the batch.  The items are integrated (1 + n_trials) times
+ * per candidate, so the batch's grids end in an unspecified state: run it
+ * on scratch grids of the production shapes (fresh maps, or copies), then
+ * apply *best with dbt_batch_set_tuning.  Synchronous. */
+dbt_status dbt_batch_autotune(dbt_batch *b, int32_t n_trials, void *stream, dbt_tuning *best);
+
+/* The same for single-scan integration: times dbt_integrate_scan of one scan
+ * into g (a scratch grid, left in an unspecified state) and sets the
+ * fastest tuning on ws. */
+dbt_status dbt_workspace_autotune(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
+                                  const float *d_xyz, int64_t n, const double pose[12],
+                                  int32_t n_trials, void *stream, dbt_tuning *best);
+
 /* dbt_integrate_scan for callers that cannot allocate device memory (the
  * paper has no counterpart; this is a deployment convenience).  Some callers
  * may not call cudaMalloc while they run -- a real-time mapping loop that

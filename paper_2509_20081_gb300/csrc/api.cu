@@ -430,6 +430,7 @@ struct dbt_workspace {
     long long max_points;
     int nx, ny, nz, pitch, K;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;   // optional timing of the integrate kernel
+    int ctas = 0;                                       // integrate grid; 0 = occupancy maximum
 };
 
 extern "C" dbt_status dbt_workspace_size(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
@@ -478,6 +479,7 @@ static void ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels *k, l
     w->d.pairs = (uint32_t *)(base + L.pairs);
     w->d.pairs_cap = L.pairs_cap;
     w->d.poses = (Pose *)(base + L.poses);
+    w->d.heavy = HEAVY_PAIRS;
 }
 
 extern "C" dbt_status dbt_workspace_create(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
@@ -556,7 +558,8 @@ static dbt_status enqueue_scan(const dbt_grid *g, const dbt_kernels *k, dbt_work
     launch_alloc(ws->d, 2 * 152, s);
     launch_fill(dg, k->dp, ni, ws->d, hcap, s);
     if (ws->ev_begin) DBT_CUDA(cudaEventRecord(ws->ev_begin, s));
-    launch_integrate(dg, k->dp, k->dt, (long long)n, ws->d, integrate_grid_ctas(k->dp), s);
+    launch_integrate(dg, k->dp, k->dt, (long long)n, ws->d,
+                     ws->ctas ? ws->ctas : integrate_grid_ctas(k->dp), s);
     if (ws->ev_end) DBT_CUDA(cudaEventRecord(ws->ev_end, s));
     DBT_CUDA(cudaGetLastError());
     return DBT_OK;
@@ -798,6 +801,7 @@ struct dbt_batch {
     int n_items = 0;
     long long n_total = 0;
     BatchDev bd;
+    int ctas = 0;                        // integrate grid; 0 = occupancy maximum
 };
 
 static dbt_status batch_layout(const dbt_grid *grids, int n_grids, const dbt_kernels *k,
@@ -983,9 +987,125 @@ extern "C" dbt_status dbt_batch_run(dbt_batch *b, void *stream) {
     }
     launch_alloc(b->d, 2 * 152, s);
     if (b->n_items > 0) launch_fill_batch(b->bd, k->dp, b->n_total, b->d, hcap, s);
-    launch_integrate_batch(b->bd, k->dp, k->dt, b->n_total, b->d, integrate_grid_ctas(k->dp), s);
+    launch_integrate_batch(b->bd, k->dp, k->dt, b->n_total, b->d,
+                           b->ctas ? b->ctas : integrate_grid_ctas(k->dp), s);
     DBT_CUDA(cudaGetLastError());
     return DBT_OK;
+}
+
+// ------------------------------------------------------------------ tuning
+static dbt_status check_tuning(const dbt_tuning *t, const dbt_kernels *k) {
+    if (!t) return fail(DBT_EINVAL, "tuning is NULL");
+    if (t->heavy_pairs < 0) return fail(DBT_EINVAL, "heavy_pairs must be >= 0");
+    const int cap = 4 * integrate_grid_ctas(k->dp);
+    if (t->integrate_ctas < 0 || t->integrate_ctas > cap)
+        return fail(DBT_EINVAL, "integrate_ctas must be in [0, %d]", cap);
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_workspace_set_tuning(dbt_workspace *ws, const dbt_kernels *k,
+                                               const dbt_tuning *t) {
+    if (!ws || !k) return fail(DBT_EINVAL, "workspace or kernels is NULL");
+    dbt_status st = check_tuning(t, k);
+    if (st != DBT_OK) return st;
+    ws->d.heavy = (uint32_t)t->heavy_pairs;
+    ws->ctas = t->integrate_ctas;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_workspace_get_tuning(const dbt_workspace *ws, dbt_tuning *t) {
+    if (!ws || !t) return fail(DBT_EINVAL, "NULL argument");
+    t->heavy_pairs = (int32_t)ws->d.heavy;
+    t->integrate_ctas = ws->ctas;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_batch_set_tuning(dbt_batch *b, const dbt_tuning *t) {
+    if (!b) return fail(DBT_EINVAL, "batch is NULL");
+    dbt_status st = check_tuning(t, b->k);
+    if (st != DBT_OK) return st;
+    b->d.heavy = (uint32_t)t->heavy_pairs;
+    b->ctas = t->integrate_ctas;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_batch_get_tuning(const dbt_batch *b, dbt_tuning *t) {
+    if (!b || !t) return fail(DBT_EINVAL, "NULL argument");
+    t->heavy_pairs = (int32_t)b->d.heavy;
+    t->integrate_ctas = b->ctas;
+    return DBT_OK;
+}
+
+// Candidates: the heavy threshold (CTA mode from 16 to 128 pairs per brick)
+// crossed with the persistent grid (one or two CTAs per SM, or the occupancy
+// maximum).  Each is timed over n_trials runs after one warm-up run.
+static std::vector<dbt_tuning> tuning_candidates(const dbt_kernels *k) {
+    const int sms = device_sm_count(), full = integrate_grid_ctas(k->dp);
+    std::vector<int> grids = {full};
+    for (int c : {2 * sms, sms})
+        if (c < full) grids.push_back(c);
+    std::vector<dbt_tuning> out;
+    for (int h : {16, 24, 32, 48, 64, 96, 128, 192, 256})
+        for (int c : grids) out.push_back(dbt_tuning{h, c});
+    return out;
+}
+
+template <typename Run>
+static dbt_status autotune(const std::vector<dbt_tuning> &cands, int n_trials, cudaStream_t s,
+                           Run run, dbt_tuning *best) {
+    if (n_trials < 1 || n_trials > 1000) return fail(DBT_EINVAL, "n_trials must be in [1, 1000]");
+    cudaEvent_t e0, e1;
+    DBT_CUDA(cudaEventCreate(&e0));
+    DBT_CUDA(cudaEventCreate(&e1));
+    float best_ms = 3.4e38f;
+    dbt_status st = DBT_OK;
+    for (const dbt_tuning &c : cands) {
+        if ((st = run(c)) != DBT_OK) break;                 // warm-up with this tuning
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < n_trials && st == DBT_OK; ++i) st = run(c);
+        cudaEventRecord(e1, s);
+        if (st != DBT_OK) break;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "cudaEventSynchronize(autotune)");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+extern "C" dbt_status dbt_batch_autotune(dbt_batch *b, int32_t n_trials, void *stream,
+                                         dbt_tuning *best) {
+    if (!b || !best) return fail(DBT_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    dbt_status st = autotune(tuning_candidates(b->k), n_trials, s, [&](const dbt_tuning &c) {
+        dbt_status r = dbt_batch_set_tuning(b, &c);
+        return r == DBT_OK ? dbt_batch_run(b, stream) : r;
+    }, best);
+    if (st != DBT_OK) return st;
+    return dbt_batch_set_tuning(b, best);
+}
+
+extern "C" dbt_status dbt_workspace_autotune(const dbt_grid *g, const dbt_kernels *k,
+                                             dbt_workspace *ws, const float *d_xyz, int64_t n,
+                                             const double pose[12], int32_t n_trials, void *stream,
+                                             dbt_tuning *best) {
+    if (!ws || !k || !best) return fail(DBT_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    dbt_status st = autotune(tuning_candidates(k), n_trials, s, [&](const dbt_tuning &c) {
+        dbt_status r = dbt_workspace_set_tuning(ws, k, &c);
+        return r == DBT_OK ? enqueue_scan(g, k, ws, d_xyz, n, pose, s) : r;
+    }, best);
+    if (st != DBT_OK) return st;
+    return dbt_workspace_set_tuning(ws, k, best);
 }
 
 extern "C" dbt_status dbt_batch_stats(const dbt_batch *b, dbt_scan_stats *per_item, int32_t n,

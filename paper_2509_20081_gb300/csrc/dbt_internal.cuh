@@ -148,6 +148,7 @@ struct WsDev {
     uint32_t *pairs;            // pair payloads grouped by brick
     unsigned long long pairs_cap;
     Pose *poses;                // motion compensation: MAX_SCAN_POSES per-slice poses
+    uint32_t heavy;             // bricks with more pairs than this go to a whole CTA
 };
 
 // Update pre-steps of dbt_integrate_scan_ex: sequential downsampling (every
@@ -160,8 +161,9 @@ struct ScanEx {
 };
 constexpr int MAX_SCAN_POSES = 256;
 
-// Bricks with more (return, brick) pairs than this are integrated by a whole
-// CTA (its warps split the pairs); the others by a single warp.
+// Default of WsDev::heavy: bricks with more (return, brick) pairs than this
+// are integrated by a whole CTA, the others by a single warp (tunable per
+// workspace or batch; any value gives the same result).
 constexpr uint32_t HEAVY_PAIRS = 48;
 
 // Return record prec.w: bin in bits 0-15, batch grid index in bits 16-23,
@@ -189,6 +191,7 @@ void launch_fill_batch(const BatchDev &bd, const DevParams &p, long long n, cons
 void launch_integrate_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
                             long long n_input, const WsDev &ws, int grid_ctas, cudaStream_t s);
 int integrate_grid_ctas(const DevParams &p);
+int device_sm_count();
 void launch_footprint(const DevGrid &g, const DevParams &p, const DevTables &t, int n,
                       const WsDev &ws, uint32_t hcap, uint32_t *bits_u, uint32_t *bits_s,
                       unsigned long long *counts, cudaStream_t s);

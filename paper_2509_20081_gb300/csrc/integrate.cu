@@ -14,7 +14,7 @@
 // table load, a staged-word load, a byte-wise min and a conditional store.
 //
 // Work split.  Persistent CTAs of WPC warps.  Bricks (32 x 8 x 8 voxels)
-// with more than HEAVY_PAIRS (return, brick) pairs are taken first, one per
+// with more than ws.heavy (return, brick) pairs are taken first, one per
 // CTA: each warp applies a share of the pairs to its own staged copy and the
 // copies are merged (byte-wise min of codes, sum of counts).  The other
 // bricks are taken one per warp.  A brick is only ever written by the CTA or
@@ -621,6 +621,13 @@ static int configure(size_t smem, size_t smem_max) {
 
 // Words of a kernel row: an x-extent of K voxels starting anywhere in a word.
 static int words_per_row(int K) { return K <= 13 ? 4 : 6; }
+
+int device_sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
 
 // Persistent grid for these parameters: every SM filled to its occupancy limit.
 int integrate_grid_ctas(const DevParams &p) {

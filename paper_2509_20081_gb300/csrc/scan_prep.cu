@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, Ws
 // One segment of the pair array per touched brick (warp-aggregated bump of
 // the pool counter), the per-brick counter reset to serve as fill cursor,
 // and the brick queued for the integrate kernel: heavy bricks (more than
-// HEAVY_PAIRS pairs) from the front of `order`, light ones from the back.
+// ws.heavy pairs) from the front of `order`, light ones from the back.
 __global__ void __launch_bounds__(256) k_alloc(WsDev ws) {
     const uint32_t nt = min(ws.hdr->n_touched, ws.max_touched);
     const int lane = threadIdx.x & 31;
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(256) k_alloc(WsDev ws) {
         uint32_t wbase = 0;
         if (lane == 31 && incl) wbase = atomicAdd(&ws.hdr->pool, incl);
         wbase = __shfl_sync(0xffffffffu, wbase, 31);
-        const bool heavy = t < nt && len > HEAVY_PAIRS;
+        const bool heavy = t < nt && len > ws.heavy;
         const bool light = t < nt && !heavy;
         const unsigned hb = __ballot_sync(0xffffffffu, heavy);
         const unsigned lb = __ballot_sync(0xffffffffu, light);

@@ -45,6 +45,13 @@ DBT_MOTION_FULL = 0
 DBT_MOTION_YAW = 1
 
 
+class dbt_tuning(ctypes.Structure):
+    _fields_ = [("heavy_pairs", ctypes.c_int32), ("integrate_ctas", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"heavy_pairs": int(self.heavy_pairs), "integrate_ctas": int(self.integrate_ctas)}
+
+
 class dbt_grid(ctypes.Structure):
     _fields_ = [("mask", ctypes.c_void_p), ("sign", ctypes.c_void_p), ("hits", ctypes.c_void_p),
                 ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
@@ -107,6 +114,13 @@ _SIGS = {
                               _P(dbt_scan_options), _vp],
     "dbt_pose_ramp": [_P(ctypes.c_double), _P(ctypes.c_double), ctypes.c_int32, ctypes.c_int32,
                       _P(ctypes.c_double)],
+    "dbt_workspace_set_tuning": [_vp, _vp, _P(dbt_tuning)],
+    "dbt_workspace_get_tuning": [_vp, _P(dbt_tuning)],
+    "dbt_batch_set_tuning": [_vp, _P(dbt_tuning)],
+    "dbt_batch_get_tuning": [_vp, _P(dbt_tuning)],
+    "dbt_batch_autotune": [_vp, ctypes.c_int32, _vp, _P(dbt_tuning)],
+    "dbt_workspace_autotune": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
+                               ctypes.c_int32, _vp, _P(dbt_tuning)],
     "dbt_sdf_field": [_P(dbt_grid), _P(ctypes.c_int32), _vp, _vp],
     "dbt_mesh_scratch_size": [_P(dbt_grid), _P(ctypes.c_int32), _P(ctypes.c_size_t)],
     "dbt_mesh_extract": [_P(dbt_grid), _P(ctypes.c_int32), ctypes.c_double, _vp, ctypes.c_size_t,
@@ -305,6 +319,16 @@ class Workspace:
     def reset(self, stream=None):
         _check(lib().dbt_workspace_reset(self.h, _stream_ptr(stream)))
 
+    def set_tuning(self, kernels: "Kernels", heavy_pairs: int = 48, integrate_ctas: int = 0):
+        """dbt_workspace_set_tuning (launch choices only; results do not change)."""
+        t = dbt_tuning(int(heavy_pairs), int(integrate_ctas))
+        _check(lib().dbt_workspace_set_tuning(self.h, kernels.h, ctypes.byref(t)))
+
+    def tuning(self) -> dict:
+        t = dbt_tuning()
+        _check(lib().dbt_workspace_get_tuning(self.h, ctypes.byref(t)))
+        return t.as_dict()
+
     def close(self):
         if self.h:
             lib().dbt_workspace_destroy(self.h)
@@ -354,6 +378,19 @@ def dbt_integrate_scan_ex(grid: Grid, kernels: Kernels, ws: Workspace, xyz, pose
     _check(lib().dbt_integrate_scan_ex(ctypes.byref(grid.c), kernels.h, ws.h,
                                        xyz.data_ptr() if n else None, n, pp, ctypes.byref(opt),
                                        _stream_ptr(stream)))
+
+
+def dbt_workspace_autotune(grid: Grid, kernels: Kernels, ws: Workspace, xyz, pose,
+                           n_trials: int = 3, stream=None) -> dict:
+    """Times the candidate tunings on one scan integrated into grid (a
+    scratch grid: it is integrated repeatedly) and sets the fastest on ws."""
+    n = int(xyz.shape[0])
+    keep, pp = _pose_arg(pose)
+    t = dbt_tuning()
+    _check(lib().dbt_workspace_autotune(ctypes.byref(grid.c), kernels.h, ws.h,
+                                        xyz.data_ptr() if n else None, n, pp, int(n_trials),
+                                        _stream_ptr(stream), ctypes.byref(t)))
+    return t.as_dict()
 
 
 def dbt_pose_ramp(start, end, n_poses: int, mode: int = DBT_MOTION_FULL) -> np.ndarray:
@@ -551,6 +588,24 @@ class Batch:
 
     def run(self, stream=None):
         _check(lib().dbt_batch_run(self.h, _stream_ptr(stream)))
+
+    def set_tuning(self, heavy_pairs: int = 48, integrate_ctas: int = 0):
+        """dbt_batch_set_tuning (launch choices only; results do not change)."""
+        t = dbt_tuning(int(heavy_pairs), int(integrate_ctas))
+        _check(lib().dbt_batch_set_tuning(self.h, ctypes.byref(t)))
+
+    def tuning(self) -> dict:
+        t = dbt_tuning()
+        _check(lib().dbt_batch_get_tuning(self.h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def autotune(self, n_trials: int = 3, stream=None) -> dict:
+        """dbt_batch_autotune: times the candidate tunings on the current
+        items (integrating them repeatedly: use scratch grids) and keeps the
+        fastest."""
+        t = dbt_tuning()
+        _check(lib().dbt_batch_autotune(self.h, int(n_trials), _stream_ptr(stream), ctypes.byref(t)))
+        return t.as_dict()
 
     def stats(self, stream=None, check=True):
         per = (dbt_scan_stats * max(1, self.n_items))()

@@ -146,3 +146,82 @@ def test_batch_argument_errors(maps):
         b.set_items([(1, x, pose)])                       # no grid 1
     with pytest.raises(dbt.DbtError):
         b.set_items([(0, x, pose)] * 3)                   # more than max_items
+
+
+# ------------------------------------------------------------------ tuning
+def test_every_tuning_gives_the_same_maps(orc):
+    """The heavy-brick threshold and the integrate grid are launch choices:
+    every candidate leaves bit-identical maps (single scans and batches)."""
+    import paper_2509_20081_gb300 as dbt
+    w = synth.urban_sequence(n_scans=3, scale=0.25)
+    k = dbt.Kernels(dbt.make_params(**w.params))
+    dims = (w.grid.nx, w.grid.ny, w.grid.nz)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ref = None
+    for heavy, ctas in [(48, 0), (0, 0), (16, sms), (1 << 30, 2 * sms), (96, 1), (24, 4 * sms)]:
+        g = dbt.Grid(*dims, w.grid.res)
+        ws = dbt.Workspace(g, k, max(len(p) for p, _ in w.scans))
+        ws.set_tuning(k, heavy, ctas)
+        assert ws.tuning() == {"heavy_pairs": heavy, "integrate_ctas": ctas}
+        for pts, pose in w.scans:
+            dbt.dbt_integrate_scan(g, k, ws, torch.from_numpy(pts).cuda(), pose)
+        st = dbt.dbt_get_scan_stats(ws)
+        assert st["error"] == 0
+        out = g.numpy()
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(out, ref):
+                np.testing.assert_array_equal(a, b)
+        gb = dbt.Grid(*dims, w.grid.res)
+        b = dbt.Batch([gb], k, sum(len(p) for p, _ in w.scans), len(w.scans))
+        b.set_tuning(heavy, ctas)
+        b.set_items([(0, torch.from_numpy(p).cuda(), pose) for p, pose in w.scans])
+        b.run()
+        for a, r in zip(gb.numpy(), ref):
+            np.testing.assert_array_equal(a, r)
+        b.close()
+
+
+def test_autotune_picks_a_candidate_and_keeps_results(orc):
+    import paper_2509_20081_gb300 as dbt
+    w = synth.urban_sequence(n_scans=2, scale=0.25)
+    k = dbt.Kernels(dbt.make_params(**w.params))
+    dims = (w.grid.nx, w.grid.ny, w.grid.nz)
+    items = [(0, torch.from_numpy(p).cuda(), pose) for p, pose in w.scans]
+    scratch = dbt.Grid(*dims, w.grid.res)
+    b = dbt.Batch([scratch], k, sum(len(p) for p, _ in w.scans), len(items))
+    b.set_items(items)
+    best = b.autotune(n_trials=2)
+    assert best["heavy_pairs"] in (16, 24, 32, 48, 64, 96, 128, 192, 256)
+    assert best == b.tuning()
+    b.close()
+    g = dbt.Grid(*dims, w.grid.res)
+    b = dbt.Batch([g], k, sum(len(p) for p, _ in w.scans), len(items))
+    b.set_tuning(**best)
+    b.set_items(items)
+    b.run()
+    og = orc.Grid.create(*dims, w.grid.res)
+    po = orc.params(**w.params)
+    for p, pose in w.scans:
+        orc.integrate_scan(og, po, p, pose)
+    m, s, h = g.numpy()
+    np.testing.assert_array_equal(m, og.mask)
+    np.testing.assert_array_equal(h, og.hits)
+    np.testing.assert_array_equal(s, og.sign)
+    ws_grid = dbt.Grid(*dims, w.grid.res)
+    ws = dbt.Workspace(ws_grid, k, len(w.scans[0][0]))
+    t = dbt.dbtsdf.dbt_workspace_autotune(ws_grid, k, ws, items[0][1], w.scans[0][1], n_trials=1)
+    assert t == ws.tuning()
+
+
+def test_tuning_refuses_bad_values():
+    import paper_2509_20081_gb300 as dbt
+    B = dbt.dbtsdf
+    k = dbt.Kernels(dbt.make_params())
+    g = dbt.Grid(64, 64, 64, 0.1)
+    ws = dbt.Workspace(g, k, 100)
+    for heavy, ctas in [(-1, 0), (48, -2), (48, 10 ** 7)]:
+        with pytest.raises(B.DbtError) as e:
+            ws.set_tuning(k, heavy, ctas)
+        assert e.value.status == B.DBT_EINVAL
