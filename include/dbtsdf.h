@@ -414,6 +414,47 @@ dbt_status dbt_mesh_extract(const dbt_grid *g, const int32_t box[6], double iso,
  * (j&1) | (j>>1)<<2 (a = 1), j (a = 2). */
 dbt_status dbt_mesh_table(uint8_t *h_ntri, uint8_t *h_edges);
 
+/* Predicted points for the quality metrics: the centroid of each of n_tri
+ * triangles (9 floats each, as written by dbt_mesh_extract) into d_out (3
+ * floats each), ((a + b) + c) / 3 in binary32.  Async. */
+dbt_status dbt_mesh_centroids(const float *d_tri, int64_t n_tri, float *d_out, void *stream);
+
+/* ---- Reconstruction quality (Sec. IV-B, "Mapping results") ----
+ * Point sets are device float32 xyz arrays (12 bytes a point, 4-byte
+ * aligned, at most 2^31 points). */
+
+/* Bytes of scratch dbt_nn_distances needs for n_ref reference points. */
+dbt_status dbt_nn_scratch_size(int64_t n_ref, size_t *bytes);
+
+/* d_dist[i] = Euclidean distance from query i to its nearest reference
+ * point, exact (uniform-grid index over the bounding box of both sets,
+ * rings searched until no closer point can remain), evaluated in binary32;
+ * +inf when n_ref == 0.  d_scratch 256-byte aligned.  Async. */
+dbt_status dbt_nn_distances(const float *d_ref, int64_t n_ref, const float *d_query,
+                            int64_t n_query, void *d_scratch, size_t bytes, float *d_dist,
+                            void *stream);
+
+typedef struct {
+    double accuracy;      /* mean predicted -> reference distance (m) */
+    double completeness;  /* mean reference -> predicted distance (m) */
+    double chamfer_l1;    /* (accuracy + completeness) / 2 */
+    double precision;     /* fraction of predicted points with distance < tolerance */
+    double recall;        /* fraction of reference points with distance < tolerance */
+    double fscore;        /* 2 P R / (P + R), 0 when P + R = 0 */
+    int64_t n_pred, n_gt;
+} dbt_quality;
+
+dbt_status dbt_quality_scratch_size(int64_t n_pred, int64_t n_gt, size_t *bytes);
+
+/* The paper's metrics of a predicted point set against reference points at
+ * a tolerance (m, finite, >= 0): distances from dbt_nn_distances, sums in
+ * binary64 in a fixed order (the same result on every run).  An empty set
+ * gives 0 for its own mean and fraction.  Synchronous (the result is copied
+ * to *h_out). */
+dbt_status dbt_quality_metrics(const float *d_pred, int64_t n_pred, const float *d_gt,
+                               int64_t n_gt, double tolerance, void *d_scratch, size_t bytes,
+                               dbt_quality *h_out, void *stream);
+
 /* Synchronises stream and reports a latched device error of the workspace
  * (ws may be NULL to only synchronise). */
 dbt_status dbt_sync(void *stream, const dbt_workspace *ws);

@@ -131,6 +131,12 @@ def _declare(L):
     L.orc_mc_config.argtypes = [ctypes.c_int, ctypes.c_void_p]
     L.orc_sdf_field.restype = None
     L.orc_sdf_field.argtypes = [P(_Grid), ctypes.c_void_p, ctypes.c_void_p]
+    L.orc_nn_distances.restype = None
+    L.orc_nn_distances.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_int64, ctypes.c_void_p]
+    L.orc_quality_from_distances.restype = None
+    L.orc_quality_from_distances.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                             ctypes.c_int64, ctypes.c_double, ctypes.c_void_p]
     L.orc_mesh.restype = ctypes.c_int64
     L.orc_mesh.argtypes = [P(_Grid), ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                            ctypes.c_int64, ctypes.c_void_p]
@@ -368,3 +374,35 @@ def mesh(g: Grid, box=None, iso: float = 0.0):
         lib().orc_mesh(ctypes.byref(gc), b.ctypes.data, float(iso), tri.ctypes.data, n,
                        cell.ctypes.data)
     return tri, cell
+
+
+# ---------------------------------------------------------------- quality
+QUALITY_KEYS = ("accuracy", "completeness", "chamfer_l1", "precision", "recall", "fscore")
+
+
+def _pts(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, np.float32).reshape(-1, 3))
+
+
+def nn_distances(ref, query) -> np.ndarray:
+    """Distance of each query point to its nearest reference point (Sec.
+    IV-B metrics), brute force in binary64."""
+    r, q = _pts(ref), _pts(query)
+    out = np.empty(q.shape[0], np.float64)
+    lib().orc_nn_distances(r.ctypes.data, r.shape[0], q.ctypes.data, q.shape[0], out.ctypes.data)
+    return out
+
+
+def quality_from_distances(d_pred, d_gt, tolerance: float) -> dict:
+    a = np.ascontiguousarray(np.asarray(d_pred, np.float64))
+    b = np.ascontiguousarray(np.asarray(d_gt, np.float64))
+    out = np.empty(6, np.float64)
+    lib().orc_quality_from_distances(a.ctypes.data, a.size, b.ctypes.data, b.size,
+                                     float(tolerance), out.ctypes.data)
+    return dict(zip(QUALITY_KEYS, out.tolist()))
+
+
+def quality(pred, gt, tolerance: float) -> dict:
+    """Accuracy, completeness, Chamfer-L1, precision, recall and F-score of a
+    predicted point set against the reference points (Sec. IV-B)."""
+    return quality_from_distances(nn_distances(gt, pred), nn_distances(pred, gt), tolerance)

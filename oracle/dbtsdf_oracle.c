@@ -823,3 +823,62 @@ int64_t orc_mesh(const orc_grid *g, const int64_t box[6], double iso, float *tri
             }
     return n;
 }
+
+/* ------------------------------------------------------------------ */
+/* Reconstruction quality (Sec. IV-B, "Mapping results"): nearest-neighbour
+ * distances between a predicted point set (sampled from the iso-surface of
+ * the reconstructed mesh) and the reference surface points.
+ *   accuracy     = mean over predicted points of the distance to the
+ *                  nearest reference point;
+ *   completeness = mean over reference points of the distance to the
+ *                  nearest predicted point;
+ *   Chamfer-L1   = (accuracy + completeness) / 2;
+ *   recall       = fraction of reference points within the tolerance t of
+ *                  the prediction, precision the same for predicted points
+ *                  against the reference, F-score their harmonic mean.
+ * Reading: "within the tolerance" is d < t; F = 0 when P + R = 0.        */
+
+/* out[i] = min over reference points of |query_i - ref_j| (binary64,
+ * brute force; +inf when there is no reference point)                     */
+void orc_nn_distances(const float *ref, int64_t n_ref, const float *q, int64_t n_q, double *out)
+{
+    for (int64_t i = 0; i < n_q; i++) {
+        double best = INFINITY;
+        for (int64_t j = 0; j < n_ref; j++) {
+            double dx = (double)q[3 * i] - (double)ref[3 * j];
+            double dy = (double)q[3 * i + 1] - (double)ref[3 * j + 1];
+            double dz = (double)q[3 * i + 2] - (double)ref[3 * j + 2];
+            double d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 < best)
+                best = d2;
+        }
+        out[i] = sqrt(best);
+    }
+}
+
+/* out: accuracy, completeness, Chamfer-L1, precision, recall, F-score,
+ * from the two distance lists of orc_nn_distances.                        */
+void orc_quality_from_distances(const double *d_pred, int64_t n_pred, const double *d_gt,
+                                int64_t n_gt, double t, double out[6])
+{
+    double sa = 0.0, sc = 0.0;
+    int64_t np_in = 0, ng_in = 0;
+    for (int64_t i = 0; i < n_pred; i++) {
+        sa += d_pred[i];
+        np_in += d_pred[i] < t;
+    }
+    for (int64_t i = 0; i < n_gt; i++) {
+        sc += d_gt[i];
+        ng_in += d_gt[i] < t;
+    }
+    double acc = n_pred ? sa / (double)n_pred : 0.0;
+    double comp = n_gt ? sc / (double)n_gt : 0.0;
+    double prec = n_pred ? (double)np_in / (double)n_pred : 0.0;
+    double rec = n_gt ? (double)ng_in / (double)n_gt : 0.0;
+    out[0] = acc;
+    out[1] = comp;
+    out[2] = (acc + comp) / 2.0;
+    out[3] = prec;
+    out[4] = rec;
+    out[5] = prec + rec > 0.0 ? 2.0 * prec * rec / (prec + rec) : 0.0;
+}

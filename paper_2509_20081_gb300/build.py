@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libdbtsdf.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["api.cu", "scan_prep.cu", "integrate.cu", "noalloc.cu", "export.cu"]
+SOURCES = ["api.cu", "scan_prep.cu", "integrate.cu", "noalloc.cu", "export.cu", "quality.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler",
               "-fPIC,-ffp-contract=off,-fno-fast-math", "-I" + INCLUDE]

@@ -1305,6 +1305,103 @@ extern "C" dbt_status dbt_mesh_extract(const dbt_grid *g, const int32_t box[6], 
     return DBT_OK;
 }
 
+// ------------------------------------------------------------------ quality
+static bool aligned4(const void *p) { return ((uintptr_t)p & 3u) == 0; }
+
+static dbt_status check_points(const float *p, int64_t n, const char *what) {
+    if (n < 0) return fail(DBT_EINVAL, "%s: n < 0", what);
+    if (n > 0 && (!p || !aligned4(p))) return fail(DBT_EINVAL, "%s: NULL or misaligned", what);
+    if (n > (1ll << 31)) return fail(DBT_EINVAL, "%s: more than 2^31 points", what);
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_nn_scratch_size(int64_t n_ref, size_t *bytes) {
+    if (!bytes || n_ref < 0) return fail(DBT_EINVAL, "bad argument");
+    *bytes = nn_scratch_bytes(n_ref);
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_nn_distances(const float *d_ref, int64_t n_ref, const float *d_query,
+                                       int64_t n_query, void *d_scratch, size_t bytes,
+                                       float *d_dist, void *stream) {
+    dbt_status st = check_points(d_ref, n_ref, "reference");
+    if (st == DBT_OK) st = check_points(d_query, n_query, "query");
+    if (st != DBT_OK) return st;
+    if (n_query > 0 && !d_dist) return fail(DBT_EINVAL, "d_dist is NULL");
+    if (!d_scratch || !aligned256(d_scratch) || bytes < nn_scratch_bytes(n_ref))
+        return fail(DBT_EINVAL, "scratch must be 256-byte aligned and >= dbt_nn_scratch_size");
+    launch_nn_distances(d_ref, n_ref, d_query, n_query, d_scratch, d_dist, (cudaStream_t)stream);
+    DBT_CUDA(cudaGetLastError());
+    return DBT_OK;
+}
+
+struct QualityLayout {
+    size_t out, part, dpred, dgt, nn, total;
+};
+
+static QualityLayout quality_layout(int64_t n_pred, int64_t n_gt) {
+    QualityLayout q;
+    size_t o = 0;
+    q.out = o;   o += 256;
+    q.part = o;  o += up256(quality_partials_bytes());
+    q.dpred = o; o += up256((size_t)n_pred * 4);
+    q.dgt = o;   o += up256((size_t)n_gt * 4);
+    q.nn = o;    o += nn_scratch_bytes(std::max(n_pred, n_gt));
+    q.total = o;
+    return q;
+}
+
+extern "C" dbt_status dbt_quality_scratch_size(int64_t n_pred, int64_t n_gt, size_t *bytes) {
+    if (!bytes || n_pred < 0 || n_gt < 0) return fail(DBT_EINVAL, "bad argument");
+    *bytes = quality_layout(n_pred, n_gt).total;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_quality_metrics(const float *d_pred, int64_t n_pred, const float *d_gt,
+                                          int64_t n_gt, double tolerance, void *d_scratch,
+                                          size_t bytes, dbt_quality *h_out, void *stream) {
+    dbt_status st = check_points(d_pred, n_pred, "predicted");
+    if (st == DBT_OK) st = check_points(d_gt, n_gt, "reference");
+    if (st != DBT_OK) return st;
+    if (!h_out) return fail(DBT_EINVAL, "h_out is NULL");
+    if (!(tolerance >= 0.0) || !std::isfinite(tolerance))
+        return fail(DBT_EINVAL, "tolerance must be finite and >= 0");
+    const QualityLayout q = quality_layout(n_pred, n_gt);
+    if (!d_scratch || !aligned256(d_scratch) || bytes < q.total)
+        return fail(DBT_EINVAL, "scratch must be 256-byte aligned and >= dbt_quality_scratch_size");
+    const cudaStream_t s = (cudaStream_t)stream;
+    char *base = static_cast<char *>(d_scratch);
+    float *dp = reinterpret_cast<float *>(base + q.dpred);
+    float *dg = reinterpret_cast<float *>(base + q.dgt);
+    launch_nn_distances(d_gt, n_gt, d_pred, n_pred, base + q.nn, dp, s);    // accuracy side
+    launch_nn_distances(d_pred, n_pred, d_gt, n_gt, base + q.nn, dg, s);    // completeness side
+    double *out = reinterpret_cast<double *>(base + q.out);
+    launch_quality_reduce(dp, n_pred, dg, n_gt, (float)tolerance, base + q.part, out, s);
+    DBT_CUDA(cudaGetLastError());
+    double h[6];
+    DBT_CUDA(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, s));
+    DBT_CUDA(cudaStreamSynchronize(s));
+    h_out->accuracy = h[0];
+    h_out->completeness = h[1];
+    h_out->chamfer_l1 = h[2];
+    h_out->precision = h[3];
+    h_out->recall = h[4];
+    h_out->fscore = h[5];
+    h_out->n_pred = n_pred;
+    h_out->n_gt = n_gt;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_mesh_centroids(const float *d_tri, int64_t n_tri, float *d_out,
+                                         void *stream) {
+    dbt_status st = check_points(d_tri, n_tri, "triangles");
+    if (st != DBT_OK) return st;
+    if (n_tri > 0 && (!d_out || !aligned4(d_out))) return fail(DBT_EINVAL, "d_out NULL or misaligned");
+    launch_centroids(d_tri, n_tri, d_out, (cudaStream_t)stream);
+    DBT_CUDA(cudaGetLastError());
+    return DBT_OK;
+}
+
 extern "C" dbt_status dbt_mesh_table(uint8_t *h_ntri, uint8_t *h_edges) {
     if (!h_ntri || !h_edges) return fail(DBT_EINVAL, "NULL output");
     mc_table_host(h_ntri, h_edges);

@@ -216,6 +216,18 @@ void launch_mc_emit(const DevGrid &g, const ExportBox &b, double res, double iso
                     uint64_t lut1, void *scratch, float *tri, long long *cell, long long max_tri,
                     cudaStream_t s);
 const unsigned long long *mc_total_ptr(void *scratch);
+void launch_exclusive_scan(const uint32_t *cnt, long long n, unsigned long long *out,
+                           unsigned long long *tile, unsigned long long *total, cudaStream_t s);
+
+// Quality metrics (quality.cu).
+size_t nn_scratch_bytes(long long n_ref);
+void launch_nn_distances(const float *ref, long long n_ref, const float *q, long long n_q,
+                         void *scratch, float *dist, cudaStream_t s);
+size_t quality_partials_bytes();
+void launch_quality_reduce(const float *d_pred, long long n_pred, const float *d_gt,
+                           long long n_gt, float tol, void *partials, double *out6,
+                           cudaStream_t s);
+void launch_centroids(const float *tri, long long n, float *out, cudaStream_t s);
 void mc_table_host(uint8_t *ntri, uint8_t *edges);
 
 // Sets the thread's error message for a failed CUDA call; returns DBT_ECUDA.

@@ -642,6 +642,20 @@ void launch_mc_emit(const DevGrid &g, const ExportBox &b, double res, double iso
                                                                  m.cnt, tri, cell, max_tri);
 }
 
+// Exclusive prefix sums of n counts into out, the grand total into *total;
+// tile holds ceil(n / 1024) partial sums.
+void launch_exclusive_scan(const uint32_t *cnt, long long n, unsigned long long *out,
+                           unsigned long long *tile, unsigned long long *total, cudaStream_t s) {
+    if (n <= 0) {
+        cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
+        return;
+    }
+    const long long nt = (n + SCAN_THREADS - 1) / SCAN_THREADS;
+    k_mc_scan_tiles<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(cnt, n, tile);
+    k_mc_scan_sums<<<1, SCAN_THREADS, 0, s>>>(tile, nt, total);
+    k_mc_scan_units<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(cnt, n, tile, out);
+}
+
 const unsigned long long *mc_total_ptr(void *scratch) {
     return static_cast<const unsigned long long *>(scratch);
 }

@@ -52,6 +52,17 @@ class dbt_tuning(ctypes.Structure):
         return {"heavy_pairs": int(self.heavy_pairs), "integrate_ctas": int(self.integrate_ctas)}
 
 
+class dbt_quality(ctypes.Structure):
+    _fields_ = [("accuracy", ctypes.c_double), ("completeness", ctypes.c_double),
+                ("chamfer_l1", ctypes.c_double), ("precision", ctypes.c_double),
+                ("recall", ctypes.c_double), ("fscore", ctypes.c_double),
+                ("n_pred", ctypes.c_int64), ("n_gt", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: (float(getattr(self, k)) if t is ctypes.c_double else int(getattr(self, k)))
+                for k, t in self._fields_}
+
+
 class dbt_grid(ctypes.Structure):
     _fields_ = [("mask", ctypes.c_void_p), ("sign", ctypes.c_void_p), ("hits", ctypes.c_void_p),
                 ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
@@ -126,6 +137,12 @@ _SIGS = {
     "dbt_mesh_extract": [_P(dbt_grid), _P(ctypes.c_int32), ctypes.c_double, _vp, ctypes.c_size_t,
                          _vp, _vp, ctypes.c_int64, _P(ctypes.c_int64), _vp],
     "dbt_mesh_table": [_vp, _vp],
+    "dbt_mesh_centroids": [_vp, ctypes.c_int64, _vp, _vp],
+    "dbt_nn_scratch_size": [ctypes.c_int64, _P(ctypes.c_size_t)],
+    "dbt_nn_distances": [_vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, ctypes.c_size_t, _vp, _vp],
+    "dbt_quality_scratch_size": [ctypes.c_int64, ctypes.c_int64, _P(ctypes.c_size_t)],
+    "dbt_quality_metrics": [_vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_double, _vp,
+                            ctypes.c_size_t, _P(dbt_quality), _vp],
 }
 
 _lib = None
@@ -625,3 +642,52 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ quality
+def _pts_arg(x):
+    n = int(x.shape[0])
+    if n and (not x.is_cuda or not x.is_contiguous() or x.dim() != 2 or x.shape[1] != 3):
+        raise DbtError(DBT_EINVAL, "points must be a contiguous CUDA float32 (n, 3) tensor")
+    return n, (x.data_ptr() if n else None)
+
+
+def dbt_mesh_centroids(tri, stream=None):
+    """Centroids (t, 3) of a (t, 3, 3) float32 triangle tensor."""
+    import torch
+    t = tri.reshape(-1, 9)
+    n = int(t.shape[0])
+    out = torch.empty((n, 3), dtype=torch.float32, device=tri.device)
+    _check(lib().dbt_mesh_centroids(t.data_ptr() if n else None, n,
+                                    out.data_ptr() if n else None, _stream_ptr(stream)))
+    return out
+
+
+def dbt_nn_distances(ref, query, stream=None):
+    """Exact nearest-neighbour distance of each query point to ref (float32)."""
+    import torch
+    nr, pr = _pts_arg(ref)
+    nq, pq = _pts_arg(query)
+    nbytes = ctypes.c_size_t()
+    _check(lib().dbt_nn_scratch_size(nr, ctypes.byref(nbytes)))
+    dev = query.device if nq else ref.device
+    scratch = torch.empty(nbytes.value, dtype=torch.uint8, device=dev)
+    out = torch.empty(nq, dtype=torch.float32, device=dev)
+    _check(lib().dbt_nn_distances(pr, nr, pq, nq, scratch.data_ptr(), nbytes.value,
+                                  out.data_ptr() if nq else None, _stream_ptr(stream)))
+    return out
+
+
+def dbt_quality_metrics(pred, gt, tolerance: float, stream=None) -> dict:
+    """Accuracy, completeness, Chamfer-L1, precision, recall, F-score (Sec. IV-B)."""
+    import torch
+    npd, pp = _pts_arg(pred)
+    ngt, pg = _pts_arg(gt)
+    nbytes = ctypes.c_size_t()
+    _check(lib().dbt_quality_scratch_size(npd, ngt, ctypes.byref(nbytes)))
+    dev = pred.device if npd else gt.device
+    scratch = torch.empty(nbytes.value, dtype=torch.uint8, device=dev)
+    q = dbt_quality()
+    _check(lib().dbt_quality_metrics(pp, npd, pg, ngt, float(tolerance), scratch.data_ptr(),
+                                     nbytes.value, ctypes.byref(q), _stream_ptr(stream)))
+    return q.as_dict()

@@ -262,7 +262,7 @@ def make_pose(R: np.ndarray, t) -> np.ndarray:
 
 def lidar_scan(scene: Scene, pose: np.ndarray, beams: int, width: int, fov_deg: float,
                rmin: float, rmax: float, sigma: float, dropout: float, rng: Rng,
-               chunk: int = 4096) -> np.ndarray:
+               chunk: int = 4096, truth: bool = False) -> np.ndarray:
     """Spinning LiDAR: ``beams`` elevations in [-fov/2, +fov/2], ``width``
     azimuths k 2 pi / width; returns (beams * width, 3) float32 in the sensor
     frame, beam-major; misses, out-of-range and dropped returns are NaN."""
@@ -292,8 +292,14 @@ def lidar_scan(scene: Scene, pose: np.ndarray, beams: int, width: int, fov_deg: 
         for c0 in range(0, idx.size, chunk):
             j = idx[c0:c0 + chunk]
             t[j] = _raycast(sub, origin, dw[j])
-    t = t + rng.normal(n, sigma)
+    noise = rng.normal(n, sigma)
     drop = rng.uniform(n) < dropout
+    if truth:
+        # the exact surface points hit by the same rays, in the map frame
+        # (the draws above are still taken, so later scans stay the same)
+        ok = np.isfinite(t) & (t >= rmin) & (t <= rmax)
+        return (origin + dw[ok] * t[ok, None]).astype(np.float32)
+    t = t + noise
     bad = ~np.isfinite(t) | (t < rmin) | (t > rmax) | drop
     with np.errstate(invalid="ignore"):
         pts = ds * t[:, None]
@@ -345,10 +351,13 @@ def room_scan(seed_offset: int = 0, side: int = 128, res: float = 0.10, beams: i
 
 def urban_sequence(n_scans: int = 100, seed_offset: int = 1, scale: float = 1.0,
                    res: float = 0.05, beams: int = 64, width: int = 1024,
-                   rmax: float = 60.0) -> Workload:
+                   rmax: float = 60.0, truth: bool = False) -> Workload:
     """Urban sequence: grid (80x80x16 m) * scale at res; poses every 1 m * scale
     along a closed path of radius 25 m * scale, yaw along the tangent with
-    +-3 deg roll/pitch sinusoids; 2 cm * scale range noise; 2 % dropouts."""
+    +-3 deg roll/pitch sinusoids; 2 cm * scale range noise; 2 % dropouts.
+    truth: each scan is instead the noise-free surface points its rays hit,
+    in the map frame, without dropouts (the reference surface the quality
+    metrics compare against)."""
     rng = Rng(BASE_SEED + seed_offset)
     extent, height, ground = 80.0 * scale, 16.0 * scale, 1.0 * scale
     scene = urban_scene(rng, extent=extent, height=height, ground=ground,
@@ -371,9 +380,21 @@ def urban_sequence(n_scans: int = 100, seed_offset: int = 1, scale: float = 1.0,
         pitch = math.radians(3.0) * math.sin(0.17 * k + 1.0)
         pose = make_pose(rotation_rpy(roll, pitch, yaw), (x[i], y[i], ground + 1.8 * scale))
         pts = lidar_scan(scene, pose, beams, width, 45.0, 1.0 * scale, rmax, 0.02 * scale,
-                         0.02, rng)
+                         0.02, rng, truth=truth)
         scans.append((pts, pose))
     return Workload("urban", GridSpec(nx, nx, nz, res), scans, dict(DEFAULT_PARAMS))
+
+
+def point_cloud(rng: Rng, n: int, extent: float, sigma: float, planes: int = 6) -> np.ndarray:
+    """n points near a few random axis-aligned planes inside [0, extent]^3
+    (offsets N(0, sigma)): surface-like sets for the distance metrics."""
+    axis = rng.integers(planes, 0, 3)
+    level = rng.uniform(planes, 0.1 * extent, 0.9 * extent)
+    which = rng.integers(n, 0, planes)
+    p = rng.uniform(3 * n, 0.0, extent).reshape(n, 3)
+    a = axis[which]
+    p[np.arange(n), a] = level[which] + rng.normal(n, sigma)
+    return p.astype(np.float32)
 
 
 def batched_maps(n_maps: int = 32, scans_per_map: int = 8, seed_offset: int = 3,
