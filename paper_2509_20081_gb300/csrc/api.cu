@@ -380,10 +380,21 @@ extern "C" dbt_status dbt_grid_init(const dbt_grid *g, void *stream) {
 }
 
 // ------------------------------------------------------------------ workspace
+// Offsets of the scratch regions; a layout function must set every one
+// (ws_bind refuses a layout with a region left unset).
+constexpr size_t kUnset = ~size_t(0);
 struct WsLayout {
-    size_t hdr, stage, prec, hkey, hidx, bcnt, boff, touched, order, pairs, poses, total;
-    uint32_t hcap_alloc, max_touched, nbricks;
-    unsigned long long pairs_cap;
+    size_t hdr = kUnset, stage = kUnset, prec = kUnset, hkey = kUnset, hidx = kUnset,
+           bcnt = kUnset, boff = kUnset, touched = kUnset, order = kUnset, order_med = kUnset,
+           pairs = kUnset, poses = kUnset, total = kUnset;
+    uint32_t hcap_alloc = 0, max_touched = 0, nbricks = 0;
+    unsigned long long pairs_cap = 0;
+    bool complete() const {
+        for (size_t v : {hdr, stage, prec, hkey, hidx, bcnt, boff, touched, order, order_med, pairs,
+                         poses, total})
+            if (v == kUnset || (v != total && v >= total)) return false;
+        return true;
+    }
 };
 
 static size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -417,6 +428,7 @@ static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long m
     L->boff = o;     o += up256((size_t)nb * 4);
     L->touched = o;  o += up256((size_t)L->max_touched * 4);
     L->order = o;    o += up256((size_t)L->max_touched * 4);
+    L->order_med = o; o += up256((size_t)L->max_touched * 4);
     L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
     L->poses = o;    o += up256((size_t)MAX_SCAN_POSES * sizeof(Pose));
     L->total = o;
@@ -454,8 +466,9 @@ extern "C" dbt_status dbt_workspace_size(const dbt_grid *g, const dbt_kernels *k
 }
 
 // Points a workspace view at the regions of base laid out by L.
-static void ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels *k, long long max_points,
-                    const WsLayout &L, void *base_ptr) {
+static dbt_status ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels *k,
+                          long long max_points, const WsLayout &L, void *base_ptr) {
+    if (!L.complete()) return fail(DBT_ESTATE, "internal error: incomplete scratch layout");
     char *base = (char *)base_ptr;
     w->L = L;
     w->buf = base_ptr;
@@ -475,11 +488,13 @@ static void ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels *k, l
     w->d.boff = (uint32_t *)(base + L.boff);
     w->d.touched = (uint32_t *)(base + L.touched);
     w->d.order = (uint32_t *)(base + L.order);
+    w->d.order_med = (uint32_t *)(base + L.order_med);
     w->d.max_touched = L.max_touched;
     w->d.pairs = (uint32_t *)(base + L.pairs);
     w->d.pairs_cap = L.pairs_cap;
     w->d.poses = (Pose *)(base + L.poses);
     w->d.heavy = HEAVY_PAIRS;
+    return DBT_OK;
 }
 
 extern "C" dbt_status dbt_workspace_create(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
@@ -498,7 +513,11 @@ extern "C" dbt_status dbt_workspace_create(const dbt_grid *g, const dbt_kernels 
         return fail(DBT_ENOMEM, "workspace too small: %zu < %zu bytes", bytes, L.total);
     dbt_workspace *w = new (std::nothrow) dbt_workspace();
     if (!w) return fail(DBT_ENOMEM, "host allocation failed");
-    ws_bind(w, g, k, max_points, L, d_buf);
+    st = ws_bind(w, g, k, max_points, L, d_buf);
+    if (st != DBT_OK) {
+        delete w;
+        return st;
+    }
     cudaError_t e = cudaMemsetAsync(d_buf, 0, L.total, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         delete w;
@@ -770,7 +789,8 @@ dbt_status dbt::integrate_on_scratch(const dbt_grid *g, const dbt_kernels *k, co
                     "grid too large for the no-allocation scratch: needs %zu bytes, limit %zu "
                     "(%u bricks of 32x8x8 voxels)", L.total, scratch_bytes, L.nbricks);
     dbt_workspace w;
-    ws_bind(&w, g, k, max_points, L, scratch);
+    st = ws_bind(&w, g, k, max_points, L, scratch);
+    if (st != DBT_OK) return st;
     char *base = (char *)scratch;
     DBT_CUDA(cudaMemsetAsync(base + L.hdr, 0, up256(sizeof(WsHeader)), s));
     DBT_CUDA(cudaMemsetAsync(base + L.hkey, 0, L.bcnt - L.hkey, s));        // hash keys + indices
@@ -841,7 +861,9 @@ static dbt_status batch_layout(const dbt_grid *grids, int n_grids, const dbt_ker
     L->boff = o;     o += up256((size_t)nb * 4);
     L->touched = o;  o += up256((size_t)L->max_touched * 4);
     L->order = o;    o += up256((size_t)L->max_touched * 4);
+    L->order_med = o; o += up256((size_t)L->max_touched * 4);
     L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
+    L->poses = o;    o += up256((size_t)MAX_SCAN_POSES * sizeof(Pose));
     L->total = o;
     tail_offs[0] = o;  o += up256((size_t)n_grids * sizeof(DevGrid));
     tail_offs[1] = o;  o += up256((size_t)(n_grids + 1) * 4);
@@ -901,7 +923,11 @@ extern "C" dbt_status dbt_batch_create(const dbt_grid *grids, int32_t n_grids, c
     }
     char *base = (char *)d_buf;
     dbt_workspace w;
-    ws_bind(&w, &grids[0], k, max_points, b->L, d_buf);
+    dbt_status bst = ws_bind(&w, &grids[0], k, max_points, b->L, d_buf);
+    if (bst != DBT_OK) {
+        delete b;
+        return bst;
+    }
     b->d = w.d;
     b->bd.grids = (const DevGrid *)(base + b->off_grids);
     b->bd.bbase = (const uint32_t *)(base + b->off_bbase);

@@ -128,7 +128,9 @@ struct WsHeader {
     uint32_t n_light;
     uint32_t next_heavy;        // dynamic queue of heavy bricks
     unsigned long long acc_valid, acc_inside, acc_kept;
-    unsigned long long pad1[5];
+    uint32_t n_med;             // light bricks with more than heavy / 2 pairs (queued first)
+    uint32_t pad0;
+    unsigned long long pad1[4];
     ScanStats last;             // published by the last integrate CTA
 };
 
@@ -143,7 +145,8 @@ struct WsDev {
     uint32_t *bcnt;             // per brick: pair count / fill cursor (kept 0 between scans)
     uint32_t *boff;             // per brick: first pair of its segment
     uint32_t *touched;          // list of touched bricks (first-touch order)
-    uint32_t *order;            // touched bricks, heavy ones first
+    uint32_t *order;            // touched bricks: heavy ones first, small light ones last
+    uint32_t *order_med;        // the larger light bricks, claimed before the small ones
     uint32_t max_touched;
     uint32_t *pairs;            // pair payloads grouped by brick
     unsigned long long pairs_cap;

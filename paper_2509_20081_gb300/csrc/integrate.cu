@@ -189,34 +189,45 @@ __device__ __forceinline__ size_t chunk_index(const DevGrid &g, int bx, int by, 
     return ((size_t)gz * g.ny + gy) * g.pitch + (size_t)bx * BX + ch * 4;
 }
 
-__device__ __forceinline__ uint32_t load_codes(const DevGrid &g, size_t gi, uint32_t &form_bad) {
-    const uint4 m = __ldcg(reinterpret_cast<const uint4 *>(g.mask + gi));
+__device__ __forceinline__ uint32_t codes_of(const uint4 m, uint32_t &form_bad) {
     form_bad |= (m.x & (m.x + 1u)) | (m.y & (m.y + 1u)) | (m.z & (m.z + 1u)) | (m.w & (m.w + 1u));
     return (uint32_t)__popc(m.x) | ((uint32_t)__popc(m.y) << 8) | ((uint32_t)__popc(m.z) << 16) |
            ((uint32_t)__popc(m.w) << 24);
 }
 
+__device__ __forceinline__ uint32_t load_codes(const DevGrid &g, size_t gi, uint32_t &form_bad) {
+    return codes_of(__ldcg(reinterpret_cast<const uint4 *>(g.mask + gi)), form_bad);
+}
+
+// Eqs. 5-6 on one chunk: old counters hv and sign bytes sv, packed counts c.
+__device__ __forceinline__ void apply_counts(uint2 &hv, uint32_t &sv, uint2 c, uint32_t T,
+                                             uint32_t Hmax) {
+    const uint32_t cnt4[4] = {c.x & 0xFFFFu, c.x >> 16, c.y & 0xFFFFu, c.y >> 16};
+    uint32_t h[4] = {hv.x & 0xFFFFu, hv.x >> 16, hv.y & 0xFFFFu, hv.y >> 16};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const uint32_t hn = min(h[e] + cnt4[e], Hmax);
+        if (cnt4[e] && h[e] < T && hn >= T) sv &= ~(0xFFu << (8 * e));
+        if (cnt4[e]) h[e] = hn;
+    }
+    hv.x = h[0] | (h[1] << 16);
+    hv.y = h[2] | (h[3] << 16);
+}
+
+__device__ __forceinline__ void store_codes(const DevGrid &g, size_t gi, uint32_t k) {
+    const uint4 m = make_uint4(code_to_mask(k & 255u), code_to_mask((k >> 8) & 255u),
+                               code_to_mask((k >> 16) & 255u), code_to_mask(k >> 24));
+    __stcg(reinterpret_cast<uint4 *>(g.mask + gi), m);
+}
+
 // Phase D for one chunk: codes k (changed when dirty) and packed counts c.
 __device__ __forceinline__ void store_chunk(const DevGrid &g, size_t gi, uint32_t k, bool dirty,
                                             uint2 c, uint32_t T, uint32_t Hmax) {
-    if (dirty) {
-        const uint4 m = make_uint4(code_to_mask(k & 255u), code_to_mask((k >> 8) & 255u),
-                                   code_to_mask((k >> 16) & 255u), code_to_mask(k >> 24));
-        __stcg(reinterpret_cast<uint4 *>(g.mask + gi), m);
-    }
+    if (dirty) store_codes(g, gi, k);
     if (c.x | c.y) {
         uint2 hv = __ldcg(reinterpret_cast<const uint2 *>(g.hits + gi));
         uint32_t sv = __ldcg(reinterpret_cast<const unsigned int *>(g.sign + gi));
-        const uint32_t cnt4[4] = {c.x & 0xFFFFu, c.x >> 16, c.y & 0xFFFFu, c.y >> 16};
-        uint32_t h[4] = {hv.x & 0xFFFFu, hv.x >> 16, hv.y & 0xFFFFu, hv.y >> 16};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const uint32_t hn = min(h[e] + cnt4[e], Hmax);
-            if (cnt4[e] && h[e] < T && hn >= T) sv &= ~(0xFFu << (8 * e));
-            if (cnt4[e]) h[e] = hn;
-        }
-        hv.x = h[0] | (h[1] << 16);
-        hv.y = h[2] | (h[3] << 16);
+        apply_counts(hv, sv, c, T, Hmax);
         __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv);
         __stcg(reinterpret_cast<unsigned int *>(g.sign + gi), sv);
     }
@@ -381,6 +392,7 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
     WarpArea *wa = areas + warp;
     const uint32_t nt = min(*(volatile uint32_t *)&ws.hdr->n_touched, ws.max_touched);
     const uint32_t nheavy = min(*(volatile uint32_t *)&ws.hdr->n_heavy, nt);
+    const uint32_t nmed = min(*(volatile uint32_t *)&ws.hdr->n_med, nt - nheavy);
     const int SR = p.sr;
     const uint32_t T = (uint32_t)p.T, Hmax = (uint32_t)p.Hmax;
     uint32_t form_bad = 0;
@@ -487,7 +499,8 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
         if (lane == 0) w = atomicAdd(&ws.hdr->next_work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (nheavy + w >= nt) break;
-        const uint32_t b = ws.order[nheavy + w];
+        // the larger light bricks first; the small ones sit at order[nheavy + nmed, nt)
+        const uint32_t b = w < nmed ? ws.order_med[w] : ws.order[nheavy + w];
         const uint32_t start = ws.boff[b];
         uint32_t len = ws.bcnt[b];
         if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing
@@ -514,13 +527,29 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
             wa->need[lane + 32] = n1;
         }
         __syncwarp();
-        // B: lanes = 4 rows x 8 chunks
+        // B: lanes = 4 rows x 8 chunks; the masks of eight chunks are loaded
+        // before any shared-memory store (the stores go through a generic
+        // pointer, so the compiler would otherwise wait for each load in turn)
         const int rs = lane >> 3, ch = lane & 7;
-        for (int i = 0; i < BROWS / 4; ++i) {
-            const int row = rs + 4 * i;
-            if ((wa->need[row] >> ch) & 1u) {
+        for (int i0 = 0; i0 < BROWS / 4; i0 += 8) {
+            uint4 m[8];
+            uint32_t nd = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int row = rs + 4 * (i0 + q);
+                m[q] = make_uint4(0u, 0u, 0u, 0u);
+                if ((wa->need[row] >> ch) & 1u) {
+                    nd |= 1u << q;
+                    m[q] = __ldcg(reinterpret_cast<const uint4 *>(
+                        g.mask + chunk_index(g, bx, by, bz, row, ch)));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (!((nd >> q) & 1u)) continue;
+                const int row = rs + 4 * (i0 + q);
                 const int wd = kword(row, ch);
-                wa->kst[wd] = load_codes(g, chunk_index(g, bx, by, bz, row, ch), form_bad);
+                wa->kst[wd] = codes_of(m[q], form_bad);
                 wa->dirty[wd] = 0;
                 *reinterpret_cast<uint2 *>(&wa->cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
             }
@@ -537,13 +566,38 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
                 __syncwarp();
             }
         }
-        // D
-        for (int i = 0; i < BROWS / 4; ++i) {
-            const int row = rs + 4 * i;
-            if ((wa->need[row] >> ch) & 1u) {
+        // D: the old counters and signs of four chunks are loaded before any
+        // of them is stored (stores in between would serialise the loads)
+        for (int i0 = 0; i0 < BROWS / 4; i0 += 4) {
+            uint2 cs[4], hv[4];
+            uint32_t sv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = rs + 4 * (i0 + q);
+                cs[q] = make_uint2(0u, 0u);
+                hv[q] = make_uint2(0u, 0u);
+                sv[q] = 0u;
+                if ((wa->need[row] >> ch) & 1u) {
+                    cs[q] = *reinterpret_cast<const uint2 *>(&wa->cnt[row * 32 + ch * 4]);
+                    if (cs[q].x | cs[q].y) {
+                        const size_t gi = chunk_index(g, bx, by, bz, row, ch);
+                        hv[q] = __ldcg(reinterpret_cast<const uint2 *>(g.hits + gi));
+                        sv[q] = __ldcg(reinterpret_cast<const unsigned int *>(g.sign + gi));
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = rs + 4 * (i0 + q);
+                if (!((wa->need[row] >> ch) & 1u)) continue;
                 const int wd = kword(row, ch);
-                store_chunk(g, chunk_index(g, bx, by, bz, row, ch), wa->kst[wd], wa->dirty[wd] != 0,
-                            *reinterpret_cast<const uint2 *>(&wa->cnt[row * 32 + ch * 4]), T, Hmax);
+                const size_t gi = chunk_index(g, bx, by, bz, row, ch);
+                if (wa->dirty[wd]) store_codes(g, gi, wa->kst[wd]);
+                if (cs[q].x | cs[q].y) {
+                    apply_counts(hv[q], sv[q], cs[q], T, Hmax);
+                    __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv[q]);
+                    __stcg(reinterpret_cast<unsigned int *>(g.sign + gi), sv[q]);
+                }
             }
         }
         if (lane == 0) ws.bcnt[b] = 0u;
@@ -571,6 +625,7 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
             h->pool = 0u;
             h->next_work = 0u;
             h->n_heavy = 0u;
+            h->n_med = 0u;
             h->n_light = 0u;
             h->next_heavy = 0u;
             h->acc_valid = 0ull;

@@ -293,7 +293,10 @@ __global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, Ws
 // One segment of the pair array per touched brick (warp-aggregated bump of
 // the pool counter), the per-brick counter reset to serve as fill cursor,
 // and the brick queued for the integrate kernel: heavy bricks (more than
-// ws.heavy pairs) from the front of `order`, light ones from the back.
+// ws.heavy pairs) from the front of `order`, the larger light bricks (more
+// than half that) in `order_med` (taken first by the warps: longest work
+// first shortens the kernel's tail), the other light ones from the back of
+// `order`.
 __global__ void __launch_bounds__(256) k_alloc(WsDev ws) {
     const uint32_t nt = min(ws.hdr->n_touched, ws.max_touched);
     const int lane = threadIdx.x & 31;
@@ -314,21 +317,26 @@ __global__ void __launch_bounds__(256) k_alloc(WsDev ws) {
         if (lane == 31 && incl) wbase = atomicAdd(&ws.hdr->pool, incl);
         wbase = __shfl_sync(0xffffffffu, wbase, 31);
         const bool heavy = t < nt && len > ws.heavy;
-        const bool light = t < nt && !heavy;
+        const bool med = t < nt && !heavy && len > ws.heavy / 2;
+        const bool light = t < nt && !heavy && !med;
         const unsigned hb = __ballot_sync(0xffffffffu, heavy);
+        const unsigned mb = __ballot_sync(0xffffffffu, med);
         const unsigned lb = __ballot_sync(0xffffffffu, light);
-        uint32_t h0 = 0, l0 = 0;
+        uint32_t h0 = 0, m0 = 0, l0 = 0;
         if (lane == 0) {
             if (hb) h0 = atomicAdd(&ws.hdr->n_heavy, (uint32_t)__popc(hb));
+            if (mb) m0 = atomicAdd(&ws.hdr->n_med, (uint32_t)__popc(mb));
             if (lb) l0 = atomicAdd(&ws.hdr->n_light, (uint32_t)__popc(lb));
         }
         h0 = __shfl_sync(0xffffffffu, h0, 0);
+        m0 = __shfl_sync(0xffffffffu, m0, 0);
         l0 = __shfl_sync(0xffffffffu, l0, 0);
         const unsigned below = (1u << lane) - 1u;
         if (t < nt) {
             ws.boff[b] = wbase + incl - len;
             ws.bcnt[b] = 0;
             if (heavy) ws.order[h0 + __popc(hb & below)] = b;
+            else if (med) ws.order_med[m0 + __popc(mb & below)] = b;
             else ws.order[nt - 1 - (l0 + __popc(lb & below))] = b;
         }
     }
@@ -550,6 +558,7 @@ __global__ void k_ws_rearm_header(WsDev ws) {
     h->next_work = 0u;
     h->done_ctas = 0u;
     h->n_heavy = 0u;
+    h->n_med = 0u;
     h->n_light = 0u;
     h->next_heavy = 0u;
     h->acc_valid = 0ull;
