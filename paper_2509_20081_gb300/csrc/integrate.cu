@@ -247,6 +247,13 @@ __device__ __forceinline__ void store_chunk(const DevGrid &g, size_t gi, uint32_
 // finite sum is at most 3 R^2 = 108, and the no-contact value DENSE_INF = 127
 // plus a tap stays below 256, so bytes never carry into each other.
 constexpr uint32_t DENSE_INF = 127u;
+// The dense path's scratch (occupancy, two passes, plane masks, row list) at
+// the largest dilated extent it serves (R = 6) fits in the other warp areas.
+constexpr int DENSE_DMAX = BY + 2 * 6;
+static_assert(8 * DENSE_DMAX * DENSE_DMAX + 32 * DENSE_DMAX * DENSE_DMAX + 4 * 64 * DENSE_DMAX +
+                  4 * DENSE_DMAX + 4 + 2 * DENSE_DMAX * DENSE_DMAX <=
+              (WPC - 1) * (int)sizeof(WarpArea),
+              "dense scratch");
 
 __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const uint32_t *pairs,
                                 uint32_t len, WarpArea *areas, const uint8_t *ctab,
@@ -258,6 +265,9 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
     unsigned long long *occ = reinterpret_cast<unsigned long long *>(scr);   // D * D rows
     uint32_t *g1 = reinterpret_cast<uint32_t *>(scr + D * D * 8);          // D * D rows x 8 words
     uint32_t *g2 = g1 + D * D * 8;                                          // D x 8 rows x 8 words
+    uint32_t *pmask = g2 + D * 64;         // per dilated plane z: bit y = row (y, z) has a contact
+    uint32_t *nlist = pmask + D;           // number of rows with a contact
+    uint16_t *list = reinterpret_cast<uint16_t *>(nlist + 1);              // those rows
     WarpArea *a0 = areas;
     const uint32_t *need = a0->need;
     const uint32_t inf4 = DENSE_INF * 0x01010101u;
@@ -272,6 +282,8 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
         }
     }
     for (int r = tid; r < D * D; r += NTHR) occ[r] = 0ull;
+    if (tid < D) pmask[tid] = 0u;
+    if (tid == 0) *nlist = 0u;
     __syncthreads();
     // contacts: payload coordinates are brick-relative + R, i.e. dilated indices
     for (uint32_t j = tid; j < len; j += NTHR) {
@@ -279,38 +291,61 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
         atomicOr(&occ[((pl >> 11) & 31u) * D + ((pl >> 6) & 31u)], 1ull << (pl & 63u));
     }
     __syncthreads();
-    // pass x: squared distance to the nearest contact of the row within +-R
+    // rows without a contact are all INF after pass x: write them directly,
+    // list the others, and note per plane which rows hold contacts
+    for (int r = tid; r < D * D; r += NTHR) {
+        if (occ[r]) {
+            atomicOr(&pmask[r / D], 1u << (r % D));
+            list[atomicAdd(nlist, 1u)] = (uint16_t)r;
+        } else {
+            uint4 *row = reinterpret_cast<uint4 *>(g1 + r * 8);
+            row[0] = make_uint4(inf4, inf4, inf4, inf4);
+            row[1] = make_uint4(inf4, inf4, inf4, inf4);
+        }
+    }
+    __syncthreads();
+    // pass x over the listed rows: squared distance to the nearest contact of
+    // the row within +-R
     const uint32_t win = (1u << (2 * R + 1)) - 1u, lmask = (1u << (R + 1)) - 1u;
-    for (int r = warp; r < D * D; r += WPC) {
+    const uint32_t nl = *nlist;
+    for (uint32_t i = warp; i < nl; i += WPC) {
+        const int r = list[i];
         const unsigned long long o = occ[r];
         uint32_t v = DENSE_INF;
-        if (o) {
-            const uint32_t wv = (uint32_t)(o >> lane) & win;   // bit j: contact at x - R + j
-            const uint32_t left = wv & lmask, right = wv >> R;
-            int d = 2 * R + 2;
-            if (left) d = R - (31 - __clz(left));
-            if (right) d = min(d, __ffs(right) - 1);
-            if (d <= R) v = (uint32_t)(d * d);
-        }
+        const uint32_t wv = (uint32_t)(o >> lane) & win;   // bit j: contact at x - R + j
+        const uint32_t left = wv & lmask, right = wv >> R;
+        int d = 2 * R + 2;
+        if (left) d = R - (31 - __clz(left));
+        if (right) d = min(d, __ffs(right) - 1);
+        if (d <= R) v = (uint32_t)(d * d);
         reinterpret_cast<unsigned char *>(g1)[r * 32 + lane] = (unsigned char)v;
     }
     __syncthreads();
-    // pass y
+    // pass y: taps only from rows with contacts (an INF row cannot lower the
+    // minimum: INF + dy^2 >= INF and the result is clamped to INF)
+    const uint32_t twin = (1u << (2 * R + 1)) - 1u;
     for (int idx = tid; idx < D * 64; idx += NTHR) {
         const int w = idx & 7, y = (idx >> 3) & 7, zp = idx >> 6;
         uint32_t acc = inf4;
-        for (int dy = -R; dy <= R; ++dy)
-            acc = vmin4(acc, g1[(zp * D + (y + dy + R)) * 8 + w] + (uint32_t)(dy * dy) * 0x01010101u);
+        for (uint32_t m = (pmask[zp] >> y) & twin; m; m &= m - 1u) {
+            const int t = __ffs(m) - 1, dy = t - R;
+            acc = vmin4(acc, g1[(zp * D + (y + t)) * 8 + w] + (uint32_t)(dy * dy) * 0x01010101u);
+        }
         g2[(zp * 8 + y) * 8 + w] = vmin4(acc, inf4);
     }
+    uint32_t planes = 0;                   // planes with any contact
+    for (int zp = 0; zp < D; ++zp) planes |= (pmask[zp] ? 1u : 0u) << zp;
     __syncthreads();
-    // pass z, codes, and Eq. 4 on the staged brick
+    // pass z (taps only from planes with contacts), codes, and Eq. 4 on the
+    // staged brick
     for (int idx = tid; idx < BROWS * 8; idx += NTHR) {
         const int w = idx & 7, row = idx >> 3, y = row & 7, z = row >> 3;
         if (!((need[row] >> w) & 1u)) continue;
         uint32_t acc = inf4;
-        for (int dz = -R; dz <= R; ++dz)
-            acc = vmin4(acc, g2[((z + dz + R) * 8 + y) * 8 + w] + (uint32_t)(dz * dz) * 0x01010101u);
+        for (uint32_t m = (planes >> z) & twin; m; m &= m - 1u) {
+            const int t = __ffs(m) - 1, dz = t - R;
+            acc = vmin4(acc, g2[((z + t) * 8 + y) * 8 + w] + (uint32_t)(dz * dz) * 0x01010101u);
+        }
         const uint32_t code = (uint32_t)ctab[acc & 255u] | ((uint32_t)ctab[(acc >> 8) & 255u] << 8) |
                               ((uint32_t)ctab[(acc >> 16) & 255u] << 16) |
                               ((uint32_t)ctab[acc >> 24] << 24);
