@@ -148,6 +148,14 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
 // several warps count into one array, so counts are added atomically to
 // their packed 16-bit halves (a voxel's total never reaches 2^16: it is at
 // most the number of lattice points within r_s).
+//
+// Offsets are packed bytes (o + 128) and the contact c is packed as bytes
+// (c - 128), so one byte-wise add gives the voxel's brick coordinates
+// o + c, which lie in [-20, 51] and wrap below zero to >= 236; one byte-wise
+// compare then tests all three against the brick (x < 32, y < 8, z < 8; the
+// zero padding entries land at c + 128 >= 108 and fail it too).
+static_assert(BX == 32 && BY == 8 && BZ == 8 && MAX_K <= 21,
+              "shadow_pair's byte packing assumes 32 x 8 x 8 bricks and |offsets| <= 10");
 template <bool ATOMIC>
 __device__ __forceinline__ void shadow_pair(uint32_t pl, uint16_t *cnt, const uint32_t *sh,
                                             const uint32_t *shs, int R, int SR, int lane) {
@@ -157,6 +165,8 @@ __device__ __forceinline__ void shadow_pair(uint32_t pl, uint16_t *cnt, const ui
     if (!(cx >= -SR && cx <= BX - 1 + SR && cy >= -SR && cy <= BY - 1 + SR && cz >= -SR &&
           cz <= BZ - 1 + SR))
         return;
+    const uint32_t cpk = ((uint32_t)(cx - 128) & 255u) | (((uint32_t)(cy - 128) & 255u) << 8) |
+                         (((uint32_t)(cz - 128) & 255u) << 16);
     const uint32_t bin = pl >> 16;
     const uint32_t e0 = shs[bin], e1 = shs[bin + 1];
     for (uint32_t e = e0; e < e1; e += 96) {
@@ -166,18 +176,13 @@ __device__ __forceinline__ void shadow_pair(uint32_t pl, uint16_t *cnt, const ui
         for (int h = 0; h < 3; ++h) o[h] = e + 32 * h + lane < e1 ? sh[e + 32 * h + lane] : 0u;
 #pragma unroll
         for (int h = 0; h < 3; ++h) {
-            if (o[h]) {   // packed offsets are never 0 (each byte is biased by 128)
-                const int vx = cx + (int)(o[h] & 255u) - 128;
-                const int vy = cy + (int)((o[h] >> 8) & 255u) - 128;
-                const int vz = cz + (int)((o[h] >> 16) & 255u) - 128;
-                if ((unsigned)vx < (unsigned)BX && (unsigned)vy < (unsigned)BY &&
-                    (unsigned)vz < (unsigned)BZ) {
-                    const int v = (vz * BY + vy) * BX + vx;
-                    if (ATOMIC)
-                        atomicAdd(reinterpret_cast<uint32_t *>(cnt) + (v >> 1), 1u << (16 * (v & 1)));
-                    else
-                        cnt[v] += 1;   // distinct voxels within one pair
-                }
+            const uint32_t u = __vadd4(o[h], cpk);                    // bytes x, y, z
+            if ((__vcmpltu4(u, 0x00080820u) & 0x00FFFFFFu) == 0x00FFFFFFu) {
+                const int v = (int)(__byte_perm(u, 0u, 0x4420u) + ((u >> 3) & 0xE0u));
+                if (ATOMIC)
+                    atomicAdd(reinterpret_cast<uint32_t *>(cnt) + (v >> 1), 1u << (16 * (v & 1)));
+                else
+                    cnt[v] += 1;   // distinct voxels within one pair
             }
         }
     }
@@ -199,19 +204,27 @@ __device__ __forceinline__ uint32_t load_codes(const DevGrid &g, size_t gi, uint
     return codes_of(__ldcg(reinterpret_cast<const uint4 *>(g.mask + gi)), form_bad);
 }
 
-// Eqs. 5-6 on one chunk: old counters hv and sign bytes sv, packed counts c.
-__device__ __forceinline__ void apply_counts(uint2 &hv, uint32_t &sv, uint2 c, uint32_t T,
-                                             uint32_t Hmax) {
+// Eqs. 5-6 on one chunk: old counters hv, packed counts c; returns bit e set
+// when voxel e's counter crosses T (its sign becomes occupied).  The sign
+// only ever goes from free to occupied, so it needs no read: the crossing
+// voxels get a zero byte, every other sign byte is left as it is.
+__device__ __forceinline__ uint32_t apply_counts(uint2 &hv, uint2 c, uint32_t T, uint32_t Hmax) {
     const uint32_t cnt4[4] = {c.x & 0xFFFFu, c.x >> 16, c.y & 0xFFFFu, c.y >> 16};
     uint32_t h[4] = {hv.x & 0xFFFFu, hv.x >> 16, hv.y & 0xFFFFu, hv.y >> 16};
+    uint32_t cross = 0;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const uint32_t hn = min(h[e] + cnt4[e], Hmax);
-        if (cnt4[e] && h[e] < T && hn >= T) sv &= ~(0xFFu << (8 * e));
+        if (cnt4[e] && h[e] < T && hn >= T) cross |= 1u << e;
         if (cnt4[e]) h[e] = hn;
     }
     hv.x = h[0] | (h[1] << 16);
     hv.y = h[2] | (h[3] << 16);
+    return cross;
+}
+
+__device__ __forceinline__ void store_crossings(const DevGrid &g, size_t gi, uint32_t cross) {
+    for (uint32_t m = cross; m; m &= m - 1u) g.sign[gi + (__ffs(m) - 1)] = 0u;
 }
 
 __device__ __forceinline__ void store_codes(const DevGrid &g, size_t gi, uint32_t k) {
@@ -226,10 +239,9 @@ __device__ __forceinline__ void store_chunk(const DevGrid &g, size_t gi, uint32_
     if (dirty) store_codes(g, gi, k);
     if (c.x | c.y) {
         uint2 hv = __ldcg(reinterpret_cast<const uint2 *>(g.hits + gi));
-        uint32_t sv = __ldcg(reinterpret_cast<const unsigned int *>(g.sign + gi));
-        apply_counts(hv, sv, c, T, Hmax);
+        const uint32_t cross = apply_counts(hv, c, T, Hmax);
         __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv);
-        __stcg(reinterpret_cast<unsigned int *>(g.sign + gi), sv);
+        store_crossings(g, gi, cross);
     }
 }
 
@@ -601,24 +613,20 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
                 __syncwarp();
             }
         }
-        // D: the old counters and signs of four chunks are loaded before any
-        // of them is stored (stores in between would serialise the loads)
+        // D: the old counters of four chunks are loaded before any of them
+        // is stored (stores in between would serialise the loads)
         for (int i0 = 0; i0 < BROWS / 4; i0 += 4) {
             uint2 cs[4], hv[4];
-            uint32_t sv[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int row = rs + 4 * (i0 + q);
                 cs[q] = make_uint2(0u, 0u);
                 hv[q] = make_uint2(0u, 0u);
-                sv[q] = 0u;
                 if ((wa->need[row] >> ch) & 1u) {
                     cs[q] = *reinterpret_cast<const uint2 *>(&wa->cnt[row * 32 + ch * 4]);
-                    if (cs[q].x | cs[q].y) {
-                        const size_t gi = chunk_index(g, bx, by, bz, row, ch);
-                        hv[q] = __ldcg(reinterpret_cast<const uint2 *>(g.hits + gi));
-                        sv[q] = __ldcg(reinterpret_cast<const unsigned int *>(g.sign + gi));
-                    }
+                    if (cs[q].x | cs[q].y)
+                        hv[q] = __ldcg(reinterpret_cast<const uint2 *>(
+                            g.hits + chunk_index(g, bx, by, bz, row, ch)));
                 }
             }
 #pragma unroll
@@ -629,9 +637,9 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
                 const size_t gi = chunk_index(g, bx, by, bz, row, ch);
                 if (wa->dirty[wd]) store_codes(g, gi, wa->kst[wd]);
                 if (cs[q].x | cs[q].y) {
-                    apply_counts(hv[q], sv[q], cs[q], T, Hmax);
+                    const uint32_t cross = apply_counts(hv[q], cs[q], T, Hmax);
                     __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv[q]);
-                    __stcg(reinterpret_cast<unsigned int *>(g.sign + gi), sv[q]);
+                    store_crossings(g, gi, cross);
                 }
             }
         }
