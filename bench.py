@@ -53,9 +53,9 @@ INTEGRATE_SRC = os.path.join(ROOT, "paper_2509_20081_gb300", "csrc", "integrate.
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_integrate, per kept
 # return, from the capture summarised under profiles/ (valid only for the
 # integrate.cu source with this sha256 prefix; otherwise traffic is null).
-NCU_TRAFFIC = {"integrate_sha": "0fd2d45b444c0bce", "bytes_per_kept_return": 1074.5,
+NCU_TRAFFIC = {"integrate_sha": "13bb4b024bdc33fd", "bytes_per_kept_return": 854.6,
                "source": "profiles/k_integrate_urban_half.md (urban_half, 39.9 k kept returns "
-                         "per scan, 42.9 MB DRAM read+write per launch), scaled by kept returns"}
+                         "per scan, 34.1 MB DRAM read+write per launch), scaled by kept returns"}
 
 WORKLOADS = {
     "urban": dict(n_scans=100, scale=1.0, res=0.05, beams=64, width=1024, seed_offset=1),
