@@ -342,7 +342,7 @@ dbt_status dbt_workspace_autotune(const dbt_grid *g, const dbt_kernels *k, dbt_w
  * point uses a fixed scratch array compiled into the library instead and
  * allocates nothing (host or device).  Limits: n <= 65,536 returns per scan,
  * and the grid's integration layout must fit in 18 MiB (true for every grid
- * of up to 524,288 bricks of 32 x 8 x 8 voxels at K <= 17, ~350,000 bricks
+ * of up to 524,288 bricks of 32 x 8 x 8 voxels at K <= 17, ~440,000 bricks
  * at K = 19 or 21); larger inputs are rejected
  * with DBT_EINVAL and a message.  The 18 MiB array occupies device memory on
  * every GPU that loads the library until the process exits.  All calls share

@@ -385,12 +385,12 @@ extern "C" dbt_status dbt_grid_init(const dbt_grid *g, void *stream) {
 constexpr size_t kUnset = ~size_t(0);
 struct WsLayout {
     size_t hdr = kUnset, stage = kUnset, prec = kUnset, hkey = kUnset, hidx = kUnset,
-           bcnt = kUnset, boff = kUnset, touched = kUnset, order = kUnset, order_med = kUnset,
+           bcnt = kUnset, boff = kUnset, order = kUnset, order_med = kUnset,
            pairs = kUnset, poses = kUnset, total = kUnset;
     uint32_t hcap_alloc = 0, max_touched = 0, nbricks = 0;
     unsigned long long pairs_cap = 0;
     bool complete() const {
-        for (size_t v : {hdr, stage, prec, hkey, hidx, bcnt, boff, touched, order, order_med, pairs,
+        for (size_t v : {hdr, stage, prec, hkey, hidx, bcnt, boff, order, order_med, pairs,
                          poses, total})
             if (v == kUnset || (v != total && v >= total)) return false;
         return true;
@@ -426,7 +426,6 @@ static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long m
     L->hidx = o;     o += up256((size_t)hc * 4);
     L->bcnt = o;     o += up256((size_t)nb * 4);
     L->boff = o;     o += up256((size_t)nb * 4);
-    L->touched = o;  o += up256((size_t)L->max_touched * 4);
     L->order = o;    o += up256((size_t)L->max_touched * 4);
     L->order_med = o; o += up256((size_t)L->max_touched * 4);
     L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
@@ -486,7 +485,6 @@ static dbt_status ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels
     w->d.hcap_alloc = L.hcap_alloc;
     w->d.bcnt = (uint32_t *)(base + L.bcnt);
     w->d.boff = (uint32_t *)(base + L.boff);
-    w->d.touched = (uint32_t *)(base + L.touched);
     w->d.order = (uint32_t *)(base + L.order);
     w->d.order_med = (uint32_t *)(base + L.order_med);
     w->d.max_touched = L.max_touched;
@@ -494,6 +492,7 @@ static dbt_status ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels
     w->d.pairs_cap = L.pairs_cap;
     w->d.poses = (Pose *)(base + L.poses);
     w->d.heavy = HEAVY_PAIRS;
+    w->d.nbricks = L.nbricks;
     return DBT_OK;
 }
 
@@ -574,7 +573,7 @@ static dbt_status enqueue_scan(const dbt_grid *g, const dbt_kernels *k, dbt_work
     dbt_status st = enqueue_prep(g, k, ws, d_xyz, n, pose, s, &dg, &hcap, opt);
     if (st != DBT_OK) return st;
     const int ni = (int)n;
-    launch_alloc(ws->d, 2 * 152, s);
+    launch_alloc(ws->d, s);
     launch_fill(dg, k->dp, ni, ws->d, hcap, s);
     if (ws->ev_begin) DBT_CUDA(cudaEventRecord(ws->ev_begin, s));
     launch_integrate(dg, k->dp, k->dt, (long long)n, ws->d,
@@ -859,7 +858,6 @@ static dbt_status batch_layout(const dbt_grid *grids, int n_grids, const dbt_ker
     L->hidx = o;     o += up256((size_t)hc * 4);
     L->bcnt = o;     o += up256((size_t)nb * 4);
     L->boff = o;     o += up256((size_t)nb * 4);
-    L->touched = o;  o += up256((size_t)L->max_touched * 4);
     L->order = o;    o += up256((size_t)L->max_touched * 4);
     L->order_med = o; o += up256((size_t)L->max_touched * 4);
     L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
@@ -1011,7 +1009,7 @@ extern "C" dbt_status dbt_batch_run(dbt_batch *b, void *stream) {
         launch_voxelize_batch(b->bd, k->dp, k->dt, b->n_total, b->d, hcap, s);
         launch_count_batch(b->bd, k->dp, b->n_total, b->d, hcap, s);
     }
-    launch_alloc(b->d, 2 * 152, s);
+    launch_alloc(b->d, s);
     if (b->n_items > 0) launch_fill_batch(b->bd, k->dp, b->n_total, b->d, hcap, s);
     launch_integrate_batch(b->bd, k->dp, k->dt, b->n_total, b->d,
                            b->ctas ? b->ctas : integrate_grid_ctas(k->dp), s);

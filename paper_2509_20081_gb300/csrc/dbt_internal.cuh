@@ -144,7 +144,6 @@ struct WsDev {
     uint32_t hcap_alloc;        // allocated slots (power of two)
     uint32_t *bcnt;             // per brick: pair count / fill cursor (kept 0 between scans)
     uint32_t *boff;             // per brick: first pair of its segment
-    uint32_t *touched;          // list of touched bricks (first-touch order)
     uint32_t *order;            // touched bricks: heavy ones first, small light ones last
     uint32_t *order_med;        // the larger light bricks, claimed before the small ones
     uint32_t max_touched;
@@ -152,6 +151,7 @@ struct WsDev {
     unsigned long long pairs_cap;
     Pose *poses;                // motion compensation: MAX_SCAN_POSES per-slice poses
     uint32_t heavy;             // bricks with more pairs than this go to a whole CTA
+    uint32_t nbricks;           // bricks of the grid(s): the range of bcnt / boff
 };
 
 // Update pre-steps of dbt_integrate_scan_ex: sequential downsampling (every
@@ -179,7 +179,7 @@ void launch_voxelize(const DevGrid &g, const DevParams &p, const DevTables &t, c
                      const ScanEx *ex = nullptr);
 void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                   cudaStream_t s);
-void launch_alloc(const WsDev &ws, int grid_ctas, cudaStream_t s);
+void launch_alloc(const WsDev &ws, cudaStream_t s);
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                  cudaStream_t s);
 void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, long long n_input,

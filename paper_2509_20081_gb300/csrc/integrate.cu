@@ -546,8 +546,8 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
         if (lane == 0) w = atomicAdd(&ws.hdr->next_work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (nheavy + w >= nt) break;
-        // the larger light bricks first; the small ones sit at order[nheavy + nmed, nt)
-        const uint32_t b = w < nmed ? ws.order_med[w] : ws.order[nheavy + w];
+        // the larger light bricks first; the small ones sit at the back of order
+        const uint32_t b = w < nmed ? ws.order_med[w] : ws.order[ws.max_touched - 1 - (w - nmed)];
         const uint32_t start = ws.boff[b];
         uint32_t len = ws.bcnt[b];
         if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing

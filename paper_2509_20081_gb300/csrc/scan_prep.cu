@@ -250,17 +250,18 @@ __device__ __forceinline__ void for_pair_bricks(bool has, const BrickSpan &s, co
 }
 
 // ------------------------------------------------------------------ K2
-// Pair counts per brick; a brick's first pair appends it to the touched list.
+// Pair counts per brick.  The counts are fire-and-forget atomics (nothing
+// waits for their old value); k_alloc finds the touched bricks afterwards
+// by scanning the counters.  AGG: lanes naming one brick add together.
 template <bool AGG>
 __device__ __forceinline__ void count_pairs(const WsDev &ws, const DevGrid &g, uint32_t b0,
                                             bool kept, const BrickSpan &s) {
     for_pair_bricks<AGG>(kept, s, g, b0, [&](bool v, uint32_t b, int, int, int) {
-        bool first;
-        brick_add<AGG>(ws.bcnt, b, v, first);
-        if (first) {
-            const uint32_t tt = atomicAdd(&ws.hdr->n_touched, 1u);
-            if (tt < ws.max_touched) ws.touched[tt] = b;
-            else atomicOr(&ws.hdr->err, ERR_TOUCHED_OVERFLOW);
+        if constexpr (AGG) {
+            const unsigned peers = __match_any_sync(0xffffffffu, v ? b : 0xFFFFFFFFu);
+            if (v && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&ws.bcnt[b], (uint32_t)__popc(peers));
+        } else {
+            if (v) atomicAdd(&ws.bcnt[b], 1u);
         }
     });
 }
@@ -290,55 +291,83 @@ __global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, Ws
 }
 
 // ------------------------------------------------------------------ K3
-// One segment of the pair array per touched brick (warp-aggregated bump of
-// the pool counter), the per-brick counter reset to serve as fill cursor,
-// and the brick queued for the integrate kernel: heavy bricks (more than
-// ws.heavy pairs) from the front of `order`, the larger light bricks (more
-// than half that) in `order_med` (taken first by the warps: longest work
-// first shortens the kernel's tail), the other light ones from the back of
-// `order`.
-__global__ void __launch_bounds__(256) k_alloc(WsDev ws) {
-    const uint32_t nt = min(ws.hdr->n_touched, ws.max_touched);
-    const int lane = threadIdx.x & 31;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < nt; base += gridDim.x * blockDim.x) {
-        const uint32_t t = base + threadIdx.x;
-        uint32_t len = 0, b = 0;
-        if (t < nt) {
-            b = ws.touched[t];
-            len = ws.bcnt[b];
-        }
+// Every brick of the grid(s) is visited: the touched ones (a non-zero pair
+// count) get one contiguous segment of the pair array (warp-aggregated bump
+// of the pool counter), are counted in n_touched, have their counter reset to
+// serve as fill cursor, and are queued for the integrate kernel: heavy
+// bricks (more than ws.heavy pairs) at the front of `order`, the larger
+// light bricks (more than half that) in `order_med` (taken first by the
+// warps: longest work first shortens the kernel's tail), the other light
+// ones from the back of `order` (index max_touched - 1 down).
+// The queue counters are shared by the whole grid, so their bumps are
+// aggregated per CTA of 1024 bricks: warp totals are scanned in shared
+// memory and one thread takes each counter's range with a single atomic.
+constexpr int ALLOC_THREADS = 1024;
+
+__global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
+    __shared__ uint32_t s_w[ALLOC_THREADS / 32][4];   // per warp: pairs, heavy, med, light
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nb = ws.nbricks;
+    for (uint32_t base = blockIdx.x * ALLOC_THREADS; base < nb; base += gridDim.x * ALLOC_THREADS) {
+        const uint32_t b = base + threadIdx.x;
+        const uint32_t len = b < nb ? ws.bcnt[b] : 0u;
+        if (!__syncthreads_or(len != 0u)) continue;        // CTA-uniform
         uint32_t incl = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += v;
         }
-        uint32_t wbase = 0;
-        if (lane == 31 && incl) wbase = atomicAdd(&ws.hdr->pool, incl);
-        wbase = __shfl_sync(0xffffffffu, wbase, 31);
-        const bool heavy = t < nt && len > ws.heavy;
-        const bool med = t < nt && !heavy && len > ws.heavy / 2;
-        const bool light = t < nt && !heavy && !med;
+        const bool touched = len != 0u;
+        const bool heavy = touched && len > ws.heavy;
+        const bool med = touched && !heavy && len > ws.heavy / 2;
+        const bool light = touched && !heavy && !med;
         const unsigned hb = __ballot_sync(0xffffffffu, heavy);
         const unsigned mb = __ballot_sync(0xffffffffu, med);
         const unsigned lb = __ballot_sync(0xffffffffu, light);
-        uint32_t h0 = 0, m0 = 0, l0 = 0;
+        if (lane == 31) s_w[warp][0] = incl;
         if (lane == 0) {
-            if (hb) h0 = atomicAdd(&ws.hdr->n_heavy, (uint32_t)__popc(hb));
-            if (mb) m0 = atomicAdd(&ws.hdr->n_med, (uint32_t)__popc(mb));
-            if (lb) l0 = atomicAdd(&ws.hdr->n_light, (uint32_t)__popc(lb));
+            s_w[warp][1] = __popc(hb);
+            s_w[warp][2] = __popc(mb);
+            s_w[warp][3] = __popc(lb);
         }
-        h0 = __shfl_sync(0xffffffffu, h0, 0);
-        m0 = __shfl_sync(0xffffffffu, m0, 0);
-        l0 = __shfl_sync(0xffffffffu, l0, 0);
+        __syncthreads();
+        if (warp == 0) {                                   // lane j: warp j's entries
+            uint32_t v[4], x[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[k] = s_w[lane][k];
+                x[k] = v[k];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x[k], o);
+                    if (lane >= o) x[k] += y;
+                }
+            }
+            uint32_t g[4] = {0u, 0u, 0u, 0u};
+            if (lane == 31) {
+                if (x[0]) g[0] = atomicAdd(&ws.hdr->pool, x[0]);
+                if (x[1]) g[1] = atomicAdd(&ws.hdr->n_heavy, x[1]);
+                if (x[2]) g[2] = atomicAdd(&ws.hdr->n_med, x[2]);
+                if (x[3]) g[3] = atomicAdd(&ws.hdr->n_light, x[3]);
+                atomicAdd(&ws.hdr->n_touched, x[1] + x[2] + x[3]);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_w[lane][k] = __shfl_sync(0xffffffffu, g[k], 31) + x[k] - v[k];
+        }
+        __syncthreads();
         const unsigned below = (1u << lane) - 1u;
-        if (t < nt) {
-            ws.boff[b] = wbase + incl - len;
+        if (touched) {
+            ws.boff[b] = s_w[warp][0] + incl - len;
             ws.bcnt[b] = 0;
-            if (heavy) ws.order[h0 + __popc(hb & below)] = b;
-            else if (med) ws.order_med[m0 + __popc(mb & below)] = b;
-            else ws.order[nt - 1 - (l0 + __popc(lb & below))] = b;
+            const int cls = heavy ? 1 : med ? 2 : 3;
+            const uint32_t q = s_w[warp][cls] + __popc((heavy ? hb : med ? mb : lb) & below);
+            if (q >= ws.max_touched) atomicOr(&ws.hdr->err, ERR_TOUCHED_OVERFLOW);   // cannot happen by sizing
+            else if (heavy) ws.order[q] = b;
+            else if (med) ws.order_med[q] = b;
+            else ws.order[ws.max_touched - 1 - q] = b;
         }
+        __syncthreads();                                   // s_w is reused next round
     }
 }
 
@@ -542,8 +571,7 @@ __global__ void __launch_bounds__(256) k_footprint(DevGrid g, DevParams p, DevTa
 __global__ void k_ws_rearm(WsDev ws, uint32_t hcap) {
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t g0 = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t nt = min(ws.hdr->n_touched, ws.max_touched);
-    for (uint32_t j = g0; j < nt; j += stride) ws.bcnt[ws.touched[j]] = 0u;
+    for (uint32_t j = g0; j < ws.nbricks; j += stride) ws.bcnt[j] = 0u;   // every brick counter
     for (uint32_t j = g0; j < hcap; j += stride) {
         ws.hkey[j] = 0ull;
         ws.hidx[j] = 0u;
@@ -637,8 +665,13 @@ void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, 
     k_count<<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, n, ws, hcap);
 }
 
-void launch_alloc(const WsDev &ws, int grid_ctas, cudaStream_t s) {
-    k_alloc<<<grid_ctas, 256, 0, s>>>(ws);
+// One thread per brick where the GPU holds them all at once (a single wave
+// hides the latency of the counter loads and queue atomics), grid-stride
+// beyond that.
+void launch_alloc(const WsDev &ws, cudaStream_t s) {
+    const long long need = ((long long)ws.nbricks + ALLOC_THREADS - 1) / ALLOC_THREADS;
+    const int ctas = (int)std::max(1LL, std::min(need, 152LL * 4));
+    k_alloc<<<ctas, ALLOC_THREADS, 0, s>>>(ws);
 }
 
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
