@@ -399,12 +399,6 @@ struct WsLayout {
 
 static size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
 
-static int max_pairs_per_return(int K) {
-    const int sx = 1 + (K - 1 + BX - 1) / BX;
-    const int sy = 1 + (K - 1 + BY - 1) / BY;
-    const int sz = 1 + (K - 1 + BZ - 1) / BZ;
-    return sx * sy * sz;
-}
 
 static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long max_points, WsLayout *L) {
     if (max_points < 1 || max_points > (1ll << 30))

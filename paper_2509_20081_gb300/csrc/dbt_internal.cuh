@@ -31,6 +31,12 @@ constexpr uint32_t ERR_TOUCHED_OVERFLOW = 1u << 2;
 constexpr uint32_t ERR_BAD_PAYLOAD = 1u << 3;
 constexpr uint32_t ERR_MASK_FORM = 1u << 4;      // a grid mask was not of the form 2^k - 1
 
+// Bricks a return's K^3 neighbourhood can touch: its x-extent K spans at most
+// 1 + ceil((K - 1) / BX) bricks, likewise in y and z.
+__host__ __device__ inline int max_pairs_per_return(int K) {
+    return (1 + (K - 1 + BX - 1) / BX) * (1 + (K - 1 + BY - 1) / BY) * (1 + (K - 1 + BZ - 1) / BZ);
+}
+
 // Shadow offsets are packed as (ox + 128) | (oy + 128) << 8 | (oz + 128) << 16.
 __host__ __device__ inline uint32_t pack_off(int ox, int oy, int oz) {
     return (uint32_t)(ox + 128) | ((uint32_t)(oy + 128) << 8) | ((uint32_t)(oz + 128) << 16);

@@ -197,36 +197,10 @@ __device__ __forceinline__ BrickSpan brick_span(int cx, int cy, int cz, int R) {
     return s;
 }
 
-// Bump of a per-brick counter; returns the counter's previous value, first:
-// this increment took it from 0.  AGG (batches, where many lanes of a warp
-// name one brick): lanes naming the same brick form one group whose lowest
-// lane adds the group size, each lane getting its rank in the group; all 32
-// lanes must call it together.  Without AGG (one scan: fewer collisions, and
-// the grid is too small to hide the extra latency) a plain atomic per lane.
-template <bool AGG>
-__device__ __forceinline__ uint32_t brick_add(uint32_t *ctr, uint32_t b, bool valid, bool &first) {
-    if constexpr (!AGG) {
-        const uint32_t old = valid ? atomicAdd(&ctr[b], 1u) : 1u;
-        first = valid && old == 0u;
-        return old;
-    } else {
-        const uint32_t key = valid ? b : 0xFFFFFFFFu;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(peers) - 1;
-        uint32_t base = 0;
-        if (valid && lane == leader) base = atomicAdd(&ctr[b], (uint32_t)__popc(peers));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        const uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
-        first = valid && base == 0u && rank == 0u;
-        return base + rank;
-    }
-}
-
 // The (up to 2 x 4 x 4) bricks of each lane's pair span; f(valid, brick,
 // bx, by, bz) per brick.  AGG: enumerated in lock-step over the warp (steps
-// past a lane's own span call f with valid = false) so that brick_add sees
-// all lanes.
+// past a lane's own span call f with valid = false) so that lanes naming one
+// brick can add together.
 template <bool AGG, typename F>
 __device__ __forceinline__ void for_pair_bricks(bool has, const BrickSpan &s, const DevGrid &g,
                                                 uint32_t b0, F f) {
@@ -374,34 +348,38 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
 // ------------------------------------------------------------------ K4
 // Pair payload: contact relative to the brick corner plus R (x: 6 bits,
 // y, z: 5 bits each) and the bin (16 bits).
-// Pair payloads into the segments, slots from the per-brick cursors.
-template <bool AGG>
-__device__ __forceinline__ void fill_pairs(const WsDev &ws, const DevGrid &g, uint32_t b0,
-                                           const DevParams &p, bool has, int4 r) {
+// Pair payloads into the segments, slots from the per-brick cursors.  One
+// thread per (return, brick of its span): a return's cursor atomics are all
+// in flight at once instead of one after another.  t -> return t / slots,
+// the j-th brick of its span (x fastest), j = t mod slots.
+__device__ __forceinline__ void fill_one(const WsDev &ws, const DevGrid &g, uint32_t b0,
+                                         const DevParams &p, int4 r, int j) {
+    const BrickSpan sp = brick_span(r.x, r.y, r.z, p.R);
+    const int sx = sp.x1 - sp.x0 + 1, sy = sp.y1 - sp.y0 + 1, sz = sp.z1 - sp.z0 + 1;
+    if (j >= sx * sy * sz) return;
+    const int ix = j % sx, jy = j / sx, iy = jy % sy, iz = jy / sy;
+    const int bx = sp.x0 + ix, by = sp.y0 + iy, bz = sp.z0 + iz;
+    const uint32_t b = b0 + ((uint32_t)bz * g.nby + by) * g.nbx + bx;
+    const uint32_t slot = atomicAdd(&ws.bcnt[b], 1u);
+    const unsigned long long pos = (unsigned long long)ws.boff[b] + slot;
+    const uint32_t rx = (uint32_t)(r.x - bx * BX + p.R);
+    const uint32_t ry = (uint32_t)(r.y - by * BY + p.R);
+    const uint32_t rz = (uint32_t)(r.z - bz * BZ + p.R);
     const uint32_t bin = (uint32_t)(r.w & 0xFFFF);
-    for_pair_bricks<AGG>(has, has ? brick_span(r.x, r.y, r.z, p.R) : BrickSpan{}, g, b0,
-                    [&](bool v, uint32_t b, int bx, int by, int bz) {
-        bool first;
-        const uint32_t slot = brick_add<AGG>(ws.bcnt, b, v, first);
-        if (v) {
-            const unsigned long long pos = (unsigned long long)ws.boff[b] + slot;
-            const uint32_t rx = (uint32_t)(r.x - bx * BX + p.R);
-            const uint32_t ry = (uint32_t)(r.y - by * BY + p.R);
-            const uint32_t rz = (uint32_t)(r.z - bz * BZ + p.R);
-            if (pos < ws.pairs_cap)
-                ws.pairs[pos] = rx | (ry << 6) | (rz << 11) | (bin << 16);
-            else
-                atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
-        }
-    });
+    if (pos < ws.pairs_cap)
+        ws.pairs[pos] = rx | (ry << 6) | (rz << 11) | (bin << 16);
+    else
+        atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
 }
 
-__global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, WsDev ws,
+__global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, int slots, WsDev ws,
                                               uint32_t hcap) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int4 r = make_int4(-1, 0, 0, 0);
-    if (i < n) r = ws.prec[i];
-    fill_pairs<false>(ws, g, 0u, p, r.x >= 0 && !(r.w & PREC_DUP), r);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = t / slots;
+    if (i < n) {
+        const int4 r = ws.prec[i];
+        if (r.x >= 0 && !(r.w & PREC_DUP)) fill_one(ws, g, 0u, p, r, (int)(t - i * slots));
+    }
     if (p.dedup) {
         const uint32_t stride = gridDim.x * blockDim.x;
         for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < hcap; j += stride) {
@@ -509,6 +487,10 @@ __global__ void __launch_bounds__(256) k_count_b(BatchDev bd, DevParams p, long 
     add_item_counts(bd, item, kept, false, &ItemCounters::kept, nullptr);
 }
 
+// Batches: many scans put many pairs on the same bricks, so the cursor bumps
+// of a warp's lanes that name one brick are aggregated (one atomic per
+// brick and warp, each lane taking its rank in the group) over the lanes'
+// spans walked in lock-step, one thread per return.
 __global__ void __launch_bounds__(256) k_fill_b(BatchDev bd, DevParams p, long long n, WsDev ws,
                                                 uint32_t hcap) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -522,7 +504,27 @@ __global__ void __launch_bounds__(256) k_fill_b(BatchDev bd, DevParams p, long l
         g = bd.grids[gi];
         b0 = bd.bbase[gi];
     }
-    fill_pairs<true>(ws, g, b0, p, has, r);
+    const int lane = threadIdx.x & 31;
+    const uint32_t bin = (uint32_t)(r.w & 0xFFFF);
+    for_pair_bricks<true>(has, has ? brick_span(r.x, r.y, r.z, p.R) : BrickSpan{}, g, b0,
+                          [&](bool v, uint32_t b, int bx, int by, int bz) {
+        const unsigned peers = __match_any_sync(0xffffffffu, v ? b : 0xFFFFFFFFu);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (v && lane == leader) base = atomicAdd(&ws.bcnt[b], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (v) {
+            const unsigned long long pos = (unsigned long long)ws.boff[b] + base +
+                                           (uint32_t)__popc(peers & ((1u << lane) - 1u));
+            const uint32_t rx = (uint32_t)(r.x - bx * BX + p.R);
+            const uint32_t ry = (uint32_t)(r.y - by * BY + p.R);
+            const uint32_t rz = (uint32_t)(r.z - bz * BZ + p.R);
+            if (pos < ws.pairs_cap)
+                ws.pairs[pos] = rx | (ry << 6) | (rz << 11) | (bin << 16);
+            else
+                atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
+        }
+    });
     if (p.dedup) {
         const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
         for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -676,7 +678,9 @@ void launch_alloc(const WsDev &ws, cudaStream_t s) {
 
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                  cudaStream_t s) {
-    k_fill<<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, n, ws, hcap);
+    const int slots = max_pairs_per_return(p.K);
+    const long long threads = std::max((long long)n * slots, (long long)hcap);
+    k_fill<<<(unsigned)std::max(1LL, (threads + 255) / 256), 256, 0, s>>>(g, p, n, slots, ws, hcap);
 }
 
 static inline unsigned batch_blocks(long long n) { return (unsigned)max(1ll, (n + 255) / 256); }
