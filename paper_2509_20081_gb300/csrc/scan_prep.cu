@@ -28,16 +28,16 @@ __device__ int bin_octa(double dx, double dy, double dz, int n) {
     double u = __dmul_rn(dx, inv);
     double v = __dmul_rn(dy, inv);
     if (dz < 0.0) {
-        double fu = __dmul_rn(__dsub_rn(1.0, fabs(v)), sgn1(u));
-        double fv = __dmul_rn(__dsub_rn(1.0, fabs(u)), sgn1(v));
-        u = fu;
-        v = fv;
+        // (1 - |v|) sgn(u): a multiplication by +-1 is an exact sign choice
+        const double fu = __dsub_rn(1.0, fabs(v)), fv = __dsub_rn(1.0, fabs(u));
+        u = sgn1(u) < 0.0 ? -fu : fu;
+        v = sgn1(v) < 0.0 ? -fv : fv;
     }
-    double fi = floor(__dmul_rn(__dmul_rn(__dadd_rn(u, 1.0), 0.5), (double)n));
-    double fj = floor(__dmul_rn(__dmul_rn(__dadd_rn(v, 1.0), 0.5), (double)n));
-    int i = (int)fmin(fmax(fi, 0.0), (double)(n - 1));
-    int j = (int)fmin(fmax(fj, 0.0), (double)(n - 1));
-    return j * n + i;
+    // floor and the clamp to [0, n - 1] in integers (the conversion rounds
+    // toward -inf: the same integer as floor() on the binary64 value)
+    const int i = __double2int_rd(__dmul_rn(__dmul_rn(__dadd_rn(u, 1.0), 0.5), (double)n));
+    const int j = __double2int_rd(__dmul_rn(__dmul_rn(__dadd_rn(v, 1.0), 0.5), (double)n));
+    return min(max(j, 0), n - 1) * n + min(max(i, 0), n - 1);
 }
 
 // Eq. 2 azimuth: number of edges theta_k (k >= 1) with theta >= theta_k.
@@ -128,18 +128,21 @@ __device__ __forceinline__ int contact_of(const DevGrid &g, const DevParams &p, 
     if (!(isfinite(fx) && isfinite(fy) && isfinite(fz)) || (fx == 0.0f && fy == 0.0f && fz == 0.0f))
         return 0;
     const double px = fx, py = fy, pz = fz;
-    double d[3], q[3];
+    double d[3];
+    long long q[3];
     const double org[3] = {g.ox, g.oy, g.oz};
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         d[r] = __fma_rn(pose.r[3 * r + 2], pz,
                         __fma_rn(pose.r[3 * r + 1], py, __dmul_rn(pose.r[3 * r + 0], px)));
         const double w = __dadd_rn(d[r], pose.t[r]);
-        q[r] = floor(__dmul_rn(__dsub_rn(w, org[r]), g.inv_res));
+        // floor((w - origin) * (1 / res)) as an integer: the conversion rounds
+        // toward -inf and saturates, so the bounds test below is the same as
+        // on the binary64 value
+        q[r] = __double2ll_rd(__dmul_rn(__dsub_rn(w, org[r]), g.inv_res));
     }
-    const double R = (double)p.R;
-    if (!(q[0] >= R && q[0] <= (double)(g.nx - 1 - p.R) && q[1] >= R &&
-          q[1] <= (double)(g.ny - 1 - p.R) && q[2] >= R && q[2] <= (double)(g.nz - 1 - p.R)))
+    if (!(q[0] >= p.R && q[0] <= g.nx - 1 - p.R && q[1] >= p.R && q[1] <= g.ny - 1 - p.R &&
+          q[2] >= p.R && q[2] <= g.nz - 1 - p.R))
         return 1;
     rec = make_int4((int)q[0], (int)q[1], (int)q[2], bin_of(p, t, d[0], d[1], d[2]));
     return 2;
