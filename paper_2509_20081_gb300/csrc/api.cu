@@ -290,7 +290,6 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
     k->dp.n_m2 = (int)n_m2;
     k->dp.sr = std::min(R, (int)std::floor(p->shadow_radius));
     k->dp.n_sh = (int)k->sh_off.size();
-    k->dp.sh_smem = shadow_in_smem(nbins, k->dp.n_sh) ? 1 : 0;
     k->dt.m2 = (const uint32_t *)(base + off_m2);
     k->dt.sh_off = (const uint32_t *)(base + off_sh);
     k->dt.sh_start = (const uint32_t *)(base + off_st);

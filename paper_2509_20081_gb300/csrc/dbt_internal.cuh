@@ -52,15 +52,7 @@ struct DevParams {
     int n_m2;         // entries of the mask-by-r^2 table
     int sr;           // min(R, floor(r_s)): no shadow offset exceeds it on any axis
     int n_sh;         // shadow offsets over all bins
-    int sh_smem;      // 1: the integrate kernel stages the shadow table in shared memory
 };
-
-// Shadow tables up to this many words (offsets + starts) are staged in
-// shared memory by the integrate kernel.
-constexpr int SHADOW_SMEM_WORDS = 4608;
-__host__ __device__ inline bool shadow_in_smem(int nbins, int n_sh) {
-    return ((nbins + 1 + 3) & ~3) + n_sh <= SHADOW_SMEM_WORDS;
-}
 
 struct DevTables {
     const uint32_t *m2;        // Eq. 3 mask as a function of r^2 = |o|^2

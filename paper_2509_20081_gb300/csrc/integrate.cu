@@ -43,7 +43,7 @@ constexpr int NTHR = WPC * 32;
 struct WarpArea {
     uint32_t kst[BROWS * 8];      // codes: word kword(row, w) = voxels 4w .. 4w+3 of a row
     uint16_t cnt[BVOX];           // shadow counts, index row * 32 + x
-    uint8_t dirty[BROWS * 8];     // word changed (index as kst)
+    uint8_t drow[BROWS];          // bit w: word w of the row changed
     uint32_t need[BROWS];         // covered chunks of each row (bit w)
 };
 static_assert(sizeof(WarpArea) % 16 == 0, "warp area alignment");
@@ -127,6 +127,7 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
         const int pb = (oy * oy + oz * oz) * W + s0;
         const int row = rz * BY + ry;
         const int rbase = row * 8, f = (row >> 2) & 7;
+        uint32_t changed = 0;
 #pragma unroll
         for (int j = 0; j < NW; ++j) {
             if (j <= nw) {
@@ -136,10 +137,12 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
                 const uint32_t nv = vmin4(a, kwd);
                 if (nv != a) {
                     wa->kst[addr] = nv;
-                    wa->dirty[addr] = 1;
+                    changed |= 1u << (w0 + j);
                 }
             }
         }
+        // each lane owns its row within one pair, so no other lane writes this byte
+        if (changed) wa->drow[row] |= (uint8_t)changed;
     }
 }
 
@@ -168,12 +171,12 @@ __device__ __forceinline__ void shadow_pair(uint32_t pl, uint16_t *cnt, const ui
     const uint32_t cpk = ((uint32_t)(cx - 128) & 255u) | (((uint32_t)(cy - 128) & 255u) << 8) |
                          (((uint32_t)(cz - 128) & 255u) << 16);
     const uint32_t bin = pl >> 16;
-    const uint32_t e0 = shs[bin], e1 = shs[bin + 1];
+    const uint32_t e0 = __ldg(shs + bin), e1 = __ldg(shs + bin + 1);
     for (uint32_t e = e0; e < e1; e += 96) {
         // three batches of 32 fetched before use (a 3-voxel shadow has <= 96 offsets)
         uint32_t o[3];
 #pragma unroll
-        for (int h = 0; h < 3; ++h) o[h] = e + 32 * h + lane < e1 ? sh[e + 32 * h + lane] : 0u;
+        for (int h = 0; h < 3; ++h) o[h] = e + 32 * h + lane < e1 ? __ldg(sh + e + 32 * h + lane) : 0u;
 #pragma unroll
         for (int h = 0; h < 3; ++h) {
             const uint32_t u = __vadd4(o[h], cpk);                    // bytes x, y, z
@@ -289,7 +292,6 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
         if ((need[row] >> ch) & 1u) {
             const int wd = kword(row, ch);
             a0->kst[wd] = load_codes(g, chunk_index(g, bx, by, bz, row, ch), form_bad);
-            a0->dirty[wd] = 0;
             *reinterpret_cast<uint2 *>(&a0->cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
         }
     }
@@ -350,24 +352,31 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
     __syncthreads();
     // pass z (taps only from planes with contacts), codes, and Eq. 4 on the
     // staged brick
+    // (a warp covers four whole rows: idx = row * 8 + w; its ballot gives the
+    // rows' changed-word bytes, each written once by the row's first lane)
     for (int idx = tid; idx < BROWS * 8; idx += NTHR) {
         const int w = idx & 7, row = idx >> 3, y = row & 7, z = row >> 3;
-        if (!((need[row] >> w) & 1u)) continue;
-        uint32_t acc = inf4;
-        for (uint32_t m = (planes >> z) & twin; m; m &= m - 1u) {
-            const int t = __ffs(m) - 1, dz = t - R;
-            acc = vmin4(acc, g2[((z + t) * 8 + y) * 8 + w] + (uint32_t)(dz * dz) * 0x01010101u);
+        bool changed = false;
+        if ((need[row] >> w) & 1u) {
+            uint32_t acc = inf4;
+            for (uint32_t m = (planes >> z) & twin; m; m &= m - 1u) {
+                const int t = __ffs(m) - 1, dz = t - R;
+                acc = vmin4(acc, g2[((z + t) * 8 + y) * 8 + w] + (uint32_t)(dz * dz) * 0x01010101u);
+            }
+            const uint32_t code = (uint32_t)ctab[acc & 255u] |
+                                  ((uint32_t)ctab[(acc >> 8) & 255u] << 8) |
+                                  ((uint32_t)ctab[(acc >> 16) & 255u] << 16) |
+                                  ((uint32_t)ctab[acc >> 24] << 24);
+            const int wd = kword(row, w);
+            const uint32_t old = a0->kst[wd];
+            const uint32_t nv = vmin4(old, code);
+            if (nv != old) {
+                a0->kst[wd] = nv;
+                changed = true;
+            }
         }
-        const uint32_t code = (uint32_t)ctab[acc & 255u] | ((uint32_t)ctab[(acc >> 8) & 255u] << 8) |
-                              ((uint32_t)ctab[(acc >> 16) & 255u] << 16) |
-                              ((uint32_t)ctab[acc >> 24] << 24);
-        const int wd = kword(row, w);
-        const uint32_t old = a0->kst[wd];
-        const uint32_t nv = vmin4(old, code);
-        if (nv != old) {
-            a0->kst[wd] = nv;
-            a0->dirty[wd] = 1;
-        }
+        const unsigned bal = __ballot_sync(0xffffffffu, changed);
+        if ((lane & 7) == 0) a0->drow[row] = (uint8_t)(bal >> (lane & 24));
     }
     // Eq. 5 counts: pairs spread over the warps, counted into one array
     for (uint32_t j = warp; j < len; j += WPC)
@@ -378,7 +387,8 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
         const int row = c >> 3, ch = c & 7;
         if ((need[row] >> ch) & 1u) {
             const int wd = kword(row, ch);
-            store_chunk(g, chunk_index(g, bx, by, bz, row, ch), a0->kst[wd], a0->dirty[wd] != 0,
+            store_chunk(g, chunk_index(g, bx, by, bz, row, ch), a0->kst[wd],
+                        ((a0->drow[row] >> ch) & 1u) != 0,
                         *reinterpret_cast<const uint2 *>(&a0->cnt[row * 32 + ch * 4]), T, Hmax);
         }
     }
@@ -408,7 +418,7 @@ __device__ __forceinline__ uint32_t brick_grid(const DevGrid &g, const BatchDev 
 }
 
 template <int NW, bool BATCH>
-__global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, DevParams p,
+__global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, DevParams p,
                                                     DevTables t, long long n_input, WsDev ws) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t s_item;
@@ -425,16 +435,9 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
     uint32_t *P = smem;
     for (int j = threadIdx.x; j < np; j += NTHR) P[j] = t.prow[j];
     WarpArea *areas = reinterpret_cast<WarpArea *>(smem + ((np + 3) & ~3));
-    // shadow offsets: in shared memory after the warp areas when they fit
+    // shadow offsets stay in global memory (read-only path, L1-resident): the
+    // shared memory they would take costs a CTA per SM
     const uint32_t *sh = t.sh_off, *shs = t.sh_start;
-    if (p.sh_smem) {
-        uint32_t *s_shs = reinterpret_cast<uint32_t *>(areas + WPC);
-        uint32_t *s_sh = s_shs + ((p.nbins + 1 + 3) & ~3);
-        for (int j = threadIdx.x; j <= p.nbins; j += NTHR) s_shs[j] = t.sh_start[j];
-        for (int j = threadIdx.x; j < p.n_sh; j += NTHR) s_sh[j] = t.sh_off[j];
-        sh = s_sh;
-        shs = s_shs;
-    }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     WarpArea *wa = areas + warp;
     const uint32_t nt = min(*(volatile uint32_t *)&ws.hdr->n_touched, ws.max_touched);
@@ -499,11 +502,11 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
 #pragma unroll
                 for (int v = 0; v < WPC; ++v) {
                     areas[v].kst[wd] = k;
-                    areas[v].dirty[wd] = 0;
                     *reinterpret_cast<uint2 *>(&areas[v].cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
                 }
             }
         }
+        for (int i = tid; i < WPC * BROWS; i += NTHR) areas[i / BROWS].drow[i % BROWS] = 0;
         __syncthreads();
         // C: warp w applies pairs w, w + WPC, w + 2 WPC, ...
         for (uint32_t base = 0; base * WPC + warp < len; base += 32) {
@@ -524,12 +527,12 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
             if ((need[row] >> ch) & 1u) {
                 const int wd = kword(row, ch);
                 uint32_t k = areas[0].kst[wd];
-                uint32_t dirty = areas[0].dirty[wd];
+                uint32_t dirty = (areas[0].drow[row] >> ch) & 1u;
                 uint2 cs = *reinterpret_cast<const uint2 *>(&areas[0].cnt[row * 32 + ch * 4]);
 #pragma unroll
                 for (int v = 1; v < WPC; ++v) {
                     k = vmin4(k, areas[v].kst[wd]);
-                    dirty |= areas[v].dirty[wd];
+                    dirty |= (areas[v].drow[row] >> ch) & 1u;
                     const uint2 cv = *reinterpret_cast<const uint2 *>(&areas[v].cnt[row * 32 + ch * 4]);
                     cs.x += cv.x;   // packed 16-bit counts: a voxel's total fits 16 bits
                     cs.y += cv.y;
@@ -597,10 +600,11 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
                 const int row = rs + 4 * (i0 + q);
                 const int wd = kword(row, ch);
                 wa->kst[wd] = codes_of(m[q], form_bad);
-                wa->dirty[wd] = 0;
                 *reinterpret_cast<uint2 *>(&wa->cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
             }
         }
+        wa->drow[lane] = 0;
+        wa->drow[lane + 32] = 0;
         __syncwarp();
         // C
         for (uint32_t base = 0; base < len; base += 32) {
@@ -635,7 +639,7 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
                 if (!((wa->need[row] >> ch) & 1u)) continue;
                 const int wd = kword(row, ch);
                 const size_t gi = chunk_index(g, bx, by, bz, row, ch);
-                if (wa->dirty[wd]) store_codes(g, gi, wa->kst[wd]);
+                if ((wa->drow[row] >> ch) & 1u) store_codes(g, gi, wa->kst[wd]);
                 if (cs[q].x | cs[q].y) {
                     const uint32_t cross = apply_counts(hv[q], cs[q], T, Hmax);
                     __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv[q]);
@@ -680,19 +684,16 @@ __global__ void __launch_bounds__(NTHR) k_integrate(DevGrid g0, BatchDev bd, Dev
     }
 }
 
-// Dynamic shared memory of one CTA: row codes, warp areas, and (when they
-// fit in SHADOW_SMEM_WORDS) the shadow offset table.
-static size_t integrate_smem(int K, int nbins, int n_sh) {
+// Dynamic shared memory of one CTA: row codes and warp areas.
+static size_t integrate_smem(int K) {
     const int R = (K - 1) / 2;
     const size_t np = (size_t)(2 * R * R + 1) * (2 * R + 4);
-    size_t bytes = ((np + 3) & ~size_t(3)) * 4 + WPC * sizeof(WarpArea);
-    if (shadow_in_smem(nbins, n_sh)) bytes += (size_t)(((nbins + 1 + 3) & ~3) + n_sh) * 4;
-    return bytes;
+    return ((np + 3) & ~size_t(3)) * 4 + WPC * sizeof(WarpArea);
 }
 
 struct IntegrateCfg {
     int device = -1;
-    int ctas[MAX_K + 1][2] = {};
+    int ctas[MAX_K + 1] = {};
 };
 static IntegrateCfg g_cfg;
 
@@ -735,21 +736,17 @@ int integrate_grid_ctas(const DevParams &p) {
         g_cfg = IntegrateCfg();
         g_cfg.device = dev;
     }
-    const int inb = p.sh_smem ? 1 : 0;
-    if (!g_cfg.ctas[p.K][inb]) {
-        const size_t smem = integrate_smem(p.K, p.nbins, p.n_sh);
-        const size_t smax = words_per_row(p.K) == 4
-                                ? integrate_smem(13, 0, 0) + SHADOW_SMEM_WORDS * 4
-                                : integrate_smem(MAX_K, 0, 0) + SHADOW_SMEM_WORDS * 4;
-        g_cfg.ctas[p.K][inb] = words_per_row(p.K) == 4 ? configure<4>(smem, smax)
-                                                      : configure<6>(smem, smax);
+    if (!g_cfg.ctas[p.K]) {
+        const size_t smem = integrate_smem(p.K);
+        const size_t smax = words_per_row(p.K) == 4 ? integrate_smem(13) : integrate_smem(MAX_K);
+        g_cfg.ctas[p.K] = words_per_row(p.K) == 4 ? configure<4>(smem, smax) : configure<6>(smem, smax);
     }
-    return g_cfg.ctas[p.K][inb];
+    return g_cfg.ctas[p.K];
 }
 
 void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, long long n_input,
                       const WsDev &ws, int grid_ctas, cudaStream_t s) {
-    const size_t smem = integrate_smem(p.K, p.nbins, p.n_sh);
+    const size_t smem = integrate_smem(p.K);
     const BatchDev none = {};
     if (words_per_row(p.K) == 4)
         k_integrate<4, false><<<grid_ctas, NTHR, smem, s>>>(g, none, p, t, n_input, ws);
@@ -759,7 +756,7 @@ void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, 
 
 void launch_integrate_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
                             long long n_input, const WsDev &ws, int grid_ctas, cudaStream_t s) {
-    const size_t smem = integrate_smem(p.K, p.nbins, p.n_sh);
+    const size_t smem = integrate_smem(p.K);
     const DevGrid none = {};
     if (words_per_row(p.K) == 4)
         k_integrate<4, true><<<grid_ctas, NTHR, smem, s>>>(none, bd, p, t, n_input, ws);
