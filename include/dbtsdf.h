@@ -149,6 +149,18 @@ dbt_status dbt_tables_host(const dbt_params *p, uint32_t *h_mask, uint8_t *h_sha
 dbt_status dbt_bin_directions(const dbt_kernels *k, const double *d_dirs, int64_t n,
                               int32_t *d_bins, void *stream);
 
+/* The first steps of Sec. III-C for every return of a scan, without
+ * integrating (the same device routine the integration starts with):
+ * d_out[4 i .. 4 i + 3] = (x, y, z, bin), the contact voxel and direction bin
+ * of return i, or (-1, 0, 0, 0) when the return is not valid (non-finite,
+ * at the sensor origin) or its K^3 neighbourhood leaves the grid (boundary
+ * discard).  The first-return rule is not applied and the grid is not read
+ * or written.  d_xyz: device float32 n x 3 (sensor frame); pose as for
+ * dbt_integrate_scan; d_out: device int32 n x 4, caller-owned.  Enqueued on
+ * `stream`; DBT_EINVAL on bad arguments (nothing enqueued). */
+dbt_status dbt_scan_contacts(const dbt_grid *g, const dbt_kernels *k, const float *d_xyz,
+                             int64_t n, const double pose[12], int32_t *d_out, void *stream);
+
 /* Handle over a caller-owned device scratch buffer used by integration: the
  * first-return hash table, per-return records, brick counters and the
  * (return, brick) work lists.  The handle is host memory; the library never

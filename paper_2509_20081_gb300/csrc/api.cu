@@ -553,6 +553,31 @@ static dbt_status check_pose(const double *pose, Pose *out) {
     return DBT_OK;
 }
 
+// Binary32 filter data of a pose for one grid.  b = (t - origin) * inv_res is
+// taken in binary64 and split into an integer B and a remainder |b - B| <=
+// 1/2, so that the binary32 coordinate fa . p + fb stays small; fe0 covers
+// the rounding of fb (<= 2^-25) and of the binary64 path's own additions
+// (<= 2^-50 (|t| + |origin|) inv_res), both with a wide margin.
+void dbt::pose_filter(Pose &P, const DevGrid &g) {
+    P.fast = 0;
+    const double org[3] = {g.ox, g.oy, g.oz};
+    for (int r = 0; r < 3; ++r) {
+        const double b = (P.t[r] - org[r]) * g.inv_res;
+        if (!(std::fabs(b) < 1e9)) return;
+        const double B = std::round(b);
+        P.fbi[r] = (int)B;
+        P.fb[r] = (float)(b - B);
+        P.fe0[r] = (float)((std::fabs(P.t[r]) + std::fabs(org[r])) * g.inv_res * 0x1p-46 + 0x1p-22);
+        for (int j = 0; j < 3; ++j) {
+            const double a = P.r[3 * r + j] * g.inv_res;
+            if (!(std::fabs(a) < 1e30)) return;
+            P.fa[3 * r + j] = (float)a;
+            P.fr[3 * r + j] = (float)P.r[3 * r + j];
+        }
+    }
+    P.fast = 1;
+}
+
 static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
                                const float *d_xyz, int64_t n, const double pose[12],
                                cudaStream_t s, DevGrid *dg_out, uint32_t *hcap_out,
@@ -593,6 +618,7 @@ static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_work
         return fail(DBT_EINVAL, "n = %lld outside [0, max_points = %lld]", (long long)n, ws->max_points);
     if (n > 0 && (!d_xyz || ((uintptr_t)d_xyz & 3u)))
         return fail(DBT_EINVAL, "points must be a non-NULL 4-byte aligned device pointer");
+    const DevGrid dg = dev_grid(g);
     Pose P{};
     ScanEx ex{1, 0, 1};
     const bool use_ex = opt != nullptr;
@@ -610,6 +636,7 @@ static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_work
             for (int m = 0; m < opt->n_poses; ++m) {
                 st = check_pose(opt->poses + 12 * m, &table[m]);
                 if (st != DBT_OK) return st;
+                pose_filter(table[m], dg);
             }
             DBT_CUDA(cudaMemcpyAsync(ws->d.poses, table, sizeof(Pose) * opt->n_poses,
                                      cudaMemcpyHostToDevice, s));
@@ -621,7 +648,7 @@ static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_work
         st = check_pose(pose, &P);
         if (st != DBT_OK) return st;
     }
-    const DevGrid dg = dev_grid(g);
+    pose_filter(P, dg);
     uint32_t hcap = 64;
     while (hcap < 2ull * (unsigned long long)n) hcap <<= 1;
     const int ni = (int)n;
@@ -629,6 +656,27 @@ static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_work
     launch_count(dg, k->dp, ni, ws->d, hcap, s);
     *dg_out = dg;
     *hcap_out = hcap;
+    return DBT_OK;
+}
+
+extern "C" dbt_status dbt_scan_contacts(const dbt_grid *g, const dbt_kernels *k, const float *d_xyz,
+                                        int64_t n, const double pose[12], int32_t *d_out,
+                                        void *stream) {
+    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    if (n < 0 || n > (int64_t)1 << 40) return fail(DBT_EINVAL, "n = %lld out of range", (long long)n);
+    if (n > 0 && (!d_xyz || ((uintptr_t)d_xyz & 3u)))
+        return fail(DBT_EINVAL, "points must be a non-NULL 4-byte aligned device pointer");
+    if (n > 0 && (!d_out || ((uintptr_t)d_out & 15u)))
+        return fail(DBT_EINVAL, "out must be a non-NULL 16-byte aligned device pointer");
+    Pose P{};
+    st = check_pose(pose, &P);
+    if (st != DBT_OK) return st;
+    const DevGrid dg = dev_grid(g);
+    pose_filter(P, dg);
+    launch_contacts(dg, k->dp, k->dt, P, d_xyz, (long long)n, (int4 *)d_out, (cudaStream_t)stream);
+    DBT_CUDA(cudaGetLastError());
     return DBT_OK;
 }
 
@@ -963,6 +1011,7 @@ extern "C" dbt_status dbt_batch_set_items(dbt_batch *b, const dbt_batch_item *it
         Pose P;
         dbt_status st = check_pose(it.pose, &P);
         if (st != DBT_OK) return fail(st, "item %d: %s", i, dbt_last_error());
+        pose_filter(P, b->grids[it.grid]);
         ItemDev &d = b->items[i];
         d.xyz = it.d_xyz;
         d.n = it.n;

@@ -78,7 +78,19 @@ struct DevGrid {
 struct Pose {
     double r[9];                // row-major rotation
     double t[3];
+    // binary32 filter data for one grid (pose_filter): with b = (t - origin)
+    // * inv_res in binary64 and B = round(b), the voxel coordinate along
+    // axis k is fa[3k..3k+2] . p + fb[k] + B[k] up to a bounded error
+    float fa[9];                // fl32(r * inv_res)
+    float fr[9];                // fl32(r)
+    float fb[3];                // fl32(b - B)
+    int fbi[3];                 // B
+    float fe0[3];               // absolute error allowance of fb[k] and of the binary64 path
+    int fast;                   // 0: every return takes the binary64 path
 };
+
+// Fills the filter fields of P for grid g (host).
+void pose_filter(Pose &P, const DevGrid &g);
 
 // One scan of a batch: its returns, the grid (index into the batch's grid
 // table) and the pose.
@@ -177,6 +189,8 @@ void launch_voxelize(const DevGrid &g, const DevParams &p, const DevTables &t, c
                      const ScanEx *ex = nullptr);
 void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                   cudaStream_t s);
+void launch_contacts(const DevGrid &g, const DevParams &p, const DevTables &t, const Pose &pose,
+                     const float *xyz, long long n, int4 *out, cudaStream_t s);
 void launch_alloc(const WsDev &ws, cudaStream_t s);
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                  cudaStream_t s);

@@ -55,6 +55,18 @@ __device__ __forceinline__ int kword(int row, int w) { return row * 8 + (w ^ ((r
 
 __device__ __forceinline__ uint32_t vmin4(uint32_t a, uint32_t b) { return __vminu4(a, b); }
 
+// Bytes of b below the matching bytes of a, as bit 7 of each byte, for bytes
+// < 128 (codes are <= 32): b + 128 - a per byte lies in [1, 255], so the
+// subtraction never borrows across bytes and bit 7 is clear exactly when
+// b < a.  code_min() then takes those bytes of b: the byte-wise minimum.
+__device__ __forceinline__ uint32_t code_lt(uint32_t a, uint32_t b) {
+    return ~((b | 0x80808080u) - a) & 0x80808080u;
+}
+__device__ __forceinline__ uint32_t code_min(uint32_t a, uint32_t b, uint32_t lt) {
+    const uint32_t m = (lt >> 7) * 0xFFu;
+    return (a & ~m) | (b & m);
+}
+
 __device__ __forceinline__ uint32_t code_to_mask(uint32_t k) {
     return k == 0u ? 0u : (0xFFFFFFFFu >> (32u - k));
 }
@@ -134,9 +146,9 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
                 const uint32_t kwd = P[pb + 4 * j];
                 const int addr = rbase + ((w0 + j) ^ f);
                 const uint32_t a = wa->kst[addr];
-                const uint32_t nv = vmin4(a, kwd);
-                if (nv != a) {
-                    wa->kst[addr] = nv;
+                const uint32_t lt = code_lt(a, kwd);
+                if (lt) {
+                    wa->kst[addr] = code_min(a, kwd, lt);
                     changed |= 1u << (w0 + j);
                 }
             }
@@ -369,9 +381,9 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
                                   ((uint32_t)ctab[acc >> 24] << 24);
             const int wd = kword(row, w);
             const uint32_t old = a0->kst[wd];
-            const uint32_t nv = vmin4(old, code);
-            if (nv != old) {
-                a0->kst[wd] = nv;
+            const uint32_t lt = code_lt(old, code);
+            if (lt) {
+                a0->kst[wd] = code_min(old, code, lt);
                 changed = true;
             }
         }

@@ -118,7 +118,75 @@ __device__ __forceinline__ unsigned long long voxel_key(const DevGrid &g, int x,
                (unsigned long long)g.pitch + (unsigned long long)x + 1ull;
 }
 
+// ------------------------------------------------------------------ filter
+// The voxel and octahedral-cell decisions are floors of binary64 values.
+// They are first taken from binary32 evaluations with a rigorous bound on
+// their distance to the exact real value (a floating-point filter in the
+// sense of Shewchuk's adaptive predicates): when the binary32 value lies
+// farther than its bound from every integer, the binary64 value (within
+// ~2^-50 relative of the same real value) has the same floor.  Otherwise,
+// and for poses without filter data, the binary64 path decides.
+//
+// Allowance of a binary32 sum of three products and a constant taken by
+// FMAs (3 roundings) with binary32-rounded coefficients (1 more): 4u (1 +
+// 4u) < 2.4e-7 relative to the sum of the terms' magnitudes, u = 2^-24;
+// 3.5e-7 leaves room for the rounding of the allowance itself.
+constexpr float FILTER_REL = 3.5e-7f;
+// Absolute allowance for products that fall into the binary32 subnormal
+// range (each loses at most 2^-150).
+constexpr float FILTER_ABS = 1e-37f;
+
+// floor(v) when every real within e of v has the same floor; false when
+// uncertain or NaN.  v - f and (f + 1) - v are exact or off by <= 2^-25,
+// far below every allowance passed in.
+__device__ __forceinline__ bool floor_certain(float v, float e, long long &q) {
+    const float f = floorf(v);
+    if (!(v - f > e && (f + 1.0f) - v > e)) return false;
+    q = (long long)f;
+    return true;
+}
+
+// bin_octa from binary32 directions d with absolute error bounds e; -1 when
+// a decision is uncertain.  |s - s*| <= es; |d_x / s - d*_x / s*| <= (e_x +
+// es) / s because |d*_x| <= s*; each later binary32 operation adds one
+// rounding of a value of magnitude <= 2 (<= 1.2e-7) before the scaling by
+// n / 2.
+__device__ __forceinline__ int bin_octa_f32(const float d[3], const float e[3], int n) {
+    const float ax = fabsf(d[0]), ay = fabsf(d[1]), az = fabsf(d[2]);
+    const float s = (ax + ay) + az;
+    const float es = (e[0] + e[1] + e[2]) * 1.001f + s * 2.5e-7f;
+    if (!(s > 4.0f * es) || !(az > e[2])) return -1;        // fold decision uncertain
+    float u = __fdiv_rn(d[0], s), v = __fdiv_rn(d[1], s);
+    float eu = __fdiv_ru(e[0] + es, s) * 1.01f + 1.2e-7f;
+    float ev = __fdiv_ru(e[1] + es, s) * 1.01f + 1.2e-7f;
+    if (d[2] < 0.0f) {
+        if (!(ax > e[0] && ay > e[1])) return -1;          // signs of u, v uncertain
+        const float fu = 1.0f - fabsf(v), fv = 1.0f - fabsf(u);
+        const float eu0 = eu;
+        eu = ev + 1.2e-7f;
+        ev = eu0 + 1.2e-7f;
+        u = d[0] < 0.0f ? -fu : fu;
+        v = d[1] < 0.0f ? -fv : fv;
+    }
+    const float h = 0.5f * (float)n;
+    const float au = (u + 1.0f) * h, av = (v + 1.0f) * h;
+    long long i, j;
+    if (!floor_certain(au, (eu + 2.4e-7f) * h * 1.01f + fabsf(au) * 1.2e-7f + 1e-6f, i) ||
+        !floor_certain(av, (ev + 2.4e-7f) * h * 1.01f + fabsf(av) * 1.2e-7f + 1e-6f, j))
+        return -1;
+    return (int)(min(max(j, 0ll), (long long)n - 1) * n + min(max(i, 0ll), (long long)n - 1));
+}
+
 // ------------------------------------------------------------------ K1
+// Map-frame direction d = R p in binary64 (the order the bins are defined on).
+__device__ __forceinline__ void direction64(const Pose &pose, double px, double py, double pz,
+                                            double d[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        d[r] = __fma_rn(pose.r[3 * r + 2], pz,
+                        __fma_rn(pose.r[3 * r + 1], py, __dmul_rn(pose.r[3 * r + 0], px)));
+}
+
 // Sec. III-C for one return: discard non-finite and origin returns, map-frame
 // transform, contact voxel, boundary discard, bin.  Returns 0 (not valid),
 // 1 (valid, outside) or 2 (inside, rec filled with contact and bin).
@@ -127,24 +195,54 @@ __device__ __forceinline__ int contact_of(const DevGrid &g, const DevParams &p, 
                                           int4 &rec) {
     if (!(isfinite(fx) && isfinite(fy) && isfinite(fz)) || (fx == 0.0f && fy == 0.0f && fz == 0.0f))
         return 0;
+    long long q[3];
+    bool certain = pose.fast != 0;
+    if (certain) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float *a = pose.fa + 3 * r;
+            const float c = fmaf(a[2], fz, fmaf(a[1], fy, fmaf(a[0], fx, pose.fb[r])));
+            const float S = fabsf(a[0] * fx) + fabsf(a[1] * fy) + fabsf(a[2] * fz) + fabsf(pose.fb[r]);
+            long long qq = 0;
+            certain = certain && floor_certain(c, fmaf(S, FILTER_REL, pose.fe0[r] + FILTER_ABS), qq);
+            q[r] = qq + pose.fbi[r];
+        }
+    }
     const double px = fx, py = fy, pz = fz;
     double d[3];
-    long long q[3];
-    const double org[3] = {g.ox, g.oy, g.oz};
+    bool have_d = false;
+    if (!certain) {
+        direction64(pose, px, py, pz, d);
+        have_d = true;
+        const double org[3] = {g.ox, g.oy, g.oz};
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        d[r] = __fma_rn(pose.r[3 * r + 2], pz,
-                        __fma_rn(pose.r[3 * r + 1], py, __dmul_rn(pose.r[3 * r + 0], px)));
-        const double w = __dadd_rn(d[r], pose.t[r]);
-        // floor((w - origin) * (1 / res)) as an integer: the conversion rounds
-        // toward -inf and saturates, so the bounds test below is the same as
-        // on the binary64 value
-        q[r] = __double2ll_rd(__dmul_rn(__dsub_rn(w, org[r]), g.inv_res));
+        for (int r = 0; r < 3; ++r) {
+            const double w = __dadd_rn(d[r], pose.t[r]);
+            // floor((w - origin) * (1 / res)) as an integer: the conversion
+            // rounds toward -inf and saturates, so the bounds test below is
+            // the same as on the binary64 value
+            q[r] = __double2ll_rd(__dmul_rn(__dsub_rn(w, org[r]), g.inv_res));
+        }
     }
     if (!(q[0] >= p.R && q[0] <= g.nx - 1 - p.R && q[1] >= p.R && q[1] <= g.ny - 1 - p.R &&
           q[2] >= p.R && q[2] <= g.nz - 1 - p.R))
         return 1;
-    rec = make_int4((int)q[0], (int)q[1], (int)q[2], bin_of(p, t, d[0], d[1], d[2]));
+    int bin = -1;
+    if (p.scheme == DBT_BINS_OCTA && pose.fast) {
+        float df[3], ef[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float *a = pose.fr + 3 * r;
+            df[r] = fmaf(a[2], fz, fmaf(a[1], fy, a[0] * fx));
+            ef[r] = fmaf(fabsf(a[0] * fx) + fabsf(a[1] * fy) + fabsf(a[2] * fz), FILTER_REL, FILTER_ABS);
+        }
+        bin = bin_octa_f32(df, ef, p.na);
+    }
+    if (bin < 0) {
+        if (!have_d) direction64(pose, px, py, pz, d);
+        bin = bin_of(p, t, d[0], d[1], d[2]);
+    }
+    rec = make_int4((int)q[0], (int)q[1], (int)q[2], bin);
     return 2;
 }
 
@@ -163,8 +261,7 @@ __global__ void __launch_bounds__(256) k_voxelize(DevGrid g, DevParams p, DevTab
             if (i % ex.ds == 0) {
                 if (ex.n_poses > 0) {
                     const long long m = ((long long)i % ex.period) * ex.n_poses / ex.period;
-                    const Pose pm = ws.poses[m];
-                    c = contact_of(g, p, t, pm, xyz[3 * i + 0], xyz[3 * i + 1], xyz[3 * i + 2], rec);
+                    c = contact_of(g, p, t, ws.poses[m], xyz[3 * i + 0], xyz[3 * i + 1], xyz[3 * i + 2], rec);
                 } else {
                     c = contact_of(g, p, t, pose, xyz[3 * i + 0], xyz[3 * i + 1], xyz[3 * i + 2], rec);
                 }
@@ -183,6 +280,17 @@ __global__ void __launch_bounds__(256) k_voxelize(DevGrid g, DevParams p, DevTab
         if (bv) atomicAdd(&ws.hdr->acc_valid, (unsigned long long)__popc(bv));
         if (bi) atomicAdd(&ws.hdr->acc_inside, (unsigned long long)__popc(bi));
     }
+}
+
+// Contact voxel and bin of every return (dbt_scan_contacts).
+__global__ void __launch_bounds__(256) k_contacts(DevGrid g, DevParams p, DevTables t, Pose pose,
+                                                  const float *__restrict__ xyz, long long n,
+                                                  int4 *__restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 rec = make_int4(-1, 0, 0, 0);
+    contact_of(g, p, t, pose, xyz[3 * i + 0], xyz[3 * i + 1], xyz[3 * i + 2], rec);
+    out[i] = rec;
 }
 
 // Brick range of the K^3 neighbourhood of contact c along one axis.
@@ -663,6 +771,11 @@ void launch_voxelize(const DevGrid &g, const DevParams &p, const DevTables &t, c
     else
         k_voxelize<false><<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, t, pose, xyz, n, ws, hcap,
                                                                     ScanEx{1, 0, 1});
+}
+
+void launch_contacts(const DevGrid &g, const DevParams &p, const DevTables &t, const Pose &pose,
+                     const float *xyz, long long n, int4 *out, cudaStream_t s) {
+    if (n > 0) k_contacts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, p, t, pose, xyz, n, out);
 }
 
 void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,

@@ -95,6 +95,7 @@ _SIGS = {
     "dbt_kernels_export": [_vp, _vp, _vp],
     "dbt_tables_host": [_P(dbt_params), _vp, _vp],
     "dbt_bin_directions": [_vp, _vp, ctypes.c_int64, _vp, _vp],
+    "dbt_scan_contacts": [_P(dbt_grid), _vp, _vp, ctypes.c_int64, _P(ctypes.c_double), _vp, _vp],
     "dbt_workspace_size": [_P(dbt_grid), _vp, ctypes.c_int64, _P(ctypes.c_size_t)],
     "dbt_workspace_create": [_P(dbt_grid), _vp, ctypes.c_int64, _vp, ctypes.c_size_t, _vp,
                              _P(_vp)],
@@ -371,6 +372,21 @@ def dbt_integrate_scan(grid: Grid, kernels: Kernels, ws: Workspace, xyz, pose, s
     keep, pp = _pose_arg(pose)
     _check(lib().dbt_integrate_scan(ctypes.byref(grid.c), kernels.h, ws.h,
                                     xyz.data_ptr() if n else None, n, pp, _stream_ptr(stream)))
+
+
+def dbt_scan_contacts(grid: Grid, kernels: Kernels, xyz, pose, stream=None):
+    """Contact voxel and bin of every return, without integrating: a CUDA
+    int32 (n, 4) tensor of (x, y, z, bin), x = -1 for returns that are not
+    valid or fall within R voxels of the grid boundary."""
+    import torch
+    n = int(xyz.shape[0])
+    if n and (not xyz.is_cuda or not xyz.is_contiguous() or xyz.dtype != torch.float32):
+        raise DbtError(DBT_EINVAL, "xyz must be a contiguous CUDA float32 tensor")
+    out = torch.empty((n, 4), dtype=torch.int32, device=xyz.device if n else "cuda")
+    keep, pp = _pose_arg(pose)
+    _check(lib().dbt_scan_contacts(ctypes.byref(grid.c), kernels.h, xyz.data_ptr() if n else None,
+                                   n, pp, out.data_ptr() if n else None, _stream_ptr(stream)))
+    return out
 
 
 def dbt_integrate_scan_ex(grid: Grid, kernels: Kernels, ws: Workspace, xyz, pose=None,
