@@ -205,8 +205,7 @@ static void export_tables(int K, int nbins, const std::vector<uint32_t> &m2,
         for (int b = 0; b < nbins; ++b)
             for (uint32_t e = sh_start[b]; e < sh_start[b + 1]; ++e) {
                 const uint32_t o = sh_off[e];
-                const int ox = (int)(o & 255u) - 128, oy = (int)((o >> 8) & 255u) - 128,
-                          oz = (int)((o >> 16) & 255u) - 128;
+                const int ox = off_axis(o, 0), oy = off_axis(o, 1), oz = off_axis(o, 2);
                 h_shadow[b * kk + ((oz + R) * K + (oy + R)) * K + (ox + R)] = 1;
             }
     }

@@ -37,9 +37,15 @@ __host__ __device__ inline int max_pairs_per_return(int K) {
     return (1 + (K - 1 + BX - 1) / BX) * (1 + (K - 1 + BY - 1) / BY) * (1 + (K - 1 + BZ - 1) / BZ);
 }
 
-// Shadow offsets are packed as (ox + 128) | (oy + 128) << 8 | (oz + 128) << 16.
+// Shadow offsets are packed as bytes (ox + OFF_BIAS) | (oy + OFF_BIAS) << 8 |
+// (oz + OFF_BIAS) << 16 (|o| <= MAX_R, so every byte is in [22, 42]).
+constexpr int OFF_BIAS = 32;
 __host__ __device__ inline uint32_t pack_off(int ox, int oy, int oz) {
-    return (uint32_t)(ox + 128) | ((uint32_t)(oy + 128) << 8) | ((uint32_t)(oz + 128) << 16);
+    return (uint32_t)(ox + OFF_BIAS) | ((uint32_t)(oy + OFF_BIAS) << 8) |
+           ((uint32_t)(oz + OFF_BIAS) << 16);
+}
+__host__ __device__ inline int off_axis(uint32_t o, int axis) {
+    return (int)((o >> (8 * axis)) & 255u) - OFF_BIAS;
 }
 
 struct DevParams {

@@ -158,19 +158,23 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
     }
 }
 
-// Eq. 5 counts of one pair: lanes walk the bin's shadow offsets (sh / shs,
-// in shared or global memory) and count those inside the brick.  ATOMIC:
-// several warps count into one array, so counts are added atomically to
-// their packed 16-bit halves (a voxel's total never reaches 2^16: it is at
-// most the number of lattice points within r_s).
+// Eq. 5 counts of one pair: lanes walk the bin's shadow offsets (sh / shs)
+// and count those inside the brick.  ATOMIC: several warps count into one
+// array, so counts are added atomically to their packed 16-bit halves (a
+// voxel's total never reaches 2^16: it is at most the number of lattice
+// points within r_s).
 //
-// Offsets are packed bytes (o + 128) and the contact c is packed as bytes
-// (c - 128), so one byte-wise add gives the voxel's brick coordinates
-// o + c, which lie in [-20, 51] and wrap below zero to >= 236; one byte-wise
-// compare then tests all three against the brick (x < 32, y < 8, z < 8; the
-// zero padding entries land at c + 128 >= 108 and fail it too).
-static_assert(BX == 32 && BY == 8 && BZ == 8 && MAX_K <= 21,
+// Offsets are packed bytes o + 32 and the contact c relative to the brick
+// is packed as bytes c + 32, so one 32-bit add gives per byte o + c + 64,
+// which lies in [44, 115] (|o| <= SR <= 10, c in [-SR, 31 + SR]): no byte
+// carries into the next.  The voxel o + c is in the brick exactly when that
+// byte is in [64, 96) for x and in [64, 72) for y and z, i.e. bits 7..5 of
+// the x byte read 010 and bits 7..3 of the y and z bytes read 01000: one AND
+// and one compare.  Lanes past the bin's list take 0x80 bytes, which set
+// bit 7 and fail.  The low bits of the bytes are then x, y and z.
+static_assert(BX == 32 && BY == 8 && BZ == 8 && MAX_R <= 10 && OFF_BIAS == 32,
               "shadow_pair's byte packing assumes 32 x 8 x 8 bricks and |offsets| <= 10");
+constexpr uint32_t SH_PAD = 0x80808080u;
 template <bool ATOMIC>
 __device__ __forceinline__ void shadow_pair(uint32_t pl, uint16_t *cnt, const uint32_t *sh,
                                             const uint32_t *shs, int R, int SR, int lane) {
@@ -180,20 +184,23 @@ __device__ __forceinline__ void shadow_pair(uint32_t pl, uint16_t *cnt, const ui
     if (!(cx >= -SR && cx <= BX - 1 + SR && cy >= -SR && cy <= BY - 1 + SR && cz >= -SR &&
           cz <= BZ - 1 + SR))
         return;
-    const uint32_t cpk = ((uint32_t)(cx - 128) & 255u) | (((uint32_t)(cy - 128) & 255u) << 8) |
-                         (((uint32_t)(cz - 128) & 255u) << 16);
+    const uint32_t cpk = (uint32_t)(cx + 32) | ((uint32_t)(cy + 32) << 8) | ((uint32_t)(cz + 32) << 16);
     const uint32_t bin = pl >> 16;
     const uint32_t e0 = __ldg(shs + bin), e1 = __ldg(shs + bin + 1);
     for (uint32_t e = e0; e < e1; e += 96) {
-        // three batches of 32 fetched before use (a 3-voxel shadow has <= 96 offsets)
+        // up to three batches of 32 fetched before use; batches past the
+        // list are skipped (warp-uniform)
+        const uint32_t left = e1 - e;
         uint32_t o[3];
 #pragma unroll
-        for (int h = 0; h < 3; ++h) o[h] = e + 32 * h + lane < e1 ? __ldg(sh + e + 32 * h + lane) : 0u;
+        for (int h = 0; h < 3; ++h)
+            o[h] = e + 32 * h + lane < e1 ? __ldg(sh + e + 32 * h + lane) : SH_PAD;
 #pragma unroll
         for (int h = 0; h < 3; ++h) {
-            const uint32_t u = __vadd4(o[h], cpk);                    // bytes x, y, z
-            if ((__vcmpltu4(u, 0x00080820u) & 0x00FFFFFFu) == 0x00FFFFFFu) {
-                const int v = (int)(__byte_perm(u, 0u, 0x4420u) + ((u >> 3) & 0xE0u));
+            if (32u * h >= left) break;
+            const uint32_t u = o[h] + cpk;
+            if ((u & 0x00F8F8E0u) == 0x00404040u) {
+                const int v = (int)((u & 31u) | ((u >> 3) & 0xE0u) | ((u >> 8) & 0x700u));
                 if (ATOMIC)
                     atomicAdd(reinterpret_cast<uint32_t *>(cnt) + (v >> 1), 1u << (16 * (v & 1)));
                 else

@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, Ws
             }
         }
     }
-    count_pairs<false>(ws, g, 0u, kept, kept ? brick_span(rx, ry, rz, p.R) : BrickSpan{});
+    count_pairs<true>(ws, g, 0u, kept, kept ? brick_span(rx, ry, rz, p.R) : BrickSpan{});
     const unsigned bk = __ballot_sync(0xffffffffu, kept);
     if ((threadIdx.x & 31) == 0 && bk) atomicAdd(&ws.hdr->acc_kept, (unsigned long long)__popc(bk));
 }
@@ -459,43 +459,58 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
 // ------------------------------------------------------------------ K4
 // Pair payload: contact relative to the brick corner plus R (x: 6 bits,
 // y, z: 5 bits each) and the bin (16 bits).
-// Pair payloads into the segments, slots from the per-brick cursors.  One
-// thread per (return, brick of its span): a return's cursor atomics are all
-// in flight at once instead of one after another.  t -> return t / slots,
-// the j-th brick of its span (x fastest), j = t mod slots.
-__device__ __forceinline__ void fill_one(const WsDev &ws, const DevGrid &g, uint32_t b0,
-                                         const DevParams &p, int4 r, int j) {
-    const BrickSpan sp = brick_span(r.x, r.y, r.z, p.R);
-    const int sx = sp.x1 - sp.x0 + 1, sy = sp.y1 - sp.y0 + 1, sz = sp.z1 - sp.z0 + 1;
-    if (j >= sx * sy * sz) return;
-    const int ix = j % sx, jy = j / sx, iy = jy % sy, iz = jy / sy;
-    const int bx = sp.x0 + ix, by = sp.y0 + iy, bz = sp.z0 + iz;
-    const uint32_t b = b0 + ((uint32_t)bz * g.nby + by) * g.nbx + bx;
-    const uint32_t slot = atomicAdd(&ws.bcnt[b], 1u);
-    const unsigned long long pos = (unsigned long long)ws.boff[b] + slot;
-    const uint32_t rx = (uint32_t)(r.x - bx * BX + p.R);
-    const uint32_t ry = (uint32_t)(r.y - by * BY + p.R);
-    const uint32_t rz = (uint32_t)(r.z - bz * BZ + p.R);
-    const uint32_t bin = (uint32_t)(r.w & 0xFFFF);
-    if (pos < ws.pairs_cap)
-        ws.pairs[pos] = rx | (ry << 6) | (rz << 11) | (bin << 16);
-    else
-        atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
+__device__ __forceinline__ uint32_t pair_payload(int4 r, int bx, int by, int bz, int R) {
+    const uint32_t rx = (uint32_t)(r.x - bx * BX + R);
+    const uint32_t ry = (uint32_t)(r.y - by * BY + R);
+    const uint32_t rz = (uint32_t)(r.z - bz * BZ + R);
+    return rx | (ry << 6) | (rz << 11) | ((uint32_t)(r.w & 0xFFFF) << 16);
 }
 
+// Pair payloads into the segments, slots from the per-brick cursors.  One
+// thread per (brick j of a span, return): t -> j = t / n32, return t mod
+// n32 (n32 = n rounded up to whole warps), so a warp holds the j-th bricks
+// of 32 consecutive returns, which mostly name the same brick: lanes naming
+// one brick take their slots with one atomic of their leader.
 __global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, int slots, WsDev ws,
                                               uint32_t hcap) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long i = t / slots;
-    if (i < n) {
-        const int4 r = ws.prec[i];
-        if (r.x >= 0 && !(r.w & PREC_DUP)) fill_one(ws, g, 0u, p, r, (int)(t - i * slots));
+    const long long n32 = ((long long)n + 31) & ~31ll;
+    const long long j = t / n32;
+    const long long i = t - j * n32;
+    if (j < slots) {                                          // warp-uniform
+        bool v = false;
+        uint32_t b = 0xFFFFFFFFu, pl = 0;
+        if (i < n) {
+            const int4 r = ws.prec[i];
+            if (r.x >= 0 && !(r.w & PREC_DUP)) {
+                const BrickSpan sp = brick_span(r.x, r.y, r.z, p.R);
+                const int sx = sp.x1 - sp.x0 + 1, sy = sp.y1 - sp.y0 + 1, sz = sp.z1 - sp.z0 + 1;
+                if (j < sx * sy * sz) {
+                    const int jj = (int)j, ix = jj % sx, jy = jj / sx, iy = jy % sy, iz = jy / sy;
+                    const int bx = sp.x0 + ix, by = sp.y0 + iy, bz = sp.z0 + iz;
+                    b = ((uint32_t)bz * g.nby + by) * g.nbx + bx;
+                    pl = pair_payload(r, bx, by, bz, p.R);
+                    v = true;
+                }
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (v && lane == leader) base = atomicAdd(&ws.bcnt[b], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (v) {
+            const unsigned long long pos =
+                (unsigned long long)ws.boff[b] + base + __popc(peers & ((1u << lane) - 1u));
+            if (pos < ws.pairs_cap) ws.pairs[pos] = pl;
+            else atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
+        }
     }
     if (p.dedup) {
         const uint32_t stride = gridDim.x * blockDim.x;
-        for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < hcap; j += stride) {
-            ws.hkey[j] = 0ull;
-            ws.hidx[j] = 0u;
+        for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < hcap; k += stride) {
+            ws.hkey[k] = 0ull;
+            ws.hidx[k] = 0u;
         }
     }
 }
@@ -670,8 +685,7 @@ __global__ void __launch_bounds__(256) k_footprint(DevGrid g, DevParams p, DevTa
     for (uint32_t e = t.sh_start[bin] + threadIdx.x; e < t.sh_start[bin + 1]; e += blockDim.x) {
         const uint32_t o = t.sh_off[e];
         const unsigned long long v =
-            voxel_key(g, r.x + (int)(o & 255u) - 128, r.y + (int)((o >> 8) & 255u) - 128,
-                      r.z + (int)((o >> 16) & 255u) - 128) - 1ull;
+            voxel_key(g, r.x + off_axis(o, 0), r.y + off_axis(o, 1), r.z + off_axis(o, 2)) - 1ull;
         const uint32_t bit = 1u << (v & 31);
         if (!(atomicOr(&bits_s[v >> 5], bit) & bit)) ++ns;
     }
@@ -795,7 +809,7 @@ void launch_alloc(const WsDev &ws, cudaStream_t s) {
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                  cudaStream_t s) {
     const int slots = max_pairs_per_return(p.K);
-    const long long threads = std::max((long long)n * slots, (long long)hcap);
+    const long long threads = std::max((((long long)n + 31) & ~31ll) * slots, (long long)hcap);
     k_fill<<<(unsigned)std::max(1LL, (threads + 255) / 256), 256, 0, s>>>(g, p, n, slots, ws, hcap);
 }
 
