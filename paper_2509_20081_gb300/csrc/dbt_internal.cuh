@@ -189,6 +189,36 @@ constexpr uint32_t HEAVY_PAIRS = 48;
 // PREC_DUP when the first-return rule drops the return.
 constexpr int PREC_DUP = 1 << 30;
 
+// Programmatic dependent launch.  The kernels of a scan are launched with
+// launch_pdl: the next kernel's CTAs may be scheduled while the previous
+// kernel on the stream drains, which hides the launch gap.  pdl_wait()
+// (griddepcontrol.wait) holds a thread until every prerequisite grid has
+// completed and its writes are visible; a kernel launched without the
+// attribute passes it at once.  Each of these kernels waits before it reads
+// or writes global memory that any other kernel (or the caller) writes.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel launch once every CTA of this grid has called it (or
+// exited).
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, kern, args...);   // errors surface through cudaGetLastError
+}
+
 // Launch helpers implemented in the .cu files.
 void launch_voxelize(const DevGrid &g, const DevParams &p, const DevTables &t, const Pose &pose,
                      const float *xyz, int n, const WsDev &ws, uint32_t hcap, cudaStream_t s,

@@ -459,6 +459,10 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
     const uint32_t *sh = t.sh_off, *shs = t.sh_start;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     WarpArea *wa = areas + warp;
+    // the tables above are the kernels' own; the workspace is the previous
+    // kernels' output
+    pdl_wait();
+    pdl_launch_dependents();
     const uint32_t nt = min(*(volatile uint32_t *)&ws.hdr->n_touched, ws.max_touched);
     const uint32_t nheavy = min(*(volatile uint32_t *)&ws.hdr->n_heavy, nt);
     const uint32_t nmed = min(*(volatile uint32_t *)&ws.hdr->n_med, nt - nheavy);
@@ -768,9 +772,9 @@ void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, 
     const size_t smem = integrate_smem(p.K);
     const BatchDev none = {};
     if (words_per_row(p.K) == 4)
-        k_integrate<4, false><<<grid_ctas, NTHR, smem, s>>>(g, none, p, t, n_input, ws);
+        launch_pdl(k_integrate<4, false>, grid_ctas, NTHR, smem, s, g, none, p, t, n_input, ws);
     else
-        k_integrate<6, false><<<grid_ctas, NTHR, smem, s>>>(g, none, p, t, n_input, ws);
+        launch_pdl(k_integrate<6, false>, grid_ctas, NTHR, smem, s, g, none, p, t, n_input, ws);
 }
 
 void launch_integrate_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
@@ -778,9 +782,9 @@ void launch_integrate_batch(const BatchDev &bd, const DevParams &p, const DevTab
     const size_t smem = integrate_smem(p.K);
     const DevGrid none = {};
     if (words_per_row(p.K) == 4)
-        k_integrate<4, true><<<grid_ctas, NTHR, smem, s>>>(none, bd, p, t, n_input, ws);
+        launch_pdl(k_integrate<4, true>, grid_ctas, NTHR, smem, s, none, bd, p, t, n_input, ws);
     else
-        k_integrate<6, true><<<grid_ctas, NTHR, smem, s>>>(none, bd, p, t, n_input, ws);
+        launch_pdl(k_integrate<6, true>, grid_ctas, NTHR, smem, s, none, bd, p, t, n_input, ws);
 }
 
 }  // namespace dbt

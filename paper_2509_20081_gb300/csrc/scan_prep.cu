@@ -177,6 +177,46 @@ __device__ __forceinline__ int bin_octa_f32(const float d[3], const float e[3], 
     return (int)(min(max(j, 0ll), (long long)n - 1) * n + min(max(i, 0ll), (long long)n - 1));
 }
 
+// ------------------------------------------------------------------ counters
+// Scan counters of one CTA.  Every warp of the grid adding its popcounts to
+// one global address would serialise those atomics at L2 (thousands per
+// launch); the warps add into shared memory instead and one thread per CTA
+// adds the totals.  Batches also count per scan: a CTA's consecutive
+// returns belong to a few consecutive scans, counted in a window of
+// TALLY_ITEMS slots from the CTA's first scan (scans past it add directly).
+constexpr int TALLY_ITEMS = 8;
+struct CtaTally {
+    uint32_t hdr[2];
+    uint32_t item[TALLY_ITEMS][2];
+    int first_item;
+};
+
+__device__ __forceinline__ void tally_init(CtaTally &s, int first_item) {
+    if (threadIdx.x < 2) s.hdr[threadIdx.x] = 0u;
+    if (threadIdx.x < 2 * TALLY_ITEMS) s.item[threadIdx.x >> 1][threadIdx.x & 1] = 0u;
+    if (threadIdx.x == 0) s.first_item = first_item;
+    __syncthreads();
+}
+
+// Warp popcounts of two flags into the CTA's header tallies.
+__device__ __forceinline__ void tally_warp(CtaTally &s, bool a, bool b) {
+    const unsigned ba = __ballot_sync(0xffffffffu, a), bb = __ballot_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0) {
+        if (ba) atomicAdd(&s.hdr[0], (uint32_t)__popc(ba));
+        if (bb) atomicAdd(&s.hdr[1], (uint32_t)__popc(bb));
+    }
+}
+
+// After the CTA's last tally: its totals to the global counters ga, gb.
+__device__ __forceinline__ void tally_flush(CtaTally &s, unsigned long long *ga,
+                                            unsigned long long *gb) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s.hdr[0]) atomicAdd(ga, (unsigned long long)s.hdr[0]);
+        if (gb && s.hdr[1]) atomicAdd(gb, (unsigned long long)s.hdr[1]);
+    }
+}
+
 // ------------------------------------------------------------------ K1
 // Map-frame direction d = R p in binary64 (the order the bins are defined on).
 __device__ __forceinline__ void direction64(const Pose &pose, double px, double py, double pz,
@@ -252,6 +292,10 @@ template <bool EX>
 __global__ void __launch_bounds__(256) k_voxelize(DevGrid g, DevParams p, DevTables t, Pose pose,
                                                   const float *__restrict__ xyz, int n, WsDev ws,
                                                   uint32_t hcap, ScanEx ex) {
+    __shared__ CtaTally s_tally;
+    tally_init(s_tally, 0);
+    pdl_wait();
+    pdl_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false, inside = false;
     if (i < n) {
@@ -274,12 +318,8 @@ __global__ void __launch_bounds__(256) k_voxelize(DevGrid g, DevParams p, DevTab
         if (inside && p.dedup) hash_insert(ws, hcap, voxel_key(g, rec.x, rec.y, rec.z), (uint32_t)i);
         ws.prec[i] = rec;
     }
-    const unsigned bv = __ballot_sync(0xffffffffu, valid);
-    const unsigned bi = __ballot_sync(0xffffffffu, inside);
-    if ((threadIdx.x & 31) == 0) {
-        if (bv) atomicAdd(&ws.hdr->acc_valid, (unsigned long long)__popc(bv));
-        if (bi) atomicAdd(&ws.hdr->acc_inside, (unsigned long long)__popc(bi));
-    }
+    tally_warp(s_tally, valid, inside);
+    tally_flush(s_tally, &ws.hdr->acc_valid, &ws.hdr->acc_inside);
 }
 
 // Contact voxel and bin of every return (dbt_scan_contacts).
@@ -353,6 +393,10 @@ __device__ __forceinline__ void count_pairs(const WsDev &ws, const DevGrid &g, u
 
 __global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, WsDev ws,
                                                uint32_t hcap) {
+    __shared__ CtaTally s_tally;
+    tally_init(s_tally, 0);
+    pdl_wait();
+    pdl_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool kept = false;
     int rx = 0, ry = 0, rz = 0;
@@ -371,8 +415,8 @@ __global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, Ws
         }
     }
     count_pairs<true>(ws, g, 0u, kept, kept ? brick_span(rx, ry, rz, p.R) : BrickSpan{});
-    const unsigned bk = __ballot_sync(0xffffffffu, kept);
-    if ((threadIdx.x & 31) == 0 && bk) atomicAdd(&ws.hdr->acc_kept, (unsigned long long)__popc(bk));
+    tally_warp(s_tally, kept, false);
+    tally_flush(s_tally, &ws.hdr->acc_kept, nullptr);
 }
 
 // ------------------------------------------------------------------ K3
@@ -391,6 +435,8 @@ constexpr int ALLOC_THREADS = 1024;
 
 __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
     __shared__ uint32_t s_w[ALLOC_THREADS / 32][4];   // per warp: pairs, heavy, med, light
+    pdl_wait();
+    pdl_launch_dependents();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nb = ws.nbricks;
     for (uint32_t base = blockIdx.x * ALLOC_THREADS; base < nb; base += gridDim.x * ALLOC_THREADS) {
@@ -473,6 +519,8 @@ __device__ __forceinline__ uint32_t pair_payload(int4 r, int bx, int by, int bz,
 // one brick take their slots with one atomic of their leader.
 __global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, int slots, WsDev ws,
                                               uint32_t hcap) {
+    pdl_wait();
+    pdl_launch_dependents();
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n32 = ((long long)n + 31) & ~31ll;
     const long long j = t / n32;
@@ -536,22 +584,51 @@ __device__ __forceinline__ unsigned long long batch_key(const DevGrid &g, int it
 }
 
 // Adds per-scan counts of a warp: lanes with the same item are summed by
-// their leader.
-__device__ __forceinline__ void add_item_counts(const BatchDev &bd, int item, bool a, bool b,
-                                                unsigned long long ItemCounters::*fa,
+// their leader, into the CTA's window (or directly past it).
+__device__ __forceinline__ void add_item_counts(const BatchDev &bd, CtaTally &s, int item, bool a,
+                                                bool b, unsigned long long ItemCounters::*fa,
                                                 unsigned long long ItemCounters::*fb) {
     const unsigned peers = __match_any_sync(0xffffffffu, item);
     const unsigned ba = __ballot_sync(0xffffffffu, a) & peers;
     const unsigned bb = __ballot_sync(0xffffffffu, b) & peers;
     const int lane = threadIdx.x & 31;
     if (item >= 0 && lane == __ffs(peers) - 1) {
-        if (ba) atomicAdd(&(bd.icnt[item].*fa), (unsigned long long)__popc(ba));
-        if (fb && bb) atomicAdd(&(bd.icnt[item].*fb), (unsigned long long)__popc(bb));
+        const int w = item - s.first_item;
+        if (w >= 0 && w < TALLY_ITEMS) {
+            if (ba) atomicAdd(&s.item[w][0], (uint32_t)__popc(ba));
+            if (fb && bb) atomicAdd(&s.item[w][1], (uint32_t)__popc(bb));
+        } else {
+            if (ba) atomicAdd(&(bd.icnt[item].*fa), (unsigned long long)__popc(ba));
+            if (fb && bb) atomicAdd(&(bd.icnt[item].*fb), (unsigned long long)__popc(bb));
+        }
     }
+}
+
+// The CTA's per-scan window to the global per-scan counters (after
+// tally_flush's barrier).
+__device__ __forceinline__ void flush_item_counts(const BatchDev &bd, CtaTally &s,
+                                                  unsigned long long ItemCounters::*fa,
+                                                  unsigned long long ItemCounters::*fb) {
+    const int w = threadIdx.x;
+    if (w < TALLY_ITEMS && s.first_item >= 0 && s.first_item + w < bd.n_items) {
+        ItemCounters &c = bd.icnt[s.first_item + w];
+        if (s.item[w][0]) atomicAdd(&(c.*fa), (unsigned long long)s.item[w][0]);
+        if (fb && s.item[w][1]) atomicAdd(&(c.*fb), (unsigned long long)s.item[w][1]);
+    }
+}
+
+// First scan of the CTA's returns (-1 when it has none).
+__device__ __forceinline__ int cta_first_item(const BatchDev &bd, long long n) {
+    const long long i0 = (long long)blockIdx.x * blockDim.x;
+    return i0 < n ? item_of(bd, i0) : -1;
 }
 
 __global__ void __launch_bounds__(256) k_voxelize_b(BatchDev bd, DevParams p, DevTables t,
                                                     long long n, WsDev ws, uint32_t hcap) {
+    __shared__ CtaTally s_tally;
+    pdl_wait();
+    pdl_launch_dependents();
+    tally_init(s_tally, threadIdx.x == 0 ? cta_first_item(bd, n) : 0);
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false, inside = false;
     int item = -1;
@@ -571,17 +648,18 @@ __global__ void __launch_bounds__(256) k_voxelize_b(BatchDev bd, DevParams p, De
         }
         ws.prec[i] = rec;
     }
-    const unsigned bv = __ballot_sync(0xffffffffu, valid);
-    const unsigned bi = __ballot_sync(0xffffffffu, inside);
-    if ((threadIdx.x & 31) == 0) {
-        if (bv) atomicAdd(&ws.hdr->acc_valid, (unsigned long long)__popc(bv));
-        if (bi) atomicAdd(&ws.hdr->acc_inside, (unsigned long long)__popc(bi));
-    }
-    add_item_counts(bd, item, valid, inside, &ItemCounters::valid, &ItemCounters::inside);
+    tally_warp(s_tally, valid, inside);
+    add_item_counts(bd, s_tally, item, valid, inside, &ItemCounters::valid, &ItemCounters::inside);
+    tally_flush(s_tally, &ws.hdr->acc_valid, &ws.hdr->acc_inside);
+    flush_item_counts(bd, s_tally, &ItemCounters::valid, &ItemCounters::inside);
 }
 
 __global__ void __launch_bounds__(256) k_count_b(BatchDev bd, DevParams p, long long n, WsDev ws,
                                                  uint32_t hcap) {
+    __shared__ CtaTally s_tally;
+    pdl_wait();
+    pdl_launch_dependents();
+    tally_init(s_tally, threadIdx.x == 0 ? cta_first_item(bd, n) : 0);
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool kept = false;
     int item = -1;
@@ -608,9 +686,10 @@ __global__ void __launch_bounds__(256) k_count_b(BatchDev bd, DevParams p, long 
         }
     }
     count_pairs<true>(ws, gk, b0k, kept, sk);
-    const unsigned bk = __ballot_sync(0xffffffffu, kept);
-    if ((threadIdx.x & 31) == 0 && bk) atomicAdd(&ws.hdr->acc_kept, (unsigned long long)__popc(bk));
-    add_item_counts(bd, item, kept, false, &ItemCounters::kept, nullptr);
+    tally_warp(s_tally, kept, false);
+    add_item_counts(bd, s_tally, item, kept, false, &ItemCounters::kept, nullptr);
+    tally_flush(s_tally, &ws.hdr->acc_kept, nullptr);
+    flush_item_counts(bd, s_tally, &ItemCounters::kept, nullptr);
 }
 
 // Batches: many scans put many pairs on the same bricks, so the cursor bumps
@@ -619,6 +698,8 @@ __global__ void __launch_bounds__(256) k_count_b(BatchDev bd, DevParams p, long 
 // spans walked in lock-step, one thread per return.
 __global__ void __launch_bounds__(256) k_fill_b(BatchDev bd, DevParams p, long long n, WsDev ws,
                                                 uint32_t hcap) {
+    pdl_wait();
+    pdl_launch_dependents();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int4 r = make_int4(-1, 0, 0, 0);
     if (i < n) r = ws.prec[i];
@@ -781,10 +862,11 @@ void launch_voxelize(const DevGrid &g, const DevParams &p, const DevTables &t, c
                      const float *xyz, int n, const WsDev &ws, uint32_t hcap, cudaStream_t s,
                      const ScanEx *ex) {
     if (ex)
-        k_voxelize<true><<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, t, pose, xyz, n, ws, hcap, *ex);
+        launch_pdl(k_voxelize<true>, max(1, blocks_for(n, 256)), 256, 0, s, g, p, t, pose, xyz, n, ws,
+                   hcap, *ex);
     else
-        k_voxelize<false><<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, t, pose, xyz, n, ws, hcap,
-                                                                    ScanEx{1, 0, 1});
+        launch_pdl(k_voxelize<false>, max(1, blocks_for(n, 256)), 256, 0, s, g, p, t, pose, xyz, n, ws,
+                   hcap, ScanEx{1, 0, 1});
 }
 
 void launch_contacts(const DevGrid &g, const DevParams &p, const DevTables &t, const Pose &pose,
@@ -794,7 +876,7 @@ void launch_contacts(const DevGrid &g, const DevParams &p, const DevTables &t, c
 
 void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                   cudaStream_t s) {
-    k_count<<<max(1, blocks_for(n, 256)), 256, 0, s>>>(g, p, n, ws, hcap);
+    launch_pdl(k_count, max(1, blocks_for(n, 256)), 256, 0, s, g, p, n, ws, hcap);
 }
 
 // One thread per brick where the GPU holds them all at once (a single wave
@@ -803,31 +885,32 @@ void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, 
 void launch_alloc(const WsDev &ws, cudaStream_t s) {
     const long long need = ((long long)ws.nbricks + ALLOC_THREADS - 1) / ALLOC_THREADS;
     const int ctas = (int)std::max(1LL, std::min(need, 152LL * 4));
-    k_alloc<<<ctas, ALLOC_THREADS, 0, s>>>(ws);
+    launch_pdl(k_alloc, ctas, ALLOC_THREADS, 0, s, ws);
 }
 
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                  cudaStream_t s) {
     const int slots = max_pairs_per_return(p.K);
     const long long threads = std::max((((long long)n + 31) & ~31ll) * slots, (long long)hcap);
-    k_fill<<<(unsigned)std::max(1LL, (threads + 255) / 256), 256, 0, s>>>(g, p, n, slots, ws, hcap);
+    launch_pdl(k_fill, (unsigned)std::max(1LL, (threads + 255) / 256), 256, 0, s, g, p, n, slots, ws,
+               hcap);
 }
 
 static inline unsigned batch_blocks(long long n) { return (unsigned)max(1ll, (n + 255) / 256); }
 
 void launch_voxelize_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
                            long long n, const WsDev &ws, uint32_t hcap, cudaStream_t s) {
-    k_voxelize_b<<<batch_blocks(n), 256, 0, s>>>(bd, p, t, n, ws, hcap);
+    launch_pdl(k_voxelize_b, batch_blocks(n), 256, 0, s, bd, p, t, n, ws, hcap);
 }
 
 void launch_count_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
                         uint32_t hcap, cudaStream_t s) {
-    k_count_b<<<batch_blocks(n), 256, 0, s>>>(bd, p, n, ws, hcap);
+    launch_pdl(k_count_b, batch_blocks(n), 256, 0, s, bd, p, n, ws, hcap);
 }
 
 void launch_fill_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
                        uint32_t hcap, cudaStream_t s) {
-    k_fill_b<<<batch_blocks(n), 256, 0, s>>>(bd, p, n, ws, hcap);
+    launch_pdl(k_fill_b, batch_blocks(n), 256, 0, s, bd, p, n, ws, hcap);
 }
 
 void launch_bin_dirs(const DevParams &p, const DevTables &t, const double *dirs, int n, int *bins,
