@@ -383,12 +383,12 @@ extern "C" dbt_status dbt_grid_init(const dbt_grid *g, void *stream) {
 constexpr size_t kUnset = ~size_t(0);
 struct WsLayout {
     size_t hdr = kUnset, stage = kUnset, prec = kUnset, hkey = kUnset, hidx = kUnset,
-           bcnt = kUnset, boff = kUnset, order = kUnset, order_med = kUnset,
+           bcnt = kUnset, boff = kUnset, order = kUnset, lq0 = kUnset, lq1 = kUnset,
            pairs = kUnset, poses = kUnset, total = kUnset;
     uint32_t hcap_alloc = 0, max_touched = 0, nbricks = 0;
     unsigned long long pairs_cap = 0;
     bool complete() const {
-        for (size_t v : {hdr, stage, prec, hkey, hidx, bcnt, boff, order, order_med, pairs,
+        for (size_t v : {hdr, stage, prec, hkey, hidx, bcnt, boff, order, lq0, lq1, pairs,
                          poses, total})
             if (v == kUnset || (v != total && v >= total)) return false;
         return true;
@@ -419,7 +419,8 @@ static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long m
     L->bcnt = o;     o += up256((size_t)nb * 4);
     L->boff = o;     o += up256((size_t)nb * 4);
     L->order = o;    o += up256((size_t)L->max_touched * 4);
-    L->order_med = o; o += up256((size_t)L->max_touched * 4);
+    L->lq0 = o;      o += up256((size_t)L->max_touched * 4);
+    L->lq1 = o;      o += up256((size_t)L->max_touched * 4);
     L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
     L->poses = o;    o += up256((size_t)MAX_SCAN_POSES * sizeof(Pose));
     L->total = o;
@@ -478,7 +479,8 @@ static dbt_status ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels
     w->d.bcnt = (uint32_t *)(base + L.bcnt);
     w->d.boff = (uint32_t *)(base + L.boff);
     w->d.order = (uint32_t *)(base + L.order);
-    w->d.order_med = (uint32_t *)(base + L.order_med);
+    w->d.lq[0] = (uint32_t *)(base + L.lq0);
+    w->d.lq[1] = (uint32_t *)(base + L.lq1);
     w->d.max_touched = L.max_touched;
     w->d.pairs = (uint32_t *)(base + L.pairs);
     w->d.pairs_cap = L.pairs_cap;
@@ -899,7 +901,8 @@ static dbt_status batch_layout(const dbt_grid *grids, int n_grids, const dbt_ker
     L->bcnt = o;     o += up256((size_t)nb * 4);
     L->boff = o;     o += up256((size_t)nb * 4);
     L->order = o;    o += up256((size_t)L->max_touched * 4);
-    L->order_med = o; o += up256((size_t)L->max_touched * 4);
+    L->lq0 = o;      o += up256((size_t)L->max_touched * 4);
+    L->lq1 = o;      o += up256((size_t)L->max_touched * 4);
     L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
     L->poses = o;    o += up256((size_t)MAX_SCAN_POSES * sizeof(Pose));
     L->total = o;

@@ -134,19 +134,29 @@ struct ScanStats {
 };
 static_assert(sizeof(ScanStats) == sizeof(dbt_scan_stats), "stats layout");
 
+// Light bricks are queued in size classes, the largest claimed first (a
+// large brick taken last would leave most warps idle while it finishes):
+// class c < LIGHT_CLASSES - 1 holds the bricks with more than heavy / 2^(c+1)
+// pairs, the last class the rest.
+constexpr int LIGHT_CLASSES = 5;
+__host__ __device__ inline int light_class(uint32_t len, uint32_t heavy) {
+    int c = 0;
+    for (uint32_t t = heavy >> 1; c < LIGHT_CLASSES - 1 && len <= t; t >>= 1) ++c;
+    return c;
+}
+
 struct WsHeader {
     uint32_t err;               // latched error bits of the current scan
     uint32_t n_touched;         // bricks touched by the current scan
     uint32_t pool;              // (return, brick) pairs allocated
     uint32_t next_work;         // dynamic queue of light bricks (one warp each)
     uint32_t done_ctas;         // integrate warps finished
-    uint32_t n_heavy;           // bricks with more than HEAVY_PAIRS pairs (one CTA each)
-    uint32_t n_light;
+    uint32_t n_heavy;           // bricks with more than `heavy` pairs (one CTA each)
     uint32_t next_heavy;        // dynamic queue of heavy bricks
-    unsigned long long acc_valid, acc_inside, acc_kept;
-    uint32_t n_med;             // light bricks with more than heavy / 2 pairs (queued first)
     uint32_t pad0;
-    unsigned long long pad1[4];
+    unsigned long long acc_valid, acc_inside, acc_kept;
+    uint32_t n_cls[LIGHT_CLASSES];   // light bricks per size class
+    uint32_t pad1[8 - LIGHT_CLASSES];
     ScanStats last;             // published by the last integrate CTA
 };
 
@@ -160,8 +170,11 @@ struct WsDev {
     uint32_t hcap_alloc;        // allocated slots (power of two)
     uint32_t *bcnt;             // per brick: pair count / fill cursor (kept 0 between scans)
     uint32_t *boff;             // per brick: first pair of its segment
-    uint32_t *order;            // touched bricks: heavy ones first, small light ones last
-    uint32_t *order_med;        // the larger light bricks, claimed before the small ones
+    // Brick queues, max_touched entries each, filled from both ends: heavy
+    // bricks at the front of order, light class c at the front (even c) or
+    // back (odd c) of lq[c / 2], the last class at the back of order.
+    uint32_t *order;
+    uint32_t *lq[2];
     uint32_t max_touched;
     uint32_t *pairs;            // pair payloads grouped by brick
     unsigned long long pairs_cap;
@@ -169,6 +182,13 @@ struct WsDev {
     uint32_t heavy;             // bricks with more pairs than this go to a whole CTA
     uint32_t nbricks;           // bricks of the grid(s): the range of bcnt / boff
 };
+
+__device__ __forceinline__ uint32_t *light_queue_slot(const WsDev &ws, int c, uint32_t q) {
+    uint32_t *a = c < 2 ? ws.lq[0] : c < 4 ? ws.lq[1] : ws.order;
+    const bool back = (c & 1) || c == LIGHT_CLASSES - 1;
+    return a + (back ? ws.max_touched - 1 - q : q);
+}
+static_assert(LIGHT_CLASSES == 5, "light_queue_slot places five classes");
 
 // Update pre-steps of dbt_integrate_scan_ex: sequential downsampling (every
 // ds-th return) and motion compensation (return i uses ws.poses[m(i)],

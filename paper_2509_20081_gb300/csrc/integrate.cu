@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
     pdl_launch_dependents();
     const uint32_t nt = min(*(volatile uint32_t *)&ws.hdr->n_touched, ws.max_touched);
     const uint32_t nheavy = min(*(volatile uint32_t *)&ws.hdr->n_heavy, nt);
-    const uint32_t nmed = min(*(volatile uint32_t *)&ws.hdr->n_med, nt - nheavy);
+
     const int SR = p.sr;
     const uint32_t T = (uint32_t)p.T, Hmax = (uint32_t)p.Hmax;
     uint32_t form_bad = 0;
@@ -572,8 +572,19 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
         if (lane == 0) w = atomicAdd(&ws.hdr->next_work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (nheavy + w >= nt) break;
-        // the larger light bricks first; the small ones sit at the back of order
-        const uint32_t b = w < nmed ? ws.order_med[w] : ws.order[ws.max_touched - 1 - (w - nmed)];
+        // the larger size classes first (the class sizes are fixed during
+        // the launch: plain loads, served from L1 after the first)
+        int c = 0;
+        uint32_t q = w;
+#pragma unroll
+        for (int k = 0; k < LIGHT_CLASSES - 1; ++k) {
+            const uint32_t nk = ws.hdr->n_cls[k];
+            if (c == k && q >= nk) {
+                q -= nk;
+                c = k + 1;
+            }
+        }
+        const uint32_t b = *light_queue_slot(ws, c, q);
         const uint32_t start = ws.boff[b];
         uint32_t len = ws.bcnt[b];
         if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing
@@ -695,8 +706,7 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
             h->pool = 0u;
             h->next_work = 0u;
             h->n_heavy = 0u;
-            h->n_med = 0u;
-            h->n_light = 0u;
+            for (int c = 0; c < LIGHT_CLASSES; ++c) h->n_cls[c] = 0u;
             h->next_heavy = 0u;
             h->acc_valid = 0ull;
             h->acc_inside = 0ull;

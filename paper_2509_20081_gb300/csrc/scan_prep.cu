@@ -424,17 +424,17 @@ __global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, Ws
 // count) get one contiguous segment of the pair array (warp-aggregated bump
 // of the pool counter), are counted in n_touched, have their counter reset to
 // serve as fill cursor, and are queued for the integrate kernel: heavy
-// bricks (more than ws.heavy pairs) at the front of `order`, the larger
-// light bricks (more than half that) in `order_med` (taken first by the
-// warps: longest work first shortens the kernel's tail), the other light
-// ones from the back of `order` (index max_touched - 1 down).
+// bricks (more than ws.heavy pairs) for whole CTAs, light ones in their size
+// class (light_class), each class claimed by the warps before the next
+// smaller one.
 // The queue counters are shared by the whole grid, so their bumps are
 // aggregated per CTA of 1024 bricks: warp totals are scanned in shared
 // memory and one thread takes each counter's range with a single atomic.
 constexpr int ALLOC_THREADS = 1024;
+constexpr int ALLOC_CTRS = 2 + LIGHT_CLASSES;          // pairs, heavy, light classes
 
 __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
-    __shared__ uint32_t s_w[ALLOC_THREADS / 32][4];   // per warp: pairs, heavy, med, light
+    __shared__ uint32_t s_w[ALLOC_THREADS / 32][ALLOC_CTRS];
     pdl_wait();
     pdl_launch_dependents();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -451,52 +451,46 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
         }
         const bool touched = len != 0u;
         const bool heavy = touched && len > ws.heavy;
-        const bool med = touched && !heavy && len > ws.heavy / 2;
-        const bool light = touched && !heavy && !med;
-        const unsigned hb = __ballot_sync(0xffffffffu, heavy);
-        const unsigned mb = __ballot_sync(0xffffffffu, med);
-        const unsigned lb = __ballot_sync(0xffffffffu, light);
+        // counter index: 1 heavy, 2 + c light class c, -1 untouched
+        const int cls = !touched ? -1 : heavy ? 1 : 2 + light_class(len, ws.heavy);
+        unsigned bal[ALLOC_CTRS];
+#pragma unroll
+        for (int k = 1; k < ALLOC_CTRS; ++k) bal[k] = __ballot_sync(0xffffffffu, cls == k);
         if (lane == 31) s_w[warp][0] = incl;
         if (lane == 0) {
-            s_w[warp][1] = __popc(hb);
-            s_w[warp][2] = __popc(mb);
-            s_w[warp][3] = __popc(lb);
+#pragma unroll
+            for (int k = 1; k < ALLOC_CTRS; ++k) s_w[warp][k] = __popc(bal[k]);
         }
         __syncthreads();
         if (warp == 0) {                                   // lane j: warp j's entries
-            uint32_t v[4], x[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                v[k] = s_w[lane][k];
-                x[k] = v[k];
+            for (int k = 0; k < ALLOC_CTRS; ++k) {
+                const uint32_t v = s_w[lane][k];
+                uint32_t x = v;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, x[k], o);
-                    if (lane >= o) x[k] += y;
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
                 }
+                uint32_t g = 0u;
+                if (lane == 31 && x) {
+                    unsigned int *ctr = k == 0 ? &ws.hdr->pool : k == 1 ? &ws.hdr->n_heavy
+                                                                        : &ws.hdr->n_cls[k - 2];
+                    g = atomicAdd(ctr, x);
+                    if (k >= 1) atomicAdd(&ws.hdr->n_touched, x);
+                }
+                s_w[lane][k] = __shfl_sync(0xffffffffu, g, 31) + x - v;
             }
-            uint32_t g[4] = {0u, 0u, 0u, 0u};
-            if (lane == 31) {
-                if (x[0]) g[0] = atomicAdd(&ws.hdr->pool, x[0]);
-                if (x[1]) g[1] = atomicAdd(&ws.hdr->n_heavy, x[1]);
-                if (x[2]) g[2] = atomicAdd(&ws.hdr->n_med, x[2]);
-                if (x[3]) g[3] = atomicAdd(&ws.hdr->n_light, x[3]);
-                atomicAdd(&ws.hdr->n_touched, x[1] + x[2] + x[3]);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s_w[lane][k] = __shfl_sync(0xffffffffu, g[k], 31) + x[k] - v[k];
         }
         __syncthreads();
         const unsigned below = (1u << lane) - 1u;
         if (touched) {
             ws.boff[b] = s_w[warp][0] + incl - len;
             ws.bcnt[b] = 0;
-            const int cls = heavy ? 1 : med ? 2 : 3;
-            const uint32_t q = s_w[warp][cls] + __popc((heavy ? hb : med ? mb : lb) & below);
+            const uint32_t q = s_w[warp][cls] + __popc(bal[cls] & below);
             if (q >= ws.max_touched) atomicOr(&ws.hdr->err, ERR_TOUCHED_OVERFLOW);   // cannot happen by sizing
             else if (heavy) ws.order[q] = b;
-            else if (med) ws.order_med[q] = b;
-            else ws.order[ws.max_touched - 1 - q] = b;
+            else *light_queue_slot(ws, cls - 2, q) = b;
         }
         __syncthreads();                                   // s_w is reused next round
     }
@@ -794,8 +788,7 @@ __global__ void k_ws_rearm_header(WsDev ws) {
     h->next_work = 0u;
     h->done_ctas = 0u;
     h->n_heavy = 0u;
-    h->n_med = 0u;
-    h->n_light = 0u;
+    for (int c = 0; c < LIGHT_CLASSES; ++c) h->n_cls[c] = 0u;
     h->next_heavy = 0u;
     h->acc_valid = 0ull;
     h->acc_inside = 0ull;
