@@ -330,8 +330,8 @@ dbt_status dbt_workspace_get_tuning(const dbt_workspace *ws, dbt_tuning *t);
 dbt_status dbt_batch_set_tuning(dbt_batch *b, const dbt_tuning *t);
 dbt_status dbt_batch_get_tuning(const dbt_batch *b, dbt_tuning *t);
 
-/* Times every candidate tuning (heavy_pairs 16..256 x one, two or the
- * maximum CTAs per SM) over n_trials runs of the batch's current items (one
+/* Times every candidate tuning (heavy_pairs 16..256 x one, two, three or
+ * the maximum CTAs per SM) over n_trials runs of the batch's current items (one
  * warm-up run each) with CUDA events on stream, keeps the fastest in *best
  * and sets it on the batch.  The items are integrated (1 + n_trials) times
  * per candidate, so the batch's grids end in an unspecified state: run it

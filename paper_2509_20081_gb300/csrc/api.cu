@@ -1110,10 +1110,10 @@ extern "C" dbt_status dbt_batch_get_tuning(const dbt_batch *b, dbt_tuning *t) {
 static std::vector<dbt_tuning> tuning_candidates(const dbt_kernels *k) {
     const int sms = device_sm_count(), full = integrate_grid_ctas(k->dp);
     std::vector<int> grids = {full};
-    for (int c : {2 * sms, sms})
+    for (int c : {3 * sms, 2 * sms, sms})
         if (c < full) grids.push_back(c);
     std::vector<dbt_tuning> out;
-    for (int h : {16, 24, 32, 48, 64, 96, 128, 192, 256})
+    for (int h : {16, 24, 32, 40, 48, 64, 96, 128, 192, 256})
         for (int c : grids) out.push_back(dbt_tuning{h, c});
     return out;
 }
