@@ -128,7 +128,9 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
     const PairBox b = decode_pair(pl, R);
     const int wy = b.y1 - b.y0 + 1;
     const int nrows = wy * (b.z1 - b.z0 + 1);
-    const int magic = (256 + wy - 1) / wy;
+    // ceil(256 / wy) for wy = 1..8, less one, as bytes 0..7 of one word
+    // (255 127 85 63 51 42 36 31): no integer division
+    const int magic = (int)((0x1F242A333F557FFFull >> (8 * (wy - 1))) & 0xFFull) + 1;
     const int w0 = b.x0 >> 2;
     const int nw = (b.x1 >> 2) - w0;
     const int s0 = 4 * w0 - b.cx + R + 3;
