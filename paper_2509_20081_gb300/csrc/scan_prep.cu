@@ -463,24 +463,33 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
         }
         __syncthreads();
         if (warp == 0) {                                   // lane j: warp j's entries
+            uint32_t v[ALLOC_CTRS], x[ALLOC_CTRS], g[ALLOC_CTRS];
 #pragma unroll
             for (int k = 0; k < ALLOC_CTRS; ++k) {
-                const uint32_t v = s_w[lane][k];
-                uint32_t x = v;
+                v[k] = s_w[lane][k];
+                x[k] = v[k];
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x[k], o);
+                    if (lane >= o) x[k] += y;
                 }
-                uint32_t g = 0u;
-                if (lane == 31 && x) {
+            }
+            // all counters' atomics in flight at once
+            uint32_t touched_sum = 0u;
+#pragma unroll
+            for (int k = 0; k < ALLOC_CTRS; ++k) {
+                g[k] = 0u;
+                if (lane == 31 && x[k]) {
                     unsigned int *ctr = k == 0 ? &ws.hdr->pool : k == 1 ? &ws.hdr->n_heavy
                                                                         : &ws.hdr->n_cls[k - 2];
-                    g = atomicAdd(ctr, x);
-                    if (k >= 1) atomicAdd(&ws.hdr->n_touched, x);
+                    g[k] = atomicAdd(ctr, x[k]);
                 }
-                s_w[lane][k] = __shfl_sync(0xffffffffu, g, 31) + x - v;
+                if (k >= 1) touched_sum += x[k];
             }
+            if (lane == 31 && touched_sum) atomicAdd(&ws.hdr->n_touched, touched_sum);
+#pragma unroll
+            for (int k = 0; k < ALLOC_CTRS; ++k)
+                s_w[lane][k] = __shfl_sync(0xffffffffu, g[k], 31) + x[k] - v[k];
         }
         __syncthreads();
         const unsigned below = (1u << lane) - 1u;
@@ -507,19 +516,18 @@ __device__ __forceinline__ uint32_t pair_payload(int4 r, int bx, int by, int bz,
 }
 
 // Pair payloads into the segments, slots from the per-brick cursors.  One
-// thread per (brick j of a span, return): t -> j = t / n32, return t mod
-// n32 (n32 = n rounded up to whole warps), so a warp holds the j-th bricks
-// of 32 consecutive returns, which mostly name the same brick: lanes naming
-// one brick take their slots with one atomic of their leader.
+// thread per (brick j of a span, return): grid row j = blockIdx.y, returns
+// along x, so a warp holds the j-th bricks of 32 consecutive returns, which
+// mostly name the same brick: lanes naming one brick take their slots with
+// one atomic of their leader.
+static_assert(MAX_K - 1 <= BX && MAX_K - 1 <= 3 * BY, "k_fill's span decomposition: sx <= 2, sy <= 4");
 __global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, int slots, WsDev ws,
                                               uint32_t hcap) {
     pdl_wait();
     pdl_launch_dependents();
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n32 = ((long long)n + 31) & ~31ll;
-    const long long j = t / n32;
-    const long long i = t - j * n32;
-    if (j < slots) {                                          // warp-uniform
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = (int)blockIdx.y;
+    {
         bool v = false;
         uint32_t b = 0xFFFFFFFFu, pl = 0;
         if (i < n) {
@@ -528,7 +536,13 @@ __global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, int
                 const BrickSpan sp = brick_span(r.x, r.y, r.z, p.R);
                 const int sx = sp.x1 - sp.x0 + 1, sy = sp.y1 - sp.y0 + 1, sz = sp.z1 - sp.z0 + 1;
                 if (j < sx * sy * sz) {
-                    const int jj = (int)j, ix = jj % sx, jy = jj / sx, iy = jy % sy, iz = jy / sy;
+                    // j -> (ix, iy, iz), x fastest; sx <= 2 and sy <= 4 for K <= 21
+                    const int ix = sx == 1 ? 0 : (j & 1);
+                    int iy = sx == 1 ? j : (j >> 1), iz = 0;
+                    while (iy >= sy) {
+                        iy -= sy;
+                        ++iz;
+                    }
                     const int bx = sp.x0 + ix, by = sp.y0 + iy, bz = sp.z0 + iz;
                     b = ((uint32_t)bz * g.nby + by) * g.nbx + bx;
                     pl = pair_payload(r, bx, by, bz, p.R);
@@ -549,8 +563,9 @@ __global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, int
         }
     }
     if (p.dedup) {
-        const uint32_t stride = gridDim.x * blockDim.x;
-        for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < hcap; k += stride) {
+        const uint32_t stride = gridDim.x * gridDim.y * blockDim.x;
+        for (uint32_t k = (blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x; k < hcap;
+             k += stride) {
             ws.hkey[k] = 0ull;
             ws.hidx[k] = 0u;
         }
@@ -884,9 +899,8 @@ void launch_alloc(const WsDev &ws, cudaStream_t s) {
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                  cudaStream_t s) {
     const int slots = max_pairs_per_return(p.K);
-    const long long threads = std::max((((long long)n + 31) & ~31ll) * slots, (long long)hcap);
-    launch_pdl(k_fill, (unsigned)std::max(1LL, (threads + 255) / 256), 256, 0, s, g, p, n, slots, ws,
-               hcap);
+    launch_pdl(k_fill, dim3((unsigned)std::max(1, (n + 255) / 256), (unsigned)slots), 256, 0, s, g, p, n,
+               slots, ws, hcap);
 }
 
 static inline unsigned batch_blocks(long long n) { return (unsigned)max(1ll, (n + 255) / 256); }

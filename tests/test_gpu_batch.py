@@ -193,7 +193,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(orc):
     b = dbt.Batch([scratch], k, sum(len(p) for p, _ in w.scans), len(items))
     b.set_items(items)
     best = b.autotune(n_trials=2)
-    assert best["heavy_pairs"] in (16, 24, 32, 48, 64, 96, 128, 192, 256)
+    assert best["heavy_pairs"] in (16, 24, 32, 40, 48, 64, 96, 128, 192, 256)
     assert best == b.tuning()
     b.close()
     g = dbt.Grid(*dims, w.grid.res)
