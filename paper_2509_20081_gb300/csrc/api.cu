@@ -383,12 +383,12 @@ extern "C" dbt_status dbt_grid_init(const dbt_grid *g, void *stream) {
 constexpr size_t kUnset = ~size_t(0);
 struct WsLayout {
     size_t hdr = kUnset, stage = kUnset, prec = kUnset, hkey = kUnset, hidx = kUnset,
-           bcnt = kUnset, boff = kUnset, order = kUnset, lq0 = kUnset, lq1 = kUnset,
+           bcnt = kUnset, boff = kUnset, order = kUnset, lq0 = kUnset, lq1 = kUnset, lq2 = kUnset,
            pairs = kUnset, poses = kUnset, total = kUnset;
     uint32_t hcap_alloc = 0, max_touched = 0, nbricks = 0;
     unsigned long long pairs_cap = 0;
     bool complete() const {
-        for (size_t v : {hdr, stage, prec, hkey, hidx, bcnt, boff, order, lq0, lq1, pairs,
+        for (size_t v : {hdr, stage, prec, hkey, hidx, bcnt, boff, order, lq0, lq1, lq2, pairs,
                          poses, total})
             if (v == kUnset || (v != total && v >= total)) return false;
         return true;
@@ -421,6 +421,7 @@ static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long m
     L->order = o;    o += up256((size_t)L->max_touched * 4);
     L->lq0 = o;      o += up256((size_t)L->max_touched * 4);
     L->lq1 = o;      o += up256((size_t)L->max_touched * 4);
+    L->lq2 = o;      o += up256((size_t)L->max_touched * 4);
     L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
     L->poses = o;    o += up256((size_t)MAX_SCAN_POSES * sizeof(Pose));
     L->total = o;
@@ -481,6 +482,7 @@ static dbt_status ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels
     w->d.order = (uint32_t *)(base + L.order);
     w->d.lq[0] = (uint32_t *)(base + L.lq0);
     w->d.lq[1] = (uint32_t *)(base + L.lq1);
+    w->d.lq[2] = (uint32_t *)(base + L.lq2);
     w->d.max_touched = L.max_touched;
     w->d.pairs = (uint32_t *)(base + L.pairs);
     w->d.pairs_cap = L.pairs_cap;
@@ -903,6 +905,7 @@ static dbt_status batch_layout(const dbt_grid *grids, int n_grids, const dbt_ker
     L->order = o;    o += up256((size_t)L->max_touched * 4);
     L->lq0 = o;      o += up256((size_t)L->max_touched * 4);
     L->lq1 = o;      o += up256((size_t)L->max_touched * 4);
+    L->lq2 = o;      o += up256((size_t)L->max_touched * 4);
     L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
     L->poses = o;    o += up256((size_t)MAX_SCAN_POSES * sizeof(Pose));
     L->total = o;

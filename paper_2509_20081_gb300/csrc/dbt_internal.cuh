@@ -153,7 +153,7 @@ struct WsHeader {
     uint32_t done_ctas;         // integrate warps finished
     uint32_t n_heavy;           // bricks with more than `heavy` pairs (one CTA each)
     uint32_t next_heavy;        // dynamic queue of heavy bricks
-    uint32_t pad0;
+    uint32_t n_vheavy;          // of those, bricks with more than 4 x `heavy` (taken first)
     unsigned long long acc_valid, acc_inside, acc_kept;
     uint32_t n_cls[LIGHT_CLASSES];   // light bricks per size class
     uint32_t pad1[8 - LIGHT_CLASSES];
@@ -171,10 +171,11 @@ struct WsDev {
     uint32_t *bcnt;             // per brick: pair count / fill cursor (kept 0 between scans)
     uint32_t *boff;             // per brick: first pair of its segment
     // Brick queues, max_touched entries each, filled from both ends: heavy
-    // bricks at the front of order, light class c at the front (even c) or
-    // back (odd c) of lq[c / 2], the last class at the back of order.
+    // bricks at the front of order and the very heavy ones (more than 4 x
+    // heavy pairs, taken first) at its back; light class c at the front
+    // (even c) or back (odd c) of lq[c / 2].
     uint32_t *order;
-    uint32_t *lq[2];
+    uint32_t *lq[3];
     uint32_t max_touched;
     uint32_t *pairs;            // pair payloads grouped by brick
     unsigned long long pairs_cap;
@@ -184,10 +185,10 @@ struct WsDev {
 };
 
 __device__ __forceinline__ uint32_t *light_queue_slot(const WsDev &ws, int c, uint32_t q) {
-    uint32_t *a = c < 2 ? ws.lq[0] : c < 4 ? ws.lq[1] : ws.order;
-    const bool back = (c & 1) || c == LIGHT_CLASSES - 1;
-    return a + (back ? ws.max_touched - 1 - q : q);
+    uint32_t *a = ws.lq[c >> 1];
+    return a + ((c & 1) ? ws.max_touched - 1 - q : q);
 }
+constexpr uint32_t VHEAVY_FACTOR = 4;
 static_assert(LIGHT_CLASSES == 5, "light_queue_slot places five classes");
 
 // Update pre-steps of dbt_integrate_scan_ex: sequential downsampling (every

@@ -55,6 +55,15 @@ __device__ __forceinline__ int kword(int row, int w) { return row * 8 + (w ^ ((r
 
 __device__ __forceinline__ uint32_t vmin4(uint32_t a, uint32_t b) { return __vminu4(a, b); }
 
+// Named barrier `id` (1 + group index) over the n threads of a heavy-brick
+// group of warps.
+__device__ __forceinline__ void group_sync(int id, int n) {
+    if (id == 1)   // immediate barrier ids: the kernel then holds three barriers, not all 16
+        asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+    else
+        asm volatile("bar.sync 2, %0;" ::"r"(n) : "memory");
+}
+
 // Bytes of b below the matching bytes of a, as bit 7 of each byte, for bytes
 // < 128 (codes are <= 32): b + 128 - a per byte lies in [1, 255], so the
 // subtraction never borrows across bytes and bit 7 is clear exactly when
@@ -283,19 +292,27 @@ __device__ __forceinline__ void store_chunk(const DevGrid &g, size_t gi, uint32_
 // finite sum is at most 3 R^2 = 108, and the no-contact value DENSE_INF = 127
 // plus a tap stays below 256, so bytes never carry into each other.
 constexpr uint32_t DENSE_INF = 127u;
-// The dense path's scratch (occupancy, two passes, plane masks, row list) at
-// the largest dilated extent it serves (R = 6) fits in the other warp areas.
-constexpr int DENSE_DMAX = BY + 2 * 6;
-static_assert(8 * DENSE_DMAX * DENSE_DMAX + 32 * DENSE_DMAX * DENSE_DMAX + 4 * 64 * DENSE_DMAX +
-                  4 * DENSE_DMAX + 4 + 2 * DENSE_DMAX * DENSE_DMAX <=
-              (WPC - 1) * (int)sizeof(WarpArea),
-              "dense scratch");
+// The dense path's scratch (occupancy, two passes, plane masks, row list)
+// lives in the warp areas of the heavy group after the first: at R = 6 all
+// eight warps form the group; up to R = 5 four do (three spare areas).
+__host__ __device__ constexpr int dense_scratch_bytes(int R) {
+    return 8 * (BY + 2 * R) * (BY + 2 * R) + 32 * (BY + 2 * R) * (BY + 2 * R) +
+           4 * 64 * (BY + 2 * R) + 4 * (BY + 2 * R) + 4 + 2 * (BY + 2 * R) * (BY + 2 * R);
+}
+constexpr int HALF_GROUP_MAX_R = 5;
+static_assert(dense_scratch_bytes(6) <= (WPC - 1) * (int)sizeof(WarpArea), "dense scratch, R = 6");
+static_assert(dense_scratch_bytes(HALF_GROUP_MAX_R) <= (WPC / 2 - 1) * (int)sizeof(WarpArea),
+              "dense scratch, half group");
 
+// Run by a heavy group of gt threads (gw = gt / 32 warps); tid is the
+// thread's index in the group, areas the group's first warp area, and the
+// group synchronises on named barrier bar.
 __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const uint32_t *pairs,
                                 uint32_t len, WarpArea *areas, const uint8_t *ctab,
                                 const uint32_t *sh, const uint32_t *shs, int R, int SR,
-                                uint32_t T, uint32_t Hmax, uint32_t &form_bad) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+                                uint32_t T, uint32_t Hmax, uint32_t &form_bad, int tid, int gt,
+                                int bar) {
+    const int lane = tid & 31, warp = tid >> 5, gw = gt >> 5;
     const int D = BY + 2 * R;                                   // dilated y / z extent
     unsigned char *scr = reinterpret_cast<unsigned char *>(areas + 1);
     unsigned long long *occ = reinterpret_cast<unsigned long long *>(scr);   // D * D rows
@@ -308,7 +325,7 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
     const uint32_t *need = a0->need;
     const uint32_t inf4 = DENSE_INF * 0x01010101u;
     // B: stage the covered chunks once; clear the occupancy
-    for (int c = tid; c < BCHUNKS; c += NTHR) {
+    for (int c = tid; c < BCHUNKS; c += gt) {
         const int row = c >> 3, ch = c & 7;
         if ((need[row] >> ch) & 1u) {
             const int wd = kword(row, ch);
@@ -316,19 +333,19 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
             *reinterpret_cast<uint2 *>(&a0->cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
         }
     }
-    for (int r = tid; r < D * D; r += NTHR) occ[r] = 0ull;
+    for (int r = tid; r < D * D; r += gt) occ[r] = 0ull;
     if (tid < D) pmask[tid] = 0u;
     if (tid == 0) *nlist = 0u;
-    __syncthreads();
+    group_sync(bar, gt);
     // contacts: payload coordinates are brick-relative + R, i.e. dilated indices
-    for (uint32_t j = tid; j < len; j += NTHR) {
+    for (uint32_t j = tid; j < len; j += gt) {
         const uint32_t pl = __ldg(pairs + j);
         atomicOr(&occ[((pl >> 11) & 31u) * D + ((pl >> 6) & 31u)], 1ull << (pl & 63u));
     }
-    __syncthreads();
+    group_sync(bar, gt);
     // rows without a contact are all INF after pass x: write them directly,
     // list the others, and note per plane which rows hold contacts
-    for (int r = tid; r < D * D; r += NTHR) {
+    for (int r = tid; r < D * D; r += gt) {
         if (occ[r]) {
             atomicOr(&pmask[r / D], 1u << (r % D));
             list[atomicAdd(nlist, 1u)] = (uint16_t)r;
@@ -338,12 +355,12 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
             row[1] = make_uint4(inf4, inf4, inf4, inf4);
         }
     }
-    __syncthreads();
+    group_sync(bar, gt);
     // pass x over the listed rows: squared distance to the nearest contact of
     // the row within +-R
     const uint32_t win = (1u << (2 * R + 1)) - 1u, lmask = (1u << (R + 1)) - 1u;
     const uint32_t nl = *nlist;
-    for (uint32_t i = warp; i < nl; i += WPC) {
+    for (uint32_t i = warp; i < nl; i += gw) {
         const int r = list[i];
         const unsigned long long o = occ[r];
         uint32_t v = DENSE_INF;
@@ -355,11 +372,11 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
         if (d <= R) v = (uint32_t)(d * d);
         reinterpret_cast<unsigned char *>(g1)[r * 32 + lane] = (unsigned char)v;
     }
-    __syncthreads();
+    group_sync(bar, gt);
     // pass y: taps only from rows with contacts (an INF row cannot lower the
     // minimum: INF + dy^2 >= INF and the result is clamped to INF)
     const uint32_t twin = (1u << (2 * R + 1)) - 1u;
-    for (int idx = tid; idx < D * 64; idx += NTHR) {
+    for (int idx = tid; idx < D * 64; idx += gt) {
         const int w = idx & 7, y = (idx >> 3) & 7, zp = idx >> 6;
         uint32_t acc = inf4;
         for (uint32_t m = (pmask[zp] >> y) & twin; m; m &= m - 1u) {
@@ -370,12 +387,12 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
     }
     uint32_t planes = 0;                   // planes with any contact
     for (int zp = 0; zp < D; ++zp) planes |= (pmask[zp] ? 1u : 0u) << zp;
-    __syncthreads();
+    group_sync(bar, gt);
     // pass z (taps only from planes with contacts), codes, and Eq. 4 on the
     // staged brick
     // (a warp covers four whole rows: idx = row * 8 + w; its ballot gives the
     // rows' changed-word bytes, each written once by the row's first lane)
-    for (int idx = tid; idx < BROWS * 8; idx += NTHR) {
+    for (int idx = tid; idx < BROWS * 8; idx += gt) {
         const int w = idx & 7, row = idx >> 3, y = row & 7, z = row >> 3;
         bool changed = false;
         if ((need[row] >> w) & 1u) {
@@ -400,11 +417,11 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
         if ((lane & 7) == 0) a0->drow[row] = (uint8_t)(bal >> (lane & 24));
     }
     // Eq. 5 counts: pairs spread over the warps, counted into one array
-    for (uint32_t j = warp; j < len; j += WPC)
+    for (uint32_t j = warp; j < len; j += gw)
         shadow_pair<true>(__ldg(pairs + j), a0->cnt, sh, shs, R, SR, lane);
-    __syncthreads();
+    group_sync(bar, gt);
     // D
-    for (int c = tid; c < BCHUNKS; c += NTHR) {
+    for (int c = tid; c < BCHUNKS; c += gt) {
         const int row = c >> 3, ch = c & 7;
         if ((need[row] >> ch) & 1u) {
             const int wd = kword(row, ch);
@@ -442,8 +459,8 @@ template <int NW, bool BATCH>
 __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, DevParams p,
                                                     DevTables t, long long n_input, WsDev ws) {
     extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ uint32_t s_item;
-    __shared__ unsigned long long s_cr[CHUNKS_PER_ROW];
+    __shared__ uint32_t s_item[2];                        // per heavy group
+    __shared__ unsigned long long s_cr[2][CHUNKS_PER_ROW];
     __shared__ uint8_t s_ctab[256];
     for (int j = threadIdx.x; j < 256; j += NTHR) {
         int kk = 0;
@@ -466,225 +483,247 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
     pdl_wait();
     pdl_launch_dependents();
     const uint32_t nt = min(*(volatile uint32_t *)&ws.hdr->n_touched, ws.max_touched);
-    const uint32_t nheavy = min(*(volatile uint32_t *)&ws.hdr->n_heavy, nt);
+    const uint32_t nvheavy = *(volatile uint32_t *)&ws.hdr->n_vheavy;
+    const uint32_t nheavy = min(*(volatile uint32_t *)&ws.hdr->n_heavy + nvheavy, nt);
 
     const int SR = p.sr;
     const uint32_t T = (uint32_t)p.T, Hmax = (uint32_t)p.Hmax;
     uint32_t form_bad = 0;
 
-    // ---------------- heavy bricks: one CTA each
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_item = atomicAdd(&ws.hdr->next_heavy, 1u);
-        if (tid < CHUNKS_PER_ROW) s_cr[tid] = 0ull;
-        __syncthreads();
-        const uint32_t it = s_item;
-        if (it >= nheavy) break;
-        const uint32_t b = ws.order[it];
-        const uint32_t start = ws.boff[b];
-        uint32_t len = ws.bcnt[b];
-        if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing
-        DevGrid g;
-        const uint32_t lb = brick_grid<BATCH>(g0, bd, b, g);
-        const int bx = (int)(lb % (uint32_t)g.nbx);
-        const uint32_t byz = lb / (uint32_t)g.nbx;
-        const int by = (int)(byz % (uint32_t)g.nby), bz = (int)(byz / (uint32_t)g.nby);
-        const uint32_t *pairs = ws.pairs + start;
+    // ---------------- work: heavy bricks by groups of hw warps, light ones by single warps
+    // At K <= 11 the dense path runs on groups of four warps (its scratch
+    // fits a group's three spare areas): group 0 (warps 0-3) takes heavy
+    // bricks first, group 1 (warps 4-7) light bricks first, so the largest
+    // light bricks start at the beginning of the launch instead of after the
+    // heavy ones; each group then turns to the other kind.  Otherwise the
+    // whole CTA is one group, heavy bricks first.
+    const int hw = (NW == 4 && R <= HALF_GROUP_MAX_R) ? WPC / 2 : WPC;
+    const int ht = hw * 32;
+    const int gidx = warp / hw;                  // group of this warp
+    const int gtid = tid - gidx * ht, gwarp = warp - gidx * hw;
+    const int gbar = 1 + gidx;                   // its named barrier
+    WarpArea *garea = areas + gidx * hw;         // its first warp area
+    __syncthreads();                             // tables above, for every warp
+    for (int phase = 0; phase < 2; ++phase) {
+        if ((phase == 0) == (gidx == 0)) {
+            // heavy bricks, one per group
+            for (;;) {
+                group_sync(gbar, ht);
+                if (gtid == 0) s_item[gidx] = atomicAdd(&ws.hdr->next_heavy, 1u);
+                if (gtid < CHUNKS_PER_ROW) s_cr[gidx][gtid] = 0ull;
+                group_sync(gbar, ht);
+                const uint32_t it = s_item[gidx];
+                if (it >= nheavy) break;
+                // the very heavy bricks (back of order) first
+                const uint32_t b = it < nvheavy ? ws.order[ws.max_touched - 1 - it] : ws.order[it - nvheavy];
+                const uint32_t start = ws.boff[b];
+                uint32_t len = ws.bcnt[b];
+                if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing
+                DevGrid g;
+                const uint32_t lb = brick_grid<BATCH>(g0, bd, b, g);
+                const int bx = (int)(lb % (uint32_t)g.nbx);
+                const uint32_t byz = lb / (uint32_t)g.nbx;
+                const int by = (int)(byz % (uint32_t)g.nby), bz = (int)(byz / (uint32_t)g.nby);
+                const uint32_t *pairs = ws.pairs + start;
 
-        // A
-        unsigned long long cr[CHUNKS_PER_ROW];
+                // A
+                unsigned long long cr[CHUNKS_PER_ROW];
 #pragma unroll
-        for (int c = 0; c < CHUNKS_PER_ROW; ++c) cr[c] = 0ull;
-        coverage(pairs, 32u * warp, len, 32u * WPC, R, lane, cr);
-        if (lane < CHUNKS_PER_ROW) {
-            unsigned long long mine = 0ull;
+                for (int c = 0; c < CHUNKS_PER_ROW; ++c) cr[c] = 0ull;
+                coverage(pairs, 32u * gwarp, len, 32u * hw, R, lane, cr);
+                if (lane < CHUNKS_PER_ROW) {
+                    unsigned long long mine = 0ull;
 #pragma unroll
-            for (int c = 0; c < CHUNKS_PER_ROW; ++c)
-                if (c == lane) mine = cr[c];
-            atomicOr(&s_cr[lane], mine);
-        }
-        __syncthreads();
-        uint32_t *need = areas[0].need;
-        if (tid < BROWS) {
-            uint32_t nb = 0;
-#pragma unroll
-            for (int c = 0; c < CHUNKS_PER_ROW; ++c) nb |= (uint32_t)((s_cr[c] >> tid) & 1ull) << c;
-            need[tid] = nb;
-        }
-        __syncthreads();
-        if constexpr (NW == 4) {
-            integrate_dense(g, bx, by, bz, pairs, len, areas, s_ctab, sh, shs, R, SR, T, Hmax,
-                            form_bad);
-            if (tid == 0) ws.bcnt[b] = 0u;
-            continue;
-        }
-        // B: stage into every warp's copy
-        for (int c = tid; c < BCHUNKS; c += NTHR) {
-            const int row = c >> 3, ch = c & 7;
-            if ((need[row] >> ch) & 1u) {
-                const uint32_t k = load_codes(g, chunk_index(g, bx, by, bz, row, ch), form_bad);
-                const int wd = kword(row, ch);
-#pragma unroll
-                for (int v = 0; v < WPC; ++v) {
-                    areas[v].kst[wd] = k;
-                    *reinterpret_cast<uint2 *>(&areas[v].cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
+                    for (int c = 0; c < CHUNKS_PER_ROW; ++c)
+                        if (c == lane) mine = cr[c];
+                    atomicOr(&s_cr[gidx][lane], mine);
                 }
+                group_sync(gbar, ht);
+                uint32_t *need = garea[0].need;
+                if (gtid < BROWS) {
+                    uint32_t nb = 0;
+#pragma unroll
+                    for (int c = 0; c < CHUNKS_PER_ROW; ++c)
+                        nb |= (uint32_t)((s_cr[gidx][c] >> gtid) & 1ull) << c;
+                    need[gtid] = nb;
+                }
+                group_sync(gbar, ht);
+                if constexpr (NW == 4) {
+                    integrate_dense(g, bx, by, bz, pairs, len, garea, s_ctab, sh, shs, R, SR, T, Hmax,
+                                    form_bad, gtid, ht, gbar);
+                    if (gtid == 0) ws.bcnt[b] = 0u;
+                    continue;
+                }
+                // B: stage into every warp's copy
+                for (int c = gtid; c < BCHUNKS; c += ht) {
+                    const int row = c >> 3, ch = c & 7;
+                    if ((need[row] >> ch) & 1u) {
+                        const uint32_t k = load_codes(g, chunk_index(g, bx, by, bz, row, ch), form_bad);
+                        const int wd = kword(row, ch);
+#pragma unroll
+                        for (int v = 0; v < WPC; ++v) {
+                            garea[v].kst[wd] = k;
+                            *reinterpret_cast<uint2 *>(&garea[v].cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
+                        }
+                    }
+                }
+                for (int i = gtid; i < hw * BROWS; i += ht) garea[i / BROWS].drow[i % BROWS] = 0;
+                group_sync(gbar, ht);
+                // C: warp w applies pairs w, w + WPC, w + 2 WPC, ...
+                for (uint32_t base = 0; base * WPC + warp < len; base += 32) {
+                    const uint32_t jj = (base + lane) * WPC + warp;
+                    const uint32_t mine = jj < len ? __ldg(pairs + jj) : 0u;
+                    const int cnt = (int)min(32u, (len - warp + WPC - 1) / WPC - base);
+                    for (int j = 0; j < cnt; ++j) {
+                        const uint32_t pl = __shfl_sync(0xffffffffu, mine, j);
+                        apply_pair<NW>(pl, wa, P, R, W, lane);
+                        shadow_pair<false>(pl, wa->cnt, sh, shs, R, SR, lane);
+                        __syncwarp();
+                    }
+                }
+                group_sync(gbar, ht);
+                // D: merge the copies and write back
+                for (int c = gtid; c < BCHUNKS; c += ht) {
+                    const int row = c >> 3, ch = c & 7;
+                    if ((need[row] >> ch) & 1u) {
+                        const int wd = kword(row, ch);
+                        uint32_t k = garea[0].kst[wd];
+                        uint32_t dirty = (garea[0].drow[row] >> ch) & 1u;
+                        uint2 cs = *reinterpret_cast<const uint2 *>(&garea[0].cnt[row * 32 + ch * 4]);
+#pragma unroll
+                        for (int v = 1; v < WPC; ++v) {
+                            k = vmin4(k, garea[v].kst[wd]);
+                            dirty |= (garea[v].drow[row] >> ch) & 1u;
+                            const uint2 cv =
+                                *reinterpret_cast<const uint2 *>(&garea[v].cnt[row * 32 + ch * 4]);
+                            cs.x += cv.x;   // packed 16-bit counts: a voxel's total fits 16 bits
+                            cs.y += cv.y;
+                        }
+                        store_chunk(g, chunk_index(g, bx, by, bz, row, ch), k, dirty != 0, cs, T, Hmax);
+                    }
+                }
+                if (gtid == 0) ws.bcnt[b] = 0u;
             }
-        }
-        for (int i = tid; i < WPC * BROWS; i += NTHR) areas[i / BROWS].drow[i % BROWS] = 0;
-        __syncthreads();
-        // C: warp w applies pairs w, w + WPC, w + 2 WPC, ...
-        for (uint32_t base = 0; base * WPC + warp < len; base += 32) {
-            const uint32_t jj = (base + lane) * WPC + warp;
-            const uint32_t mine = jj < len ? __ldg(pairs + jj) : 0u;
-            const int cnt = (int)min(32u, (len - warp + WPC - 1) / WPC - base);
-            for (int j = 0; j < cnt; ++j) {
-                const uint32_t pl = __shfl_sync(0xffffffffu, mine, j);
-                apply_pair<NW>(pl, wa, P, R, W, lane);
-                shadow_pair<false>(pl, wa->cnt, sh, shs, R, SR, lane);
+        } else {
+            // light bricks, one per warp
+            for (;;) {
+                uint32_t w = 0;
+                if (lane == 0) w = atomicAdd(&ws.hdr->next_work, 1u);
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (nheavy + w >= nt) break;
+                // the larger size classes first (the class sizes are fixed during
+                // the launch: plain loads, served from L1 after the first)
+                int c = 0;
+                uint32_t q = w;
+#pragma unroll
+                for (int k = 0; k < LIGHT_CLASSES - 1; ++k) {
+                    const uint32_t nk = ws.hdr->n_cls[k];
+                    if (c == k && q >= nk) {
+                        q -= nk;
+                        c = k + 1;
+                    }
+                }
+                const uint32_t b = *light_queue_slot(ws, c, q);
+                const uint32_t start = ws.boff[b];
+                uint32_t len = ws.bcnt[b];
+                if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing
+                DevGrid g;
+                const uint32_t lb = brick_grid<BATCH>(g0, bd, b, g);
+                const int bx = (int)(lb % (uint32_t)g.nbx);
+                const uint32_t byz = lb / (uint32_t)g.nbx;
+                const int by = (int)(byz % (uint32_t)g.nby), bz = (int)(byz / (uint32_t)g.nby);
+                const uint32_t *pairs = ws.pairs + start;
+
+                // A
+                unsigned long long cr[CHUNKS_PER_ROW];
+#pragma unroll
+                for (int c = 0; c < CHUNKS_PER_ROW; ++c) cr[c] = 0ull;
+                coverage(pairs, 0u, len, 32u, R, lane, cr);
+                {
+                    uint32_t n0 = 0, n1 = 0;
+#pragma unroll
+                    for (int c = 0; c < CHUNKS_PER_ROW; ++c) {
+                        n0 |= (uint32_t)((cr[c] >> lane) & 1ull) << c;
+                        n1 |= (uint32_t)((cr[c] >> (lane + 32)) & 1ull) << c;
+                    }
+                    wa->need[lane] = n0;
+                    wa->need[lane + 32] = n1;
+                }
+                __syncwarp();
+                // B: lanes = 4 rows x 8 chunks; the masks of eight chunks are loaded
+                // before any shared-memory store (the stores go through a generic
+                // pointer, so the compiler would otherwise wait for each load in turn)
+                const int rs = lane >> 3, ch = lane & 7;
+                for (int i0 = 0; i0 < BROWS / 4; i0 += 8) {
+                    uint4 m[8];
+                    uint32_t nd = 0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int row = rs + 4 * (i0 + q);
+                        m[q] = make_uint4(0u, 0u, 0u, 0u);
+                        if ((wa->need[row] >> ch) & 1u) {
+                            nd |= 1u << q;
+                            m[q] = __ldcg(reinterpret_cast<const uint4 *>(
+                                g.mask + chunk_index(g, bx, by, bz, row, ch)));
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (!((nd >> q) & 1u)) continue;
+                        const int row = rs + 4 * (i0 + q);
+                        const int wd = kword(row, ch);
+                        wa->kst[wd] = codes_of(m[q], form_bad);
+                        *reinterpret_cast<uint2 *>(&wa->cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
+                    }
+                }
+                wa->drow[lane] = 0;
+                wa->drow[lane + 32] = 0;
+                __syncwarp();
+                // C
+                for (uint32_t base = 0; base < len; base += 32) {
+                    const uint32_t mine = base + lane < len ? __ldg(pairs + base + lane) : 0u;
+                    const int cnt = (int)min(32u, len - base);
+                    for (int j = 0; j < cnt; ++j) {
+                        const uint32_t pl = __shfl_sync(0xffffffffu, mine, j);
+                        apply_pair<NW>(pl, wa, P, R, W, lane);
+                        shadow_pair<false>(pl, wa->cnt, sh, shs, R, SR, lane);
+                        __syncwarp();
+                    }
+                }
+                // D: the old counters of four chunks are loaded before any of them
+                // is stored (stores in between would serialise the loads)
+                for (int i0 = 0; i0 < BROWS / 4; i0 += 4) {
+                    uint2 cs[4], hv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int row = rs + 4 * (i0 + q);
+                        cs[q] = make_uint2(0u, 0u);
+                        hv[q] = make_uint2(0u, 0u);
+                        if ((wa->need[row] >> ch) & 1u) {
+                            cs[q] = *reinterpret_cast<const uint2 *>(&wa->cnt[row * 32 + ch * 4]);
+                            if (cs[q].x | cs[q].y)
+                                hv[q] = __ldcg(reinterpret_cast<const uint2 *>(
+                                    g.hits + chunk_index(g, bx, by, bz, row, ch)));
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int row = rs + 4 * (i0 + q);
+                        if (!((wa->need[row] >> ch) & 1u)) continue;
+                        const int wd = kword(row, ch);
+                        const size_t gi = chunk_index(g, bx, by, bz, row, ch);
+                        if ((wa->drow[row] >> ch) & 1u) store_codes(g, gi, wa->kst[wd]);
+                        if (cs[q].x | cs[q].y) {
+                            const uint32_t cross = apply_counts(hv[q], cs[q], T, Hmax);
+                            __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv[q]);
+                            store_crossings(g, gi, cross);
+                        }
+                    }
+                }
+                if (lane == 0) ws.bcnt[b] = 0u;
                 __syncwarp();
             }
         }
-        __syncthreads();
-        // D: merge the copies and write back
-        for (int c = tid; c < BCHUNKS; c += NTHR) {
-            const int row = c >> 3, ch = c & 7;
-            if ((need[row] >> ch) & 1u) {
-                const int wd = kword(row, ch);
-                uint32_t k = areas[0].kst[wd];
-                uint32_t dirty = (areas[0].drow[row] >> ch) & 1u;
-                uint2 cs = *reinterpret_cast<const uint2 *>(&areas[0].cnt[row * 32 + ch * 4]);
-#pragma unroll
-                for (int v = 1; v < WPC; ++v) {
-                    k = vmin4(k, areas[v].kst[wd]);
-                    dirty |= (areas[v].drow[row] >> ch) & 1u;
-                    const uint2 cv = *reinterpret_cast<const uint2 *>(&areas[v].cnt[row * 32 + ch * 4]);
-                    cs.x += cv.x;   // packed 16-bit counts: a voxel's total fits 16 bits
-                    cs.y += cv.y;
-                }
-                store_chunk(g, chunk_index(g, bx, by, bz, row, ch), k, dirty != 0, cs, T, Hmax);
-            }
-        }
-        if (tid == 0) ws.bcnt[b] = 0u;
-    }
-
-    // ---------------- light bricks: one warp each
-    for (;;) {
-        uint32_t w = 0;
-        if (lane == 0) w = atomicAdd(&ws.hdr->next_work, 1u);
-        w = __shfl_sync(0xffffffffu, w, 0);
-        if (nheavy + w >= nt) break;
-        // the larger size classes first (the class sizes are fixed during
-        // the launch: plain loads, served from L1 after the first)
-        int c = 0;
-        uint32_t q = w;
-#pragma unroll
-        for (int k = 0; k < LIGHT_CLASSES - 1; ++k) {
-            const uint32_t nk = ws.hdr->n_cls[k];
-            if (c == k && q >= nk) {
-                q -= nk;
-                c = k + 1;
-            }
-        }
-        const uint32_t b = *light_queue_slot(ws, c, q);
-        const uint32_t start = ws.boff[b];
-        uint32_t len = ws.bcnt[b];
-        if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing
-        DevGrid g;
-        const uint32_t lb = brick_grid<BATCH>(g0, bd, b, g);
-        const int bx = (int)(lb % (uint32_t)g.nbx);
-        const uint32_t byz = lb / (uint32_t)g.nbx;
-        const int by = (int)(byz % (uint32_t)g.nby), bz = (int)(byz / (uint32_t)g.nby);
-        const uint32_t *pairs = ws.pairs + start;
-
-        // A
-        unsigned long long cr[CHUNKS_PER_ROW];
-#pragma unroll
-        for (int c = 0; c < CHUNKS_PER_ROW; ++c) cr[c] = 0ull;
-        coverage(pairs, 0u, len, 32u, R, lane, cr);
-        {
-            uint32_t n0 = 0, n1 = 0;
-#pragma unroll
-            for (int c = 0; c < CHUNKS_PER_ROW; ++c) {
-                n0 |= (uint32_t)((cr[c] >> lane) & 1ull) << c;
-                n1 |= (uint32_t)((cr[c] >> (lane + 32)) & 1ull) << c;
-            }
-            wa->need[lane] = n0;
-            wa->need[lane + 32] = n1;
-        }
-        __syncwarp();
-        // B: lanes = 4 rows x 8 chunks; the masks of eight chunks are loaded
-        // before any shared-memory store (the stores go through a generic
-        // pointer, so the compiler would otherwise wait for each load in turn)
-        const int rs = lane >> 3, ch = lane & 7;
-        for (int i0 = 0; i0 < BROWS / 4; i0 += 8) {
-            uint4 m[8];
-            uint32_t nd = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int row = rs + 4 * (i0 + q);
-                m[q] = make_uint4(0u, 0u, 0u, 0u);
-                if ((wa->need[row] >> ch) & 1u) {
-                    nd |= 1u << q;
-                    m[q] = __ldcg(reinterpret_cast<const uint4 *>(
-                        g.mask + chunk_index(g, bx, by, bz, row, ch)));
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (!((nd >> q) & 1u)) continue;
-                const int row = rs + 4 * (i0 + q);
-                const int wd = kword(row, ch);
-                wa->kst[wd] = codes_of(m[q], form_bad);
-                *reinterpret_cast<uint2 *>(&wa->cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
-            }
-        }
-        wa->drow[lane] = 0;
-        wa->drow[lane + 32] = 0;
-        __syncwarp();
-        // C
-        for (uint32_t base = 0; base < len; base += 32) {
-            const uint32_t mine = base + lane < len ? __ldg(pairs + base + lane) : 0u;
-            const int cnt = (int)min(32u, len - base);
-            for (int j = 0; j < cnt; ++j) {
-                const uint32_t pl = __shfl_sync(0xffffffffu, mine, j);
-                apply_pair<NW>(pl, wa, P, R, W, lane);
-                shadow_pair<false>(pl, wa->cnt, sh, shs, R, SR, lane);
-                __syncwarp();
-            }
-        }
-        // D: the old counters of four chunks are loaded before any of them
-        // is stored (stores in between would serialise the loads)
-        for (int i0 = 0; i0 < BROWS / 4; i0 += 4) {
-            uint2 cs[4], hv[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = rs + 4 * (i0 + q);
-                cs[q] = make_uint2(0u, 0u);
-                hv[q] = make_uint2(0u, 0u);
-                if ((wa->need[row] >> ch) & 1u) {
-                    cs[q] = *reinterpret_cast<const uint2 *>(&wa->cnt[row * 32 + ch * 4]);
-                    if (cs[q].x | cs[q].y)
-                        hv[q] = __ldcg(reinterpret_cast<const uint2 *>(
-                            g.hits + chunk_index(g, bx, by, bz, row, ch)));
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = rs + 4 * (i0 + q);
-                if (!((wa->need[row] >> ch) & 1u)) continue;
-                const int wd = kword(row, ch);
-                const size_t gi = chunk_index(g, bx, by, bz, row, ch);
-                if ((wa->drow[row] >> ch) & 1u) store_codes(g, gi, wa->kst[wd]);
-                if (cs[q].x | cs[q].y) {
-                    const uint32_t cross = apply_counts(hv[q], cs[q], T, Hmax);
-                    __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv[q]);
-                    store_crossings(g, gi, cross);
-                }
-            }
-        }
-        if (lane == 0) ws.bcnt[b] = 0u;
-        __syncwarp();
     }
     if (form_bad) atomicOr(&ws.hdr->err, ERR_MASK_FORM);
 
@@ -708,6 +747,7 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
             h->pool = 0u;
             h->next_work = 0u;
             h->n_heavy = 0u;
+            h->n_vheavy = 0u;
             for (int c = 0; c < LIGHT_CLASSES; ++c) h->n_cls[c] = 0u;
             h->next_heavy = 0u;
             h->acc_valid = 0ull;

@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, Ws
 // aggregated per CTA of 1024 bricks: warp totals are scanned in shared
 // memory and one thread takes each counter's range with a single atomic.
 constexpr int ALLOC_THREADS = 1024;
-constexpr int ALLOC_CTRS = 2 + LIGHT_CLASSES;          // pairs, heavy, light classes
+constexpr int ALLOC_CTRS = 3 + LIGHT_CLASSES;          // pairs, heavy, very heavy, light classes
 
 __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
     __shared__ uint32_t s_w[ALLOC_THREADS / 32][ALLOC_CTRS];
@@ -451,8 +451,9 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
         }
         const bool touched = len != 0u;
         const bool heavy = touched && len > ws.heavy;
-        // counter index: 1 heavy, 2 + c light class c, -1 untouched
-        const int cls = !touched ? -1 : heavy ? 1 : 2 + light_class(len, ws.heavy);
+        const bool vheavy = heavy && len / VHEAVY_FACTOR > ws.heavy;
+        // counter index: 1 heavy, 2 very heavy, 3 + c light class c, -1 untouched
+        const int cls = !touched ? -1 : vheavy ? 2 : heavy ? 1 : 3 + light_class(len, ws.heavy);
         unsigned bal[ALLOC_CTRS];
 #pragma unroll
         for (int k = 1; k < ALLOC_CTRS; ++k) bal[k] = __ballot_sync(0xffffffffu, cls == k);
@@ -480,8 +481,10 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
             for (int k = 0; k < ALLOC_CTRS; ++k) {
                 g[k] = 0u;
                 if (lane == 31 && x[k]) {
-                    unsigned int *ctr = k == 0 ? &ws.hdr->pool : k == 1 ? &ws.hdr->n_heavy
-                                                                        : &ws.hdr->n_cls[k - 2];
+                    unsigned int *ctr = k == 0   ? &ws.hdr->pool
+                                        : k == 1 ? &ws.hdr->n_heavy
+                                        : k == 2 ? &ws.hdr->n_vheavy
+                                                 : &ws.hdr->n_cls[k - 3];
                     g[k] = atomicAdd(ctr, x[k]);
                 }
                 if (k >= 1) touched_sum += x[k];
@@ -498,8 +501,9 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
             ws.bcnt[b] = 0;
             const uint32_t q = s_w[warp][cls] + __popc(bal[cls] & below);
             if (q >= ws.max_touched) atomicOr(&ws.hdr->err, ERR_TOUCHED_OVERFLOW);   // cannot happen by sizing
+            else if (vheavy) ws.order[ws.max_touched - 1 - q] = b;
             else if (heavy) ws.order[q] = b;
-            else *light_queue_slot(ws, cls - 2, q) = b;
+            else *light_queue_slot(ws, cls - 3, q) = b;
         }
         __syncthreads();                                   // s_w is reused next round
     }
@@ -803,6 +807,7 @@ __global__ void k_ws_rearm_header(WsDev ws) {
     h->next_work = 0u;
     h->done_ctas = 0u;
     h->n_heavy = 0u;
+    h->n_vheavy = 0u;
     for (int c = 0; c < LIGHT_CLASSES; ++c) h->n_cls[c] = 0u;
     h->next_heavy = 0u;
     h->acc_valid = 0ull;
