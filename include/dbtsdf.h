@@ -353,10 +353,10 @@ dbt_status dbt_workspace_autotune(const dbt_grid *g, const dbt_kernels *k, dbt_w
  * every device allocation -- so they cannot provide a workspace.  This entry
  * point uses a fixed scratch array compiled into the library instead and
  * allocates nothing (host or device).  Limits: n <= 65,536 returns per scan,
- * and the grid's integration layout must fit in 20 MiB (true for every grid
- * of up to 524,288 bricks of 32 x 8 x 8 voxels at K <= 17, ~450,000 bricks
+ * and the grid's integration layout must fit in 22 MiB (true for every grid
+ * of up to 524,288 bricks of 32 x 8 x 8 voxels at K <= 17, ~465,000 bricks
  * at K = 19 or 21); larger inputs are rejected
- * with DBT_EINVAL and a message.  The 20 MiB array occupies device memory on
+ * with DBT_EINVAL and a message.  The 22 MiB array occupies device memory on
  * every GPU that loads the library until the process exits.  All calls share
  * it: calls whose work overlaps on the GPU race, so issue them on one stream
  * (or otherwise serialise them).  The first call on a device looks up the
