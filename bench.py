@@ -53,7 +53,7 @@ INTEGRATE_SRC = os.path.join(ROOT, "paper_2509_20081_gb300", "csrc", "integrate.
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_integrate, per kept
 # return, from the capture summarised under profiles/ (valid only for the
 # integrate.cu source with this sha256 prefix; otherwise traffic is null).
-NCU_TRAFFIC = {"integrate_sha": "13bb4b024bdc33fd", "bytes_per_kept_return": 854.6,
+NCU_TRAFFIC = {"integrate_sha": "736eec9ac75091de", "bytes_per_kept_return": 854.7,
                "source": "profiles/k_integrate_urban_half.md (urban_half, 39.9 k kept returns "
                          "per scan, 34.1 MB DRAM read+write per launch), scaled by kept returns"}
 
@@ -104,9 +104,18 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def wait_first(self, timeout_s: float = 5.0):
+        """Blocks until nvidia-smi has written its first sample (it takes a
+        moment to start), so that the samples cover the timed region."""
+        t_end = time.time() + timeout_s
+        while self.proc is not None and time.time() < t_end:
+            if os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -264,10 +273,12 @@ def run_ours(args, rank, world):
     t1 = torch.cuda.Event(enable_timing=True)
     for e in evb + eve:          # torch creates the CUDA event on first record
         e.record(stream)
+    clocks = ClockSampler(dev.index) if rank == 0 else None
+    if clocks:
+        clocks.wait_first()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(dev.index) if rank == 0 else None
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     t0.record(stream)
     for s in range(args.steps):
@@ -556,6 +567,7 @@ def run_mesh(args, rank, world):
         return sum(a.elapsed_time(b) for a, b in ev) / args.steps
 
     clk = ClockSampler(dev.index or 0)
+    clk.wait_first()
     ms_count = timed(lambda: extract(None, 0))
     ms_full = timed(lambda: extract(tri.data_ptr(), ntri))
     sample = clk.stop()
