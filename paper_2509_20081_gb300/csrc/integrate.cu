@@ -14,11 +14,15 @@
 // table load, a staged-word load, a byte-wise min and a conditional store.
 //
 // Work split.  Persistent CTAs of WPC warps.  Bricks (32 x 8 x 8 voxels)
-// with more than ws.heavy (return, brick) pairs are taken first, one per
-// CTA: each warp applies a share of the pairs to its own staged copy and the
+// with more than ws.heavy (return, brick) pairs ("heavy") are taken one per
+// group of warps: at K <= 13 by the separable dense path below, otherwise
+// each warp applies a share of the pairs to its own staged copy and the
 // copies are merged (byte-wise min of codes, sum of counts).  The other
-// bricks are taken one per warp.  A brick is only ever written by the CTA or
-// warp that took it, so no atomics touch the grid.
+// bricks are taken one per warp, in size classes, largest first.  At K <= 11
+// a CTA holds two groups of four warps, one starting on heavy and one on
+// light bricks; otherwise the CTA is one group, heavy bricks first.  A brick
+// is only ever written by the group or warp that took it, so no atomics
+// touch the grid.
 //
 // Per brick:
 //   A. the 16-byte chunks of each brick row that any pair's kernel covers

@@ -435,6 +435,7 @@ constexpr int ALLOC_CTRS = 3 + LIGHT_CLASSES;          // pairs, heavy, very hea
 
 __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
     __shared__ uint32_t s_w[ALLOC_THREADS / 32][ALLOC_CTRS];
+    __shared__ uint32_t s_tot[ALLOC_CTRS];             // the CTA's total of each counter
     pdl_wait();
     pdl_launch_dependents();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -463,38 +464,35 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
             for (int k = 1; k < ALLOC_CTRS; ++k) s_w[warp][k] = __popc(bal[k]);
         }
         __syncthreads();
-        if (warp == 0) {                                   // lane j: warp j's entries
-            uint32_t v[ALLOC_CTRS], x[ALLOC_CTRS], g[ALLOC_CTRS];
+        if (warp < ALLOC_CTRS) {                           // warp k: counter k; lane j: warp j's entry
+            const int k = warp;
+            const uint32_t v = s_w[lane][k];
+            uint32_t x = v;
 #pragma unroll
-            for (int k = 0; k < ALLOC_CTRS; ++k) {
-                v[k] = s_w[lane][k];
-                x[k] = v[k];
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, x[k], o);
-                    if (lane >= o) x[k] += y;
-                }
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
             }
-            // all counters' atomics in flight at once
-            uint32_t touched_sum = 0u;
-#pragma unroll
-            for (int k = 0; k < ALLOC_CTRS; ++k) {
-                g[k] = 0u;
-                if (lane == 31 && x[k]) {
+            uint32_t g = 0u;
+            if (lane == 31) {
+                s_tot[k] = x;
+                if (x) {
                     unsigned int *ctr = k == 0   ? &ws.hdr->pool
                                         : k == 1 ? &ws.hdr->n_heavy
                                         : k == 2 ? &ws.hdr->n_vheavy
                                                  : &ws.hdr->n_cls[k - 3];
-                    g[k] = atomicAdd(ctr, x[k]);
+                    g = atomicAdd(ctr, x);
                 }
-                if (k >= 1) touched_sum += x[k];
             }
-            if (lane == 31 && touched_sum) atomicAdd(&ws.hdr->n_touched, touched_sum);
-#pragma unroll
-            for (int k = 0; k < ALLOC_CTRS; ++k)
-                s_w[lane][k] = __shfl_sync(0xffffffffu, g[k], 31) + x[k] - v[k];
+            s_w[lane][k] = __shfl_sync(0xffffffffu, g, 31) + x - v;
         }
         __syncthreads();
+        if (threadIdx.x == 0) {                            // touched bricks: every class
+            uint32_t t = 0u;
+#pragma unroll
+            for (int k = 1; k < ALLOC_CTRS; ++k) t += s_tot[k];
+            if (t) atomicAdd(&ws.hdr->n_touched, t);
+        }
         const unsigned below = (1u << lane) - 1u;
         if (touched) {
             ws.boff[b] = s_w[warp][0] + incl - len;

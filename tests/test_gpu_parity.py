@@ -122,6 +122,26 @@ def test_room_variants(orc, room3, variant):
     assert_same(gpu, ora, gs, os_)
 
 
+@pytest.mark.parametrize("K", [9, 13])
+@pytest.mark.parametrize("heavy", [0, 8, 1 << 30])
+def test_group_schedules_match_oracle(orc, room3, K, heavy):
+    """K = 9 runs heavy bricks on two four-warp groups per CTA, K = 13 on the
+    whole CTA; every brick heavy (0), a mix with very heavy bricks (8: more
+    than 32 pairs first) and every brick light (2^30)."""
+    dbt = _dbt()
+    pd = params(kernel_size=K, shadow_radius=3.0)
+    k = dbt.Kernels(dbt.make_params(**pd))
+    g = dbt.Grid(128, 128, 128, 0.1)
+    ws = dbt.Workspace(g, k, max(len(s[0]) for s in room3.scans))
+    ws.set_tuning(k, heavy, 0)
+    gs = []
+    for pts, pose in room3.scans[:2]:
+        dbt.dbt_integrate_scan(g, k, ws, torch.from_numpy(pts).cuda(), pose)
+        gs.append(dbt.dbt_get_scan_stats(ws))
+    ora, os_ = run_oracle(orc, pd, (128, 128, 128), 0.1, room3.scans[:2])
+    assert_same(g.numpy(), ora, gs, os_)
+
+
 def _tiny(seed, n, dims, res, dup):
     rng = synth.Rng(seed)
     nx, ny, nz = dims
