@@ -507,13 +507,23 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
     const int gtid = tid - gidx * ht, gwarp = warp - gidx * hw;
     const int gbar = 1 + gidx;                   // its named barrier
     WarpArea *garea = areas + gidx * hw;         // its first warp area
+    // First claims are static (heavy item blockIdx.x for group 0, light item
+    // blockIdx.x * hw + gwarp for group 1's warps): a launch's thousands of
+    // warps claiming at once through one counter would wait on each other's
+    // atomics.  Later claims take counter values past the static ranges.
+    const uint32_t n_static_heavy = gridDim.x;
+    const uint32_t n_static_light = hw < WPC ? gridDim.x * (uint32_t)(WPC - hw) : 0u;
+    bool first_heavy = gidx == 0, first_light = gidx == 1;
     __syncthreads();                             // tables above, for every warp
     for (int phase = 0; phase < 2; ++phase) {
         if ((phase == 0) == (gidx == 0)) {
             // heavy bricks, one per group
             for (;;) {
                 group_sync(gbar, ht);
-                if (gtid == 0) s_item[gidx] = atomicAdd(&ws.hdr->next_heavy, 1u);
+                if (gtid == 0)
+                    s_item[gidx] = first_heavy ? blockIdx.x
+                                               : n_static_heavy + atomicAdd(&ws.hdr->next_heavy, 1u);
+                first_heavy = false;
                 if (gtid < CHUNKS_PER_ROW) s_cr[gidx][gtid] = 0ull;
                 group_sync(gbar, ht);
                 const uint32_t it = s_item[gidx];
@@ -612,8 +622,13 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
             // light bricks, one per warp
             for (;;) {
                 uint32_t w = 0;
-                if (lane == 0) w = atomicAdd(&ws.hdr->next_work, 1u);
-                w = __shfl_sync(0xffffffffu, w, 0);
+                if (first_light) {
+                    w = blockIdx.x * (uint32_t)hw + (uint32_t)gwarp;
+                    first_light = false;
+                } else {
+                    if (lane == 0) w = atomicAdd(&ws.hdr->next_work, 1u);
+                    w = n_static_light + __shfl_sync(0xffffffffu, w, 0);
+                }
                 if (nheavy + w >= nt) break;
                 // the larger size classes first (the class sizes are fixed during
                 // the launch: plain loads, served from L1 after the first)
