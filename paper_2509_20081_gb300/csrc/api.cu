@@ -594,7 +594,7 @@ static dbt_status enqueue_scan(const dbt_grid *g, const dbt_kernels *k, dbt_work
     dbt_status st = enqueue_prep(g, k, ws, d_xyz, n, pose, s, &dg, &hcap, opt);
     if (st != DBT_OK) return st;
     const int ni = (int)n;
-    launch_alloc(ws->d, s);
+    launch_alloc(dg, k->dp, n, ws->d, hcap, s);
     launch_fill(dg, k->dp, ni, ws->d, hcap, s);
     if (ws->ev_begin) DBT_CUDA(cudaEventRecord(ws->ev_begin, s));
     launch_integrate(dg, k->dp, k->dt, (long long)n, ws->d,
@@ -656,7 +656,6 @@ static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_work
     while (hcap < 2ull * (unsigned long long)n) hcap <<= 1;
     const int ni = (int)n;
     launch_voxelize(dg, k->dp, k->dt, P, d_xyz, ni, ws->d, hcap, s, use_ex ? &ex : nullptr);
-    launch_count(dg, k->dp, ni, ws->d, hcap, s);
     *dg_out = dg;
     *hcap_out = hcap;
     return DBT_OK;
@@ -1054,9 +1053,8 @@ extern "C" dbt_status dbt_batch_run(dbt_batch *b, void *stream) {
         DBT_CUDA(cudaMemsetAsync((char *)b->buf + b->off_icnt, 0, b->n_items * sizeof(ItemCounters), s));
     if (b->n_items > 0) {
         launch_voxelize_batch(b->bd, k->dp, k->dt, b->n_total, b->d, hcap, s);
-        launch_count_batch(b->bd, k->dp, b->n_total, b->d, hcap, s);
     }
-    launch_alloc(b->d, s);
+    launch_alloc_batch(b->bd, k->dp, b->n_total, b->d, hcap, s);
     if (b->n_items > 0) launch_fill_batch(b->bd, k->dp, b->n_total, b->d, hcap, s);
     launch_integrate_batch(b->bd, k->dp, k->dt, b->n_total, b->d,
                            b->ctas ? b->ctas : integrate_grid_ctas(k->dp), s);

@@ -244,11 +244,13 @@ inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
 void launch_voxelize(const DevGrid &g, const DevParams &p, const DevTables &t, const Pose &pose,
                      const float *xyz, int n, const WsDev &ws, uint32_t hcap, cudaStream_t s,
                      const ScanEx *ex = nullptr);
-void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
-                  cudaStream_t s);
+
 void launch_contacts(const DevGrid &g, const DevParams &p, const DevTables &t, const Pose &pose,
                      const float *xyz, long long n, int4 *out, cudaStream_t s);
-void launch_alloc(const WsDev &ws, cudaStream_t s);
+void launch_alloc(const DevGrid &g, const DevParams &p, long long n, const WsDev &ws, uint32_t hcap,
+                  cudaStream_t s);
+void launch_alloc_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
+                        uint32_t hcap, cudaStream_t s);
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                  cudaStream_t s);
 void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, long long n_input,
@@ -256,8 +258,7 @@ void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, 
 // Batched forms: every scan of bd at once (one brick pass over all grids).
 void launch_voxelize_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
                            long long n, const WsDev &ws, uint32_t hcap, cudaStream_t s);
-void launch_count_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
-                        uint32_t hcap, cudaStream_t s);
+
 void launch_fill_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
                        uint32_t hcap, cudaStream_t s);
 void launch_integrate_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,

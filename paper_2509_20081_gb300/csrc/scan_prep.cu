@@ -1,8 +1,9 @@
 // Per-return stages of one scan (Sec. III-C), before the brick integration:
 //   k_voxelize  map-frame transform, contact voxel, boundary discard,
-//               direction bin, first-return hash insert
-//   k_count     first-return resolve, (return, brick) pair counts
-//   k_alloc     one contiguous pair segment per touched brick
+//               direction bin, first-return hash insert, and the
+//               (return, brick) pair counts of each distinct contact voxel
+//   k_alloc     first-return resolve; one contiguous pair segment per
+//               touched brick
 //   k_fill      pair payloads into the segments; clears the hash table
 // plus the direction-bin and voxel readout kernels.
 //
@@ -88,17 +89,20 @@ __device__ __forceinline__ uint32_t hslot(unsigned long long key, uint32_t hcap)
 
 // First-return rule (Sec. IV-B): the slot of a contact voxel keeps the
 // bitwise complement of the lowest return index seen, via atomicMax.
-__device__ void hash_insert(const WsDev &ws, uint32_t hcap, unsigned long long key, uint32_t i) {
+// Returns true for the one insert that created the slot (the voxel's first
+// insert in time, not necessarily its lowest index).
+__device__ bool hash_insert(const WsDev &ws, uint32_t hcap, unsigned long long key, uint32_t i) {
     uint32_t s = hslot(key, hcap);
     for (uint32_t probe = 0; probe < hcap; ++probe) {
         unsigned long long prev = atomicCAS(&ws.hkey[s], 0ull, key);
         if (prev == 0ull || prev == key) {
             atomicMax(&ws.hidx[s], ~i);
-            return;
+            return prev == 0ull;
         }
         s = (s + 1) & (hcap - 1);
     }
     atomicOr(&ws.hdr->err, ERR_HASH_FULL);
+    return false;
 }
 
 __device__ bool hash_is_first(const WsDev &ws, uint32_t hcap, unsigned long long key, uint32_t i) {
@@ -185,36 +189,96 @@ __device__ __forceinline__ int bin_octa_f32(const float d[3], const float e[3], 
 // returns belong to a few consecutive scans, counted in a window of
 // TALLY_ITEMS slots from the CTA's first scan (scans past it add directly).
 constexpr int TALLY_ITEMS = 8;
+constexpr int TALLY_FLAGS = 3;            // valid, inside, kept
 struct CtaTally {
-    uint32_t hdr[2];
-    uint32_t item[TALLY_ITEMS][2];
+    uint32_t hdr[TALLY_FLAGS];
+    uint32_t item[TALLY_ITEMS][TALLY_FLAGS];
     int first_item;
 };
 
 __device__ __forceinline__ void tally_init(CtaTally &s, int first_item) {
-    if (threadIdx.x < 2) s.hdr[threadIdx.x] = 0u;
-    if (threadIdx.x < 2 * TALLY_ITEMS) s.item[threadIdx.x >> 1][threadIdx.x & 1] = 0u;
+    if (threadIdx.x < TALLY_FLAGS) s.hdr[threadIdx.x] = 0u;
+    if (threadIdx.x < TALLY_FLAGS * TALLY_ITEMS)
+        s.item[threadIdx.x / TALLY_FLAGS][threadIdx.x % TALLY_FLAGS] = 0u;
     if (threadIdx.x == 0) s.first_item = first_item;
     __syncthreads();
 }
 
-// Warp popcounts of two flags into the CTA's header tallies.
-__device__ __forceinline__ void tally_warp(CtaTally &s, bool a, bool b) {
-    const unsigned ba = __ballot_sync(0xffffffffu, a), bb = __ballot_sync(0xffffffffu, b);
-    if ((threadIdx.x & 31) == 0) {
-        if (ba) atomicAdd(&s.hdr[0], (uint32_t)__popc(ba));
-        if (bb) atomicAdd(&s.hdr[1], (uint32_t)__popc(bb));
+// Warp popcounts of the three flags into the CTA's header tallies.
+__device__ __forceinline__ void tally_warp(CtaTally &s, const bool f[TALLY_FLAGS]) {
+#pragma unroll
+    for (int k = 0; k < TALLY_FLAGS; ++k) {
+        const unsigned b = __ballot_sync(0xffffffffu, f[k]);
+        if ((threadIdx.x & 31) == 0 && b) atomicAdd(&s.hdr[k], (uint32_t)__popc(b));
     }
 }
 
-// After the CTA's last tally: its totals to the global counters ga, gb.
-__device__ __forceinline__ void tally_flush(CtaTally &s, unsigned long long *ga,
-                                            unsigned long long *gb) {
+// After the CTA's last tally: its totals to the scan counters.
+__device__ __forceinline__ void tally_flush(CtaTally &s, const WsDev &ws) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (s.hdr[0]) atomicAdd(ga, (unsigned long long)s.hdr[0]);
-        if (gb && s.hdr[1]) atomicAdd(gb, (unsigned long long)s.hdr[1]);
+        if (s.hdr[0]) atomicAdd(&ws.hdr->acc_valid, (unsigned long long)s.hdr[0]);
+        if (s.hdr[1]) atomicAdd(&ws.hdr->acc_inside, (unsigned long long)s.hdr[1]);
+        if (s.hdr[2]) atomicAdd(&ws.hdr->acc_kept, (unsigned long long)s.hdr[2]);
     }
+}
+
+// ------------------------------------------------------------------ pairs
+// Brick range of the K^3 neighbourhood of contact c along one axis.
+struct BrickSpan {
+    int x0, x1, y0, y1, z0, z1;
+};
+__device__ __forceinline__ BrickSpan brick_span(int cx, int cy, int cz, int R) {
+    BrickSpan s;
+    s.x0 = (cx - R) / BX;  // contacts are >= R, so these are non-negative
+    s.x1 = (cx + R) / BX;
+    s.y0 = (cy - R) / BY;
+    s.y1 = (cy + R) / BY;
+    s.z0 = (cz - R) / BZ;
+    s.z1 = (cz + R) / BZ;
+    return s;
+}
+
+// The (up to 2 x 4 x 4) bricks of each lane's pair span; f(valid, brick,
+// bx, by, bz) per brick.  AGG: enumerated in lock-step over the warp (steps
+// past a lane's own span call f with valid = false) so that lanes naming one
+// brick can add together.
+template <bool AGG, typename F>
+__device__ __forceinline__ void for_pair_bricks(bool has, const BrickSpan &s, const DevGrid &g,
+                                                uint32_t b0, F f) {
+    const int sx = s.x1 - s.x0 + 1, sy = s.y1 - s.y0 + 1, sz = s.z1 - s.z0 + 1;
+    const int np = has ? sx * sy * sz : 0;
+    const int nsteps = AGG ? __reduce_max_sync(0xffffffffu, np) : np;
+    int ix = 0, iy = 0, iz = 0;
+    for (int j = 0; j < nsteps; ++j) {
+        const bool v = j < np;
+        const uint32_t b = v ? b0 + ((uint32_t)(s.z0 + iz) * g.nby + (s.y0 + iy)) * g.nbx + (s.x0 + ix)
+                             : 0u;
+        f(v, b, s.x0 + ix, s.y0 + iy, s.z0 + iz);
+        if (++ix == sx) {
+            ix = 0;
+            if (++iy == sy) {
+                iy = 0;
+                ++iz;
+            }
+        }
+    }
+}
+
+// Pair counts per brick.  The counts are fire-and-forget atomics (nothing
+// waits for their old value); k_alloc finds the touched bricks afterwards
+// by scanning the counters.  AGG: lanes naming one brick add together.
+template <bool AGG>
+__device__ __forceinline__ void count_pairs(const WsDev &ws, const DevGrid &g, uint32_t b0,
+                                            bool kept, const BrickSpan &s) {
+    for_pair_bricks<AGG>(kept, s, g, b0, [&](bool v, uint32_t b, int, int, int) {
+        if constexpr (AGG) {
+            const unsigned peers = __match_any_sync(0xffffffffu, v ? b : 0xFFFFFFFFu);
+            if (v && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&ws.bcnt[b], (uint32_t)__popc(peers));
+        } else {
+            if (v) atomicAdd(&ws.bcnt[b], 1u);
+        }
+    });
 }
 
 // ------------------------------------------------------------------ K1
@@ -297,9 +361,9 @@ __global__ void __launch_bounds__(256) k_voxelize(DevGrid g, DevParams p, DevTab
     pdl_wait();
     pdl_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = false, inside = false;
+    bool f[TALLY_FLAGS] = {false, false, false};      // valid, inside, first of its voxel
+    int4 rec = make_int4(-1, 0, 0, 0);
     if (i < n) {
-        int4 rec = make_int4(-1, 0, 0, 0);
         int c = 0;
         if constexpr (EX) {
             if (i % ex.ds == 0) {
@@ -313,13 +377,16 @@ __global__ void __launch_bounds__(256) k_voxelize(DevGrid g, DevParams p, DevTab
         } else {
             c = contact_of(g, p, t, pose, xyz[3 * i + 0], xyz[3 * i + 1], xyz[3 * i + 2], rec);
         }
-        valid = c > 0;
-        inside = c == 2;
-        if (inside && p.dedup) hash_insert(ws, hcap, voxel_key(g, rec.x, rec.y, rec.z), (uint32_t)i);
+        f[0] = c > 0;
+        f[1] = c == 2;
+        // the pairs of a contact voxel are counted once, by the insert that
+        // created its slot: the kept return's bricks are those of its voxel
+        if (f[1]) f[2] = !p.dedup || hash_insert(ws, hcap, voxel_key(g, rec.x, rec.y, rec.z), (uint32_t)i);
         ws.prec[i] = rec;
     }
-    tally_warp(s_tally, valid, inside);
-    tally_flush(s_tally, &ws.hdr->acc_valid, &ws.hdr->acc_inside);
+    count_pairs<true>(ws, g, 0u, f[2], f[2] ? brick_span(rec.x, rec.y, rec.z, p.R) : BrickSpan{});
+    tally_warp(s_tally, f);
+    tally_flush(s_tally, ws);
 }
 
 // Contact voxel and bin of every return (dbt_scan_contacts).
@@ -333,91 +400,9 @@ __global__ void __launch_bounds__(256) k_contacts(DevGrid g, DevParams p, DevTab
     out[i] = rec;
 }
 
-// Brick range of the K^3 neighbourhood of contact c along one axis.
-struct BrickSpan {
-    int x0, x1, y0, y1, z0, z1;
-};
-__device__ __forceinline__ BrickSpan brick_span(int cx, int cy, int cz, int R) {
-    BrickSpan s;
-    s.x0 = (cx - R) / BX;  // contacts are >= R, so these are non-negative
-    s.x1 = (cx + R) / BX;
-    s.y0 = (cy - R) / BY;
-    s.y1 = (cy + R) / BY;
-    s.z0 = (cz - R) / BZ;
-    s.z1 = (cz + R) / BZ;
-    return s;
-}
-
-// The (up to 2 x 4 x 4) bricks of each lane's pair span; f(valid, brick,
-// bx, by, bz) per brick.  AGG: enumerated in lock-step over the warp (steps
-// past a lane's own span call f with valid = false) so that lanes naming one
-// brick can add together.
-template <bool AGG, typename F>
-__device__ __forceinline__ void for_pair_bricks(bool has, const BrickSpan &s, const DevGrid &g,
-                                                uint32_t b0, F f) {
-    const int sx = s.x1 - s.x0 + 1, sy = s.y1 - s.y0 + 1, sz = s.z1 - s.z0 + 1;
-    const int np = has ? sx * sy * sz : 0;
-    const int nsteps = AGG ? __reduce_max_sync(0xffffffffu, np) : np;
-    int ix = 0, iy = 0, iz = 0;
-    for (int j = 0; j < nsteps; ++j) {
-        const bool v = j < np;
-        const uint32_t b = v ? b0 + ((uint32_t)(s.z0 + iz) * g.nby + (s.y0 + iy)) * g.nbx + (s.x0 + ix)
-                             : 0u;
-        f(v, b, s.x0 + ix, s.y0 + iy, s.z0 + iz);
-        if (++ix == sx) {
-            ix = 0;
-            if (++iy == sy) {
-                iy = 0;
-                ++iz;
-            }
-        }
-    }
-}
-
-// ------------------------------------------------------------------ K2
-// Pair counts per brick.  The counts are fire-and-forget atomics (nothing
-// waits for their old value); k_alloc finds the touched bricks afterwards
-// by scanning the counters.  AGG: lanes naming one brick add together.
-template <bool AGG>
-__device__ __forceinline__ void count_pairs(const WsDev &ws, const DevGrid &g, uint32_t b0,
-                                            bool kept, const BrickSpan &s) {
-    for_pair_bricks<AGG>(kept, s, g, b0, [&](bool v, uint32_t b, int, int, int) {
-        if constexpr (AGG) {
-            const unsigned peers = __match_any_sync(0xffffffffu, v ? b : 0xFFFFFFFFu);
-            if (v && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&ws.bcnt[b], (uint32_t)__popc(peers));
-        } else {
-            if (v) atomicAdd(&ws.bcnt[b], 1u);
-        }
-    });
-}
-
-__global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, WsDev ws,
-                                               uint32_t hcap) {
-    __shared__ CtaTally s_tally;
-    tally_init(s_tally, 0);
-    pdl_wait();
-    pdl_launch_dependents();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool kept = false;
-    int rx = 0, ry = 0, rz = 0;
-    if (i < n) {
-        int4 r = ws.prec[i];
-        rx = r.x;
-        ry = r.y;
-        rz = r.z;
-        if (r.x >= 0) {
-            kept = true;
-            if (p.dedup && !hash_is_first(ws, hcap, voxel_key(g, r.x, r.y, r.z), (uint32_t)i)) {
-                kept = false;
-                r.w |= PREC_DUP;
-                ws.prec[i] = r;
-            }
-        }
-    }
-    count_pairs<true>(ws, g, 0u, kept, kept ? brick_span(rx, ry, rz, p.R) : BrickSpan{});
-    tally_warp(s_tally, kept, false);
-    tally_flush(s_tally, &ws.hdr->acc_kept, nullptr);
-}
+__device__ __forceinline__ int item_of(const BatchDev &bd, long long i);
+__device__ __forceinline__ unsigned long long batch_key(const DevGrid &g, int item, int x, int y,
+                                                        int z);
 
 // ------------------------------------------------------------------ K3
 // Every brick of the grid(s) is visited: the touched ones (a non-zero pair
@@ -433,11 +418,30 @@ __global__ void __launch_bounds__(256) k_count(DevGrid g, DevParams p, int n, Ws
 constexpr int ALLOC_THREADS = 1024;
 constexpr int ALLOC_CTRS = 3 + LIGHT_CLASSES;          // pairs, heavy, very heavy, light classes
 
-__global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(WsDev ws) {
+// The first-return rule resolved for every return of the scan(s): a kept
+// contact that is not its voxel's lowest index is flagged PREC_DUP (grid
+// stride over the returns, beside the brick visit below).
+template <bool BATCH>
+__global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(DevGrid g0, BatchDev bd, DevParams p,
+                                                         long long n, WsDev ws, uint32_t hcap) {
     __shared__ uint32_t s_w[ALLOC_THREADS / 32][ALLOC_CTRS];
     __shared__ uint32_t s_tot[ALLOC_CTRS];             // the CTA's total of each counter
     pdl_wait();
     pdl_launch_dependents();
+    if (p.dedup) {
+        const long long stride = (long long)gridDim.x * ALLOC_THREADS;
+        for (long long i = (long long)blockIdx.x * ALLOC_THREADS + threadIdx.x; i < n; i += stride) {
+            int4 r = ws.prec[i];
+            if (r.x < 0) continue;
+            unsigned long long key;
+            if constexpr (BATCH) key = batch_key(bd.grids[(r.w >> 16) & 0xFF], item_of(bd, i), r.x, r.y, r.z);
+            else key = voxel_key(g0, r.x, r.y, r.z);
+            if (!hash_is_first(ws, hcap, key, (uint32_t)i)) {
+                r.w |= PREC_DUP;
+                ws.prec[i] = r;
+            }
+        }
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nb = ws.nbricks;
     for (uint32_t base = blockIdx.x * ALLOC_THREADS; base < nb; base += gridDim.x * ALLOC_THREADS) {
@@ -594,37 +598,38 @@ __device__ __forceinline__ unsigned long long batch_key(const DevGrid &g, int it
     return ((unsigned long long)item << 40) + voxel_key(g, x, y, z);
 }
 
-// Adds per-scan counts of a warp: lanes with the same item are summed by
-// their leader, into the CTA's window (or directly past it).
-__device__ __forceinline__ void add_item_counts(const BatchDev &bd, CtaTally &s, int item, bool a,
-                                                bool b, unsigned long long ItemCounters::*fa,
-                                                unsigned long long ItemCounters::*fb) {
+// Adds per-scan counts of a warp (valid, inside, kept): lanes with the same
+// item are summed by their leader, into the CTA's window (or directly past
+// it).
+__device__ __forceinline__ void add_item_counts(const BatchDev &bd, CtaTally &s, int item,
+                                                const bool f[TALLY_FLAGS]) {
     const unsigned peers = __match_any_sync(0xffffffffu, item);
-    const unsigned ba = __ballot_sync(0xffffffffu, a) & peers;
-    const unsigned bb = __ballot_sync(0xffffffffu, b) & peers;
+    unsigned bal[TALLY_FLAGS];
+#pragma unroll
+    for (int k = 0; k < TALLY_FLAGS; ++k) bal[k] = __ballot_sync(0xffffffffu, f[k]) & peers;
     const int lane = threadIdx.x & 31;
     if (item >= 0 && lane == __ffs(peers) - 1) {
         const int w = item - s.first_item;
-        if (w >= 0 && w < TALLY_ITEMS) {
-            if (ba) atomicAdd(&s.item[w][0], (uint32_t)__popc(ba));
-            if (fb && bb) atomicAdd(&s.item[w][1], (uint32_t)__popc(bb));
-        } else {
-            if (ba) atomicAdd(&(bd.icnt[item].*fa), (unsigned long long)__popc(ba));
-            if (fb && bb) atomicAdd(&(bd.icnt[item].*fb), (unsigned long long)__popc(bb));
+        unsigned long long *g[TALLY_FLAGS] = {&bd.icnt[item].valid, &bd.icnt[item].inside,
+                                             &bd.icnt[item].kept};
+#pragma unroll
+        for (int k = 0; k < TALLY_FLAGS; ++k) {
+            if (!bal[k]) continue;
+            if (w >= 0 && w < TALLY_ITEMS) atomicAdd(&s.item[w][k], (uint32_t)__popc(bal[k]));
+            else atomicAdd(g[k], (unsigned long long)__popc(bal[k]));
         }
     }
 }
 
 // The CTA's per-scan window to the global per-scan counters (after
 // tally_flush's barrier).
-__device__ __forceinline__ void flush_item_counts(const BatchDev &bd, CtaTally &s,
-                                                  unsigned long long ItemCounters::*fa,
-                                                  unsigned long long ItemCounters::*fb) {
+__device__ __forceinline__ void flush_item_counts(const BatchDev &bd, CtaTally &s) {
     const int w = threadIdx.x;
     if (w < TALLY_ITEMS && s.first_item >= 0 && s.first_item + w < bd.n_items) {
         ItemCounters &c = bd.icnt[s.first_item + w];
-        if (s.item[w][0]) atomicAdd(&(c.*fa), (unsigned long long)s.item[w][0]);
-        if (fb && s.item[w][1]) atomicAdd(&(c.*fb), (unsigned long long)s.item[w][1]);
+        if (s.item[w][0]) atomicAdd(&c.valid, (unsigned long long)s.item[w][0]);
+        if (s.item[w][1]) atomicAdd(&c.inside, (unsigned long long)s.item[w][1]);
+        if (s.item[w][2]) atomicAdd(&c.kept, (unsigned long long)s.item[w][2]);
     }
 }
 
@@ -641,66 +646,33 @@ __global__ void __launch_bounds__(256) k_voxelize_b(BatchDev bd, DevParams p, De
     pdl_launch_dependents();
     tally_init(s_tally, threadIdx.x == 0 ? cta_first_item(bd, n) : 0);
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = false, inside = false;
+    bool f[TALLY_FLAGS] = {false, false, false};      // valid, inside, first of its voxel
     int item = -1;
+    int4 rec = make_int4(-1, 0, 0, 0);
+    DevGrid g = {};
+    uint32_t b0 = 0;
     if (i < n) {
         item = item_of(bd, i);
         const ItemDev &it = bd.items[item];
-        const DevGrid g = bd.grids[it.grid];
+        g = bd.grids[it.grid];
+        b0 = bd.bbase[it.grid];
         const long long j = i - bd.istart[item];
-        int4 rec = make_int4(-1, 0, 0, 0);
         const int c = contact_of(g, p, t, it.pose, it.xyz[3 * j + 0], it.xyz[3 * j + 1],
                                  it.xyz[3 * j + 2], rec);
-        valid = c > 0;
-        inside = c == 2;
-        if (inside) {
-            rec.w |= it.grid << 16;
-            if (p.dedup) hash_insert(ws, hcap, batch_key(g, item, rec.x, rec.y, rec.z), (uint32_t)i);
-        }
-        ws.prec[i] = rec;
-    }
-    tally_warp(s_tally, valid, inside);
-    add_item_counts(bd, s_tally, item, valid, inside, &ItemCounters::valid, &ItemCounters::inside);
-    tally_flush(s_tally, &ws.hdr->acc_valid, &ws.hdr->acc_inside);
-    flush_item_counts(bd, s_tally, &ItemCounters::valid, &ItemCounters::inside);
-}
-
-__global__ void __launch_bounds__(256) k_count_b(BatchDev bd, DevParams p, long long n, WsDev ws,
-                                                 uint32_t hcap) {
-    __shared__ CtaTally s_tally;
-    pdl_wait();
-    pdl_launch_dependents();
-    tally_init(s_tally, threadIdx.x == 0 ? cta_first_item(bd, n) : 0);
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool kept = false;
-    int item = -1;
-    DevGrid gk = {};
-    uint32_t b0k = 0;
-    BrickSpan sk = {};
-    if (i < n) {
-        item = item_of(bd, i);
-        int4 r = ws.prec[i];
-        if (r.x >= 0) {
-            const int gi = (r.w >> 16) & 0xFF;
-            const DevGrid g = bd.grids[gi];
-            kept = true;
-            if (p.dedup && !hash_is_first(ws, hcap, batch_key(g, item, r.x, r.y, r.z), (uint32_t)i)) {
-                kept = false;
-                r.w |= PREC_DUP;
-                ws.prec[i] = r;
-            }
-            if (kept) {
-                gk = g;
-                b0k = bd.bbase[gi];
-                sk = brick_span(r.x, r.y, r.z, p.R);
-            }
+        f[0] = c > 0;
+        f[1] = c == 2;
+        if (f[1]) {
+            f[2] = !p.dedup || hash_insert(ws, hcap, batch_key(g, item, rec.x, rec.y, rec.z), (uint32_t)i);
+            ws.prec[i] = make_int4(rec.x, rec.y, rec.z, rec.w | (it.grid << 16));
+        } else {
+            ws.prec[i] = rec;
         }
     }
-    count_pairs<true>(ws, gk, b0k, kept, sk);
-    tally_warp(s_tally, kept, false);
-    add_item_counts(bd, s_tally, item, kept, false, &ItemCounters::kept, nullptr);
-    tally_flush(s_tally, &ws.hdr->acc_kept, nullptr);
-    flush_item_counts(bd, s_tally, &ItemCounters::kept, nullptr);
+    count_pairs<true>(ws, g, b0, f[2], f[2] ? brick_span(rec.x, rec.y, rec.z, p.R) : BrickSpan{});
+    tally_warp(s_tally, f);
+    add_item_counts(bd, s_tally, item, f);
+    tally_flush(s_tally, ws);
+    flush_item_counts(bd, s_tally);
 }
 
 // Batches: many scans put many pairs on the same bricks, so the cursor bumps
@@ -759,12 +731,14 @@ __global__ void __launch_bounds__(256) k_fill_b(BatchDev bd, DevParams p, long l
 // neighbourhood and of its shadow set, and counts first-time marks.  The
 // counts U and U_s give the algorithmic bytes of a scan's integration.
 __global__ void __launch_bounds__(256) k_footprint(DevGrid g, DevParams p, DevTables t, int n,
+                                                   uint32_t hcap,
                                                    WsDev ws, uint32_t *bits_u, uint32_t *bits_s,
                                                    unsigned long long *counts) {
     const int i = blockIdx.x;
     if (i >= n) return;
     const int4 r = ws.prec[i];
-    if (r.x < 0 || (r.w & PREC_DUP)) return;
+    if (r.x < 0) return;
+    if (p.dedup && !hash_is_first(ws, hcap, voxel_key(g, r.x, r.y, r.z), (uint32_t)i)) return;
     const int R = p.R, K = p.K;
     unsigned long long nu = 0, ns = 0;
     for (int e = threadIdx.x; e < K * K * K; e += blockDim.x) {
@@ -785,8 +759,8 @@ __global__ void __launch_bounds__(256) k_footprint(DevGrid g, DevParams p, DevTa
     if (ns) atomicAdd(&counts[1], ns);
 }
 
-// Returns the workspace to its between-scans state after k_voxelize and
-// k_count ran without the rest of the pipeline.
+// Returns the workspace to its between-scans state after k_voxelize ran
+// without the rest of the pipeline (brick counters, hash table, header).
 __global__ void k_ws_rearm(WsDev ws, uint32_t hcap) {
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t g0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -816,7 +790,7 @@ __global__ void k_ws_rearm_header(WsDev ws) {
 void launch_footprint(const DevGrid &g, const DevParams &p, const DevTables &t, int n,
                       const WsDev &ws, uint32_t hcap, uint32_t *bits_u, uint32_t *bits_s,
                       unsigned long long *counts, cudaStream_t s) {
-    if (n > 0) k_footprint<<<n, 256, 0, s>>>(g, p, t, n, ws, bits_u, bits_s, counts);
+    if (n > 0) k_footprint<<<n, 256, 0, s>>>(g, p, t, n, hcap, ws, bits_u, bits_s, counts);
     k_ws_rearm<<<2 * 152, 256, 0, s>>>(ws, hcap);
     k_ws_rearm_header<<<1, 1, 0, s>>>(ws);
 }
@@ -885,18 +859,24 @@ void launch_contacts(const DevGrid &g, const DevParams &p, const DevTables &t, c
     if (n > 0) k_contacts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, p, t, pose, xyz, n, out);
 }
 
-void launch_count(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
-                  cudaStream_t s) {
-    launch_pdl(k_count, max(1, blocks_for(n, 256)), 256, 0, s, g, p, n, ws, hcap);
-}
-
 // One thread per brick where the GPU holds them all at once (a single wave
 // hides the latency of the counter loads and queue atomics), grid-stride
-// beyond that.
-void launch_alloc(const WsDev &ws, cudaStream_t s) {
-    const long long need = ((long long)ws.nbricks + ALLOC_THREADS - 1) / ALLOC_THREADS;
-    const int ctas = (int)std::max(1LL, std::min(need, 152LL * 4));
-    launch_pdl(k_alloc, ctas, ALLOC_THREADS, 0, s, ws);
+// beyond that; the first-return resolve strides over the returns.
+static int alloc_ctas(long long nbricks, long long n) {
+    const long long need = (std::max(nbricks, n) + ALLOC_THREADS - 1) / ALLOC_THREADS;
+    return (int)std::max(1LL, std::min(need, 152LL * 4));
+}
+
+void launch_alloc(const DevGrid &g, const DevParams &p, long long n, const WsDev &ws, uint32_t hcap,
+                  cudaStream_t s) {
+    launch_pdl(k_alloc<false>, alloc_ctas(ws.nbricks, n), ALLOC_THREADS, 0, s, g, BatchDev{}, p, n, ws,
+               hcap);
+}
+
+void launch_alloc_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
+                        uint32_t hcap, cudaStream_t s) {
+    launch_pdl(k_alloc<true>, alloc_ctas(ws.nbricks, n), ALLOC_THREADS, 0, s, DevGrid{}, bd, p, n, ws,
+               hcap);
 }
 
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
@@ -911,11 +891,6 @@ static inline unsigned batch_blocks(long long n) { return (unsigned)max(1ll, (n 
 void launch_voxelize_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
                            long long n, const WsDev &ws, uint32_t hcap, cudaStream_t s) {
     launch_pdl(k_voxelize_b, batch_blocks(n), 256, 0, s, bd, p, t, n, ws, hcap);
-}
-
-void launch_count_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
-                        uint32_t hcap, cudaStream_t s) {
-    launch_pdl(k_count_b, batch_blocks(n), 256, 0, s, bd, p, n, ws, hcap);
 }
 
 void launch_fill_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
