@@ -34,7 +34,7 @@ def _alone(dbt, k, w, scans):
     return g
 
 
-def test_serving_mix_equals_alone():
+def test_serving_mix_equals_alone(orc):
     import paper_2509_20081_gb300 as dbt
     from paper_2509_20081_gb300 import serve
     maps, arrivals = _robots()
@@ -53,6 +53,17 @@ def test_serving_mix_equals_alone():
         mixed = srv.map_state(rid)
         for a, b in ((alone.mask, mixed.mask), (alone.sign, mixed.sign), (alone.hits, mixed.hits)):
             assert torch.equal(a, b)
+    # two robots' served maps against the oracle's sequential replay of their streams
+    po = orc.params(**maps[0].params)
+    for rid in (0, 1):
+        w = maps[rid]
+        og = orc.Grid.create(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.res)
+        for pts, pose in w.scans:
+            orc.integrate_scan(og, po, pts, pose)
+        m, sg, h = srv.map_state(rid).numpy()
+        np.testing.assert_array_equal(m, og.mask)
+        np.testing.assert_array_equal(sg, og.sign)
+        np.testing.assert_array_equal(h, og.hits)
     st = serve.latency_stats(done)
     assert st["n"] == len(scans) and st["p99_ms"] >= st["p50_ms"] >= 0.0
     srv.close()
