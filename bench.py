@@ -57,6 +57,9 @@ NCU_TRAFFIC = {"integrate_sha": "4fdc34a016b6cb5e", "bytes_per_kept_return": 855
                "source": "profiles/k_integrate_urban_half.md (urban_half, 39.9 k kept returns "
                          "per scan, 34.1 MB DRAM read+write per launch), scaled by kept returns"}
 
+# Kernels one scan (or one batch run) launches: voxelize, alloc, fill, integrate.
+KERNELS_PER_SCAN = 4
+
 WORKLOADS = {
     "urban": dict(n_scans=100, scale=1.0, res=0.05, beams=64, width=1024, seed_offset=1),
     "urban_half": dict(n_scans=20, scale=0.5, res=0.05, beams=64, width=1024, seed_offset=1),
@@ -347,7 +350,7 @@ def run_ours(args, rank, world):
                        "what": "device time per scan, plain per-scan launches"},
         "batched": batched,
         "tuning": tuning,
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": KERNELS_PER_SCAN * args.steps,
         "roofline": {"bound": "hbm", "kernel": "k_integrate", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "traffic_source": traffic_note,
@@ -512,8 +515,9 @@ def run_maps(args, rank, world):
                         "launch": "one CUDA graph of dbt_batch_run over all scans",
                         "tuning": tuning},
             "plain": {"value": world * npts / (ms_plain * 1e-3), "ms_per_step": ms_plain,
-                      "launch": f"{len(items)} dbt_integrate_scan calls (5 kernels each)"},
-            "gpu_launches": 5 * args.steps}
+                      "launch": f"{len(items)} dbt_integrate_scan calls "
+                                f"({KERNELS_PER_SCAN} kernels each)"},
+            "gpu_launches": KERNELS_PER_SCAN * args.steps}
     print(json.dumps(line), flush=True)
     return 0
 
