@@ -195,18 +195,10 @@ __device__ __forceinline__ bool inside_of(uint32_t mask, uint32_t sign, int p_fr
     return sign ? pc < p_free : pc > p_occ;
 }
 
-// Bit i of the byte c moved to bit 4 i.
-__device__ __forceinline__ uint32_t spread4(uint32_t c) {
-    c = (c | (c << 12)) & 0x000F000Fu;
-    c = (c | (c << 6)) & 0x03030303u;
-    c = (c | (c << 3)) & 0x11111111u;
-    return c;
-}
-
 // One warp per plane row.  With x0 a multiple of 4 (rows 16-byte aligned)
-// each lane reads four voxels at once (uint4 masks, one word of signs) and
-// the four ballots (bit l = voxel 4 l + q) are interleaved into the row's
-// four words of 32 voxels; otherwise one voxel per lane per word.
+// each lane reads four voxels at once (uint4 masks, one word of signs) into
+// a 4-bit nibble, and eight lanes' nibbles OR-reduce (three xor shuffles)
+// into one word of 32 voxels; otherwise one voxel per lane per word.
 __global__ void __launch_bounds__(256) k_mc_bits(DevGrid g, ExportBox b, int p_free, int p_occ,
                                                  int wpr, uint32_t *__restrict__ bits) {
     const int lane = threadIdx.x & 31;
@@ -223,36 +215,34 @@ __global__ void __launch_bounds__(256) k_mc_bits(DevGrid g, ExportBox b, int p_f
         uint32_t *out = bits + r * wpr;
         if (vec) {
             for (int x0 = 0; x0 < b.bx; x0 += 256) {        // two chunks of 128 in flight
-                bool in[2][4] = {};
+                uint32_t nib[2] = {0u, 0u};                   // bit q: voxel 4 lane + q inside
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int x = x0 + 128 * h + 4 * lane;
                     if (x + 3 < b.bx) {
                         const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(mrow + x));
                         const uint32_t s4 = __ldg(reinterpret_cast<const uint32_t *>(srow + x));
-                        in[h][0] = inside_of(m4.x, s4 & 0xFFu, p_free, p_occ);
-                        in[h][1] = inside_of(m4.y, (s4 >> 8) & 0xFFu, p_free, p_occ);
-                        in[h][2] = inside_of(m4.z, (s4 >> 16) & 0xFFu, p_free, p_occ);
-                        in[h][3] = inside_of(m4.w, s4 >> 24, p_free, p_occ);
+                        nib[h] = (uint32_t)inside_of(m4.x, s4 & 0xFFu, p_free, p_occ) |
+                                 ((uint32_t)inside_of(m4.y, (s4 >> 8) & 0xFFu, p_free, p_occ) << 1) |
+                                 ((uint32_t)inside_of(m4.z, (s4 >> 16) & 0xFFu, p_free, p_occ) << 2) |
+                                 ((uint32_t)inside_of(m4.w, s4 >> 24, p_free, p_occ) << 3);
                     } else {
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
-                            if (x + q < b.bx)
-                                in[h][q] = inside_of(__ldg(mrow + x + q), __ldg(srow + x + q), p_free, p_occ);
+                            if (x + q < b.bx &&
+                                inside_of(__ldg(mrow + x + q), __ldg(srow + x + q), p_free, p_occ))
+                                nib[h] |= 1u << q;
                     }
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const uint32_t b0 = __ballot_sync(0xffffffffu, in[h][0]);
-                    const uint32_t b1 = __ballot_sync(0xffffffffu, in[h][1]);
-                    const uint32_t b2 = __ballot_sync(0xffffffffu, in[h][2]);
-                    const uint32_t b3 = __ballot_sync(0xffffffffu, in[h][3]);
-                    const int w = ((x0 + 128 * h) >> 5) + lane;   // lanes 0-3: the four words
-                    if (lane < 4 && w < wpr) {
-                        const int sh = 8 * lane;
-                        out[w] = spread4((b0 >> sh) & 0xFFu) | (spread4((b1 >> sh) & 0xFFu) << 1) |
-                                 (spread4((b2 >> sh) & 0xFFu) << 2) | (spread4((b3 >> sh) & 0xFFu) << 3);
-                    }
+                    // eight lanes' nibbles form one 32-voxel word (lane l at bits 4 (l & 7))
+                    uint32_t v = nib[h] << (4 * (lane & 7));
+                    v |= __shfl_xor_sync(0xffffffffu, v, 1);
+                    v |= __shfl_xor_sync(0xffffffffu, v, 2);
+                    v |= __shfl_xor_sync(0xffffffffu, v, 4);
+                    const int w = ((x0 + 128 * h) >> 5) + (lane >> 3);
+                    if ((lane & 7) == 0 && w < wpr) out[w] = v;
                 }
             }
         } else {
