@@ -316,7 +316,7 @@ dbt_status dbt_batch_destroy(dbt_batch *b);
  * this implementation; every setting gives bit-identical maps) ----
  *  heavy_pairs     bricks with more (return, brick) pairs than this are
  *                  integrated by a whole CTA, the others by one warp
- *                  (default 48; >= 0).
+ *                  (default 64; >= 0).
  *  integrate_ctas  CTAs of the persistent integrate kernel; 0 = every SM
  *                  filled to its occupancy limit (the default); at most 4x
  *                  that. */

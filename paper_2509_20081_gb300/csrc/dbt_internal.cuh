@@ -204,7 +204,7 @@ constexpr int MAX_SCAN_POSES = 256;
 // Default of WsDev::heavy: bricks with more (return, brick) pairs than this
 // are integrated by a whole CTA, the others by a single warp (tunable per
 // workspace or batch; any value gives the same result).
-constexpr uint32_t HEAVY_PAIRS = 48;
+constexpr uint32_t HEAVY_PAIRS = 64;
 
 // Return record prec.w: bin in bits 0-15, batch grid index in bits 16-23,
 // PREC_DUP when the first-return rule drops the return.

@@ -337,7 +337,7 @@ class Workspace:
     def reset(self, stream=None):
         _check(lib().dbt_workspace_reset(self.h, _stream_ptr(stream)))
 
-    def set_tuning(self, kernels: "Kernels", heavy_pairs: int = 48, integrate_ctas: int = 0):
+    def set_tuning(self, kernels: "Kernels", heavy_pairs: int = 64, integrate_ctas: int = 0):
         """dbt_workspace_set_tuning (launch choices only; results do not change)."""
         t = dbt_tuning(int(heavy_pairs), int(integrate_ctas))
         _check(lib().dbt_workspace_set_tuning(self.h, kernels.h, ctypes.byref(t)))
@@ -622,7 +622,7 @@ class Batch:
     def run(self, stream=None):
         _check(lib().dbt_batch_run(self.h, _stream_ptr(stream)))
 
-    def set_tuning(self, heavy_pairs: int = 48, integrate_ctas: int = 0):
+    def set_tuning(self, heavy_pairs: int = 64, integrate_ctas: int = 0):
         """dbt_batch_set_tuning (launch choices only; results do not change)."""
         t = dbt_tuning(int(heavy_pairs), int(integrate_ctas))
         _check(lib().dbt_batch_set_tuning(self.h, ctypes.byref(t)))
