@@ -242,9 +242,13 @@ dbt_status dbt_pose_ramp(const double start[12], const double end[12], int32_t n
                          int32_t mode, double *out);
 
 /* dbt_integrate_scan from host memory: copies the n returns at h_xyz into
- * the workspace's staging area (pinned memory keeps the copy asynchronous),
- * integrates them, and copies the scan's counters into *h_stats, which must
- * stay valid until the stream reaches that point.  Asynchronous. */
+ * one of the workspace's two staging buffers (on a copy stream the workspace
+ * creates at its first call, so that the copy overlaps the previous scan's
+ * kernels; pinned memory keeps it asynchronous), integrates them on
+ * `stream` once the copy is done, and copies the scan's counters into
+ * *h_stats, which must stay valid until the stream reaches that point.
+ * h_xyz must stay unchanged until `stream` has passed this scan.
+ * Asynchronous.  Workspaces of this call belong to one device. */
 dbt_status dbt_integrate_scan_host(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
                                    const float *h_xyz, int64_t n, const double pose[12],
                                    dbt_scan_stats *h_stats, void *stream);
@@ -354,7 +358,7 @@ dbt_status dbt_workspace_autotune(const dbt_grid *g, const dbt_kernels *k, dbt_w
  * point uses a fixed scratch array compiled into the library instead and
  * allocates nothing (host or device).  Limits: n <= 65,536 returns per scan,
  * and the grid's integration layout must fit in 22 MiB (true for every grid
- * of up to 524,288 bricks of 32 x 8 x 8 voxels at K <= 17, ~465,000 bricks
+ * of up to 524,288 bricks of 32 x 8 x 8 voxels at K <= 17, ~500,000 bricks
  * at K = 19 or 21); larger inputs are rejected
  * with DBT_EINVAL and a message.  The 22 MiB array occupies device memory on
  * every GPU that loads the library until the process exits.  All calls share

@@ -382,13 +382,13 @@ extern "C" dbt_status dbt_grid_init(const dbt_grid *g, void *stream) {
 // (ws_bind refuses a layout with a region left unset).
 constexpr size_t kUnset = ~size_t(0);
 struct WsLayout {
-    size_t hdr = kUnset, stage = kUnset, prec = kUnset, hkey = kUnset, hidx = kUnset,
+    size_t hdr = kUnset, stage = kUnset, stage_b = kUnset, prec = kUnset, hkey = kUnset, hidx = kUnset,
            bcnt = kUnset, boff = kUnset, order = kUnset, lq0 = kUnset, lq1 = kUnset, lq2 = kUnset,
            pairs = kUnset, poses = kUnset, total = kUnset;
     uint32_t hcap_alloc = 0, max_touched = 0, nbricks = 0;
     unsigned long long pairs_cap = 0;
     bool complete() const {
-        for (size_t v : {hdr, stage, prec, hkey, hidx, bcnt, boff, order, lq0, lq1, lq2, pairs,
+        for (size_t v : {hdr, stage, stage_b, prec, hkey, hidx, bcnt, boff, order, lq0, lq1, lq2, pairs,
                          poses, total})
             if (v == kUnset || (v != total && v >= total)) return false;
         return true;
@@ -398,7 +398,11 @@ struct WsLayout {
 static size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
 
 
-static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long max_points, WsLayout *L) {
+// staging: two host-input staging buffers (dbt_integrate_scan_host copies
+// the next scan into one while the previous scan reads the other); the
+// no-allocation entry point takes device input only and needs none.
+static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long max_points, WsLayout *L,
+                            bool staging = true) {
     if (max_points < 1 || max_points > (1ll << 30))
         return fail(DBT_EINVAL, "max_points must be in [1, 2^30]");
     const DevGrid d = dev_grid(g);
@@ -412,7 +416,8 @@ static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long m
     L->max_touched = (uint32_t)std::min<unsigned long long>(nb, L->pairs_cap);
     size_t o = 0;
     L->hdr = o;      o += up256(sizeof(WsHeader));
-    L->stage = o;    o += up256((size_t)max_points * 12);
+    L->stage = o;    o += up256(staging ? (size_t)max_points * 12 : 16);
+    L->stage_b = o;  o += up256(staging ? (size_t)max_points * 12 : 16);
     L->prec = o;     o += up256((size_t)max_points * 16);
     L->hkey = o;     o += up256((size_t)hc * 8);
     L->hidx = o;     o += up256((size_t)hc * 4);
@@ -436,6 +441,19 @@ struct dbt_workspace {
     int nx, ny, nz, pitch, K;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;   // optional timing of the integrate kernel
     int ctas = 0;                                       // integrate grid; 0 = occupancy maximum
+    // dbt_integrate_scan_host: the second staging buffer, the copy stream and
+    // per buffer an event after its copy and one after the scan that read it
+    float *stage_b = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    int stage_next = 0;
+    ~dbt_workspace() {
+        for (int i = 0; i < 2; ++i) {
+            if (ev_copied[i]) cudaEventDestroy(ev_copied[i]);
+            if (ev_free[i]) cudaEventDestroy(ev_free[i]);
+        }
+        if (copy_stream) cudaStreamDestroy(copy_stream);
+    }
 };
 
 extern "C" dbt_status dbt_workspace_size(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
@@ -473,6 +491,8 @@ static dbt_status ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels
     w->K = k->dp.K;
     w->d.hdr = (WsHeader *)(base + L.hdr);
     w->d.stage = (float *)(base + L.stage);
+    // host staging only where the layout gave both buffers room for max_points
+    w->stage_b = L.prec - L.stage_b >= (size_t)max_points * 12 ? (float *)(base + L.stage_b) : nullptr;
     w->d.prec = (int4 *)(base + L.prec);
     w->d.hkey = (unsigned long long *)(base + L.hkey);
     w->d.hidx = (uint32_t *)(base + L.hidx);
@@ -824,7 +844,7 @@ dbt_status dbt::integrate_on_scratch(const dbt_grid *g, const dbt_kernels *k, co
         return fail(DBT_EINVAL, "n = %lld exceeds the no-allocation limit of %lld returns per scan",
                     (long long)n, max_points);
     WsLayout L;
-    st = ws_layout(g, k, max_points, &L);
+    st = ws_layout(g, k, max_points, &L, false);
     if (st != DBT_OK) return st;
     if (L.total > scratch_bytes)
         return fail(DBT_EINVAL,
@@ -896,6 +916,7 @@ static dbt_status batch_layout(const dbt_grid *grids, int n_grids, const dbt_ker
     size_t o = 0;
     L->hdr = o;      o += up256(sizeof(WsHeader));
     L->stage = o;    o += up256(16);
+    L->stage_b = o;  o += up256(16);
     L->prec = o;     o += up256((size_t)max_points * 16);
     L->hkey = o;     o += up256((size_t)hc * 8);
     L->hidx = o;     o += up256((size_t)hc * 4);
@@ -1217,10 +1238,29 @@ extern "C" dbt_status dbt_integrate_scan_host(const dbt_grid *g, const dbt_kerne
     if (!ws) return fail(DBT_EINVAL, "workspace is NULL");
     if (n < 0 || n > ws->max_points) return fail(DBT_EINVAL, "n outside [0, max_points]");
     if (n > 0 && !h_xyz) return fail(DBT_EINVAL, "h_xyz is NULL");
+    if (!ws->stage_b) return fail(DBT_ESTATE, "workspace has no host staging");
     cudaStream_t s = (cudaStream_t)stream;
-    if (n > 0) DBT_CUDA(cudaMemcpyAsync(ws->d.stage, h_xyz, (size_t)n * 12, cudaMemcpyHostToDevice, s));
-    dbt_status st = enqueue_scan(g, k, ws, ws->d.stage, n, pose, s);
+    // The scan's returns are copied on the workspace's copy stream into the
+    // staging buffer the scan before last used, so the copy overlaps the
+    // previous scan's kernels; the scan's kernels wait for the copy.
+    if (!ws->copy_stream) {
+        DBT_CUDA(cudaStreamCreateWithFlags(&ws->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            DBT_CUDA(cudaEventCreateWithFlags(&ws->ev_copied[i], cudaEventDisableTiming));
+            DBT_CUDA(cudaEventCreateWithFlags(&ws->ev_free[i], cudaEventDisableTiming));
+        }
+    }
+    const int i = ws->stage_next;
+    float *buf = i ? ws->stage_b : ws->d.stage;
+    DBT_CUDA(cudaStreamWaitEvent(ws->copy_stream, ws->ev_free[i], 0));   // its last reader is done
+    if (n > 0)
+        DBT_CUDA(cudaMemcpyAsync(buf, h_xyz, (size_t)n * 12, cudaMemcpyHostToDevice, ws->copy_stream));
+    DBT_CUDA(cudaEventRecord(ws->ev_copied[i], ws->copy_stream));
+    DBT_CUDA(cudaStreamWaitEvent(s, ws->ev_copied[i], 0));
+    dbt_status st = enqueue_scan(g, k, ws, buf, n, pose, s);
     if (st != DBT_OK) return st;
+    DBT_CUDA(cudaEventRecord(ws->ev_free[i], s));
+    ws->stage_next = i ^ 1;
     if (h_stats)
         DBT_CUDA(cudaMemcpyAsync(h_stats, &ws->d.hdr->last, sizeof(dbt_scan_stats),
                                  cudaMemcpyDeviceToHost, s));

@@ -22,9 +22,9 @@
 // Limits of the fixed scratch: scans of up to 65,536 returns, and grids whose
 // integration layout fits in 22 MiB: every grid of up to 524,288 bricks of
 // 32 x 8 x 8 voxels (e.g. 1600 x 1600 x 320 voxels) at kernel sizes up to
-// 17, and up to ~465,000 bricks at K = 19 or 21, whose returns touch up to
-// 32 bricks each (~3.5 MB of per-return regions, 4 B per pair slot, 24 B per
-// brick).  Larger layouts are refused with DBT_EINVAL.
+// 17, and up to ~500,000 bricks at K = 19 or 21, whose returns touch up to
+// 32 bricks each (~2.7 MB of per-return regions, no host staging, 4 B per
+// pair slot, 24 B per brick).  Larger layouts are refused with DBT_EINVAL.
 static constexpr long long kMaxPoints = 65536;
 static constexpr size_t kScratchBytes = size_t(22) << 20;
 
