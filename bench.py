@@ -30,6 +30,7 @@ workload and metric, on a bounded sample of returns per step.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -338,7 +339,8 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     ms_e2e = e0.elapsed_time(e1)
-    assert all(sp.error == 0 for sp in st_ptrs)
+    assert all(sp.error == 0 and sp.n_input == int(h_scans[s % nsc].shape[0])
+               for s, sp in enumerate(st_ptrs)), "scan counters of the host entry point"
 
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev, world)
     if rank != 0:
@@ -362,7 +364,8 @@ def run_ours(args, rank, world):
         "data": "synthetic", "config": workload_config(args, w),
         "kept_points_per_s": world * kept_timed / (ms * 1e-3),
         "e2e": {"value": world * args.steps * npts / (ms_e2e * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": npts * 12, "d2h_bytes_per_step": 64,
+                "h2d_bytes_per_step": npts * 12,
+                "d2h_bytes_per_step": ctypes.sizeof(B.dbt_scan_stats),
                 "ms_per_step": ms_e2e / args.steps},
         "latency_ms": {"p50": pct(t_scan, 50), "p99": pct(t_scan, 99), "max": t_scan[-1],
                        "what": "device time per scan, plain per-scan launches (a separate pass "

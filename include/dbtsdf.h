@@ -245,8 +245,10 @@ dbt_status dbt_pose_ramp(const double start[12], const double end[12], int32_t n
  * one of the workspace's two staging buffers (on a copy stream the workspace
  * creates at its first call, so that the copy overlaps the previous scan's
  * kernels; pinned memory keeps it asynchronous), integrates them on
- * `stream` once the copy is done, and copies the scan's counters into
- * *h_stats, which must stay valid until the stream reaches that point.
+ * `stream` once the copy is done, and delivers the scan's counters to
+ * *h_stats (8-byte aligned pinned host memory is written by the integrate
+ * kernel itself; other host memory gets a copy on `stream`), which must stay
+ * valid until the stream reaches that point.
  * h_xyz must stay unchanged until `stream` has passed this scan.
  * Asynchronous.  Workspaces of this call belong to one device. */
 dbt_status dbt_integrate_scan_host(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,

@@ -1257,11 +1257,25 @@ extern "C" dbt_status dbt_integrate_scan_host(const dbt_grid *g, const dbt_kerne
         DBT_CUDA(cudaMemcpyAsync(buf, h_xyz, (size_t)n * 12, cudaMemcpyHostToDevice, ws->copy_stream));
     DBT_CUDA(cudaEventRecord(ws->ev_copied[i], ws->copy_stream));
     DBT_CUDA(cudaStreamWaitEvent(s, ws->ev_copied[i], 0));
+    // Counters into pinned (device-mapped) host memory are stored by the
+    // integrate kernel that publishes them, so no copy sits between this
+    // scan's kernels and the next scan's; other host memory gets a copy.
+    ScanStats *mapped = nullptr;
+    if (h_stats) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, h_stats) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+            a.devicePointer && (reinterpret_cast<uintptr_t>(a.devicePointer) & 7u) == 0u)
+            mapped = static_cast<ScanStats *>(a.devicePointer);
+        else
+            (void)cudaGetLastError();
+    }
+    ws->d.stats_out = mapped;
     dbt_status st = enqueue_scan(g, k, ws, buf, n, pose, s);
+    ws->d.stats_out = nullptr;
     if (st != DBT_OK) return st;
     DBT_CUDA(cudaEventRecord(ws->ev_free[i], s));
     ws->stage_next = i ^ 1;
-    if (h_stats)
+    if (h_stats && !mapped)
         DBT_CUDA(cudaMemcpyAsync(h_stats, &ws->d.hdr->last, sizeof(dbt_scan_stats),
                                  cudaMemcpyDeviceToHost, s));
     return DBT_OK;

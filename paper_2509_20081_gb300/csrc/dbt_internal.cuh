@@ -182,6 +182,9 @@ struct WsDev {
     Pose *poses;                // motion compensation: MAX_SCAN_POSES per-slice poses
     uint32_t heavy;             // bricks with more pairs than this go to a whole CTA
     uint32_t nbricks;           // bricks of the grid(s): the range of bcnt / boff
+    // Host memory the device can write (pinned, mapped) that also receives
+    // the scan's counters when they are published, or null.
+    ScanStats *stats_out = nullptr;
 };
 
 __device__ __forceinline__ uint32_t *light_queue_slot(const WsDev &ws, int c, uint32_t q) {

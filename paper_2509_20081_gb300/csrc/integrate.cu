@@ -761,6 +761,7 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
             h->last.n_bricks = (long long)vh->n_touched;
             h->last.error = atomicOr(&h->err, 0u);
             h->last.reserved = 0u;
+            if (ws.stats_out) *ws.stats_out = h->last;      // written through to host memory
             h->err = 0u;
             h->n_touched = 0u;
             h->pool = 0u;

@@ -440,7 +440,8 @@ def dbt_pose_ramp(start, end, n_poses: int, mode: int = DBT_MOTION_FULL) -> np.n
 def dbt_integrate_scan_host(grid: Grid, kernels: Kernels, ws: Workspace, xyz_host, pose,
                             stats: dbt_scan_stats | None = None, stream=None):
     """Integrate one scan from host memory (a pinned CPU float32 tensor or a
-    numpy array); the scan counters land in ``stats`` when the stream gets there."""
+    numpy array); the scan counters land in ``stats`` when the stream gets there
+    (stored by the integrate kernel when ``stats`` lies in pinned memory)."""
     n = int(xyz_host.shape[0])
     ptr = xyz_host.data_ptr() if hasattr(xyz_host, "data_ptr") else xyz_host.ctypes.data
     keep, pp = _pose_arg(pose)

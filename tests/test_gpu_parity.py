@@ -107,7 +107,9 @@ def test_host_entry_point_matches(orc, room3):
 def test_host_entry_point_pipelined(orc):
     """Scans handed in from host buffers back to back, no synchronisation in
     between: each copy overlaps the previous scan (two staging buffers, each
-    reused three times) and the map equals the oracle's."""
+    reused three times) and the map equals the oracle's.  The counters of
+    every other scan go to pinned memory (stored by the integrate kernel),
+    the others to pageable memory (copied)."""
     dbt = _dbt()
     w = synth.urban_sequence(n_scans=6, scale=0.25)
     dims = (w.grid.nx, w.grid.ny, w.grid.nz)
@@ -115,7 +117,9 @@ def test_host_entry_point_pipelined(orc):
     g = dbt.Grid(*dims, w.grid.res, w.grid.origin)
     ws = dbt.Workspace(g, k, max(len(p) for p, _ in w.scans))
     hosts = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p, _ in w.scans]
-    sts = [dbt.dbtsdf.dbt_scan_stats() for _ in w.scans]
+    h_st = torch.full((len(w.scans), 64), 0xAB, dtype=torch.uint8).pin_memory()
+    sts = [dbt.dbtsdf.dbt_scan_stats.from_address(h_st[i].data_ptr()) if i % 2 == 0
+           else dbt.dbtsdf.dbt_scan_stats() for i in range(len(w.scans))]
     for h, (_, pose), st in zip(hosts, w.scans, sts):
         dbt.dbt_integrate_scan_host(g, k, ws, h, pose, st)
     torch.cuda.synchronize()
