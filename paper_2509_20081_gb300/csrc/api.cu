@@ -606,6 +606,23 @@ static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_work
                                cudaStream_t s, DevGrid *dg_out, uint32_t *hcap_out,
                                const dbt_scan_options *opt = nullptr);
 
+// Counters for pinned (device-mapped, 8-byte aligned) host memory are
+// stored by the integrate kernel that publishes them, so no copy sits between
+// one scan's kernels and the next scan's; null for other memory, which gets
+// a copy on the stream.
+static ScanStats *mapped_stats(dbt_scan_stats *h_stats) {
+    if (!h_stats) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, h_stats) != cudaSuccess) {
+        (void)cudaGetLastError();                      // this query's own error only
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer &&
+        (reinterpret_cast<uintptr_t>(a.devicePointer) & 7u) == 0u)
+        return static_cast<ScanStats *>(a.devicePointer);
+    return nullptr;
+}
+
 static dbt_status enqueue_scan(const dbt_grid *g, const dbt_kernels *k, dbt_workspace *ws,
                                const float *d_xyz, int64_t n, const double pose[12],
                                cudaStream_t s, const dbt_scan_options *opt = nullptr) {
@@ -857,9 +874,11 @@ dbt_status dbt::integrate_on_scratch(const dbt_grid *g, const dbt_kernels *k, co
     DBT_CUDA(cudaMemsetAsync(base + L.hdr, 0, up256(sizeof(WsHeader)), s));
     DBT_CUDA(cudaMemsetAsync(base + L.hkey, 0, L.bcnt - L.hkey, s));        // hash keys + indices
     DBT_CUDA(cudaMemsetAsync(base + L.bcnt, 0, (size_t)L.nbricks * 4, s));  // brick counters
+    ScanStats *mapped = mapped_stats(h_stats);
+    w.d.stats_out = mapped;
     st = enqueue_scan(g, k, &w, d_xyz, n, pose, s);
     if (st != DBT_OK) return st;
-    if (h_stats)
+    if (h_stats && !mapped)
         DBT_CUDA(cudaMemcpyAsync(h_stats, &w.d.hdr->last, sizeof(dbt_scan_stats),
                                  cudaMemcpyDeviceToHost, s));
     return DBT_OK;
@@ -1257,18 +1276,7 @@ extern "C" dbt_status dbt_integrate_scan_host(const dbt_grid *g, const dbt_kerne
         DBT_CUDA(cudaMemcpyAsync(buf, h_xyz, (size_t)n * 12, cudaMemcpyHostToDevice, ws->copy_stream));
     DBT_CUDA(cudaEventRecord(ws->ev_copied[i], ws->copy_stream));
     DBT_CUDA(cudaStreamWaitEvent(s, ws->ev_copied[i], 0));
-    // Counters into pinned (device-mapped) host memory are stored by the
-    // integrate kernel that publishes them, so no copy sits between this
-    // scan's kernels and the next scan's; other host memory gets a copy.
-    ScanStats *mapped = nullptr;
-    if (h_stats) {
-        cudaPointerAttributes a{};
-        if (cudaPointerGetAttributes(&a, h_stats) == cudaSuccess && a.type == cudaMemoryTypeHost &&
-            a.devicePointer && (reinterpret_cast<uintptr_t>(a.devicePointer) & 7u) == 0u)
-            mapped = static_cast<ScanStats *>(a.devicePointer);
-        else
-            (void)cudaGetLastError();
-    }
+    ScanStats *mapped = mapped_stats(h_stats);
     ws->d.stats_out = mapped;
     dbt_status st = enqueue_scan(g, k, ws, buf, n, pose, s);
     ws->d.stats_out = nullptr;

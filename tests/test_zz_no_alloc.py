@@ -37,11 +37,13 @@ def _both(w, n_scans):
     ga = dbt.Grid(*dims, w.grid.res, w.grid.origin)
     gb = dbt.Grid(*dims, w.grid.res, w.grid.origin)
     ws = dbt.Workspace(ga, k, max(len(s[0]) for s in w.scans[:n_scans]))
-    for pts, pose in w.scans[:n_scans]:
+    pinned = torch.full((n_scans, 64), 0xAB, dtype=torch.uint8).pin_memory()
+    for i, (pts, pose) in enumerate(w.scans[:n_scans]):
         x = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
         dbt.dbt_integrate_scan(ga, k, ws, x, pose)
         sa = dbt.dbt_get_scan_stats(ws)
-        st = B.dbt_scan_stats()
+        # counters into pageable memory (copied) and pinned memory (stored by the kernel)
+        st = B.dbt_scan_stats() if i % 2 == 0 else B.dbt_scan_stats.from_address(pinned[i].data_ptr())
         B.dbt_integrate_scan_noalloc(gb, k, x, pose, st)
         torch.cuda.synchronize()
         sb = st.as_dict()
