@@ -586,7 +586,7 @@ size_t mc_scratch_bytes(const ExportBox &b) { return mc_layout(b, nullptr).bytes
 
 static int grid_for(long long work, int per_block) {
     const long long b = (work + per_block - 1) / per_block;
-    return (int)std::max(1LL, std::min(b, (long long)152 * 16));
+    return (int)std::max(1LL, std::min(b, 16LL * device_sm_count()));
 }
 
 void launch_sdf_field(const DevGrid &g, double res, const ExportBox &b, float *out, cudaStream_t s) {
@@ -627,9 +627,9 @@ void launch_mc_emit(const DevGrid &g, const ExportBox &b, double res, double iso
     if (nu == 0 || max_tri <= 0) return;
     const float resf = (float)res, isof = (float)iso;
     k_mc_fractions<<<(MC_LEVELS * MC_LEVELS + 255) / 256, 256, 0, s>>>(resf, isof, m.frac);
-    k_mc_emit<<<std::min(grid_for(nu, 8), 152 * 8), 256, 0, s>>>(g, b, resf, m.bits, mc_wpr(b),
-                                                                 mc_upr(b), m.frac, nu, m.uoff,
-                                                                 m.cnt, tri, cell, max_tri);
+    const int emit_ctas = std::min(grid_for(nu, 8), 8 * device_sm_count());
+    k_mc_emit<<<emit_ctas, 256, 0, s>>>(g, b, resf, m.bits, mc_wpr(b), mc_upr(b), m.frac, nu, m.uoff,
+                                        m.cnt, tri, cell, max_tri);
 }
 
 // Exclusive prefix sums of n counts into out, the grand total into *total;

@@ -37,6 +37,8 @@
 // depends only on the total count, so D gives exactly the state of applying
 // the returns one by one in scan order (the first-return rule is resolved
 // before this kernel).
+#include <mutex>
+
 #include "dbt_internal.cuh"
 
 namespace dbt {
@@ -786,27 +788,29 @@ static size_t integrate_smem(int K) {
     return ((np + 3) & ~size_t(3)) * 4 + WPC * sizeof(WarpArea);
 }
 
+// Launch configuration, cached per device.  Calls for different devices or
+// workspaces may come from several host threads, so the cache is guarded.
+constexpr int kCfgDevices = 64;
 struct IntegrateCfg {
-    int device = -1;
+    bool limits_set[2] = {};            // shared-memory limit raised: 4-word, 6-word rows
     int ctas[MAX_K + 1] = {};
 };
-static IntegrateCfg g_cfg;
+static IntegrateCfg g_cfg[kCfgDevices];
+static std::mutex g_cfg_mutex;
 
 // Occupancy-based persistent grid for one kernel size; the shared-memory
 // limit of each template instance is raised once per device to what its
 // largest kernel size needs (the attribute belongs to the function, so it
 // must not be lowered for a smaller K).
 template <int NW>
-static int configure(size_t smem, size_t smem_max) {
-    static int limit_set_on = -1;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    if (limit_set_on != dev) {
+static int configure(int dev, bool &limits_set, size_t smem, size_t smem_max) {
+    int sms = 0, per_sm = 0;
+    if (!limits_set) {
         cudaFuncSetAttribute(k_integrate<NW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_max);
         cudaFuncSetAttribute(k_integrate<NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_max);
-        limit_set_on = dev;
+        limits_set = true;
     }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<NW, true>, NTHR, smem);
@@ -827,16 +831,17 @@ int device_sm_count() {
 int integrate_grid_ctas(const DevParams &p) {
     int dev = 0;
     cudaGetDevice(&dev);
-    if (g_cfg.device != dev) {
-        g_cfg = IntegrateCfg();
-        g_cfg.device = dev;
-    }
-    if (!g_cfg.ctas[p.K]) {
+    IntegrateCfg local;                                 // devices past the cache: not cached
+    IntegrateCfg &c = (dev >= 0 && dev < kCfgDevices) ? g_cfg[dev] : local;
+    std::lock_guard<std::mutex> lock(g_cfg_mutex);
+    if (!c.ctas[p.K]) {
         const size_t smem = integrate_smem(p.K);
-        const size_t smax = words_per_row(p.K) == 4 ? integrate_smem(13) : integrate_smem(MAX_K);
-        g_cfg.ctas[p.K] = words_per_row(p.K) == 4 ? configure<4>(smem, smax) : configure<6>(smem, smax);
+        const bool four = words_per_row(p.K) == 4;
+        const size_t smax = four ? integrate_smem(13) : integrate_smem(MAX_K);
+        c.ctas[p.K] = four ? configure<4>(dev, c.limits_set[0], smem, smax)
+                           : configure<6>(dev, c.limits_set[1], smem, smax);
     }
-    return g_cfg.ctas[p.K];
+    return c.ctas[p.K];
 }
 
 void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, long long n_input,

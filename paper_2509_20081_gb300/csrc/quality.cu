@@ -350,7 +350,7 @@ __global__ void k_fill_inf(float *d, long long n) {
 
 int blocks_for(long long n) {
     const long long b = (n + 255) / 256;
-    return (int)std::max(1LL, std::min(b, 152LL * 8));
+    return (int)std::max(1LL, std::min(b, 8LL * device_sm_count()));
 }
 
 }  // namespace

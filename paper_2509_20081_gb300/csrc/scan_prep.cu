@@ -791,7 +791,7 @@ void launch_footprint(const DevGrid &g, const DevParams &p, const DevTables &t, 
                       const WsDev &ws, uint32_t hcap, uint32_t *bits_u, uint32_t *bits_s,
                       unsigned long long *counts, cudaStream_t s) {
     if (n > 0) k_footprint<<<n, 256, 0, s>>>(g, p, t, n, hcap, ws, bits_u, bits_s, counts);
-    k_ws_rearm<<<2 * 152, 256, 0, s>>>(ws, hcap);
+    k_ws_rearm<<<2 * device_sm_count(), 256, 0, s>>>(ws, hcap);
     k_ws_rearm_header<<<1, 1, 0, s>>>(ws);
 }
 
@@ -864,7 +864,7 @@ void launch_contacts(const DevGrid &g, const DevParams &p, const DevTables &t, c
 // beyond that; the first-return resolve strides over the returns.
 static int alloc_ctas(long long nbricks, long long n) {
     const long long need = (std::max(nbricks, n) + ALLOC_THREADS - 1) / ALLOC_THREADS;
-    return (int)std::max(1LL, std::min(need, 152LL * 4));
+    return (int)std::max(1LL, std::min(need, 4LL * device_sm_count()));
 }
 
 void launch_alloc(const DevGrid &g, const DevParams &p, long long n, const WsDev &ws, uint32_t hcap,
