@@ -27,17 +27,33 @@ SCHEME_OCTA = 0
 SCHEME_AZEL = 1
 
 
+_SRC_OMP = os.path.join(_HERE, "dbtsdf_oracle_omp.c")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def _compile(lib_path: str, srcs: list, extra: list, force: bool) -> str:
+    if (not force and os.path.exists(lib_path)
+            and all(os.path.getmtime(lib_path) >= os.path.getmtime(s) for s in srcs)):
+        return lib_path
+    tmp = lib_path + f".{os.getpid()}.tmp"
+    subprocess.run(["gcc"] + _CFLAGS + extra + ["-o", tmp, srcs[0], "-lm"], check=True)
+    os.replace(tmp, lib_path)
+    return lib_path
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (binary64, no fused multiply-add)."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    return _compile(_LIB, [_SRC], [], force)
+
+
+def build_omp(force: bool = False) -> str | None:
+    """Compile the points-parallel variant (OpenMP; it includes the oracle's
+    source).  None when the compiler has no OpenMP runtime."""
+    try:
+        return _compile(_LIB_OMP, [_SRC_OMP, _SRC], ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        return None
 
 
 class Params(ctypes.Structure):
@@ -285,6 +301,49 @@ def integrate_scan(g: Grid, p: Params, xyz, pose) -> dict:
     if r < 0:
         raise RuntimeError("oracle integrate_scan failed")
     return st.as_dict()
+
+
+_lib_omp = None
+
+
+def lib_omp():
+    """The points-parallel variant's library (built on first use)."""
+    global _lib_omp
+    if _lib_omp is None:
+        path = build_omp()
+        if path is None:
+            raise RuntimeError("the OpenMP variant of the oracle could not be built (no OpenMP runtime)")
+        L = load(path)
+        P = ctypes.POINTER
+        L.orc_integrate_scan_omp.restype = ctypes.c_int64
+        L.orc_integrate_scan_omp.argtypes = [P(_Grid), P(Params), ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_void_p, ctypes.c_int, P(Stats)]
+        L.orc_omp_max_threads.restype = ctypes.c_int
+        L.orc_omp_max_threads.argtypes = []
+        _lib_omp = L
+    return _lib_omp
+
+
+def integrate_scan_omp(g: Grid, p: Params, xyz, pose, threads: int | None = None) -> dict:
+    """The same Sec. III-C update as integrate_scan, with the returns' contacts
+    and Eq. 4-6 updates spread over `threads` host threads (per-voxel atomics;
+    the first-return rule still in array order).  Bit-identical map; the
+    n_mask_writes counter depends on the threads' order."""
+    pts = _as_points(xyz)
+    ps = _as_pose(pose)
+    L = lib_omp()
+    nt = int(threads) if threads else int(L.orc_omp_max_threads())
+    st = Stats()
+    r = L.orc_integrate_scan_omp(ctypes.byref(g._c()), ctypes.byref(p), pts.ctypes.data,
+                                 pts.shape[0], ps.ctypes.data, nt, ctypes.byref(st))
+    if r < 0:
+        raise RuntimeError("oracle integrate_scan_omp failed")
+    return st.as_dict()
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP runtime uses by default (all host cores)."""
+    return int(lib_omp().orc_omp_max_threads())
 
 
 def scan_kept(g: Grid, p: Params, xyz, pose):
