@@ -178,6 +178,26 @@ def cpu_baseline(w: synth.Workload, budget_s: float = 15.0, max_scans: int | Non
     return pts_total / dt, done, dt
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo, else lscpu, else the ISA)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline_parallel(w: synth.Workload, budget_s: float = 15.0) -> dict:
     """The oracle's points-parallel variant (OpenMP over the returns, atomic
     per-voxel updates, as the paper runs on its host cores) on all host
@@ -200,7 +220,7 @@ def cpu_baseline_parallel(w: synth.Workload, budget_s: float = 15.0) -> dict:
     dt = time.perf_counter() - t0
     return {"value": pts_total / dt, "unit": UNIT, "cores": threads, "kind": "oracle_openmp",
             "sample": f"first {done} scans of the workload, full grid, {dt:.1f} s on "
-                      f"{threads} threads"}
+                      f"{threads} threads", "cpu": cpu_model(), "host_cores": os.cpu_count()}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -232,7 +252,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": workload_config(args, w),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample_desc},
+                             "sample": sample_desc, "cpu": cpu_model(), "host_cores": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -413,7 +433,8 @@ def run_ours(args, rank, world):
         v, nsc_run, secs = cpu_baseline(w, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"first {nsc_run} scans of the workload, full grid, "
-                                          f"{secs:.1f} s of single-thread CPU"}
+                                          f"{secs:.1f} s of single-thread CPU",
+                                "cpu": cpu_model(), "host_cores": os.cpu_count()}
         line["cpu_parallel_baseline"] = cpu_baseline_parallel(w, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
     return 0
