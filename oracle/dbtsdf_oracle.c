@@ -8,13 +8,14 @@
  * shares no code, header, table or constant with the CUDA library.
  *
  * Floating point: every step that turns a float into an integer (voxel index,
- * direction bin) is evaluated in IEEE binary64, in the order written here,
- * with basic operations and the C99 fma() where it is written out; this file
- * must be compiled with -ffp-contract=off so that no other multiply-add is
- * fused.  The arithmetic readings are:
- *   d = R p with each row as fma(r2, z, fma(r1, y, r0 * x)); w = d + t;
- *   c = floor((w - origin) * (1 / res)), 1 / res rounded once;
- *   octahedral u = d_x * (1 / s), v = d_y * (1 / s), s = (|x| + |y|) + |z|.
+ * direction bin) is evaluated in IEEE binary64 with basic operations only
+ * (each rounded to nearest), in the order written here; this file must be
+ * compiled with -ffp-contract=off so that no multiply-add is fused.  The
+ * paper writes the steps as formulas (Sec. III-C: p_w = R p + t, voxel index
+ * floor((p_w - o) / res)); they are evaluated as written:
+ *   d = R p with each row as (r0 * x + r1 * y) + r2 * z; w = d + t;
+ *   c = floor((w - origin) / res), a true division;
+ *   octahedral u = d_x / s, v = d_y / s, s = (|x| + |y|) + |z|.
  *
  * Readings of the paper taken where it is silent or ambiguous (each is listed
  * with its reason in the design notes of the repository):
@@ -123,9 +124,8 @@ int orc_bin_octa(double dx, double dy, double dz, int n)
     double s = (fabs(dx) + fabs(dy)) + fabs(dz);
     if (!(s > 0.0))
         return 0;                       /* no direction (not reached for a rotation) */
-    double inv = 1.0 / s;
-    double u = dx * inv;
-    double v = dy * inv;
+    double u = dx / s;
+    double v = dy / s;
     if (dz < 0.0) {
         double fu = (1.0 - fabs(v)) * orc_sgn(u);
         double fv = (1.0 - fabs(u)) * orc_sgn(v);
@@ -281,14 +281,13 @@ int orc_contact(const orc_params *p, const orc_grid *g, const float *xyz,
     *valid = 1;
     double d[3], w[3];
     for (int r = 0; r < 3; r++) {
-        d[r] = fma(pose[4 * r + 2], pz, fma(pose[4 * r + 1], py, pose[4 * r + 0] * px));
+        d[r] = (pose[4 * r + 0] * px + pose[4 * r + 1] * py) + pose[4 * r + 2] * pz;
         w[r] = d[r] + pose[4 * r + 3];
     }
     int R = (p->kernel_size - 1) / 2;
     int64_t n[3] = {g->nx, g->ny, g->nz};
-    double inv_res = 1.0 / g->res;
     for (int a = 0; a < 3; a++) {
-        double q = floor((w[a] - g->origin[a]) * inv_res);
+        double q = floor((w[a] - g->origin[a]) / g->res);
         if (!(q >= (double)R && q <= (double)(n[a] - 1 - R)))
             return 0;
         c[a] = (int64_t)q;

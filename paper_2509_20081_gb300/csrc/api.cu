@@ -344,6 +344,7 @@ static DevGrid dev_grid(const dbt_grid *g) {
     d.nbx = g->pitch_x / BX;
     d.nby = (g->ny + BY - 1) / BY;
     d.nbz = (g->nz + BZ - 1) / BZ;
+    d.res = g->res;
     d.inv_res = 1.0 / g->res;
     d.ox = g->origin[0];
     d.oy = g->origin[1];

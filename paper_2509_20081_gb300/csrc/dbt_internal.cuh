@@ -77,7 +77,8 @@ struct DevGrid {
     uint16_t *hits;
     int nx, ny, nz, pitch;
     int nbx, nby, nbz;          // bricks per axis
-    double inv_res;             // 1 / res, rounded once on the host
+    double res;                 // voxel edge (the binary64 voxel floor divides by it)
+    double inv_res;             // 1 / res, rounded once on the host (binary32 filter data only)
     double ox, oy, oz;          // origin
 };
 

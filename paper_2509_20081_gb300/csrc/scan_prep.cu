@@ -7,12 +7,15 @@
 //   k_fill      pair payloads into the segments; clears the hash table
 // plus the direction-bin and voxel readout kernels.
 //
-// Float -> integer decisions use binary64 with explicit round-to-nearest
-// intrinsics, so that nvcc cannot contract or reorder them:
-//   d = R p, row r = fma(R_r2, z, fma(R_r1, y, R_r0 * x)); w = d + t
-//   c = floor((w - origin) * inv_res)
-//   octahedral: u = d_x * (1/s), v = d_y * (1/s), s = (|x| + |y|) + |z|
+// Float -> integer decisions are the binary64 evaluation of Sec. III-C's
+// formulas as written, each operation an explicit round-to-nearest
+// intrinsic so that nvcc cannot contract or reorder them:
+//   d = R p, row r = (R_r0 * x + R_r1 * y) + R_r2 * z; w = d + t
+//   c = floor((w - origin) / res), a true division
+//   octahedral: u = d_x / s, v = d_y / s, s = (|x| + |y|) + |z|
 //   Eq. 2: edge comparisons against host-built cos/sin tables.
+// A binary32 filter with rigorous error bounds reaches the same decisions
+// without binary64 for all but the returns near a boundary.
 #include "dbt_internal.cuh"
 
 namespace dbt {
@@ -25,9 +28,8 @@ __device__ __forceinline__ double sgn1(double v) { return v < 0.0 ? -1.0 : 1.0; 
 __device__ int bin_octa(double dx, double dy, double dz, int n) {
     double s = __dadd_rn(__dadd_rn(fabs(dx), fabs(dy)), fabs(dz));
     if (!(s > 0.0)) return 0;
-    double inv = __drcp_rn(s);
-    double u = __dmul_rn(dx, inv);
-    double v = __dmul_rn(dy, inv);
+    double u = __ddiv_rn(dx, s);
+    double v = __ddiv_rn(dy, s);
     if (dz < 0.0) {
         // (1 - |v|) sgn(u): a multiplication by +-1 is an exact sign choice
         const double fu = __dsub_rn(1.0, fabs(v)), fv = __dsub_rn(1.0, fabs(u));
@@ -282,13 +284,14 @@ __device__ __forceinline__ void count_pairs(const WsDev &ws, const DevGrid &g, u
 }
 
 // ------------------------------------------------------------------ K1
-// Map-frame direction d = R p in binary64 (the order the bins are defined on).
+// Map-frame direction d = R p in binary64, each row (r0 x + r1 y) + r2 z
+// with every product and sum rounded on its own (no fused multiply-add).
 __device__ __forceinline__ void direction64(const Pose &pose, double px, double py, double pz,
                                             double d[3]) {
 #pragma unroll
     for (int r = 0; r < 3; ++r)
-        d[r] = __fma_rn(pose.r[3 * r + 2], pz,
-                        __fma_rn(pose.r[3 * r + 1], py, __dmul_rn(pose.r[3 * r + 0], px)));
+        d[r] = __dadd_rn(__dadd_rn(__dmul_rn(pose.r[3 * r + 0], px), __dmul_rn(pose.r[3 * r + 1], py)),
+                         __dmul_rn(pose.r[3 * r + 2], pz));
 }
 
 // Sec. III-C for one return: discard non-finite and origin returns, map-frame
@@ -322,10 +325,10 @@ __device__ __forceinline__ int contact_of(const DevGrid &g, const DevParams &p, 
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             const double w = __dadd_rn(d[r], pose.t[r]);
-            // floor((w - origin) * (1 / res)) as an integer: the conversion
+            // floor((w - origin) / res) as an integer: the conversion
             // rounds toward -inf and saturates, so the bounds test below is
             // the same as on the binary64 value
-            q[r] = __double2ll_rd(__dmul_rn(__dsub_rn(w, org[r]), g.inv_res));
+            q[r] = __double2ll_rd(__ddiv_rn(__dsub_rn(w, org[r]), g.res));
         }
     }
     if (!(q[0] >= p.R && q[0] <= g.nx - 1 - p.R && q[1] >= p.R && q[1] <= g.ny - 1 - p.R &&

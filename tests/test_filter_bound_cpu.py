@@ -73,8 +73,11 @@ def r64(x: Fr) -> float:
     return float(x)                   # correctly rounded
 
 
-def fma64(a, b, c):
-    return r64(Fr(a) * Fr(b) + Fr(c))
+def row64(r, p):
+    """Sec. III-C's row (r0 x + r1 y) + r2 z in binary64, as the oracle and
+    the device's binary64 path evaluate it (no fused multiply-add)."""
+    return r64(Fr(r64(Fr(r64(Fr(r[0]) * Fr(p[0]))) + Fr(r64(Fr(r[1]) * Fr(p[1]))))) +
+               Fr(r64(Fr(r[2]) * Fr(p[2]))))
 
 
 def pose_filter(R, t, org, inv_res):
@@ -97,8 +100,11 @@ def floor_certain(v, e):
     return (sub(v, f) > e and sub(add(f, 1.0), v) > e), int(f)
 
 
-def voxel_checks(R, t, org, inv_res, p):
-    """Returns (decided, floors) and asserts the bounds; p binary32 values."""
+def voxel_checks(R, t, org, res, p):
+    """Returns (decided, floors) and asserts the bounds; p binary32 values.
+    The filter's data use the host's 1 / res; the value it must decide is
+    the binary64 floor((p_w - o) / res) with a true division."""
+    inv_res = 1.0 / res
     fa, fr, fb, fbi, fe0 = pose_filter(R, t, org, inv_res)
     out = []
     decided = True
@@ -107,12 +113,12 @@ def voxel_checks(R, t, org, inv_res, p):
         c = fma(a[2], p[2], fma(a[1], p[1], fma(a[0], p[0], fb[r])))
         S = add(add(add(abs(mul(a[0], p[0])), abs(mul(a[1], p[1]))), abs(mul(a[2], p[2]))), abs(fb[r]))
         e = fma(S, f32(U32_REL), add(fe0[r], f32(U32_ABS)))
-        exact = (sum(Fr(R[r][j]) * Fr(p[j]) for j in range(3)) + Fr(t[r]) - Fr(org[r])) * Fr(inv_res)
+        exact = (sum(Fr(R[r][j]) * Fr(p[j]) for j in range(3)) + Fr(t[r]) - Fr(org[r])) / Fr(res)
         assert abs(Fr(c) + fbi[r] - exact) <= Fr(e), (r, c, e)
         ok, q = floor_certain(c, e)
         # the binary64 value the oracle and the fallback compute
-        d = fma64(R[r][2], p[2], fma64(R[r][1], p[1], r64(Fr(R[r][0]) * Fr(p[0]))))
-        c64 = r64((Fr(r64(Fr(r64(Fr(d) + Fr(t[r]))) - Fr(org[r])))) * Fr(inv_res))
+        d = row64(R[r], p)
+        c64 = r64(Fr(r64(Fr(r64(Fr(d) + Fr(t[r]))) - Fr(org[r]))) / Fr(res))
         if ok:
             assert q + fbi[r] == math.floor(c64), (r, c, e, c64)
         decided = decided and ok
@@ -160,7 +166,7 @@ def direction_checks(orc, po, R, p, n):
         assert abs(Fr(d32[r]) - exact) <= Fr(e32[r])
     b = octa_bin_f32(d32, e32, n)
     if b >= 0:
-        d64 = [fma64(R[r][2], p[2], fma64(R[r][1], p[1], r64(Fr(R[r][0]) * Fr(p[0])))) for r in range(3)]
+        d64 = [row64(R[r], p) for r in range(3)]
         assert b == orc.bin_of(po, np.array(d64)), (p, d32, b)
     return b >= 0
 
@@ -175,13 +181,12 @@ def test_voxel_bound_random(seed, res):
     R = _rotation(rng)
     t = (rng.uniform(3, -120.0, 120.0)).tolist()
     org = (rng.uniform(3, -1000.0, 1000.0)).tolist()
-    inv = 1.0 / res
     decided = 0
     for k in range(300):
         dr = rng.normal(3)
         rr = float(rng.uniform(1, 0.01, 80.0)[0])
         p = [f32(x) for x in (dr / np.linalg.norm(dr) * rr)]
-        ok, _ = voxel_checks(R, t, org, inv, p)
+        ok, _ = voxel_checks(R, t, org, res, p)
         decided += ok
     assert decided > 280          # the filter decides nearly every return
 
@@ -201,7 +206,7 @@ def test_voxel_bound_on_faces():
         vox = rng.integers(3, 20, 380).astype(np.float64)
         w = np.array(org) + vox * res + rng.normal(3) * 1e-9
         p = [f32(x) for x in (Rn.T @ (w - np.array(t)))]
-        ok, _ = voxel_checks(R, t, org, 1.0 / res, p)
+        ok, _ = voxel_checks(R, t, org, res, p)
         deferred += not ok
     assert deferred > 100
 

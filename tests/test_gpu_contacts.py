@@ -167,3 +167,21 @@ def test_urban_scans_full_size(orc):
         inside = check_contacts(orc, _params(**w.params), (w.grid.nx, w.grid.ny, w.grid.nz),
                                 w.grid.res, w.grid.origin, pts, pose)
         assert inside > 30000
+
+
+def test_floors_follow_the_written_formulas(orc):
+    """Returns crafted so that a reciprocal multiply (voxel floor, octahedral
+    u) or a fused transform would land in another voxel or cell
+    (tests/contact_cases.py): the device gives the written form's answer,
+    the oracle's.  All of them take the binary64 path (each lies within an
+    ulp of a boundary)."""
+    import contact_cases as cc
+    for c in cc.all_cases():
+        pd = _params(kernel_size=c.kernel_size, shadow_radius=1.0)
+        assert check_contacts(orc, pd, c.dims, c.res, c.origin, c.pts, c.pose) == 1
+        dbt = _dbt()
+        k = dbt.Kernels(dbt.make_params(**pd))
+        g = dbt.Grid(*c.dims, c.res, c.origin)
+        out = dbt.dbt_scan_contacts(g, k, torch.from_numpy(c.pts).cuda(), c.pose).cpu().numpy()
+        got = tuple(int(v) for v in out[0, :3]) if c.kind != "octa" else (int(out[0, 3]),)
+        assert got == c.plain and got != c.variant, (c.kind, got, c.plain, c.variant)

@@ -36,8 +36,8 @@ MUTATIONS = {
                           "                        h_new = p->hit_max;\n"
                           "                    g->hits[v] = (uint16_t)h_new;",
                           "                    g->hits[v] = (uint16_t)h_new;"),
-    "pose_transposed": ("d[r] = fma(pose[4 * r + 2], pz, fma(pose[4 * r + 1], py, pose[4 * r + 0] * px));",
-                        "d[r] = fma(pose[4 * 2 + r], pz, fma(pose[4 * 1 + r], py, pose[4 * 0 + r] * px));"),
+    "pose_transposed": ("d[r] = (pose[4 * r + 0] * px + pose[4 * r + 1] * py) + pose[4 * r + 2] * pz;",
+                        "d[r] = (pose[4 * 0 + r] * px + pose[4 * 1 + r] * py) + pose[4 * 2 + r] * pz;"),
     "translation_dropped": ("w[r] = d[r] + pose[4 * r + 3];", "w[r] = d[r];"),
     "boundary_off_by_one": ("if (!(q >= (double)R && q <= (double)(n[a] - 1 - R)))",
                             "if (!(q >= (double)R && q <= (double)(n[a] - R)))"),
@@ -59,6 +59,12 @@ MUTATIONS = {
                         "        while (0)\n            dpsi += 2.0 * ORC_PI;"),
     "full_interp_wrong_side": ("Q[r][c] = R0[r][0] * E[0][c] + R0[r][1] * E[1][c] + R0[r][2] * E[2][c];",
                                "Q[r][c] = E[r][0] * R0[0][c] + E[r][1] * R0[1][c] + E[r][2] * R0[2][c];"),
+    "voxel_reciprocal": ("double q = floor((w[a] - g->origin[a]) / g->res);",
+                         "double q = floor((w[a] - g->origin[a]) * (1.0 / g->res));"),
+    "transform_fused": ("d[r] = (pose[4 * r + 0] * px + pose[4 * r + 1] * py) + pose[4 * r + 2] * pz;",
+                        "d[r] = fma(pose[4 * r + 2], pz, fma(pose[4 * r + 1], py, pose[4 * r + 0] * px));"),
+    "octa_reciprocal": ("    double u = dx / s;\n    double v = dy / s;",
+                        "    double u = dx * (1.0 / s);\n    double v = dy * (1.0 / s);"),
     "octa_dir_not_folded": ("    if (Z < 0.0) {\n        double fu = ((double)n - fabs(V)) * orc_sgn(U);",
                             "    if (Z < -1e300) {\n        double fu = ((double)n - fabs(V)) * orc_sgn(U);"),
 }
@@ -86,6 +92,7 @@ def _battery(room):
         lambda: pins.test_first_return_rule_uses_first_bin(orc),
         lambda: pins.test_border_returns_change_nothing(orc),
         lambda: pins.test_rs0_hits_count_points_per_voxel(orc, room),
+        lambda: pins.test_contact_floors_follow_the_written_formulas(orc),
         lambda: deskew.test_downsampling_is_every_ds_th_return(orc, 3),
         lambda: deskew.test_one_pose_per_slice_equals_returns_one_by_one(orc),
         lambda: [deskew.test_interp_endpoints_and_rotations(orc, k, m) for k in range(4) for m in (0, 1)],

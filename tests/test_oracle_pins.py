@@ -269,11 +269,6 @@ def test_single_point_worked_example(orc):
 
 
 # ------------------------------------------------------------------ brute force
-def _fma(a, b, c):
-    """Exactly rounded a * b + c via rational arithmetic."""
-    return float(Fraction(a) * Fraction(b) + Fraction(c))
-
-
 def _brute_force(orc, p, dims, res, origin, scans):
     """Gather form of Sec. III-C: per voxel, min ceil-distance over kept
     returns in range and the count of returns whose shadow covers it."""
@@ -289,10 +284,10 @@ def _brute_force(orc, p, dims, res, origin, scans):
                 continue
             if px == 0.0 and py == 0.0 and pz == 0.0:
                 continue
-            d = [_fma(pose[r][2], pz, _fma(pose[r][1], py, pose[r][0] * px)) for r in range(3)]
+            # Sec. III-C as written: p_w = R p + t, floor((p_w - o) / res)
+            d = [(pose[r][0] * px + pose[r][1] * py) + pose[r][2] * pz for r in range(3)]
             w = [d[r] + pose[r][3] for r in range(3)]
-            inv_res = 1.0 / res
-            c = [math.floor((w[a] - origin[a]) * inv_res) for a in range(3)]
+            c = [math.floor((w[a] - origin[a]) / res) for a in range(3)]
             if any(c[a] < R or c[a] > (nx, ny, nz)[a] - 1 - R for a in range(3)):
                 continue
             if p.dedup_first:
@@ -508,3 +503,27 @@ def test_signed_distance_readout(orc):
     assert orc.signed_distance(0x7, 1, 0.1) == pytest.approx(0.3)
     assert orc.signed_distance(0x1F, 0, 0.05) == pytest.approx(-0.25)
     assert orc.signed_distance(0x0, 0, 0.05) == 0.0
+
+
+# ------------------------------------------------------------------ arithmetic of the floors
+def test_contact_floors_follow_the_written_formulas(orc):
+    """Sec. III-C: p_w = R p + t and voxel floor((p_w - o) / res), evaluated
+    as written (unfused products and sums, a true division; the octahedral
+    u = d_x / s likewise).  On returns crafted so that a reciprocal multiply
+    or a fused transform would give another voxel or cell (rational
+    emulation in tests/contact_cases.py), the oracle gives the written
+    form's answer, which where it is decided is also the floor of the exact
+    real value."""
+    import contact_cases as cc
+    cases = cc.all_cases()
+    assert {c.kind for c in cases} == {"division", "transform", "octa"}
+    for c in cases:
+        assert c.plain != c.variant
+        p = orc.params(kernel_size=c.kernel_size)
+        g = orc.Grid(c.dims[0], c.dims[1], c.dims[2], c.res, c.origin, None, None, None)
+        cont, bins = orc.scan_kept(g, p, c.pts, c.pose)
+        assert len(cont) == 1, c
+        got = tuple(int(v) for v in cont[0]) if c.kind != "octa" else (int(bins[0]),)
+        assert got == c.plain, (c.kind, got, c.plain, c.variant)
+        if c.exact is not None:
+            assert got == c.exact
