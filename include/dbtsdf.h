@@ -365,13 +365,23 @@ dbt_status dbt_workspace_autotune(const dbt_grid *g, const dbt_kernels *k, dbt_w
  * with DBT_EINVAL and a message.  The 22 MiB array occupies device memory on
  * every GPU that loads the library until the process exits.  All calls share
  * it: calls whose work overlaps on the GPU race, so issue them on one stream
- * (or otherwise serialise them).  The first call on a device looks up the
- * array's device address; make it before capturing a stream into a graph.
+ * (or otherwise serialise them).  The first call in a CUDA context looks up
+ * the array's device address in that context (the address is remembered per
+ * context, so a context created later, e.g. after cudaDeviceReset, gets its
+ * own); make that first call before capturing a stream into a graph.
  * Other arguments as dbt_integrate_scan; *h_stats (may be NULL) receives the
  * scan's counters asynchronously, like dbt_integrate_scan_host. */
 dbt_status dbt_integrate_scan_noalloc(const dbt_grid *g, const dbt_kernels *k, const float *d_xyz,
                                       int64_t n, const double pose[12], dbt_scan_stats *h_stats,
                                       void *stream);
+
+/* Whether dbt_integrate_scan_noalloc can take a scan of n returns on a grid
+ * of nx x ny x nz voxels (rows padded to a multiple of 32, as
+ * dbt_grid_layout pads them) at kernel size kernel_size: DBT_OK, or
+ * DBT_EINVAL with the reason in dbt_last_error().  The entry point applies
+ * the same check (to the grid's own pitch) before any CUDA call.  Host only:
+ * no CUDA call, no GPU needed.  The paper has no counterpart. */
+dbt_status dbt_noalloc_check(int32_t nx, int32_t ny, int32_t nz, int32_t kernel_size, int64_t n);
 
 /* Synchronises stream and copies the last scan's counters (may be NULL).
  * Returns DBT_ESTATE when the device latched an error. */

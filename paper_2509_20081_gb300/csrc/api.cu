@@ -402,18 +402,19 @@ static size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
 // staging: two host-input staging buffers (dbt_integrate_scan_host copies
 // the next scan into one while the previous scan reads the other); the
 // no-allocation entry point takes device input only and needs none.
-static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long max_points, WsLayout *L,
-                            bool staging = true) {
+// Scratch layout for grids of pitch_x x ny x nz voxels and kernel size K.
+static dbt_status ws_layout_dims(int pitch_x, int ny, int nz, int K, long long max_points,
+                                 WsLayout *L, bool staging) {
     if (max_points < 1 || max_points > (1ll << 30))
         return fail(DBT_EINVAL, "max_points must be in [1, 2^30]");
-    const DevGrid d = dev_grid(g);
-    const unsigned long long nb = (unsigned long long)d.nbx * d.nby * d.nbz;
+    const unsigned long long nb = (unsigned long long)(pitch_x / BX) * ((ny + BY - 1) / BY) *
+                                  ((nz + BZ - 1) / BZ);
     if (nb >= (1ull << 32)) return fail(DBT_EINVAL, "too many bricks");
     L->nbricks = (uint32_t)nb;
     uint32_t hc = 64;
     while (hc < 2ull * (unsigned long long)max_points) hc <<= 1;
     L->hcap_alloc = hc;
-    L->pairs_cap = (unsigned long long)max_points * max_pairs_per_return(k->dp.K);
+    L->pairs_cap = (unsigned long long)max_points * max_pairs_per_return(K);
     L->max_touched = (uint32_t)std::min<unsigned long long>(nb, L->pairs_cap);
     size_t o = 0;
     L->hdr = o;      o += up256(sizeof(WsHeader));
@@ -432,6 +433,11 @@ static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long m
     L->poses = o;    o += up256((size_t)MAX_SCAN_POSES * sizeof(Pose));
     L->total = o;
     return DBT_OK;
+}
+
+static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long max_points, WsLayout *L,
+                            bool staging = true) {
+    return ws_layout_dims(g->pitch_x, g->ny, g->nz, k->dp.K, max_points, L, staging);
 }
 
 struct dbt_workspace {
@@ -851,23 +857,45 @@ extern "C" dbt_status dbt_pose_ramp(const double start[12], const double end[12]
 // no-allocation entry point): a workspace view lives on the stack, the
 // regions that must start at zero are cleared on the stream, and nothing is
 // allocated on the host or the device.
-dbt_status dbt::integrate_on_scratch(const dbt_grid *g, const dbt_kernels *k, const float *d_xyz,
-                                     int64_t n, const double pose[12], void *scratch,
-                                     size_t scratch_bytes, long long max_points,
-                                     dbt_scan_stats *h_stats, cudaStream_t s) {
-    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
-    dbt_status st = check_grid(g);
-    if (st != DBT_OK) return st;
+dbt_status dbt::report_einval(const char *msg) { return fail(DBT_EINVAL, "%s", msg); }
+
+dbt_status dbt::scratch_fits(int32_t pitch_x, int32_t ny, int32_t nz, int32_t K, int64_t n,
+                             size_t bytes, long long max_points) {
+    if (K < 1 || K > MAX_K || (K % 2) == 0)
+        return fail(DBT_EINVAL, "kernel_size must be odd and in [1, %d]", MAX_K);
+    if (pitch_x < 32 || (pitch_x % 32) != 0 || ny < 1 || nz < 1)
+        return fail(DBT_EINVAL, "grid dims must be >= 1 (pitch a multiple of 32)");
     if (n < 0 || n > max_points)
         return fail(DBT_EINVAL, "n = %lld exceeds the no-allocation limit of %lld returns per scan",
                     (long long)n, max_points);
     WsLayout L;
-    st = ws_layout(g, k, max_points, &L, false);
+    dbt_status st = ws_layout_dims(pitch_x, ny, nz, K, max_points, &L, false);
     if (st != DBT_OK) return st;
-    if (L.total > scratch_bytes)
+    if (L.total > bytes)
         return fail(DBT_EINVAL,
                     "grid too large for the no-allocation scratch: needs %zu bytes, limit %zu "
-                    "(%u bricks of 32x8x8 voxels)", L.total, scratch_bytes, L.nbricks);
+                    "(%u bricks of 32x8x8 voxels)", L.total, bytes, L.nbricks);
+    return DBT_OK;
+}
+
+dbt_status dbt::scratch_fits_grid(const dbt_grid *g, const dbt_kernels *k, int64_t n, size_t bytes,
+                                  long long max_points) {
+    if (!k) return fail(DBT_EINVAL, "kernels is NULL");
+    dbt_status st = check_grid(g);
+    if (st != DBT_OK) return st;
+    return scratch_fits(g->pitch_x, g->ny, g->nz, k->dp.K, n, bytes, max_points);
+}
+
+dbt_status dbt::integrate_on_scratch(const dbt_grid *g, const dbt_kernels *k, const float *d_xyz,
+                                     int64_t n, const double pose[12], void *scratch,
+                                     size_t scratch_bytes, long long max_points,
+                                     dbt_scan_stats *h_stats, cudaStream_t s) {
+    dbt_status st = scratch_fits_grid(g, k, n, scratch_bytes, max_points);
+    if (st != DBT_OK) return st;
+    if (!scratch) return fail(DBT_EINVAL, "scratch is NULL");
+    WsLayout L;
+    st = ws_layout(g, k, max_points, &L, false);
+    if (st != DBT_OK) return st;
     dbt_workspace w;
     st = ws_bind(&w, g, k, max_points, L, scratch);
     if (st != DBT_OK) return st;

@@ -310,6 +310,17 @@ void mc_table_host(uint8_t *ntri, uint8_t *edges);
 // Sets the thread's error message for a failed CUDA call; returns DBT_ECUDA.
 dbt_status report_cuda_error(cudaError_t e, const char *what);
 
+// Limits of a fixed scratch of `bytes` for scans of up to max_points
+// returns: n returns on a grid of pitch_x x ny x nz voxels at kernel size K
+// (DBT_EINVAL with a message when they do not fit); host only, no CUDA call.
+dbt_status scratch_fits(int32_t pitch_x, int32_t ny, int32_t nz, int32_t K, int64_t n,
+                        size_t bytes, long long max_points);
+// The same for grid g and kernels k (also checks the grid's fields).
+dbt_status scratch_fits_grid(const dbt_grid *g, const dbt_kernels *k, int64_t n, size_t bytes,
+                             long long max_points);
+// Sets the thread's error message; returns DBT_EINVAL.
+dbt_status report_einval(const char *msg);
+
 // One scan on a caller-provided scratch buffer (see noalloc.cu); defined in api.cu.
 dbt_status integrate_on_scratch(const dbt_grid *g, const dbt_kernels *k, const float *d_xyz,
                                 int64_t n, const double pose[12], void *scratch,

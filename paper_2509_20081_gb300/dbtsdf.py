@@ -120,6 +120,8 @@ _SIGS = {
     "dbt_batch_destroy": [_vp],
     "dbt_integrate_scan_noalloc": [_P(dbt_grid), _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
                                    _P(dbt_scan_stats), _vp],
+    "dbt_noalloc_check": [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                          ctypes.c_int64],
     "dbt_scan_footprint": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
                            _vp, ctypes.c_size_t, _P(ctypes.c_int64), _vp],
     "dbt_integrate_scan_ex": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
@@ -578,6 +580,12 @@ def dbt_integrate_scan_noalloc(grid: Grid, kernels: Kernels, xyz, pose,
                                             xyz.data_ptr() if n else None, n, pp,
                                             ctypes.byref(stats) if stats is not None else None,
                                             _stream_ptr(stream)))
+
+
+def dbt_noalloc_check(nx: int, ny: int, nz: int, kernel_size: int, n: int) -> None:
+    """Raises DbtError (DBT_EINVAL) when dbt_integrate_scan_noalloc cannot
+    take n returns on an nx x ny x nz grid at this kernel size.  Host only."""
+    _check(lib().dbt_noalloc_check(nx, ny, nz, kernel_size, n))
 
 
 class Batch:

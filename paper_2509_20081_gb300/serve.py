@@ -63,6 +63,36 @@ def grid_bytes(nx: int, ny: int, nz: int) -> int:
     return mb + sb + hb
 
 
+def check_scan_size(n: int, max_round_points: int) -> None:
+    """A scan larger than a round's point budget could never be scheduled
+    (it would wait forever and hold its robot's later scans behind it), so
+    it is refused when submitted."""
+    if n > max_round_points:
+        raise ValueError(f"scan of {n} returns exceeds the round budget of "
+                         f"{max_round_points} returns (max_round_points)")
+
+
+def select_round(order, busy_maps, pending, max_round_points: int, max_round_items: int):
+    """Scans of the next round: for each map in order that is not in a round
+    already, the longest prefix of its pending scans (scans of one map stay
+    in arrival order) that keeps the round within max_round_points returns
+    and max_round_items scans.  Returns [(map, number of scans taken)]."""
+    takes, pts, n_items = [], 0, 0
+    for rid in order:
+        if rid in busy_maps or not pending[rid]:
+            continue
+        k = 0
+        for sc in pending[rid]:
+            if pts + sc.n > max_round_points or n_items + k >= max_round_items:
+                break
+            k += 1
+            pts += sc.n
+        if k:
+            takes.append((rid, k))
+            n_items += k
+    return takes
+
+
 @dataclass
 class _Slot:
     stream: object
@@ -171,22 +201,16 @@ class Server:
         if scan.robot not in self.grids:
             raise KeyError(f"robot {scan.robot} has no admitted map")
         scan.n = int(scan.xyz.shape[0])
+        check_scan_size(scan.n, self.max_round_points)
         self.pending[scan.robot].append(scan)
 
     def _launch(self, slot: _Slot, now: float):
-        items, scans, maps, pts = [], [], set(), 0
-        for rid in self.order:
-            if rid in self.busy_maps or not self.pending[rid]:
-                continue
-            take = []
-            for sc in self.pending[rid]:
-                if pts + sc.n > self.max_round_points or len(items) + len(take) >= self.max_round_items:
-                    break
-                take.append(sc)
-                pts += sc.n
-            if not take:
-                continue
-            del self.pending[rid][:len(take)]
+        takes = select_round(self.order, self.busy_maps, self.pending, self.max_round_points,
+                             self.max_round_items)
+        items, scans, maps = [], [], set()
+        for rid, k in takes:
+            take = self.pending[rid][:k]
+            del self.pending[rid][:k]
             maps.add(rid)
             for sc in take:
                 items.append((self.index[rid], sc.xyz, sc.pose))
