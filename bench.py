@@ -16,13 +16,24 @@ trajectory order from an empty map (scan k = trajectory scan k mod 100), as
 in online mapping.  The 5.7 GB grid exceeds the 129 MB L2; consecutive scans
 share map regions as a moving robot's do, and no L2 flush is inserted.
 
-value: returns/s with the scans resident in HBM; e2e: the same through the
-host-buffer entry point dbt_integrate_scan_host (pinned host scans copied
-in, scan counters copied out, inside the timed region).  roofline: the brick
-integration kernel's algorithmic bytes (4 U + 4 W + 6 U_s per scan: read
-every covered mask, write the masks that change, read and write counter and
-sign of every shadow voxel; U, U_s and W counted exactly per scan before
-timing) over its CUDA-event time, against the measured HBM copy bandwidth.
+value: kept returns integrated per second (the returns that reach Eqs.
+4-6: valid, neighbourhood inside the map, first of their voxel), with the
+scans resident in HBM; raw_points_per_s counts every return handed in.
+e2e: the same through the host-buffer entry point dbt_integrate_scan_host
+(pinned host scans copied in, scan counters copied out, inside the timed
+region).  roofline: the brick integration kernel against two ceilings --
+bytes, 12 N + 8 U + 6 U_s + 96 per scan (points in, read and write every
+covered mask, counter and sign of every shadow voxel, the pose; U and U_s
+counted exactly per scan before timing) over the measured HBM copy
+bandwidth, and ops, N_kept K^3 voxel-ANDs plus the shadow increments (Eq. 7)
+over the measured peak rates of the kernel's own shared-memory updates
+(dbt_op_rates) -- frac = the larger ceiling time over the kernel's CUDA-event
+time.  Extra keys: per-scan latency over all 100 workload scans, the batched
+graph-replayed form, the high-resolution workload (2000 x 2000 x 400 at 0.02
+m, 262,144 returns per scan), the paper's parameters (K = 21, 40 x 40 az/el
+bins) on the room and urban scans, 32 uneven maps in one graph against 256
+plain launches, and the serving loop (continuous batching against FIFO at
+equal offered loads).
 
 --impl reference times the oracle (plain single-threaded C) on the same
 workload and metric, on a bounded sample of returns per step.
@@ -96,54 +107,125 @@ def load_workload(name: str) -> synth.Workload:
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi sampling during the timed region (SM clock, throttle reasons)."""
+    """SM clock and clock-event (throttle) reasons sampled during the run.
+
+    NVML (libnvidia-ml, read-only queries) is polled from a thread every
+    ~0.25 ms, so that even a few-millisecond timed region gets samples;
+    without NVML, nvidia-smi is run at its fastest period (20 ms).
+    mark() stamps a region; stats(region) summarises its samples."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # nvmlClocksEventReason* bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, pci_bus_id: str | None = None, period_s: float = 0.00025):
+        import threading
+        self.samples = []            # (time, sm_mhz, reasons bitmask)
+        self.max_mhz = None
+        self.marks = {}
         self.proc = None
         self.path = None
+        self.thread = None
+        self.stop_flag = threading.Event()
+        self.source = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            ok = False
+            if pci_bus_id:
+                ok = nv.nvmlDeviceGetHandleByPciBusId_v2(pci_bus_id.encode(), ctypes.byref(h)) == 0
+            if not ok and nv.nvmlDeviceGetHandleByIndex_v2(gpu_index, ctypes.byref(h)) != 0:
+                raise OSError("no NVML handle")
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:     # NVML_CLOCK_SM
+                self.max_mhz = float(mx.value)
+            reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+
+            def poll():
+                c = ctypes.c_uint()
+                r = ctypes.c_ulonglong()
+                while not self.stop_flag.is_set():
+                    if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(c)) == 0:
+                        rr = r.value if reasons_fn(h, ctypes.byref(r)) == 0 else 0
+                        self.samples.append((time.perf_counter(), float(c.value), rr))
+                    time.sleep(period_s)
+            self.thread = threading.Thread(target=poll, daemon=True)
+            self.thread.start()
+            self.source = "nvml"
+        except (OSError, AttributeError):
+            self._start_smi(gpu_index)
+
+    def _start_smi(self, gpu_index):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                  "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            self.source = "nvidia-smi"
         except Exception:
             self.proc = None
 
     def wait_first(self, timeout_s: float = 5.0):
-        """Blocks until nvidia-smi has written its first sample (it takes a
-        moment to start), so that the samples cover the timed region."""
+        """Blocks until the first sample exists, so that samples cover what follows."""
         t_end = time.time() + timeout_s
-        while self.proc is not None and time.time() < t_end:
-            if os.path.getsize(self.path) > 0:
+        while time.time() < t_end:
+            if self.samples or (self.path and os.path.exists(self.path) and os.path.getsize(self.path) > 0):
                 return
-            time.sleep(0.01)
+            if self.thread is None and self.proc is None:
+                return
+            time.sleep(0.001)
+
+    def mark(self, name: str, begin: bool):
+        self.marks.setdefault(name, [None, None])[0 if begin else 1] = time.perf_counter()
 
     def stop(self):
-        if self.proc is None:
-            return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) >= 9:
-                rows.append(f)
-        os.unlink(self.path)
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=2)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            now = time.perf_counter()
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    bits = sum(b for b, k in ((0x8, 5), (0x40, 6), (0x20, 7), (0x4, 8))
+                               if f[k].lower() == "active")
+                    self.samples.append((now, float(f[1]), bits))
+                    if f[2].replace(".", "").isdigit():
+                        self.max_mhz = max(self.max_mhz or 0.0, float(f[2]))
+            os.unlink(self.path)
+
+    def stats(self, region: str | None = None):
+        rows = self.samples
+        if region is not None and self.source == "nvml" and region in self.marks:
+            t0, t1 = self.marks[region]
+            rows = [r for r in rows if t0 is not None and t1 is not None and t0 <= r[0] <= t1]
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+        bits = 0
+        for r in rows:
+            bits |= r[2]
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(v for b, v in self.REASONS.items() if bits & b),
+                "samples": len(rows), "source": self.source}
+
+
+def pci_bus_id(torch, dev) -> str | None:
+    p = torch.cuda.get_device_properties(dev)
+    try:
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except AttributeError:
+        return None
 
 
 def measured_peaks():
@@ -168,14 +250,16 @@ def cpu_baseline(w: synth.Workload, budget_s: float = 15.0, max_scans: int | Non
     t0 = time.perf_counter()
     done = 0
     pts_total = 0
+    kept_total = 0
     for pts, pose in w.scans:
-        oracle.integrate_scan(g, p, pts, pose)
+        st = oracle.integrate_scan(g, p, pts, pose)
         done += 1
         pts_total += len(pts)
+        kept_total += st["n_kept"]
         if time.perf_counter() - t0 > budget_s or (max_scans and done >= max_scans):
             break
     dt = time.perf_counter() - t0
-    return pts_total / dt, done, dt
+    return pts_total / dt, done, dt, kept_total / dt
 
 
 def cpu_model() -> str:
@@ -211,14 +295,17 @@ def cpu_baseline_parallel(w: synth.Workload, budget_s: float = 15.0) -> dict:
     t0 = time.perf_counter()
     done = 0
     pts_total = 0
+    kept_total = 0
     for pts, pose in w.scans:
-        oracle.integrate_scan_omp(g, p, pts, pose, threads=threads)
+        st = oracle.integrate_scan_omp(g, p, pts, pose, threads=threads)
         done += 1
         pts_total += len(pts)
+        kept_total += st["n_kept"]
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": pts_total / dt, "unit": UNIT, "cores": threads, "kind": "oracle_openmp",
+    return {"value": kept_total / dt, "raw_points_per_s": pts_total / dt, "unit": UNIT,
+            "cores": threads, "kind": "oracle_openmp",
             "sample": f"first {done} scans of the workload, full grid, {dt:.1f} s on "
                       f"{threads} threads", "cpu": cpu_model(), "host_cores": os.cpu_count()}
 
@@ -234,23 +321,29 @@ def run_reference(args, rank, world):
     stride = args.ref_stride
     times = []
     pts_done = 0
+    kept_done = 0
     for s in range(args.warmup + args.steps):
         pts, pose = w.scans[s % len(w.scans)]
         sample = np.ascontiguousarray(pts[::stride])
         t0 = time.perf_counter()
-        oracle.integrate_scan(g, p, sample, pose)
+        st = oracle.integrate_scan(g, p, sample, pose)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
             pts_done += len(sample)
+            kept_done += st["n_kept"]
     total = sum(times)
-    value = pts_done / total
+    value = kept_done / total
     sample_desc = (f"every {stride}th return of each scan ({pts_done // max(1, args.steps)} "
-                   f"returns/step) of the {args.workload} workload, grid at full size")
+                   f"returns/step, {kept_done // max(1, args.steps)} kept) of the "
+                   f"{args.workload} workload, grid at full size")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": workload_config(args, w),
+            "points_counted": "kept returns (valid, K^3 neighbourhood inside the map, first of "
+                              "their voxel)",
+            "raw_points_per_s": pts_done / total,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample_desc, "cpu": cpu_model(), "host_cores": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -269,175 +362,330 @@ def workload_config(args, w):
 
 
 # ------------------------------------------------------------------ our arm
-def run_ours(args, rank, world):
-    import torch
+class Ctx:
+    """What every leg of our arm shares: the modules, the device, the
+    measured peaks and the clock sampler."""
 
-    import paper_2509_20081_gb300 as dbt
-    from paper_2509_20081_gb300 import dbtsdf as B
+    def __init__(self, args, rank, world):
+        import torch
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    w = load_workload(args.workload)
+        import paper_2509_20081_gb300 as dbt
+        from paper_2509_20081_gb300 import dbtsdf as B
+        self.torch, self.dbt, self.B = torch, dbt, B
+        self.args, self.rank, self.world = args, rank, world
+        self.dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+        torch.cuda.set_device(self.dev)
+        self.stream = torch.cuda.current_stream()
+        self.peak, self.peak_kind = measured_peaks()
+        self._op_rates = None
+        self.clocks = ClockSampler(self.dev.index, pci_bus_id(torch, self.dev)) if rank == 0 else None
+        if self.clocks:
+            self.clocks.wait_first()
+
+    def op_rates(self):
+        if self._op_rates is None:
+            self._op_rates = self.B.dbt_op_rates(1 << 14)
+        return self._op_rates
+
+    def barrier(self):
+        if self.world > 1:
+            self.torch.distributed.barrier()
+
+
+def shadow_sizes(B, params) -> np.ndarray:
+    """|S_b| per bin, from the library's host-built tables (Sec. III-B)."""
+    _, sh = B.dbt_tables_host(params)
+    return sh.reshape(sh.shape[0], -1).astype(np.int64).sum(1)
+
+
+def scan_work(ctx, g, k, ws, params, x, pose, bits, s_sizes) -> dict:
+    """Exact work of one scan, outside any timed region: N returns handed
+    in, U and U_s (distinct voxels under the kept returns' K^3 neighbourhoods
+    and shadow sets, dbt_scan_footprint), the kept returns (first of their
+    contact voxel among those inside, from dbt_scan_contacts) and their
+    shadow increments sum |S_b|."""
+    dbt, B = ctx.dbt, ctx.B
+    u, us = B.dbt_scan_footprint(g, k, ws, x, pose, bits)
+    c = dbt.dbt_scan_contacts(g, k, x, pose).cpu().numpy()
+    v = c[:, 0] >= 0
+    key = (c[v, 2].astype(np.int64) * g.c.ny + c[v, 1]) * g.c.pitch_x + c[v, 0]
+    bins = c[v, 3]
+    if params.dedup_first:
+        _, first = np.unique(key, return_index=True)
+        bins = bins[first]
+    return {"n": int(x.shape[0]), "u": int(u), "us": int(us), "kept": int(len(bins)),
+            "shadow": int(s_sizes[bins].sum())}
+
+
+def alg_bytes(wk: dict) -> int:
+    """Bytes one scan must move at least (12 N + 8 U + 6 U_s + 96): its
+    returns in, each covered mask read and written, counter (2 + 2) and sign
+    (1 + 1) of each shadow voxel, the binary64 pose."""
+    return 12 * wk["n"] + 8 * wk["u"] + 6 * wk["us"] + 96
+
+
+def roofline(ctx, works: list, ms_int: float, K: int, traffic) -> dict:
+    """The integrate kernel against its byte and op ceilings; frac = the
+    larger ceiling time over the measured time."""
+    and_rate, cnt_rate = ctx.op_rates()
+    ab = statistics.mean(alg_bytes(w) for w in works)
+    n_and = statistics.mean(w["kept"] * K ** 3 for w in works)
+    n_cnt = statistics.mean(w["shadow"] for w in works)
+    t = ms_int * 1e-3
+    t_hbm = ab / (ctx.peak * 1e9)
+    t_op = n_and / and_rate + n_cnt / cnt_rate
+    op_side = {"voxel_ands": n_and, "counter_incs": n_cnt, "and_per_s": and_rate,
+               "count_per_s": cnt_rate, "t_ms": t_op * 1e3, "frac": t_op / t,
+               "source": "dbt_op_rates micro-benchmark on this GPU (Eq. 4 as byte-wise minima of "
+                         "packed codes, Eq. 5 16-bit increments, shared memory, 4 CTAs/SM)"}
+    hbm_side = {"alg_bytes": ab, "t_ms": t_hbm * 1e3, "frac": t_hbm / t,
+                "achieved_gbs": ab / t / 1e9, "peak_gbs": ctx.peak}
+    base = {"kernel": "k_integrate", "ms_per_launch": ms_int, "traffic": traffic,
+            "alg_bytes_per_launch": ab, "peak_source": f"{ctx.peak_kind} hbm_gbs",
+            "hbm_side": hbm_side, "op_side": op_side}
+    if t_hbm >= t_op:
+        base.update({"bound": "hbm", "achieved": ab / t / 1e9, "peak": ctx.peak, "unit": "GB/s",
+                     "frac": t_hbm / t})
+    else:
+        ops = n_and + n_cnt
+        base.update({"bound": "alu", "achieved": ops / t / 1e12, "peak": ops / t_op / 1e12,
+                     "unit": "T updates/s", "frac": t_op / t})
+    return base
+
+
+def plain_leg(ctx, w, pdict, steps: int, warmup: int, autotune: bool, e2e: bool = False,
+              region: str | None = None, latency_scans: int | None = None, traffic_fn=None):
+    """Per-scan launches of w's scans on a fresh map: the timed region (K
+    scans back to back, the integrate kernel of every tenth bracketed by
+    events), per-scan latency over the workload's scans (an event between
+    scans), optionally the host-buffer entry point."""
+    torch, dbt, B = ctx.torch, ctx.dbt, ctx.B
+    stream = ctx.stream
     nsc = len(w.scans)
-    npts = len(w.scans[0][0])
-    p = dbt.make_params(**w.params)
+    p = dbt.make_params(**pdict)
     k = dbt.Kernels(p)
     g = dbt.Grid(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.res, w.grid.origin)
-    ws = dbt.Workspace(g, k, npts)
-    d_scans = [torch.from_numpy(s[0]).to(dev) for s in w.scans]
+    ws = dbt.Workspace(g, k, max(len(s[0]) for s in w.scans))
+    d_scans = [torch.from_numpy(np.ascontiguousarray(s[0])).to(ctx.dev) for s in w.scans]
     poses = [s[1] for s in w.scans]
-    stream = torch.cuda.current_stream()
-
-    # exact footprint (U, U_s) and changed masks W per scan, from an empty map
-    bits = torch.empty(B.footprint_bytes(g), dtype=torch.uint8, device=dev)
-    alg = []
-    kept = []
-    for s in range(nsc):
-        u, us = B.dbt_scan_footprint(g, k, ws, d_scans[s], poses[s], bits)
-        before = g.mask.clone()
-        dbt.dbt_integrate_scan(g, k, ws, d_scans[s], poses[s])
-        st = dbt.dbt_get_scan_stats(ws)
-        wchg = int((g.mask != before).sum())
-        del before
-        alg.append(4 * u + 4 * wchg + 6 * us)
-        kept.append(st["n_kept"])
+    bits = torch.empty(B.footprint_bytes(g), dtype=torch.uint8, device=ctx.dev)
+    ss = shadow_sizes(B, p)
+    works = [scan_work(ctx, g, k, ws, p, d_scans[i], poses[i], bits, ss) for i in range(nsc)]
     del bits
     torch.cuda.empty_cache()
-
-    # the library's autotuner picks the launch tuning on the first scan (the
-    # map is a scratch here: it is re-initialised below); results do not
-    # depend on the tuning
-    if args.no_autotune:
-        tuning = ws.tuning()
-    else:
-        tuning = B.dbt_workspace_autotune(g, k, ws, d_scans[0], poses[0], n_trials=3)
-
-    # warm-up, then a fresh map
-    for s in range(args.warmup):
-        dbt.dbt_integrate_scan(g, k, ws, d_scans[s % nsc], poses[s % nsc])
+    tuning = (B.dbt_workspace_autotune(g, k, ws, d_scans[0], poses[0], n_trials=3) if autotune
+              else ws.tuning())
+    for s_ in range(warmup):
+        dbt.dbt_integrate_scan(g, k, ws, d_scans[s_ % nsc], poses[s_ % nsc])
     dbt.dbt_grid_init(g)
     ws.reset()
-    # the integrate kernel of every INTEGRATE_TIMING_EVERY-th scan is timed
-    # with CUDA events inside the timed region (an event between two kernels
-    # stops the next one from launching early, so not every scan carries them)
-    timed_steps = list(range(0, args.steps, INTEGRATE_TIMING_EVERY))
-    evb = {s: torch.cuda.Event(enable_timing=True) for s in timed_steps}
-    eve = {s: torch.cuda.Event(enable_timing=True) for s in timed_steps}
+    timed_steps = list(range(0, steps, INTEGRATE_TIMING_EVERY))
+    evb = {s_: torch.cuda.Event(enable_timing=True) for s_ in timed_steps}
+    eve = {s_: torch.cuda.Event(enable_timing=True) for s_ in timed_steps}
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     for e in list(evb.values()) + list(eve.values()):   # torch creates the CUDA event on first record
         e.record(stream)
-    clocks = ClockSampler(dev.index) if rank == 0 else None
-    if clocks:
-        clocks.wait_first()
-    if world > 1:
-        torch.distributed.barrier()
+    ctx.barrier()
     torch.cuda.synchronize()
+    if ctx.clocks and region:
+        ctx.clocks.mark(region, True)
     t0.record(stream)
-    for s in range(args.steps):
-        if s in evb:
-            B.dbt_workspace_set_timing(ws, evb[s], eve[s])
-        dbt.dbt_integrate_scan(g, k, ws, d_scans[s % nsc], poses[s % nsc])
-        if s in evb:
+    for s_ in range(steps):
+        if s_ in evb:
+            B.dbt_workspace_set_timing(ws, evb[s_], eve[s_])
+        dbt.dbt_integrate_scan(g, k, ws, d_scans[s_ % nsc], poses[s_ % nsc])
+        if s_ in evb:
             B.dbt_workspace_set_timing(ws, None, None)
     t1.record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop() if clocks else None
+    if ctx.clocks and region:
+        ctx.clocks.mark(region, False)
+    ctx.barrier()
     ms = t0.elapsed_time(t1)
     st = dbt.dbt_get_scan_stats(ws)
     assert st["error"] == 0, st
-    t_int = [evb[s].elapsed_time(eve[s]) for s in timed_steps]
+    t_int = [evb[s_].elapsed_time(eve[s_]) for s_ in timed_steps]
 
-    # per-scan latency: a separate pass over the same scans on a fresh map,
-    # an event before and after every scan
+    # per-scan latency over the workload's scans on a fresh map: an event
+    # between scans, and around each integrate kernel
+    nl = latency_scans or nsc
     dbt.dbt_grid_init(g)
     ws.reset()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(nl + 1)]
+    ib = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
+    ie = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
+    for e in ib + ie:                # created by torch on its first record
+        e.record(stream)
     torch.cuda.synchronize()
-    for s in range(args.steps):
-        evs[s].record(stream)
-        dbt.dbt_integrate_scan(g, k, ws, d_scans[s % nsc], poses[s % nsc])
-    evs[args.steps].record(stream)
+    for s_ in range(nl):
+        evs[s_].record(stream)
+        B.dbt_workspace_set_timing(ws, ib[s_], ie[s_])
+        dbt.dbt_integrate_scan(g, k, ws, d_scans[s_ % nsc], poses[s_ % nsc])
+    evs[nl].record(stream)
     torch.cuda.synchronize()
-    t_scan = sorted(evs[s].elapsed_time(evs[s + 1]) for s in range(args.steps))
-    batched = run_batched(args, w, k, g, d_scans, poses, stream, world)
-    kept_timed = sum(kept[s % nsc] for s in range(args.steps))
+    B.dbt_workspace_set_timing(ws, None, None)
+    t_scan = sorted(evs[s_].elapsed_time(evs[s_ + 1]) for s_ in range(nl))
+    t_int_all = [ib[s_].elapsed_time(ie[s_]) for s_ in range(nl)]
 
-    # end to end through the host-buffer entry point
-    dbt.dbt_grid_init(g)
-    ws.reset()
-    h_scans = [torch.from_numpy(s[0]).pin_memory() for s in w.scans]
-    h_stats = torch.zeros((args.steps, 64), dtype=torch.uint8).pin_memory()
-    st_ptrs = [B.dbt_scan_stats.from_address(h_stats[s].data_ptr()) for s in range(args.steps)]
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for s in range(args.steps):
-        B.dbt_integrate_scan_host(g, k, ws, h_scans[s % nsc], poses[s % nsc], st_ptrs[s])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    ms_e2e = e0.elapsed_time(e1)
-    assert all(sp.error == 0 and sp.n_input == int(h_scans[s % nsc].shape[0])
-               for s, sp in enumerate(st_ptrs)), "scan counters of the host entry point"
+    kept_timed = sum(works[s_ % nsc]["kept"] for s_ in range(steps))
+    raw_timed = sum(works[s_ % nsc]["n"] for s_ in range(steps))
+    ms_int = statistics.mean(t_int)
+    tw = [works[s_ % nsc] for s_ in timed_steps]
+    traffic = traffic_fn(statistics.mean(x["kept"] for x in tw)) if traffic_fn else None
+    out = {"value": ctx.world * kept_timed / (ms * 1e-3), "unit": UNIT,
+           "raw_points_per_s": ctx.world * raw_timed / (ms * 1e-3),
+           "ms_per_step": ms / steps, "steps": steps,
+           "kept_per_scan": kept_timed / steps, "returns_per_scan": raw_timed / steps,
+           "latency_ms": {"p50": pct(t_scan, 50), "p99": pct(t_scan, 99), "max": t_scan[-1],
+                          "scans": nl,
+                          "what": "device time per scan, plain per-scan launches, over the "
+                                  "workload's scans from an empty map (an event between scans)"},
+           "tuning": tuning,
+           "roofline": roofline(ctx, tw, ms_int, pdict["kernel_size"], traffic),
+           "integrate_ms_all_scans": {"mean": statistics.mean(t_int_all), "max": max(t_int_all),
+                                      "share_of_scan": statistics.mean(t_int_all) /
+                                      statistics.mean(t_scan)}}
+    out["roofline"].update({"timed_launches": f"{len(t_int)} of {steps} (every "
+                                              f"{INTEGRATE_TIMING_EVERY}th scan of the timed region)",
+                            "share_of_step": ms_int / (ms / steps)})
+    if e2e:
+        dbt.dbt_grid_init(g)
+        ws.reset()
+        h_scans = [torch.from_numpy(np.ascontiguousarray(s[0])).pin_memory() for s in w.scans]
+        h_stats = torch.zeros((steps, 64), dtype=torch.uint8).pin_memory()
+        st_ptrs = [B.dbt_scan_stats.from_address(h_stats[s_].data_ptr()) for s_ in range(steps)]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ctx.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s_ in range(steps):
+            B.dbt_integrate_scan_host(g, k, ws, h_scans[s_ % nsc], poses[s_ % nsc], st_ptrs[s_])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.barrier()
+        ms_e2e = e0.elapsed_time(e1)
+        assert all(sp.error == 0 and sp.n_input == int(h_scans[s_ % nsc].shape[0])
+                   and sp.n_kept == works[s_ % nsc]["kept"]
+                   for s_, sp in enumerate(st_ptrs)), "scan counters of the host entry point"
+        npts = len(w.scans[0][0])
+        out["e2e_ms"] = ms_e2e
+        out["e2e"] = {"value": ctx.world * kept_timed / (ms_e2e * 1e-3), "unit": UNIT,
+                      "h2d_bytes_per_step": npts * 12,
+                      "d2h_bytes_per_step": ctypes.sizeof(B.dbt_scan_stats),
+                      "ms_per_step": ms_e2e / steps,
+                      "raw_points_per_s": ctx.world * raw_timed / (ms_e2e * 1e-3)}
+    out["_state"] = (k, g, d_scans, poses, works)
+    return out
 
-    ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev, world)
+
+def run_ours(args, rank, world):
+    ctx = Ctx(args, rank, world)
+    torch = ctx.torch
+    w = load_workload(args.workload)
+    pdict = dict(w.params)
+
+    def traffic_fn(kept):
+        if NCU_TRAFFIC["integrate_sha"] == integrate_sha() and NCU_TRAFFIC["bytes_per_kept_return"]:
+            return NCU_TRAFFIC["bytes_per_kept_return"] * kept
+        return None
+
+    main = plain_leg(ctx, w, pdict, args.steps, args.warmup, not args.no_autotune, e2e=True,
+                     region="timed", traffic_fn=traffic_fn)
+    k, g, d_scans, poses, works = main.pop("_state")
+    batched = run_batched(ctx, w, k, g, d_scans, poses, args.steps, works)
+    del k, g, d_scans, poses
+    torch.cuda.empty_cache()
+    ms, ms_e2e = max_over_ranks([main["ms_per_step"] * args.steps, main["e2e_ms"]], ctx.dev, world)
+    extra = {}
+    if not args.no_extra_legs and args.workload == "urban":
+        extra = extra_legs(ctx, args)
+    if ctx.clocks:
+        ctx.clocks.stop()
     if rank != 0:
         return 0
-
-    peak, peak_kind = measured_peaks()
-    ms_int = statistics.mean(t_int)
-    alg_int = statistics.mean(alg[s % nsc] for s in timed_steps)      # the timed launches' scans
-    kept_int = statistics.mean(kept[s % nsc] for s in timed_steps)
-    achieved = alg_int / (ms_int * 1e-3) / 1e9
-    traffic = None
-    if NCU_TRAFFIC["integrate_sha"] == integrate_sha() and NCU_TRAFFIC["bytes_per_kept_return"]:
-        traffic = NCU_TRAFFIC["bytes_per_kept_return"] * kept_int
-        traffic_note = NCU_TRAFFIC["source"]
-    else:
-        traffic_note = "no ncu capture of this integrate.cu yet"
+    rf = main["roofline"]
+    rf["traffic_source"] = (NCU_TRAFFIC["source"] if rf["traffic"] is not None
+                            else "no ncu capture of this integrate.cu yet")
     line = {
-        "metric": METRIC, "value": world * args.steps * npts / (ms * 1e-3), "unit": UNIT,
+        "metric": METRIC, "value": main["value"], "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "config": workload_config(args, w),
-        "kept_points_per_s": world * kept_timed / (ms * 1e-3),
-        "e2e": {"value": world * args.steps * npts / (ms_e2e * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": npts * 12,
-                "d2h_bytes_per_step": ctypes.sizeof(B.dbt_scan_stats),
-                "ms_per_step": ms_e2e / args.steps},
-        "latency_ms": {"p50": pct(t_scan, 50), "p99": pct(t_scan, 99), "max": t_scan[-1],
-                       "what": "device time per scan, plain per-scan launches (a separate pass "
-                               "with an event between scans)"},
+        "points_counted": "kept returns (valid, K^3 neighbourhood inside the map, first of their "
+                          "voxel): the returns Eqs. 4-6 integrate",
+        "raw_points_per_s": main["raw_points_per_s"],
+        "kept_per_scan": main["kept_per_scan"], "returns_per_scan": main["returns_per_scan"],
+        "e2e": main["e2e"],
+        "latency_ms": main["latency_ms"],
         "batched": batched,
-        "tuning": tuning,
+        "tuning": main["tuning"],
         "gpu_launches": KERNELS_PER_SCAN * args.steps,
-        "roofline": {"bound": "hbm", "kernel": "k_integrate", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "traffic_source": traffic_note,
-                     "peak_source": f"{peak_kind} hbm_gbs",
-                     "alg_bytes_per_launch": alg_int,
-                     "ms_per_launch": ms_int,
-                     "timed_launches": f"{len(t_int)} of {args.steps} (every "
-                                       f"{INTEGRATE_TIMING_EVERY}th scan of the timed region)",
-                     "share_of_step": ms_int / (ms / args.steps)},
-        "clocks": clk,
+        "roofline": rf,
+        "integrate_ms_all_scans": main["integrate_ms_all_scans"],
+        "clocks": ctx.clocks.stats("timed") if ctx.clocks else None,
+        "clocks_whole_run": ctx.clocks.stats() if ctx.clocks else None,
     }
+    line.update(extra)
     if not args.no_cpu_baseline and world == 1:
-        v, nsc_run, secs = cpu_baseline(w, budget_s=args.cpu_budget)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        v, nsc_run, secs, kept_per_s = cpu_baseline(w, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": kept_per_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "raw_points_per_s": v,
                                 "sample": f"first {nsc_run} scans of the workload, full grid, "
                                           f"{secs:.1f} s of single-thread CPU",
                                 "cpu": cpu_model(), "host_cores": os.cpu_count()}
         line["cpu_parallel_baseline"] = cpu_baseline_parallel(w, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def extra_legs(ctx, args) -> dict:
+    """The other workloads of the line, each measured the same way (kept
+    returns/s, latency, roofline), after the headline's timed region."""
+    torch = ctx.torch
+    out = {}
+    # high resolution: 2000 x 2000 x 400 at 0.02 m, 50 scans of 262,144 returns
+    wh = load_workload("highres")
+    leg = plain_leg(ctx, wh, dict(wh.params), len(wh.scans), 3, autotune=False)
+    k, g, d_scans, poses, works = leg.pop("_state")
+    leg["batched"] = run_batched(ctx, wh, k, g, d_scans, poses, len(wh.scans), works)
+    leg["config"] = workload_config_of("highres", wh)
+    out["highres"] = leg
+    del k, g, d_scans, poses, wh
+    torch.cuda.empty_cache()
+    # the paper's parameters (Sec. III-B: K = 21, 40 x 40 azimuth / elevation bins)
+    paper = dict(synth.DEFAULT_PARAMS, kernel_size=21, scheme=1, bins_a=40, bins_b=40)
+    pp = {}
+    wr = synth.room_scan(n_scans=20)
+    leg = plain_leg(ctx, wr, paper, 20, 3, autotune=False)
+    leg.pop("_state")
+    leg["config"] = workload_config_of("room", wr, paper)
+    pp["room"] = leg
+    wu = load_workload("urban")
+    wu = synth.Workload(wu.name, wu.grid, wu.scans[:20], wu.params)
+    leg = plain_leg(ctx, wu, paper, 20, 3, autotune=False)
+    leg.pop("_state")
+    leg["config"] = workload_config_of("urban", wu, paper)
+    pp["urban"] = leg
+    out["paper_params"] = pp
+    del wr, wu
+    torch.cuda.empty_cache()
+    out["maps"] = maps_leg(ctx, steps=3, warmup=3, autotune=not ctx.args.no_autotune)
+    torch.cuda.empty_cache()
+    out["serving"] = serving_leg(ctx, duration=args.serving_duration,
+                                 speeds=[float(x) for x in args.serving_speeds.split(",")])
+    torch.cuda.empty_cache()
+    return out
+
+
+def workload_config_of(name, w, pdict=None) -> dict:
+    pdict = pdict or w.params
+    bins = (f"octahedral {pdict['bins_a']}x{pdict['bins_b']}" if pdict["scheme"] == 0
+            else f"az/el {pdict['bins_a']}x{pdict['bins_b']}")
+    return {"workload": f"{name}: {len(w.scans)} scans x {len(w.scans[0][0])} returns, "
+                        f"grid {w.grid.nx}x{w.grid.ny}x{w.grid.nz} at {w.grid.res} m",
+            "kernel": pdict["kernel_size"], "bins": bins, "shadow_radius": pdict["shadow_radius"]}
 
 
 def max_over_ranks(vals, dev, world):
@@ -455,15 +703,14 @@ def pct(sorted_vals, q):
     return sorted_vals[i]
 
 
-def run_batched(args, w, k, g, d_scans, poses, stream, world):
-    """The same K scans as graph-replayed batches of args.batch consecutive
+def run_batched(ctx, w, k, g, d_scans, poses, steps, works):
+    """The same scans as graph-replayed batches of args.batch consecutive
     scans (one dbt_batch_run per batch, captured once, replayed in order)."""
-    import torch
-
-    import paper_2509_20081_gb300 as dbt
+    torch, dbt = ctx.torch, ctx.dbt
+    args, stream, world = ctx.args, ctx.stream, ctx.world
     S = max(1, args.batch)
     nsc = len(w.scans)
-    groups = [list(range(i, min(i + S, args.steps))) for i in range(0, args.steps, S)]
+    groups = [list(range(i, min(i + S, steps))) for i in range(0, steps, S)]
     batches, graphs = [], []
     cap = torch.cuda.Stream()
     for grp in groups:
@@ -489,22 +736,24 @@ def run_batched(args, w, k, g, d_scans, poses, stream, world):
     dbt.dbt_grid_init(g)
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(graphs) + 1)]
-    if world > 1:
-        torch.distributed.barrier()
+    ctx.barrier()
     torch.cuda.synchronize()
     ev[0].record(stream)
     for i, gr in enumerate(graphs):
         gr.replay()
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    ctx.barrier()
     per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(len(graphs)))
     ms = ev[0].elapsed_time(ev[-1])
-    _, tot = batches[-1].stats()
-    npts = sum(int(d_scans[s % nsc].shape[0]) for s in range(args.steps))
-    out = {"value": world * npts / (ms * 1e-3), "unit": UNIT, "scans_per_batch": S,
-           "ms_per_scan": ms / args.steps, "batch_ms_p50": pct(per, 50), "batch_ms_p99": pct(per, 99),
+    kept = sum(works[s % nsc]["kept"] for s in range(steps))
+    raw = sum(works[s % nsc]["n"] for s in range(steps))
+    out = {"value": world * kept / (ms * 1e-3), "unit": UNIT,
+           "raw_points_per_s": world * raw / (ms * 1e-3), "scans_per_batch": S,
+           "ms_per_scan": ms / steps, "batch_ms_p50": pct(per, 50), "batch_ms_p99": pct(per, 99),
+           "scan_latency_ms_p99": pct(per, 99),
+           "latency_note": "a scan's result is ready when its batch completes: its latency is "
+                           "the batch's (plus waiting for the batch to fill, not counted here)",
            "launch": "one CUDA graph per batch (dbt_batch_run captured), replayed in order",
            "tuning": tuning}
     for b in batches:
@@ -512,23 +761,19 @@ def run_batched(args, w, k, g, d_scans, poses, stream, world):
     return out
 
 
-def run_maps(args, rank, world):
+def maps_leg(ctx, steps: int, warmup: int, autotune: bool, n_maps: int = 32) -> dict:
     """Uneven independent maps (side 64-512 voxels at 0.05-0.2 m), 8 scans
     of 4,096-131,072 returns each: a step integrates all scans of all maps,
-    either as one graph-replayed batch (value) or as one plain launch sequence
-    per scan (plain)."""
-    import torch
-
-    import paper_2509_20081_gb300 as dbt
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    maps = synth.batched_maps(n_maps=args.maps, scans_per_map=8)
+    either as one graph-replayed batch or as one plain launch sequence per
+    scan.  Both from freshly initialised maps, same scans, same device."""
+    torch, dbt = ctx.torch, ctx.dbt
+    dev, stream = ctx.dev, ctx.stream
+    maps = synth.batched_maps(n_maps=n_maps, scans_per_map=8)
     k = dbt.Kernels(dbt.make_params(**maps[0].params))
     grids = [dbt.Grid(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.res) for w in maps]
     items = [(m, torch.from_numpy(pts).to(dev), pose) for m, w in enumerate(maps)
              for pts, pose in w.scans]
     npts = sum(int(x.shape[0]) for _, x, _ in items)
-    stream = torch.cuda.current_stream()
     # plain: one workspace per map, one dbt_integrate_scan per scan
     wss = [dbt.Workspace(grids[m], k, max(int(x.shape[0]) for mm, x, _ in items if mm == m))
            for m in range(len(maps))]
@@ -543,52 +788,70 @@ def run_maps(args, rank, world):
     torch.cuda.synchronize()
     with torch.cuda.stream(cap):
         b.run(stream=cap)
-        tuning = (b.tuning() if args.no_autotune
-                  else b.autotune(n_trials=2, stream=cap))   # the maps are re-initialised before timing
+        tuning = b.autotune(n_trials=2, stream=cap) if autotune else b.tuning()
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=cap):
         b.run(stream=cap)
 
-    def timed(fn, steps):
-        for _ in range(args.warmup):
+    def timed(fn):
+        for _ in range(warmup):
             fn()
-        for g in grids:
-            dbt.dbt_grid_init(g)
+        for gg in grids:
+            dbt.dbt_grid_init(gg)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        if world > 1:
-            torch.distributed.barrier()
+        ctx.barrier()
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(steps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        ctx.barrier()
         return e0.elapsed_time(e1) / steps
 
-    ms_batch = timed(graph.replay, args.steps)
-    ms_plain = timed(plain_pass, args.steps)
-    ms_batch, ms_plain = max_over_ranks([ms_batch, ms_plain], dev, world)
-    if rank != 0:
-        return 0
+    ms_batch = timed(graph.replay)
+    ms_plain = timed(plain_pass)
+    # kept returns of one step (every scan counted once, from its own counters)
+    for gg in grids:
+        dbt.dbt_grid_init(gg)
+    kept = 0
+    for m, x, pose in items:
+        dbt.dbt_integrate_scan(grids[m], k, wss[m], x, pose)
+        kept += dbt.dbt_get_scan_stats(wss[m])["n_kept"]
+    ms_batch, ms_plain = max_over_ranks([ms_batch, ms_plain], dev, ctx.world)
+    b.close()
     vox = sum(w.grid.nx * w.grid.ny * w.grid.nz for w in maps)
-    line = {"metric": METRIC, "value": world * npts / (ms_batch * 1e-3), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic",
+    return {"value": ctx.world * kept / (ms_batch * 1e-3), "unit": UNIT,
             "config": {"workload": f"maps: {len(maps)} maps ({vox / 1e6:.0f} M voxels), "
-                                   f"{len(items)} scans, {npts} returns per step",
-                       "parallelism": f"replicas x{args.gpus}",
-                       "l2": "grids larger than L2 in total; no flush"},
-            "batched": {"value": world * npts / (ms_batch * 1e-3), "ms_per_step": ms_batch,
+                                   f"{len(items)} scans, {npts} returns ({kept} kept) per step"},
+            "batched": {"value": ctx.world * kept / (ms_batch * 1e-3), "ms_per_step": ms_batch,
+                        "raw_points_per_s": ctx.world * npts / (ms_batch * 1e-3),
                         "launch": "one CUDA graph of dbt_batch_run over all scans",
                         "tuning": tuning},
-            "plain": {"value": world * npts / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+            "plain": {"value": ctx.world * kept / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                      "raw_points_per_s": ctx.world * npts / (ms_plain * 1e-3),
                       "launch": f"{len(items)} dbt_integrate_scan calls "
                                 f"({KERNELS_PER_SCAN} kernels each)"},
-            "gpu_launches": KERNELS_PER_SCAN * args.steps}
+            "batched_over_plain": ms_plain / ms_batch, "steps": steps}
+
+
+def run_maps(args, rank, world):
+    ctx = Ctx(args, rank, world)
+    leg = maps_leg(ctx, args.steps, args.warmup, not args.no_autotune, n_maps=args.maps)
+    if ctx.clocks:
+        ctx.clocks.stop()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": leg["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": leg["batched"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": dict(leg["config"], parallelism=f"replicas x{args.gpus}",
+                           l2="grids larger than L2 in total; no flush"),
+            "batched": leg["batched"], "plain": leg["plain"],
+            "gpu_launches": KERNELS_PER_SCAN * args.steps,
+            "clocks": ctx.clocks.stats() if ctx.clocks else None}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -641,11 +904,12 @@ def run_mesh(args, rank, world):
             torch.distributed.barrier()
         return sum(a.elapsed_time(b) for a, b in ev) / args.steps
 
-    clk = ClockSampler(dev.index or 0)
+    clk = ClockSampler(dev.index or 0, pci_bus_id(torch, dev))
     clk.wait_first()
     ms_count = timed(lambda: extract(None, 0))
     ms_full = timed(lambda: extract(tri.data_ptr(), ntri))
-    sample = clk.stop()
+    clk.stop()
+    sample = clk.stats()
 
     def e2e():
         extract(tri.data_ptr(), ntri)
@@ -771,26 +1035,23 @@ def run_quality(args, rank, world):
     return 0
 
 
-def run_serving(args, rank, world):
-    """16 robots with resident maps, Poisson scan arrivals (10-20 Hz each),
-    replayed at several speed-ups: continuous batching (2 streams, rounds of
-    all pending scans) against plain FIFO (one scan per round).  value: the
-    batched loop's sustained returns/s at the highest speed-up that keeps
-    p99 latency under the SLO."""
-    import torch
-
-    import paper_2509_20081_gb300 as dbt
+def serving_leg(ctx, duration: float, speeds: list, slo_ms: float = 100.0,
+                hbm_budget_gb: float = 120.0) -> dict:
+    """16 robots with resident maps, Poisson scan arrivals (10-20 Hz each)
+    over `duration` simulated seconds, replayed at each speed-up (offered
+    load = the trace's returns / (duration / speed-up)): continuous batching
+    (2 streams, rounds of all pending scans of maps not in flight) against
+    plain FIFO (one scan per round, one stream), the same trace for both.
+    Latency = completion - arrival on the simulated clock."""
+    torch, dbt = ctx.torch, ctx.dbt
     from paper_2509_20081_gb300 import serve
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    maps, arrivals = synth.serving_robots(duration=args.duration)
+    maps, arrivals = synth.serving_robots(duration=duration)
     k = dbt.Kernels(dbt.make_params(**maps[0].params))
     robots = {r: (w.grid.nx, w.grid.ny, w.grid.nz, w.grid.res, (0.0, 0.0, 0.0))
               for r, w in enumerate(maps)}
-    pools = [[torch.from_numpy(p).to(dev) for p, _ in w.scans] for w in maps]
+    pools = [[torch.from_numpy(p).to(ctx.dev) for p, _ in w.scans] for w in maps]
     npts = sum(int(pools[r][i].shape[0]) for r, _, i in arrivals)
-    speeds = [float(x) for x in args.speeds.split(",")]
-    budget = int(args.hbm_budget_gb * (1 << 30))
+    budget = int(hbm_budget_gb * (1 << 30))
     results = {}
     for mode, kw in (("batched", dict(n_streams=2, max_round_points=4 << 20, max_round_items=1024)),
                      ("plain", dict(n_streams=1, max_round_points=262144, max_round_items=1))):
@@ -807,30 +1068,51 @@ def run_serving(args, rank, world):
             st = serve.latency_stats(done)
             st.update({"speedup": sp, "wall_s": wall, "rounds": srv.rounds,
                        "points_per_s": sum(s.n for s in done) / wall,
-                       "offered_points_per_s": sum(s.n for s in trace) / (args.duration / sp)})
+                       "offered_points_per_s": sum(s.n for s in trace) / (duration / sp)})
             res.append(st)
         results[mode] = {"admitted_maps": admitted, "runs": res}
         srv.close()
-    if rank != 0:
-        return 0
-    slo = args.slo_ms
+        del srv
+        torch.cuda.empty_cache()
 
     def sustained(runs):
-        ok = [r for r in runs if r.get("p99_ms", 1e9) <= slo]
+        ok = [r for r in runs if r.get("p99_ms", 1e9) <= slo_ms]
         return max(ok, key=lambda r: r["speedup"]) if ok else None
 
-    best_b, best_p = sustained(results["batched"]["runs"]), sustained(results["plain"]["runs"])
+    at_load = []
+    for rb, rp in zip(results["batched"]["runs"], results["plain"]["runs"]):
+        at_load.append({"speedup": rb["speedup"], "offered_points_per_s": rb["offered_points_per_s"],
+                        "batched_p50_ms": rb.get("p50_ms"), "batched_p99_ms": rb.get("p99_ms"),
+                        "plain_p50_ms": rp.get("p50_ms"), "plain_p99_ms": rp.get("p99_ms"),
+                        "batched_points_per_s": rb["points_per_s"],
+                        "plain_points_per_s": rp["points_per_s"]})
+    return {"config": {"workload": f"serving: {len(maps)} robots, {len(arrivals)} scans "
+                                   f"({npts} returns) over {duration} s simulated, Poisson "
+                                   f"10-20 Hz per robot", "slo_p99_ms": slo_ms,
+                       "hbm_budget_gb": hbm_budget_gb,
+                       "points_counted": "returns handed in (raw)"},
+            "at_equal_load": at_load,
+            "sustained": {"batched": sustained(results["batched"]["runs"]),
+                          "plain": sustained(results["plain"]["runs"])},
+            "runs": results}
+
+
+def run_serving(args, rank, world):
+    ctx = Ctx(args, rank, world)
+    leg = serving_leg(ctx, args.duration, [float(x) for x in args.speeds.split(",")],
+                      slo_ms=args.slo_ms, hbm_budget_gb=args.hbm_budget_gb)
+    if ctx.clocks:
+        ctx.clocks.stop()
+    if rank != 0:
+        return 0
+    best_b = leg["sustained"]["batched"]
     line = {"metric": METRIC, "value": best_b["points_per_s"] if best_b else 0.0, "unit": UNIT,
-            "n_gpus": world, "steps": len(arrivals), "warmup": 0,
-            "ms_per_step": 1e3 * args.duration / max(1, len(arrivals)),
+            "n_gpus": world, "steps": 0, "warmup": 0, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": f"serving: {len(maps)} robots, {len(arrivals)} scans "
-                                   f"({npts} returns) over {args.duration} s simulated, "
-                                   f"Poisson 10-20 Hz per robot",
-                       "slo_p99_ms": slo, "hbm_budget_gb": args.hbm_budget_gb,
-                       "parallelism": f"replicas x{args.gpus}"},
-            "sustained": {"batched": best_b, "plain": best_p}, "serving": results}
+            "config": dict(leg["config"], parallelism=f"replicas x{args.gpus}"),
+            "at_equal_load": leg["at_equal_load"], "sustained": leg["sustained"],
+            "serving": leg["runs"], "clocks": ctx.clocks.stats() if ctx.clocks else None}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -851,6 +1133,14 @@ def main():
     ap.add_argument("--slo-ms", type=float, default=100.0, help="serving: p99 latency bound")
     ap.add_argument("--hbm-budget-gb", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-legs", action="store_true",
+                    help="urban: only the headline legs (no highres, paper-parameter, maps, "
+                         "serving keys)")
+    ap.add_argument("--serving-duration", type=float, default=20.0,
+                    help="serving key of the default line: simulated seconds")
+    ap.add_argument("--serving-speeds", default="16,48",
+                    help="serving key of the default line: replay speed-ups (equal loads for both "
+                         "modes)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch tuning (short runs, profiler captures)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

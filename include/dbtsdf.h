@@ -270,6 +270,17 @@ dbt_status dbt_scan_footprint(const dbt_grid *g, const dbt_kernels *k, dbt_works
                               const float *d_xyz, int64_t n, const double pose[12], void *d_bits,
                               size_t bits_bytes, int64_t h_counts[2], void *stream);
 
+/* Measurement hook: peak rates of the elementary updates the integration is
+ * built from (the op-side ceiling of Eq. 7, T_update ~ N_p K^3 C_op),
+ * measured alone by a micro-benchmark on the current device at the
+ * integration's occupancy: *and_per_s = Eq. 4 voxel-ANDs per second as
+ * byte-wise minima of packed 4-voxel code words in shared memory (the
+ * faster of always / only-when-changed stores), *count_per_s = Eq. 5 counter
+ * increments per second (16-bit counters in shared memory).  iters in
+ * [16, 2^24] sets the loop length (2^14 takes a few ms).  Synchronous on
+ * the default stream; allocates and frees 8 bytes of device memory. */
+dbt_status dbt_op_rates(int32_t iters, double *and_per_s, double *count_per_s);
+
 /* Batches: many scans of many grids (maps of any size) integrated by one
  * launch sequence.  The result on every grid equals integrating its scans
  * one by one with dbt_integrate_scan, in any order: a scan's effect depends

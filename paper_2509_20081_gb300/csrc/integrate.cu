@@ -864,4 +864,90 @@ void launch_integrate_batch(const BatchDev &bd, const DevParams &p, const DevTab
         launch_pdl(k_integrate<6, true>, grid_ctas, NTHR, smem, s, none, bd, p, t, n_input, ws);
 }
 
+// ---------------------------------------------------------------- op-rate micro-benchmark
+// Peak rates of the two shared-memory updates the brick integration is built
+// from, each measured alone at the integration's occupancy (4 CTAs of 256
+// threads per SM): the op-side ceiling of the roofline (Eq. 7: the update
+// time is the number of elementary updates times their cost).
+//   MODE 0, 1: Eq. 4 on packed codes: a kernel-row table word and a staged
+//              4-voxel word loaded from shared memory and their byte-wise
+//              minimum (code_lt / code_min) stored back, always (0) or only
+//              when it changes the word (1; the table words are then never
+//              below the staged ones); 4 voxel-ANDs per update.
+//   MODE 2:    Eq. 5 counts: a staged 16-bit counter incremented.
+// Every lane works in words of its own bank (no conflicts); the unrolled
+// inner loop leaves issue, not loop overhead, as the limit.  The staged
+// words are accessed through a volatile pointer, so that every update
+// loads and stores shared memory as the integration's do (a thread's own
+// word would otherwise stay in a register across the loop).
+constexpr int OP_WORDS = 4;
+template <int MODE>
+__global__ void __launch_bounds__(NTHR, 4) k_op_rate(int iters, unsigned long long *sink) {
+    __shared__ uint32_t s_tab_[8 * NTHR];
+    __shared__ uint32_t s_st_[OP_WORDS * NTHR];
+    volatile uint32_t *s_tab = s_tab_;
+    volatile uint32_t *s_st = s_st_;
+    const int tid = threadIdx.x;
+    for (int j = 0; j < 8; ++j)
+        s_tab[j * NTHR + tid] = MODE == 1 ? 0x20202020u : 0x01010101u * (uint32_t)((tid + j) % 30 + 1);
+    for (int w = 0; w < OP_WORDS; ++w) s_st[w * NTHR + tid] = MODE == 1 ? 0x10101010u : 0x1F1F1F1Fu;
+    __syncthreads();
+    uint32_t acc = 0;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int w = 0; w < OP_WORDS; ++w) {
+            const int ti = ((it * OP_WORDS + w) & 7) * NTHR + tid, si = w * NTHR + tid;
+            if constexpr (MODE == 2) {
+                volatile uint16_t *c = reinterpret_cast<volatile uint16_t *>(s_st) + 2 * si;
+                *c = (uint16_t)(*c + 1u);
+            } else {
+                const uint32_t kwd = s_tab[ti];
+                const uint32_t a = s_st[si];
+                const uint32_t lt = code_lt(a, kwd);
+                if (MODE == 0 || lt) s_st[si] = code_min(a, kwd, lt);
+                acc += lt;
+            }
+        }
+    }
+    __syncthreads();
+    for (int w = 0; w < OP_WORDS; ++w) acc += s_st[w * NTHR + tid];
+    if (acc == 0x9E3779B9u) atomicAdd(sink, 1ull);     // keeps the loop; practically never true
+}
+
 }  // namespace dbt
+
+using namespace dbt;
+
+extern "C" dbt_status dbt_op_rates(int32_t iters, double *and_per_s, double *count_per_s) {
+    if (iters < 16 || iters > (1 << 24) || !and_per_s || !count_per_s) {
+        return report_einval("dbt_op_rates: iters in [16, 2^24] and non-NULL outputs");
+    }
+    const int ctas = device_sm_count() * 4;
+    unsigned long long *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float ms[3] = {0.f, 0.f, 0.f};
+    for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode) {
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {     // the first run warms up
+            cudaEventRecord(e0, 0);
+            if (mode == 0) k_op_rate<0><<<ctas, NTHR>>>(iters, sink);
+            else if (mode == 1) k_op_rate<1><<<ctas, NTHR>>>(iters, sink);
+            else k_op_rate<2><<<ctas, NTHR>>>(iters, sink);
+            cudaEventRecord(e1, 0);
+            e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[mode], e0, e1);
+        }
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sink) cudaFree(sink);
+    if (e != cudaSuccess) return report_cuda_error(e, "dbt_op_rates");
+    const double updates = (double)ctas * NTHR * (double)iters * OP_WORDS;
+    const double best_and_ms = std::min(ms[0], ms[1]);
+    *and_per_s = 4.0 * updates / (best_and_ms * 1e-3);
+    *count_per_s = updates / (ms[2] * 1e-3);
+    return DBT_OK;
+}

@@ -120,6 +120,7 @@ _SIGS = {
     "dbt_batch_destroy": [_vp],
     "dbt_integrate_scan_noalloc": [_P(dbt_grid), _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
                                    _P(dbt_scan_stats), _vp],
+    "dbt_op_rates": [ctypes.c_int32, _P(ctypes.c_double), _P(ctypes.c_double)],
     "dbt_noalloc_check": [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                           ctypes.c_int64],
     "dbt_scan_footprint": [_P(dbt_grid), _vp, _vp, _vp, ctypes.c_int64, _P(ctypes.c_double),
@@ -580,6 +581,14 @@ def dbt_integrate_scan_noalloc(grid: Grid, kernels: Kernels, xyz, pose,
                                             xyz.data_ptr() if n else None, n, pp,
                                             ctypes.byref(stats) if stats is not None else None,
                                             _stream_ptr(stream)))
+
+
+def dbt_op_rates(iters: int = 1 << 14) -> tuple[float, float]:
+    """(voxel-ANDs/s, counter increments/s): the measured peak rates of the
+    integration's elementary shared-memory updates on the current device."""
+    a, c = ctypes.c_double(), ctypes.c_double()
+    _check(lib().dbt_op_rates(iters, ctypes.byref(a), ctypes.byref(c)))
+    return a.value, c.value
 
 
 def dbt_noalloc_check(nx: int, ny: int, nz: int, kernel_size: int, n: int) -> None:
