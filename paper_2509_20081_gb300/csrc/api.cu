@@ -1,6 +1,7 @@
 // C ABI entry points (include/dbtsdf.h): argument checks, the host build of
 // the directional kernel tables, workspace layout, and the launch sequence
 // of one scan.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -244,6 +245,32 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
         }
         for (int j = 1; j < p->bins_b; ++j) el_s[j] = std::sin(el_edge(j, p->bins_b));
     }
+    // Shadow sub-ranges.  Each bin's offsets are listed oz-major (sh_off, as
+    // built) and again oy-major (sh_y); sh_zs[b * (sw + 1) + k] is the first
+    // entry of bin b's oz-major list with oz >= k - sr (k = 0 .. sw), sh_ys
+    // the same for oy in the oy-major list.  A pair whose contact lies
+    // outside its brick along z (or y) then walks only the entries whose
+    // plane (or row) falls in the brick.
+    const int sr = std::min(R, (int)std::floor(p->shadow_radius));
+    const int sw = 2 * sr + 1;
+    std::vector<uint32_t> sh_y(k->sh_off.size()), sh_zs((size_t)nbins * (sw + 1)),
+        sh_ys((size_t)nbins * (sw + 1));
+    for (int b = 0; b < nbins; ++b) {
+        const uint32_t e0 = k->sh_start[b], e1 = k->sh_start[b + 1];
+        std::vector<uint32_t> by(k->sh_off.begin() + e0, k->sh_off.begin() + e1);
+        std::stable_sort(by.begin(), by.end(), [](uint32_t a, uint32_t c) {
+            return off_axis(a, 1) != off_axis(c, 1) ? off_axis(a, 1) < off_axis(c, 1)
+                                                    : off_axis(a, 2) < off_axis(c, 2);
+        });
+        std::copy(by.begin(), by.end(), sh_y.begin() + e0);
+        for (int kk = 0; kk <= sw; ++kk) {
+            uint32_t ez = e0, ey = e0;
+            while (ez < e1 && off_axis(k->sh_off[ez], 2) < kk - sr) ++ez;
+            while (ey < e1 && off_axis(sh_y[ey], 1) < kk - sr) ++ey;
+            sh_zs[(size_t)b * (sw + 1) + kk] = ez;
+            sh_ys[(size_t)b * (sw + 1) + kk] = ey;
+        }
+    }
     // one device block for all tables
     const size_t n_m2 = k->m2.size(), n_off = std::max<size_t>(1, k->sh_off.size());
     size_t off_m2 = 0;
@@ -254,7 +281,10 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
     size_t off_els = off_azs + MAX_EDGES * 8;
     size_t off_up = off_els + MAX_EDGES * 8;
     size_t off_pr = off_up + MAX_EDGES * 4;
-    size_t total = off_pr + k->prow.size() * 4;
+    size_t off_shy = off_pr + ((k->prow.size() * 4 + 255) & ~size_t(255));
+    size_t off_zs = off_shy + ((n_off * 4 + 255) & ~size_t(255));
+    size_t off_ys = off_zs + ((sh_zs.size() * 4 + 255) & ~size_t(255));
+    size_t total = off_ys + sh_ys.size() * 4;
     cudaError_t e = cudaMalloc(&k->d_base, total);
     if (e != cudaSuccess) {
         delete k;
@@ -272,6 +302,12 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
     if (e == cudaSuccess) e = cudaMemcpy(base + off_up, az_up.data(), MAX_EDGES * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(base + off_pr, k->prow.data(), k->prow.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !sh_y.empty())
+        e = cudaMemcpy(base + off_shy, sh_y.data(), sh_y.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + off_zs, sh_zs.data(), sh_zs.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + off_ys, sh_ys.data(), sh_ys.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(k->d_base);
         delete k;
@@ -287,7 +323,7 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
     k->dp.Hmax = p->hit_max;
     k->dp.dedup = p->dedup_first;
     k->dp.n_m2 = (int)n_m2;
-    k->dp.sr = std::min(R, (int)std::floor(p->shadow_radius));
+    k->dp.sr = sr;
     k->dp.n_sh = (int)k->sh_off.size();
     k->dt.m2 = (const uint32_t *)(base + off_m2);
     k->dt.sh_off = (const uint32_t *)(base + off_sh);
@@ -297,6 +333,9 @@ extern "C" dbt_status dbt_kernels_build(const dbt_params *p, dbt_kernels **out) 
     k->dt.el_s = (const double *)(base + off_els);
     k->dt.az_up = (const int *)(base + off_up);
     k->dt.prow = (const uint32_t *)(base + off_pr);
+    k->dt.sh_y = (const uint32_t *)(base + off_shy);
+    k->dt.sh_zs = (const uint32_t *)(base + off_zs);
+    k->dt.sh_ys = (const uint32_t *)(base + off_ys);
     *out = k;
     return DBT_OK;
 }

@@ -69,6 +69,13 @@ struct DevTables {
     const int *az_up;          // theta_k < pi
     const double *el_s;        // elevation edge k: sin(phi_k), k = 0..B_el-1
     const uint32_t *prow;      // kernel-row codes P[q * (2R + 4) + s], q = 0 .. 2 R^2
+    // shadow sub-ranges (sw = 2 sr + 1): sh_y lists each bin's offsets
+    // oy-major (the same per-bin ranges as sh_off, which is oz-major);
+    // sh_zs[b * (sw + 1) + k] / sh_ys[...] = first entry of bin b with
+    // oz (resp. oy) >= k - sr in sh_off (resp. sh_y), k = 0 .. sw
+    const uint32_t *sh_y;
+    const uint32_t *sh_zs;
+    const uint32_t *sh_ys;
 };
 
 struct DevGrid {

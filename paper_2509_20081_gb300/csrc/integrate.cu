@@ -3,21 +3,29 @@
 // Distance codes.  A mask of the form 2^k - 1 is stored as k = popcount; the
 // Eq. 4 AND of two such masks is the mask of min(k).  Grid masks start all
 // ones (Sec. III-A) and only ever meet Eq. 3 masks, so they keep this form
-// (checked on load; a violation latches ERR_MASK_FORM).  A staged brick holds
-// 8-bit codes, four voxels per 32-bit word, and the AND of four voxels is one
-// byte-wise minimum.
+// (checked on load; a violation latches ERR_MASK_FORM).
+//
+// Per brick, the kernels of all its (return, brick) pairs are first folded
+// among themselves: a warp area holds, per voxel, the minimum code of the
+// kernels applied so far (8-bit codes, four voxels per 32-bit word, 32 =
+// none), so the AND of four voxels is one byte-wise minimum and nothing is
+// read from the grid before the kernels are applied.  The grid's masks are
+// read once, at write-back, where each covered voxel takes min(old, kernel
+// minimum) -- the same result as AND-ing the kernels into the mask one by
+// one, because the AND of masks of the form 2^k - 1 is the minimum of codes,
+// which is associative and commutative.
 //
 // Kernel rows.  For a row of the K^3 kernel at squared lateral offset
 // q = oy^2 + oz^2 the codes along x are ceil(sqrt(ox^2 + q)).  The host builds
 // P[q][s]: the four codes a 4-voxel word receives when its first voxel sits
 // at ox = s - 3 - R (32, no change, outside the kernel).  A word update is a
-// table load, a staged-word load, a byte-wise min and a conditional store.
+// table load, an area-word load, a byte-wise min and a conditional store.
 //
 // Work split.  Persistent CTAs of WPC warps.  Bricks (32 x 8 x 8 voxels)
 // with more than ws.heavy (return, brick) pairs ("heavy") are taken one per
 // group of warps: at K <= 13 by the separable dense path below, otherwise
-// each warp applies a share of the pairs to its own staged copy and the
-// copies are merged (byte-wise min of codes, sum of counts).  The other
+// each warp applies a share of the pairs to its own area and the areas are
+// merged at write-back (byte-wise min of codes, sum of counts).  The other
 // bricks are taken one per warp, in size classes, largest first.  At K <= 11
 // a CTA holds two groups of four warps, one starting on heavy and one on
 // light bricks; otherwise the CTA is one group, heavy bricks first.  A brick
@@ -25,18 +33,17 @@
 // touch the grid.
 //
 // Per brick:
-//   A. the 16-byte chunks of each brick row that any pair's kernel covers
-//      (lanes take one pair each and OR-reduce 64-bit row masks per chunk),
-//   B. those chunks staged as codes; shadow counts zeroed,
-//   C. every pair applied (lanes = 8 rows x 4 planes, each lane updating the
-//      up to NW words of its kernel row), then the bin's shadow offsets that
-//      fall in the brick counted (Eq. 5),
-//   D. chunks whose codes changed written back as masks; for chunks with
-//      shadow counts c: h' = min(h + c, H_max), sign 0 when h < T <= h' (Eq. 6).
-// AND is commutative and the saturating count with a threshold crossing
-// depends only on the total count, so D gives exactly the state of applying
-// the returns one by one in scan order (the first-return rule is resolved
-// before this kernel).
+//   I. the area cleared: no code (32) and zero counts,
+//   C. every pair applied (lanes = the kernel rows inside the brick, each
+//      updating the up to NW words of its row), then the bin's shadow offsets
+//      that fall in the brick counted (Eq. 5),
+//   D. write-back: every chunk of four voxels that some kernel covers reads
+//      its masks, takes the minimum with the kernel codes and stores the
+//      masks that change; chunks with shadow counts c take
+//      h' = min(h + c, H_max) and sign 0 when h < T <= h' (Eq. 6).
+// The saturating count with a threshold crossing depends only on the total
+// count, so D gives exactly the state of applying the returns one by one in
+// scan order (the first-return rule is resolved before this kernel).
 #include <mutex>
 
 #include "dbt_internal.cuh"
@@ -47,16 +54,15 @@ constexpr int WPC = 8;            // warps per CTA
 constexpr int NTHR = WPC * 32;
 
 struct WarpArea {
-    uint32_t kst[BROWS * 8];      // codes: word kword(row, w) = voxels 4w .. 4w+3 of a row
+    uint32_t kst[BROWS * 8];      // kernel codes: word kword(row, w) = voxels 4w .. 4w+3 of a row
     uint16_t cnt[BVOX];           // shadow counts, index row * 32 + x
-    uint8_t drow[BROWS];          // bit w: word w of the row changed
-    uint32_t need[BROWS];         // covered chunks of each row (bit w)
 };
 static_assert(sizeof(WarpArea) % 16 == 0, "warp area alignment");
+constexpr uint32_t NO_CODE4 = 0x20202020u;      // four voxels without a kernel code (32)
 
 // Word w of brick row `row` (row = z * 8 + y).  The XOR with bits 2..4 of the
 // row spreads both access patterns over all 32 banks: phase C (8 rows x 4
-// consecutive planes, same w) and phases B/D (4 consecutive rows x 8 words).
+// consecutive planes, same w) and phase D (4 consecutive rows x 8 words).
 __device__ __forceinline__ int kword(int row, int w) { return row * 8 + (w ^ ((row >> 2) & 7)); }
 
 __device__ __forceinline__ uint32_t vmin4(uint32_t a, uint32_t b) { return __vminu4(a, b); }
@@ -105,38 +111,11 @@ __device__ __forceinline__ PairBox decode_pair(uint32_t pl, int R) {
     return b;
 }
 
-// Phase A for pairs[j] with j = first + lane + step k, j < len: cr[c] gets
-// bit `row` set when some pair's kernel covers chunk c of that brick row.
-__device__ __forceinline__ void coverage(const uint32_t *pairs, uint32_t first, uint32_t len,
-                                         uint32_t step, int R, int lane,
-                                         unsigned long long cr[CHUNKS_PER_ROW]) {
-    for (uint32_t base = first; base < len; base += step) {
-        const uint32_t j = base + lane;
-        unsigned long long rows = 0ull;
-        uint32_t cm = 0;
-        if (j < len) {
-            const PairBox b = decode_pair(__ldg(pairs + j), R);
-            const unsigned long long ybits =
-                (unsigned long long)((0xFFu >> (7 - (b.y1 - b.y0))) << b.y0);
-            const unsigned long long zspread =
-                (0x0101010101010101ull >> (8 * (7 - (b.z1 - b.z0)))) << (8 * b.z0);
-            rows = ybits * zspread;
-            cm = (0xFFu >> (7 - (b.x1 >> 2))) & (0xFFu << (b.x0 >> 2));
-        }
-#pragma unroll
-        for (int c = 0; c < CHUNKS_PER_ROW; ++c) {
-            const unsigned long long v = ((cm >> c) & 1u) ? rows : 0ull;
-            const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)v);
-            const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(v >> 32));
-            cr[c] |= ((unsigned long long)hi << 32) | lo;
-        }
-    }
-}
-
-// Phase C (Eq. 4) for one pair on a warp's staged copy.  The box's wy x wz
-// kernel rows are spread over the lanes (row r -> z = r / wy, y = r % wy, the
+// Phase C (Eq. 4) for one pair on a warp's area.  The box's wy x wz kernel
+// rows are spread over the lanes (row r -> z = r / wy, y = r % wy, the
 // division by wy <= 8 done exactly as (r * ceil(256 / wy)) >> 8 for r < 64);
-// each lane updates the up to NW words of its row.
+// each lane lowers the codes of the up to NW words of its row.  Each lane
+// owns its row within one pair, so no two lanes write one word.
 template <int NW>
 __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint32_t *P, int R,
                                            int W, int lane) {
@@ -156,7 +135,6 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
         const int pb = (oy * oy + oz * oz) * W + s0;
         const int row = rz * BY + ry;
         const int rbase = row * 8, f = (row >> 2) & 7;
-        uint32_t changed = 0;
 #pragma unroll
         for (int j = 0; j < NW; ++j) {
             if (j <= nw) {
@@ -164,22 +142,25 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
                 const int addr = rbase + ((w0 + j) ^ f);
                 const uint32_t a = wa->kst[addr];
                 const uint32_t lt = code_lt(a, kwd);
-                if (lt) {
-                    wa->kst[addr] = code_min(a, kwd, lt);
-                    changed |= 1u << (w0 + j);
-                }
+                if (lt) wa->kst[addr] = code_min(a, kwd, lt);
             }
         }
-        // each lane owns its row within one pair, so no other lane writes this byte
-        if (changed) wa->drow[row] |= (uint8_t)changed;
     }
 }
 
-// Eq. 5 counts of one pair: lanes walk the bin's shadow offsets (sh / shs)
-// and count those inside the brick.  ATOMIC: several warps count into one
-// array, so counts are added atomically to their packed 16-bit halves (a
-// voxel's total never reaches 2^16: it is at most the number of lattice
-// points within r_s).
+// Eq. 5 counts of up to 32 pairs (lane j holds pair j's payload in `mine`,
+// j < n): lanes walk each pair's shadow offsets and count those inside the
+// brick.  The per-pair set-up is taken lane-parallel first: whether the
+// contact lies within r_s of the brick (else no offset can fall in it), the
+// contact packed as bytes, and the pair's range of offsets -- for a contact
+// outside the brick along z only the offsets whose plane falls in the brick
+// (a sub-range of the oz-major list, sh_zs), along y (z inside) only the
+// rows that fall in it (oy-major list, sh_ys), else the bin's whole list.
+// Then the pairs with offsets to walk are taken one by one (ballot).
+// ATOMIC: several warps count into one array, so counts are added
+// atomically to their packed 16-bit halves.  A pair adds at most 1 to a
+// voxel, and a brick's pairs are counted in rounds of at most CNT_ROUND, so
+// a count stays below 2^16; the write-back saturates the counter at H_max.
 //
 // Offsets are packed bytes o + 32 and the contact c relative to the brick
 // is packed as bytes c + 32, so one 32-bit add gives per byte o + c + 64,
@@ -187,35 +168,48 @@ __device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint
 // carries into the next.  The voxel o + c is in the brick exactly when that
 // byte is in [64, 96) for x and in [64, 72) for y and z, i.e. bits 7..5 of
 // the x byte read 010 and bits 7..3 of the y and z bytes read 01000: one AND
-// and one compare.  Lanes past the bin's list take 0x80 bytes, which set
-// bit 7 and fail.  The low bits of the bytes are then x, y and z.
+// and one compare.  Lanes past the range take 0x80 bytes, which set bit 7
+// and fail.  The low bits of the bytes are then x, y and z.
 static_assert(BX == 32 && BY == 8 && BZ == 8 && MAX_R <= 10 && OFF_BIAS == 32,
-              "shadow_pair's byte packing assumes 32 x 8 x 8 bricks and |offsets| <= 10");
+              "shadow_pairs' byte packing assumes 32 x 8 x 8 bricks and |offsets| <= 10");
 constexpr uint32_t SH_PAD = 0x80808080u;
+constexpr uint32_t CNT_ROUND = 65535u;
 template <bool ATOMIC>
-__device__ __forceinline__ void shadow_pair(uint32_t pl, uint16_t *cnt, const uint32_t *sh,
-                                            const uint32_t *shs, int R, int SR, int lane) {
-    const int cx = (int)(pl & 63u) - R;
-    const int cy = (int)((pl >> 6) & 31u) - R;
-    const int cz = (int)((pl >> 11) & 31u) - R;
-    if (!(cx >= -SR && cx <= BX - 1 + SR && cy >= -SR && cy <= BY - 1 + SR && cz >= -SR &&
-          cz <= BZ - 1 + SR))
-        return;
-    const uint32_t cpk = (uint32_t)(cx + 32) | ((uint32_t)(cy + 32) << 8) | ((uint32_t)(cz + 32) << 16);
-    const uint32_t bin = pl >> 16;
-    const uint32_t e0 = __ldg(shs + bin), e1 = __ldg(shs + bin + 1);
-    for (uint32_t e = e0; e < e1; e += 96) {
-        // up to three batches of 32 fetched before use; batches past the
-        // list are skipped (warp-uniform)
-        const uint32_t left = e1 - e;
-        uint32_t o[3];
-#pragma unroll
-        for (int h = 0; h < 3; ++h)
-            o[h] = e + 32 * h + lane < e1 ? __ldg(sh + e + 32 * h + lane) : SH_PAD;
-#pragma unroll
-        for (int h = 0; h < 3; ++h) {
-            if (32u * h >= left) break;
-            const uint32_t u = o[h] + cpk;
+__device__ __forceinline__ void shadow_pairs(uint32_t mine, int n, uint16_t *cnt, const DevTables &t,
+                                             int R, int SR, int lane) {
+    uint32_t e0 = 0, e1 = 0, cpk = 0;
+    bool ylist = false;
+    if (lane < n) {
+        const int cx = (int)(mine & 63u) - R;
+        const int cy = (int)((mine >> 6) & 31u) - R;
+        const int cz = (int)((mine >> 11) & 31u) - R;
+        if (cx >= -SR && cx <= BX - 1 + SR && cy >= -SR && cy <= BY - 1 + SR && cz >= -SR &&
+            cz <= BZ - 1 + SR) {
+            cpk = (uint32_t)(cx + 32) | ((uint32_t)(cy + 32) << 8) | ((uint32_t)(cz + 32) << 16);
+            const uint32_t bin = mine >> 16;
+            if (cz < 0 || cz >= BZ) {
+                const uint32_t *zs = t.sh_zs + bin * (uint32_t)(2 * SR + 2);
+                e0 = __ldg(zs + (max(-SR, -cz) + SR));
+                e1 = __ldg(zs + (min(SR, BZ - 1 - cz) + SR + 1));
+            } else if (cy < 0 || cy >= BY) {
+                const uint32_t *ys = t.sh_ys + bin * (uint32_t)(2 * SR + 2);
+                e0 = __ldg(ys + (max(-SR, -cy) + SR));
+                e1 = __ldg(ys + (min(SR, BY - 1 - cy) + SR + 1));
+                ylist = true;
+            } else {
+                e0 = __ldg(t.sh_start + bin);
+                e1 = __ldg(t.sh_start + bin + 1);
+            }
+        }
+    }
+    for (unsigned todo = __ballot_sync(0xffffffffu, e1 > e0); todo; todo &= todo - 1u) {
+        const int j = __ffs(todo) - 1;
+        const uint32_t a0 = __shfl_sync(0xffffffffu, e0, j), a1 = __shfl_sync(0xffffffffu, e1, j);
+        const uint32_t pk = __shfl_sync(0xffffffffu, cpk, j);
+        const uint32_t *sh = __shfl_sync(0xffffffffu, (int)ylist, j) ? t.sh_y : t.sh_off;
+        for (uint32_t e = a0; e < a1; e += 32) {
+            const uint32_t o = e + lane < a1 ? __ldg(sh + e + lane) : SH_PAD;
+            const uint32_t u = o + pk;
             if ((u & 0x00F8F8E0u) == 0x00404040u) {
                 const int v = (int)((u & 31u) | ((u >> 3) & 0xE0u) | ((u >> 8) & 0x700u));
                 if (ATOMIC)
@@ -224,6 +218,7 @@ __device__ __forceinline__ void shadow_pair(uint32_t pl, uint16_t *cnt, const ui
                     cnt[v] += 1;   // distinct voxels within one pair
             }
         }
+        __syncwarp();              // the next pair's lanes may count the same voxels
     }
 }
 
@@ -239,14 +234,6 @@ __device__ __forceinline__ uint32_t codes_of(const uint4 m, uint32_t &form_bad) 
            ((uint32_t)__popc(m.w) << 24);
 }
 
-__device__ __forceinline__ uint32_t load_codes(const DevGrid &g, size_t gi, uint32_t &form_bad) {
-    return codes_of(__ldcg(reinterpret_cast<const uint4 *>(g.mask + gi)), form_bad);
-}
-
-// Eqs. 5-6 on one chunk: old counters hv, packed counts c; returns bit e set
-// when voxel e's counter crosses T (its sign becomes occupied).  The sign
-// only ever goes from free to occupied, so it needs no read: the crossing
-// voxels get a zero byte, every other sign byte is left as it is.
 __device__ __forceinline__ uint32_t apply_counts(uint2 &hv, uint2 c, uint32_t T, uint32_t Hmax) {
     const uint32_t cnt4[4] = {c.x & 0xFFFFu, c.x >> 16, c.y & 0xFFFFu, c.y >> 16};
     uint32_t h[4] = {hv.x & 0xFFFFu, hv.x >> 16, hv.y & 0xFFFFu, hv.y >> 16};
@@ -272,15 +259,100 @@ __device__ __forceinline__ void store_codes(const DevGrid &g, size_t gi, uint32_
     __stcg(reinterpret_cast<uint4 *>(g.mask + gi), m);
 }
 
-// Phase D for one chunk: codes k (changed when dirty) and packed counts c.
-__device__ __forceinline__ void store_chunk(const DevGrid &g, size_t gi, uint32_t k, bool dirty,
-                                            uint2 c, uint32_t T, uint32_t Hmax) {
-    if (dirty) store_codes(g, gi, k);
-    if (c.x | c.y) {
-        uint2 hv = __ldcg(reinterpret_cast<const uint2 *>(g.hits + gi));
-        const uint32_t cross = apply_counts(hv, c, T, Hmax);
-        __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv);
-        store_crossings(g, gi, cross);
+// Phase I: clears the areas [a, a + na) (no codes, zero counts), thread tid
+// of gt.
+__device__ __forceinline__ void clear_areas(WarpArea *a, int na, int tid, int gt) {
+    const uint4 none = make_uint4(NO_CODE4, NO_CODE4, NO_CODE4, NO_CODE4);
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    constexpr int K4 = BROWS * 8 / 4, C4 = BVOX / 8;          // uint4 words of kst, cnt
+    for (int v = 0; v < na; ++v) {
+        uint4 *k = reinterpret_cast<uint4 *>(a[v].kst);
+        uint4 *c = reinterpret_cast<uint4 *>(a[v].cnt);
+        for (int i = tid; i < K4; i += gt) k[i] = none;
+        for (int i = tid; i < C4; i += gt) c[i] = zero;
+    }
+}
+
+// Kernel codes and shadow counts of chunk (row, ch), merged over NA areas.
+template <int NA>
+__device__ __forceinline__ uint32_t chunk_codes(const WarpArea *a, int wd) {
+    uint32_t k = a[0].kst[wd];
+#pragma unroll
+    for (int v = 1; v < NA; ++v) k = vmin4(k, a[v].kst[wd]);
+    return k;
+}
+template <int NA>
+__device__ __forceinline__ uint2 chunk_counts(const WarpArea *a, int row, int ch) {
+    uint2 cs = *reinterpret_cast<const uint2 *>(&a[0].cnt[row * 32 + ch * 4]);
+#pragma unroll
+    for (int v = 1; v < NA; ++v) {
+        const uint2 cv = *reinterpret_cast<const uint2 *>(&a[v].cnt[row * 32 + ch * 4]);
+        cs.x += cv.x;   // packed 16-bit counts: a voxel's total fits 16 bits
+        cs.y += cv.y;
+    }
+    return cs;
+}
+
+// Phase D by thread tid of gt over the brick's 512 chunks (chunk c = row * 8
+// + ch): the grid masks of every chunk with kernel codes are loaded (BATCH
+// per thread before any is used), lowered to the kernel codes and stored
+// where they change; then the counters of every chunk with shadow counts are
+// loaded, bumped with saturation and stored, and the crossing voxels' signs
+// set (Eqs. 5-6).
+template <int NA, int BATCH>
+__device__ __forceinline__ void write_back(const DevGrid &g, int bx, int by, int bz,
+                                           const WarpArea *a, int tid, int gt, uint32_t T,
+                                           uint32_t Hmax, uint32_t &form_bad) {
+    for (int c0 = tid; c0 < BCHUNKS; c0 += BATCH * gt) {
+        uint4 m[BATCH];
+        uint32_t has = 0;
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) {
+            const int c = c0 + q * gt;
+            m[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (c < BCHUNKS) {
+                const int row = c >> 3, ch = c & 7;
+                if (chunk_codes<NA>(a, kword(row, ch)) != NO_CODE4) {
+                    has |= 1u << q;
+                    m[q] = __ldcg(reinterpret_cast<const uint4 *>(
+                        g.mask + chunk_index(g, bx, by, bz, row, ch)));
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) {
+            if (!((has >> q) & 1u)) continue;
+            const int c = c0 + q * gt, row = c >> 3, ch = c & 7;
+            const uint32_t k = chunk_codes<NA>(a, kword(row, ch));
+            const uint32_t old = codes_of(m[q], form_bad);
+            const uint32_t lt = code_lt(old, k);
+            if (lt) store_codes(g, chunk_index(g, bx, by, bz, row, ch), code_min(old, k, lt));
+        }
+        uint2 hv[BATCH];
+        uint32_t hc = 0;
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) {
+            const int c = c0 + q * gt;
+            hv[q] = make_uint2(0u, 0u);
+            if (c < BCHUNKS) {
+                const int row = c >> 3, ch = c & 7;
+                const uint2 cs = chunk_counts<NA>(a, row, ch);
+                if (cs.x | cs.y) {
+                    hc |= 1u << q;
+                    hv[q] = __ldcg(reinterpret_cast<const uint2 *>(
+                        g.hits + chunk_index(g, bx, by, bz, row, ch)));
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) {
+            if (!((hc >> q) & 1u)) continue;
+            const int c = c0 + q * gt, row = c >> 3, ch = c & 7;
+            const size_t gi = chunk_index(g, bx, by, bz, row, ch);
+            const uint32_t cross = apply_counts(hv[q], chunk_counts<NA>(a, row, ch), T, Hmax);
+            __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv[q]);
+            store_crossings(g, gi, cross);
+        }
     }
 }
 
@@ -312,10 +384,12 @@ static_assert(dense_scratch_bytes(HALF_GROUP_MAX_R) <= (WPC / 2 - 1) * (int)size
 
 // Run by a heavy group of gt threads (gw = gt / 32 warps); tid is the
 // thread's index in the group, areas the group's first warp area, and the
-// group synchronises on named barrier bar.
+// group synchronises on named barrier bar.  The codes of area 0 are all
+// written by pass z (32 where no contact's window reaches), its counts
+// cleared here.
 __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const uint32_t *pairs,
                                 uint32_t len, WarpArea *areas, const uint8_t *ctab,
-                                const uint32_t *sh, const uint32_t *shs, int R, int SR,
+                                const DevTables &t, int R, int SR,
                                 uint32_t T, uint32_t Hmax, uint32_t &form_bad, int tid, int gt,
                                 int bar) {
     const int lane = tid & 31, warp = tid >> 5, gw = gt >> 5;
@@ -328,16 +402,11 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
     uint32_t *nlist = pmask + D;           // number of rows with a contact
     uint16_t *list = reinterpret_cast<uint16_t *>(nlist + 1);              // those rows
     WarpArea *a0 = areas;
-    const uint32_t *need = a0->need;
     const uint32_t inf4 = DENSE_INF * 0x01010101u;
-    // B: stage the covered chunks once; clear the occupancy
-    for (int c = tid; c < BCHUNKS; c += gt) {
-        const int row = c >> 3, ch = c & 7;
-        if ((need[row] >> ch) & 1u) {
-            const int wd = kword(row, ch);
-            a0->kst[wd] = load_codes(g, chunk_index(g, bx, by, bz, row, ch), form_bad);
-            *reinterpret_cast<uint2 *>(&a0->cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
-        }
+    // clear the counts and the occupancy
+    {
+        uint4 *c = reinterpret_cast<uint4 *>(a0->cnt);
+        for (int i = tid; i < BVOX / 8; i += gt) c[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     for (int r = tid; r < D * D; r += gt) occ[r] = 0ull;
     if (tid < D) pmask[tid] = 0u;
@@ -394,48 +463,26 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
     uint32_t planes = 0;                   // planes with any contact
     for (int zp = 0; zp < D; ++zp) planes |= (pmask[zp] ? 1u : 0u) << zp;
     group_sync(bar, gt);
-    // pass z (taps only from planes with contacts), codes, and Eq. 4 on the
-    // staged brick
-    // (a warp covers four whole rows: idx = row * 8 + w; its ballot gives the
-    // rows' changed-word bytes, each written once by the row's first lane)
+    // pass z (taps only from planes with contacts) and the codes: the
+    // minimum kernel code of every voxel of the brick
     for (int idx = tid; idx < BROWS * 8; idx += gt) {
         const int w = idx & 7, row = idx >> 3, y = row & 7, z = row >> 3;
-        bool changed = false;
-        if ((need[row] >> w) & 1u) {
-            uint32_t acc = inf4;
-            for (uint32_t m = (planes >> z) & twin; m; m &= m - 1u) {
-                const int t = __ffs(m) - 1, dz = t - R;
-                acc = vmin4(acc, g2[((z + t) * 8 + y) * 8 + w] + (uint32_t)(dz * dz) * 0x01010101u);
-            }
-            const uint32_t code = (uint32_t)ctab[acc & 255u] |
-                                  ((uint32_t)ctab[(acc >> 8) & 255u] << 8) |
-                                  ((uint32_t)ctab[(acc >> 16) & 255u] << 16) |
-                                  ((uint32_t)ctab[acc >> 24] << 24);
-            const int wd = kword(row, w);
-            const uint32_t old = a0->kst[wd];
-            const uint32_t lt = code_lt(old, code);
-            if (lt) {
-                a0->kst[wd] = code_min(old, code, lt);
-                changed = true;
-            }
+        uint32_t acc = inf4;
+        for (uint32_t m = (planes >> z) & twin; m; m &= m - 1u) {
+            const int t = __ffs(m) - 1, dz = t - R;
+            acc = vmin4(acc, g2[((z + t) * 8 + y) * 8 + w] + (uint32_t)(dz * dz) * 0x01010101u);
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, changed);
-        if ((lane & 7) == 0) a0->drow[row] = (uint8_t)(bal >> (lane & 24));
+        a0->kst[kword(row, w)] = (uint32_t)ctab[acc & 255u] | ((uint32_t)ctab[(acc >> 8) & 255u] << 8) |
+                                 ((uint32_t)ctab[(acc >> 16) & 255u] << 16) |
+                                 ((uint32_t)ctab[acc >> 24] << 24);
     }
-    // Eq. 5 counts: pairs spread over the warps, counted into one array
-    for (uint32_t j = warp; j < len; j += gw)
-        shadow_pair<true>(__ldg(pairs + j), a0->cnt, sh, shs, R, SR, lane);
+    // Eq. 5 counts: pairs 32 at a time per warp, counted into one array
+    for (uint32_t j0 = 32u * warp; j0 < len; j0 += 32u * gw) {
+        const uint32_t mine = j0 + lane < len ? __ldg(pairs + j0 + lane) : 0u;
+        shadow_pairs<true>(mine, (int)min(32u, len - j0), a0->cnt, t, R, SR, lane);
+    }
     group_sync(bar, gt);
-    // D
-    for (int c = tid; c < BCHUNKS; c += gt) {
-        const int row = c >> 3, ch = c & 7;
-        if ((need[row] >> ch) & 1u) {
-            const int wd = kword(row, ch);
-            store_chunk(g, chunk_index(g, bx, by, bz, row, ch), a0->kst[wd],
-                        ((a0->drow[row] >> ch) & 1u) != 0,
-                        *reinterpret_cast<const uint2 *>(&a0->cnt[row * 32 + ch * 4]), T, Hmax);
-        }
-    }
+    write_back<1, 4>(g, bx, by, bz, a0, tid, gt, T, Hmax, form_bad);
 }
 
 // Grid of global brick b in a batch (bricks of grid m are [bbase[m], bbase[m+1])).
@@ -466,7 +513,6 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
                                                     DevTables t, long long n_input, WsDev ws) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t s_item[2];                        // per heavy group
-    __shared__ unsigned long long s_cr[2][CHUNKS_PER_ROW];
     __shared__ uint8_t s_ctab[256];
     for (int j = threadIdx.x; j < 256; j += NTHR) {
         int kk = 0;
@@ -479,9 +525,8 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
     uint32_t *P = smem;
     for (int j = threadIdx.x; j < np; j += NTHR) P[j] = t.prow[j];
     WarpArea *areas = reinterpret_cast<WarpArea *>(smem + ((np + 3) & ~3));
-    // shadow offsets stay in global memory (read-only path, L1-resident): the
-    // shared memory they would take costs a CTA per SM
-    const uint32_t *sh = t.sh_off, *shs = t.sh_start;
+    // shadow offset lists stay in global memory (read-only path,
+    // L1-resident): the shared memory they would take costs a CTA per SM
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     WarpArea *wa = areas + warp;
     // the tables above are the kernels' own; the workspace is the previous
@@ -526,7 +571,6 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
                     s_item[gidx] = first_heavy ? blockIdx.x
                                                : n_static_heavy + atomicAdd(&ws.hdr->next_heavy, 1u);
                 first_heavy = false;
-                if (gtid < CHUNKS_PER_ROW) s_cr[gidx][gtid] = 0ull;
                 group_sync(gbar, ht);
                 const uint32_t it = s_item[gidx];
                 if (it >= nheavy) break;
@@ -542,81 +586,35 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
                 const int by = (int)(byz % (uint32_t)g.nby), bz = (int)(byz / (uint32_t)g.nby);
                 const uint32_t *pairs = ws.pairs + start;
 
-                // A
-                unsigned long long cr[CHUNKS_PER_ROW];
-#pragma unroll
-                for (int c = 0; c < CHUNKS_PER_ROW; ++c) cr[c] = 0ull;
-                coverage(pairs, 32u * gwarp, len, 32u * hw, R, lane, cr);
-                if (lane < CHUNKS_PER_ROW) {
-                    unsigned long long mine = 0ull;
-#pragma unroll
-                    for (int c = 0; c < CHUNKS_PER_ROW; ++c)
-                        if (c == lane) mine = cr[c];
-                    atomicOr(&s_cr[gidx][lane], mine);
-                }
-                group_sync(gbar, ht);
-                uint32_t *need = garea[0].need;
-                if (gtid < BROWS) {
-                    uint32_t nb = 0;
-#pragma unroll
-                    for (int c = 0; c < CHUNKS_PER_ROW; ++c)
-                        nb |= (uint32_t)((s_cr[gidx][c] >> gtid) & 1ull) << c;
-                    need[gtid] = nb;
-                }
-                group_sync(gbar, ht);
-                if constexpr (NW == 4) {
-                    integrate_dense(g, bx, by, bz, pairs, len, garea, s_ctab, sh, shs, R, SR, T, Hmax,
-                                    form_bad, gtid, ht, gbar);
-                    if (gtid == 0) ws.bcnt[b] = 0u;
-                    continue;
-                }
-                // B: stage into every warp's copy
-                for (int c = gtid; c < BCHUNKS; c += ht) {
-                    const int row = c >> 3, ch = c & 7;
-                    if ((need[row] >> ch) & 1u) {
-                        const uint32_t k = load_codes(g, chunk_index(g, bx, by, bz, row, ch), form_bad);
-                        const int wd = kword(row, ch);
-#pragma unroll
-                        for (int v = 0; v < WPC; ++v) {
-                            garea[v].kst[wd] = k;
-                            *reinterpret_cast<uint2 *>(&garea[v].cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
+                // the pairs in rounds of at most CNT_ROUND, so that no count can
+                // pass 2^16 (group-uniform: every thread sees the same len)
+                for (uint32_t r0 = 0; r0 < len; r0 += CNT_ROUND) {
+                    const uint32_t *rp = pairs + r0;
+                    const uint32_t rl = min(len - r0, CNT_ROUND);
+                    if constexpr (NW == 4) {
+                        integrate_dense(g, bx, by, bz, rp, rl, garea, s_ctab, t, R, SR, T, Hmax,
+                                        form_bad, gtid, ht, gbar);
+                        group_sync(gbar, ht);
+                        continue;
+                    }
+                    // I: every warp's area
+                    clear_areas(garea, hw, gtid, ht);
+                    group_sync(gbar, ht);
+                    // C: warp w applies pairs w, w + WPC, w + 2 WPC, ... to its own area
+                    for (uint32_t base = 0; base * WPC + warp < rl; base += 32) {
+                        const uint32_t jj = (base + lane) * WPC + warp;
+                        const uint32_t mine = jj < rl ? __ldg(rp + jj) : 0u;
+                        const int cnt = (int)min(32u, (rl - warp + WPC - 1) / WPC - base);
+                        for (int j = 0; j < cnt; ++j) {
+                            apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, R, W, lane);
+                            __syncwarp();
                         }
+                        shadow_pairs<false>(mine, cnt, wa->cnt, t, R, SR, lane);
                     }
-                }
-                for (int i = gtid; i < hw * BROWS; i += ht) garea[i / BROWS].drow[i % BROWS] = 0;
-                group_sync(gbar, ht);
-                // C: warp w applies pairs w, w + WPC, w + 2 WPC, ...
-                for (uint32_t base = 0; base * WPC + warp < len; base += 32) {
-                    const uint32_t jj = (base + lane) * WPC + warp;
-                    const uint32_t mine = jj < len ? __ldg(pairs + jj) : 0u;
-                    const int cnt = (int)min(32u, (len - warp + WPC - 1) / WPC - base);
-                    for (int j = 0; j < cnt; ++j) {
-                        const uint32_t pl = __shfl_sync(0xffffffffu, mine, j);
-                        apply_pair<NW>(pl, wa, P, R, W, lane);
-                        shadow_pair<false>(pl, wa->cnt, sh, shs, R, SR, lane);
-                        __syncwarp();
-                    }
-                }
-                group_sync(gbar, ht);
-                // D: merge the copies and write back
-                for (int c = gtid; c < BCHUNKS; c += ht) {
-                    const int row = c >> 3, ch = c & 7;
-                    if ((need[row] >> ch) & 1u) {
-                        const int wd = kword(row, ch);
-                        uint32_t k = garea[0].kst[wd];
-                        uint32_t dirty = (garea[0].drow[row] >> ch) & 1u;
-                        uint2 cs = *reinterpret_cast<const uint2 *>(&garea[0].cnt[row * 32 + ch * 4]);
-#pragma unroll
-                        for (int v = 1; v < WPC; ++v) {
-                            k = vmin4(k, garea[v].kst[wd]);
-                            dirty |= (garea[v].drow[row] >> ch) & 1u;
-                            const uint2 cv =
-                                *reinterpret_cast<const uint2 *>(&garea[v].cnt[row * 32 + ch * 4]);
-                            cs.x += cv.x;   // packed 16-bit counts: a voxel's total fits 16 bits
-                            cs.y += cv.y;
-                        }
-                        store_chunk(g, chunk_index(g, bx, by, bz, row, ch), k, dirty != 0, cs, T, Hmax);
-                    }
+                    group_sync(gbar, ht);
+                    // D: the areas merged (byte-wise min of codes, sum of counts) and written back
+                    write_back<WPC, 2>(g, bx, by, bz, garea, gtid, ht, T, Hmax, form_bad);
+                    group_sync(gbar, ht);
                 }
                 if (gtid == 0) ws.bcnt[b] = 0u;
             }
@@ -655,91 +653,26 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
                 const int by = (int)(byz % (uint32_t)g.nby), bz = (int)(byz / (uint32_t)g.nby);
                 const uint32_t *pairs = ws.pairs + start;
 
-                // A
-                unsigned long long cr[CHUNKS_PER_ROW];
-#pragma unroll
-                for (int c = 0; c < CHUNKS_PER_ROW; ++c) cr[c] = 0ull;
-                coverage(pairs, 0u, len, 32u, R, lane, cr);
-                {
-                    uint32_t n0 = 0, n1 = 0;
-#pragma unroll
-                    for (int c = 0; c < CHUNKS_PER_ROW; ++c) {
-                        n0 |= (uint32_t)((cr[c] >> lane) & 1ull) << c;
-                        n1 |= (uint32_t)((cr[c] >> (lane + 32)) & 1ull) << c;
-                    }
-                    wa->need[lane] = n0;
-                    wa->need[lane + 32] = n1;
-                }
-                __syncwarp();
-                // B: lanes = 4 rows x 8 chunks; the masks of eight chunks are loaded
-                // before any shared-memory store (the stores go through a generic
-                // pointer, so the compiler would otherwise wait for each load in turn)
-                const int rs = lane >> 3, ch = lane & 7;
-                for (int i0 = 0; i0 < BROWS / 4; i0 += 8) {
-                    uint4 m[8];
-                    uint32_t nd = 0;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int row = rs + 4 * (i0 + q);
-                        m[q] = make_uint4(0u, 0u, 0u, 0u);
-                        if ((wa->need[row] >> ch) & 1u) {
-                            nd |= 1u << q;
-                            m[q] = __ldcg(reinterpret_cast<const uint4 *>(
-                                g.mask + chunk_index(g, bx, by, bz, row, ch)));
+                for (uint32_t r0 = 0; r0 < len; r0 += CNT_ROUND) {   // rounds as for heavy bricks
+                    const uint32_t *rp = pairs + r0;
+                    const uint32_t rl = min(len - r0, CNT_ROUND);
+                    // I
+                    clear_areas(wa, 1, lane, 32);
+                    __syncwarp();
+                    // C
+                    for (uint32_t base = 0; base < rl; base += 32) {
+                        const uint32_t mine = base + lane < rl ? __ldg(rp + base + lane) : 0u;
+                        const int cnt = (int)min(32u, rl - base);
+                        for (int j = 0; j < cnt; ++j) {
+                            apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, R, W, lane);
+                            __syncwarp();
                         }
+                        shadow_pairs<false>(mine, cnt, wa->cnt, t, R, SR, lane);
                     }
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        if (!((nd >> q) & 1u)) continue;
-                        const int row = rs + 4 * (i0 + q);
-                        const int wd = kword(row, ch);
-                        wa->kst[wd] = codes_of(m[q], form_bad);
-                        *reinterpret_cast<uint2 *>(&wa->cnt[row * 32 + ch * 4]) = make_uint2(0u, 0u);
-                    }
-                }
-                wa->drow[lane] = 0;
-                wa->drow[lane + 32] = 0;
-                __syncwarp();
-                // C
-                for (uint32_t base = 0; base < len; base += 32) {
-                    const uint32_t mine = base + lane < len ? __ldg(pairs + base + lane) : 0u;
-                    const int cnt = (int)min(32u, len - base);
-                    for (int j = 0; j < cnt; ++j) {
-                        const uint32_t pl = __shfl_sync(0xffffffffu, mine, j);
-                        apply_pair<NW>(pl, wa, P, R, W, lane);
-                        shadow_pair<false>(pl, wa->cnt, sh, shs, R, SR, lane);
-                        __syncwarp();
-                    }
-                }
-                // D: the old counters of four chunks are loaded before any of them
-                // is stored (stores in between would serialise the loads)
-                for (int i0 = 0; i0 < BROWS / 4; i0 += 4) {
-                    uint2 cs[4], hv[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int row = rs + 4 * (i0 + q);
-                        cs[q] = make_uint2(0u, 0u);
-                        hv[q] = make_uint2(0u, 0u);
-                        if ((wa->need[row] >> ch) & 1u) {
-                            cs[q] = *reinterpret_cast<const uint2 *>(&wa->cnt[row * 32 + ch * 4]);
-                            if (cs[q].x | cs[q].y)
-                                hv[q] = __ldcg(reinterpret_cast<const uint2 *>(
-                                    g.hits + chunk_index(g, bx, by, bz, row, ch)));
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int row = rs + 4 * (i0 + q);
-                        if (!((wa->need[row] >> ch) & 1u)) continue;
-                        const int wd = kword(row, ch);
-                        const size_t gi = chunk_index(g, bx, by, bz, row, ch);
-                        if ((wa->drow[row] >> ch) & 1u) store_codes(g, gi, wa->kst[wd]);
-                        if (cs[q].x | cs[q].y) {
-                            const uint32_t cross = apply_counts(hv[q], cs[q], T, Hmax);
-                            __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv[q]);
-                            store_crossings(g, gi, cross);
-                        }
-                    }
+                    // D
+                    __syncwarp();
+                    write_back<1, 4>(g, bx, by, bz, wa, lane, 32, T, Hmax, form_bad);
+                    __syncwarp();
                 }
                 if (lane == 0) ws.bcnt[b] = 0u;
                 __syncwarp();

@@ -130,6 +130,7 @@ def test_host_entry_point_pipelined(orc):
 @pytest.mark.parametrize("variant", [
     dict(dedup_first=0),
     dict(shadow_radius=0.0, dedup_first=0, hit_max=65535),
+    dict(dedup_first=0, hit_threshold=5, hit_max=60000),     # counters by compare-and-swap
     dict(shadow_radius=5.0, hit_threshold=1, hit_max=2),
     dict(kernel_size=3, shadow_radius=1.0),
     dict(kernel_size=21, scheme=1, bins_a=40, bins_b=40, shadow_radius=3.0),   # the paper's
