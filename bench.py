@@ -858,7 +858,8 @@ def run_maps(args, rank, world):
 
 def run_mesh(args, rank, world):
     """Map export (Fig. 3: Marching Cubes at iso = 0) at the urban map's size:
-    a 1600 x 1600 x 320 stepped-terrain map state (819 M cells).  A step is
+    a 1600 x 1600 x 320 stepped-terrain map state (819 M cells; --mesh-side
+    scales it).  A step is
     one dbt_mesh_extract of the whole map (count pass, scan, emit pass);
     value = cells meshed per second.  Roofline: the count pass, 5 bytes read
     per voxel (mask + sign)."""
@@ -867,7 +868,8 @@ def run_mesh(args, rank, world):
     import paper_2509_20081_gb300 as dbt
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    nx, ny, nz, res = 1600, 1600, 320, 0.05
+    nx = ny = args.mesh_side
+    nz, res = args.mesh_side // 5, 0.05
     m, s, _ = synth.terrain_state(nx, ny, nz, 21)
     g = dbt.Grid(nx, ny, nz, res)
     g.load(m, s)
@@ -1127,6 +1129,9 @@ def main():
                     choices=["urban", "urban_half", "highres", "maps", "serving", "mesh", "quality"],
                     default="urban")
     ap.add_argument("--maps", type=int, default=32, help="maps workload: number of maps")
+    ap.add_argument("--mesh-side", type=int, default=1600,
+                    help="mesh workload: map side in voxels (height side / 5), e.g. 800 for a "
+                         "profiler-sized case")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: simulated seconds")
     ap.add_argument("--speeds", default="1,8,16,24,32,48,64",
                     help="serving: replay speed-ups")
