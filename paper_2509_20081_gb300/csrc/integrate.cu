@@ -115,23 +115,46 @@ __device__ __forceinline__ PairBox decode_pair(uint32_t pl, int R) {
 // rows are spread over the lanes (row r -> z = r / wy, y = r % wy, the
 // division by wy <= 8 done exactly as (r * ceil(256 / wy)) >> 8 for r < 64);
 // each lane lowers the codes of the up to NW words of its row.  Each lane
-// owns its row within one pair, so no two lanes write one word.
-template <int NW>
-__device__ __forceinline__ void apply_pair(uint32_t pl, WarpArea *wa, const uint32_t *P, int R,
-                                           int W, int lane) {
+// owns its row within one pair, so no two lanes write one word.  The pair's
+// set-up (clipped box, first word, table shift) is taken by the lane that
+// holds the pair, for 32 pairs at once, and handed out packed in two words:
+//   a = nrows | (magic - 1) << 7 | wy << 15 | y0 << 19 | z0 << 22 | nw << 25 | w0 << 28
+//   b = s0 | (cy + 32) << 8 | (cz + 32) << 16
+struct RowsSetup {
+    uint32_t a, b;
+};
+
+__device__ __forceinline__ RowsSetup rows_setup(uint32_t pl, int R) {
     const PairBox b = decode_pair(pl, R);
     const int wy = b.y1 - b.y0 + 1;
     const int nrows = wy * (b.z1 - b.z0 + 1);
-    // ceil(256 / wy) for wy = 1..8, less one, as bytes 0..7 of one word
+    // ceil(256 / wy) - 1 for wy = 1..8 as bytes 0..7 of one word
     // (255 127 85 63 51 42 36 31): no integer division
-    const int magic = (int)((0x1F242A333F557FFFull >> (8 * (wy - 1))) & 0xFFull) + 1;
+    const uint32_t magic1 = (uint32_t)((0x1F242A333F557FFFull >> (8 * (wy - 1))) & 0xFFull);
     const int w0 = b.x0 >> 2;
     const int nw = (b.x1 >> 2) - w0;
     const int s0 = 4 * w0 - b.cx + R + 3;
+    RowsSetup su;
+    su.a = (uint32_t)nrows | (magic1 << 7) | ((uint32_t)wy << 15) | ((uint32_t)b.y0 << 19) |
+           ((uint32_t)b.z0 << 22) | ((uint32_t)nw << 25) | ((uint32_t)w0 << 28);
+    su.b = (uint32_t)s0 | ((uint32_t)(b.cy + 32) << 8) | ((uint32_t)(b.cz + 32) << 16);
+    return su;
+}
+
+template <int NW>
+__device__ __forceinline__ void apply_rows(RowsSetup su, WarpArea *wa, const uint32_t *P, int W,
+                                           int lane) {
+    const int nrows = (int)(su.a & 127u);
+    const int magic = (int)((su.a >> 7) & 255u) + 1;
+    const int wy = (int)((su.a >> 15) & 15u);
+    const int y0 = (int)((su.a >> 19) & 7u), z0 = (int)((su.a >> 22) & 7u);
+    const int nw = (int)((su.a >> 25) & 7u), w0 = (int)(su.a >> 28);
+    const int s0 = (int)(su.b & 255u);
+    const int cy = (int)((su.b >> 8) & 255u) - 32, cz = (int)((su.b >> 16) & 255u) - 32;
     for (int r = lane; r < nrows; r += 32) {
         const int qz = (r * magic) >> 8;
-        const int ry = b.y0 + (r - qz * wy), rz = b.z0 + qz;
-        const int oy = ry - b.cy, oz = rz - b.cz;
+        const int ry = y0 + (r - qz * wy), rz = z0 + qz;
+        const int oy = ry - cy, oz = rz - cz;
         const int pb = (oy * oy + oz * oz) * W + s0;
         const int row = rz * BY + ry;
         const int rbase = row * 8, f = (row >> 2) & 7;
@@ -294,11 +317,11 @@ __device__ __forceinline__ uint2 chunk_counts(const WarpArea *a, int row, int ch
 }
 
 // Phase D by thread tid of gt over the brick's 512 chunks (chunk c = row * 8
-// + ch): the grid masks of every chunk with kernel codes are loaded (BATCH
-// per thread before any is used), lowered to the kernel codes and stored
-// where they change; then the counters of every chunk with shadow counts are
-// loaded, bumped with saturation and stored, and the crossing voxels' signs
-// set (Eqs. 5-6).
+// + ch), BATCH chunks per thread at a time: the grid masks of the chunks with
+// kernel codes and the counters of the chunks with shadow counts are all
+// loaded before any is used; masks are lowered to the kernel codes and
+// stored where they change, counters bumped with saturation and stored, and
+// the crossing voxels' signs set (Eqs. 5-6).
 template <int NA, int BATCH>
 __device__ __forceinline__ void write_back(const DevGrid &g, int bx, int by, int bz,
                                            const WarpArea *a, int tid, int gt, uint32_t T,
@@ -319,15 +342,6 @@ __device__ __forceinline__ void write_back(const DevGrid &g, int bx, int by, int
                 }
             }
         }
-#pragma unroll
-        for (int q = 0; q < BATCH; ++q) {
-            if (!((has >> q) & 1u)) continue;
-            const int c = c0 + q * gt, row = c >> 3, ch = c & 7;
-            const uint32_t k = chunk_codes<NA>(a, kword(row, ch));
-            const uint32_t old = codes_of(m[q], form_bad);
-            const uint32_t lt = code_lt(old, k);
-            if (lt) store_codes(g, chunk_index(g, bx, by, bz, row, ch), code_min(old, k, lt));
-        }
         uint2 hv[BATCH];
         uint32_t hc = 0;
 #pragma unroll
@@ -343,6 +357,15 @@ __device__ __forceinline__ void write_back(const DevGrid &g, int bx, int by, int
                         g.hits + chunk_index(g, bx, by, bz, row, ch)));
                 }
             }
+        }
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) {
+            if (!((has >> q) & 1u)) continue;
+            const int c = c0 + q * gt, row = c >> 3, ch = c & 7;
+            const uint32_t k = chunk_codes<NA>(a, kword(row, ch));
+            const uint32_t old = codes_of(m[q], form_bad);
+            const uint32_t lt = code_lt(old, k);
+            if (lt) store_codes(g, chunk_index(g, bx, by, bz, row, ch), code_min(old, k, lt));
         }
 #pragma unroll
         for (int q = 0; q < BATCH; ++q) {
@@ -605,8 +628,11 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
                         const uint32_t jj = (base + lane) * WPC + warp;
                         const uint32_t mine = jj < rl ? __ldg(rp + jj) : 0u;
                         const int cnt = (int)min(32u, (rl - warp + WPC - 1) / WPC - base);
+                        const RowsSetup su = rows_setup(mine, R);    // lanes >= cnt: unused
                         for (int j = 0; j < cnt; ++j) {
-                            apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, R, W, lane);
+                            const RowsSetup sj = {__shfl_sync(0xffffffffu, su.a, j),
+                                                  __shfl_sync(0xffffffffu, su.b, j)};
+                            apply_rows<NW>(sj, wa, P, W, lane);
                             __syncwarp();
                         }
                         shadow_pairs<false>(mine, cnt, wa->cnt, t, R, SR, lane);
@@ -663,8 +689,11 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
                     for (uint32_t base = 0; base < rl; base += 32) {
                         const uint32_t mine = base + lane < rl ? __ldg(rp + base + lane) : 0u;
                         const int cnt = (int)min(32u, rl - base);
+                        const RowsSetup su = rows_setup(mine, R);    // lanes >= cnt: unused
                         for (int j = 0; j < cnt; ++j) {
-                            apply_pair<NW>(__shfl_sync(0xffffffffu, mine, j), wa, P, R, W, lane);
+                            const RowsSetup sj = {__shfl_sync(0xffffffffu, su.a, j),
+                                                  __shfl_sync(0xffffffffu, su.b, j)};
+                            apply_rows<NW>(sj, wa, P, W, lane);
                             __syncwarp();
                         }
                         shadow_pairs<false>(mine, cnt, wa->cnt, t, R, SR, lane);
