@@ -118,8 +118,9 @@ __device__ __forceinline__ PairBox decode_pair(uint32_t pl, int R) {
 // owns its row within one pair, so no two lanes write one word.  The pair's
 // set-up (clipped box, first word, table shift) is taken by the lane that
 // holds the pair, for 32 pairs at once, and handed out packed in two words:
-//   a = nrows | (magic - 1) << 7 | wy << 15 | y0 << 19 | z0 << 22 | nw << 25 | w0 << 28
+//   a = nrows | wy << 8 | y0 << 12 | z0 << 16 | nw << 21 | w0 << 24
 //   b = s0 | (cy + 32) << 8 | (cz + 32) << 16
+// The row split r / wy is (r * ceil(65536 / wy)) >> 16, exact for r < 1024.
 struct RowsSetup {
     uint32_t a, b;
 };
@@ -128,15 +129,12 @@ __device__ __forceinline__ RowsSetup rows_setup(uint32_t pl, int R) {
     const PairBox b = decode_pair(pl, R);
     const int wy = b.y1 - b.y0 + 1;
     const int nrows = wy * (b.z1 - b.z0 + 1);
-    // ceil(256 / wy) - 1 for wy = 1..8 as bytes 0..7 of one word
-    // (255 127 85 63 51 42 36 31): no integer division
-    const uint32_t magic1 = (uint32_t)((0x1F242A333F557FFFull >> (8 * (wy - 1))) & 0xFFull);
     const int w0 = b.x0 >> 2;
     const int nw = (b.x1 >> 2) - w0;
     const int s0 = 4 * w0 - b.cx + R + 3;
     RowsSetup su;
-    su.a = (uint32_t)nrows | (magic1 << 7) | ((uint32_t)wy << 15) | ((uint32_t)b.y0 << 19) |
-           ((uint32_t)b.z0 << 22) | ((uint32_t)nw << 25) | ((uint32_t)w0 << 28);
+    su.a = (uint32_t)nrows | ((uint32_t)wy << 8) | ((uint32_t)b.y0 << 12) | ((uint32_t)b.z0 << 16) |
+           ((uint32_t)nw << 21) | ((uint32_t)w0 << 24);
     su.b = (uint32_t)s0 | ((uint32_t)(b.cy + 32) << 8) | ((uint32_t)(b.cz + 32) << 16);
     return su;
 }
@@ -144,15 +142,17 @@ __device__ __forceinline__ RowsSetup rows_setup(uint32_t pl, int R) {
 template <int NW>
 __device__ __forceinline__ void apply_rows(RowsSetup su, WarpArea *wa, const uint32_t *P, int W,
                                            int lane) {
-    const int nrows = (int)(su.a & 127u);
-    const int magic = (int)((su.a >> 7) & 255u) + 1;
-    const int wy = (int)((su.a >> 15) & 15u);
-    const int y0 = (int)((su.a >> 19) & 7u), z0 = (int)((su.a >> 22) & 7u);
-    const int nw = (int)((su.a >> 25) & 7u), w0 = (int)(su.a >> 28);
+    const int nrows = (int)(su.a & 255u);
+    const int wy = (int)((su.a >> 8) & 15u);
+    const int y0 = (int)((su.a >> 12) & 15u), z0 = (int)((su.a >> 16) & 31u);
+    const int nw = (int)((su.a >> 21) & 7u), w0 = (int)((su.a >> 24) & 15u);
+    // ceil(65536 / wy) - 1 for wy = 1..8 as 16-bit fields (no integer division)
+    const uint64_t mt = wy <= 4 ? 0x3FFF55557FFFFFFFull : 0x1FFF24922AAA3333ull;
+    const int magic = (int)((mt >> (16 * ((wy - 1) & 3))) & 0xFFFFull) + 1;
     const int s0 = (int)(su.b & 255u);
     const int cy = (int)((su.b >> 8) & 255u) - 32, cz = (int)((su.b >> 16) & 255u) - 32;
     for (int r = lane; r < nrows; r += 32) {
-        const int qz = (r * magic) >> 8;
+        const int qz = (r * magic) >> 16;
         const int ry = y0 + (r - qz * wy), rz = z0 + qz;
         const int oy = ry - cy, oz = rz - cz;
         const int pb = (oy * oy + oz * oz) * W + s0;
@@ -189,13 +189,16 @@ __device__ __forceinline__ void apply_rows(RowsSetup su, WarpArea *wa, const uin
 // is packed as bytes c + 32, so one 32-bit add gives per byte o + c + 64,
 // which lies in [44, 115] (|o| <= SR <= 10, c in [-SR, 31 + SR]): no byte
 // carries into the next.  The voxel o + c is in the brick exactly when that
-// byte is in [64, 96) for x and in [64, 72) for y and z, i.e. bits 7..5 of
-// the x byte read 010 and bits 7..3 of the y and z bytes read 01000: one AND
-// and one compare.  Lanes past the range take 0x80 bytes, which set bit 7
-// and fail.  The low bits of the bytes are then x, y and z.
-static_assert(BX == 32 && BY == 8 && BZ == 8 && MAX_R <= 10 && OFF_BIAS == 32,
-              "shadow_pairs' byte packing assumes 32 x 8 x 8 bricks and |offsets| <= 10");
+// byte is in [64, 64 + BX) for x, [64, 64 + BY) for y and [64, 64 + BZ) for
+// z, i.e. (for power-of-two sides dividing 64) when the bits above the side
+// read 01: one AND and one compare.  Lanes past the range take 0x80 bytes,
+// which set bit 7 and fail.  The low bits of the bytes are then x, y and z.
+static_assert(BX == 32 && BY == 8 && (BZ == 4 || BZ == 8 || BZ == 16) && MAX_R <= 10 &&
+                  OFF_BIAS == 32 && BZ - 1 + 4 * MAX_R + 64 < 128,
+              "shadow_pairs' byte packing: 32 x 8 x BZ bricks, |offsets| <= 10, no byte carry");
 constexpr uint32_t SH_PAD = 0x80808080u;
+constexpr uint32_t SH_INMASK = (uint32_t)(0xFF & ~(BX - 1)) | ((uint32_t)(0xFF & ~(BY - 1)) << 8) |
+                               ((uint32_t)(0xFF & ~(BZ - 1)) << 16);
 constexpr uint32_t CNT_ROUND = 65535u;
 template <bool ATOMIC>
 __device__ __forceinline__ void shadow_pairs(uint32_t mine, int n, uint16_t *cnt, const DevTables &t,
@@ -233,8 +236,9 @@ __device__ __forceinline__ void shadow_pairs(uint32_t mine, int n, uint16_t *cnt
         for (uint32_t e = a0; e < a1; e += 32) {
             const uint32_t o = e + lane < a1 ? __ldg(sh + e + lane) : SH_PAD;
             const uint32_t u = o + pk;
-            if ((u & 0x00F8F8E0u) == 0x00404040u) {
-                const int v = (int)((u & 31u) | ((u >> 3) & 0xE0u) | ((u >> 8) & 0x700u));
+            if ((u & SH_INMASK) == 0x00404040u) {
+                // v = x + 32 (y + 8 z)
+                const int v = (int)((u & 31u) | ((u >> 3) & 0xE0u) | ((u >> 8) & ((BZ - 1u) << 8)));
                 if (ATOMIC)
                     atomicAdd(reinterpret_cast<uint32_t *>(cnt) + (v >> 1), 1u << (16 * (v & 1)));
                 else
@@ -397,8 +401,8 @@ constexpr uint32_t DENSE_INF = 127u;
 // lives in the warp areas of the heavy group after the first: at R = 6 all
 // eight warps form the group; up to R = 5 four do (three spare areas).
 __host__ __device__ constexpr int dense_scratch_bytes(int R) {
-    return 8 * (BY + 2 * R) * (BY + 2 * R) + 32 * (BY + 2 * R) * (BY + 2 * R) +
-           4 * 64 * (BY + 2 * R) + 4 * (BY + 2 * R) + 4 + 2 * (BY + 2 * R) * (BY + 2 * R);
+    return 8 * (BY + 2 * R) * (BZ + 2 * R) + 32 * (BY + 2 * R) * (BZ + 2 * R) +
+           4 * 8 * BY * (BZ + 2 * R) + 4 * (BZ + 2 * R) + 4 + 2 * (BY + 2 * R) * (BZ + 2 * R);
 }
 constexpr int HALF_GROUP_MAX_R = 5;
 static_assert(dense_scratch_bytes(6) <= (WPC - 1) * (int)sizeof(WarpArea), "dense scratch, R = 6");
@@ -416,13 +420,13 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
                                 uint32_t T, uint32_t Hmax, uint32_t &form_bad, int tid, int gt,
                                 int bar) {
     const int lane = tid & 31, warp = tid >> 5, gw = gt >> 5;
-    const int D = BY + 2 * R;                                   // dilated y / z extent
+    const int DY = BY + 2 * R, DZ = BZ + 2 * R;                 // dilated y / z extents
     unsigned char *scr = reinterpret_cast<unsigned char *>(areas + 1);
-    unsigned long long *occ = reinterpret_cast<unsigned long long *>(scr);   // D * D rows
-    uint32_t *g1 = reinterpret_cast<uint32_t *>(scr + D * D * 8);          // D * D rows x 8 words
-    uint32_t *g2 = g1 + D * D * 8;                                          // D x 8 rows x 8 words
-    uint32_t *pmask = g2 + D * 64;         // per dilated plane z: bit y = row (y, z) has a contact
-    uint32_t *nlist = pmask + D;           // number of rows with a contact
+    unsigned long long *occ = reinterpret_cast<unsigned long long *>(scr);   // DZ x DY rows
+    uint32_t *g1 = reinterpret_cast<uint32_t *>(scr + DY * DZ * 8);        // DZ x DY rows x 8 words
+    uint32_t *g2 = g1 + DY * DZ * 8;                                        // DZ x BY rows x 8 words
+    uint32_t *pmask = g2 + DZ * BY * 8;    // per dilated plane z: bit y = row (y, z) has a contact
+    uint32_t *nlist = pmask + DZ;          // number of rows with a contact
     uint16_t *list = reinterpret_cast<uint16_t *>(nlist + 1);              // those rows
     WarpArea *a0 = areas;
     const uint32_t inf4 = DENSE_INF * 0x01010101u;
@@ -431,21 +435,21 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
         uint4 *c = reinterpret_cast<uint4 *>(a0->cnt);
         for (int i = tid; i < BVOX / 8; i += gt) c[i] = make_uint4(0u, 0u, 0u, 0u);
     }
-    for (int r = tid; r < D * D; r += gt) occ[r] = 0ull;
-    if (tid < D) pmask[tid] = 0u;
+    for (int r = tid; r < DY * DZ; r += gt) occ[r] = 0ull;
+    if (tid < DZ) pmask[tid] = 0u;
     if (tid == 0) *nlist = 0u;
     group_sync(bar, gt);
     // contacts: payload coordinates are brick-relative + R, i.e. dilated indices
     for (uint32_t j = tid; j < len; j += gt) {
         const uint32_t pl = __ldg(pairs + j);
-        atomicOr(&occ[((pl >> 11) & 31u) * D + ((pl >> 6) & 31u)], 1ull << (pl & 63u));
+        atomicOr(&occ[((pl >> 11) & 31u) * DY + ((pl >> 6) & 31u)], 1ull << (pl & 63u));
     }
     group_sync(bar, gt);
     // rows without a contact are all INF after pass x: write them directly,
     // list the others, and note per plane which rows hold contacts
-    for (int r = tid; r < D * D; r += gt) {
+    for (int r = tid; r < DY * DZ; r += gt) {
         if (occ[r]) {
-            atomicOr(&pmask[r / D], 1u << (r % D));
+            atomicOr(&pmask[r / DY], 1u << (r % DY));
             list[atomicAdd(nlist, 1u)] = (uint16_t)r;
         } else {
             uint4 *row = reinterpret_cast<uint4 *>(g1 + r * 8);
@@ -474,17 +478,18 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
     // pass y: taps only from rows with contacts (an INF row cannot lower the
     // minimum: INF + dy^2 >= INF and the result is clamped to INF)
     const uint32_t twin = (1u << (2 * R + 1)) - 1u;
-    for (int idx = tid; idx < D * 64; idx += gt) {
+    static_assert(BY == 8, "pass y indexes brick rows y by 3 bits");
+    for (int idx = tid; idx < DZ * BY * 8; idx += gt) {
         const int w = idx & 7, y = (idx >> 3) & 7, zp = idx >> 6;
         uint32_t acc = inf4;
         for (uint32_t m = (pmask[zp] >> y) & twin; m; m &= m - 1u) {
             const int t = __ffs(m) - 1, dy = t - R;
-            acc = vmin4(acc, g1[(zp * D + (y + t)) * 8 + w] + (uint32_t)(dy * dy) * 0x01010101u);
+            acc = vmin4(acc, g1[(zp * DY + (y + t)) * 8 + w] + (uint32_t)(dy * dy) * 0x01010101u);
         }
         g2[(zp * 8 + y) * 8 + w] = vmin4(acc, inf4);
     }
     uint32_t planes = 0;                   // planes with any contact
-    for (int zp = 0; zp < D; ++zp) planes |= (pmask[zp] ? 1u : 0u) << zp;
+    for (int zp = 0; zp < DZ; ++zp) planes |= (pmask[zp] ? 1u : 0u) << zp;
     group_sync(bar, gt);
     // pass z (taps only from planes with contacts) and the codes: the
     // minimum kernel code of every voxel of the brick
