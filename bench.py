@@ -647,7 +647,7 @@ def extra_legs(ctx, args) -> dict:
     out = {}
     # high resolution: 2000 x 2000 x 400 at 0.02 m, 50 scans of 262,144 returns
     wh = load_workload("highres")
-    leg = plain_leg(ctx, wh, dict(wh.params), len(wh.scans), 3, autotune=False)
+    leg = plain_leg(ctx, wh, dict(wh.params), len(wh.scans), 3, autotune=not args.no_autotune)
     k, g, d_scans, poses, works = leg.pop("_state")
     leg["batched"] = run_batched(ctx, wh, k, g, d_scans, poses, len(wh.scans), works)
     leg["config"] = workload_config_of("highres", wh)
@@ -658,13 +658,13 @@ def extra_legs(ctx, args) -> dict:
     paper = dict(synth.DEFAULT_PARAMS, kernel_size=21, scheme=1, bins_a=40, bins_b=40)
     pp = {}
     wr = synth.room_scan(n_scans=20)
-    leg = plain_leg(ctx, wr, paper, 20, 3, autotune=False)
+    leg = plain_leg(ctx, wr, paper, 20, 3, autotune=not args.no_autotune)
     leg.pop("_state")
     leg["config"] = workload_config_of("room", wr, paper)
     pp["room"] = leg
     wu = load_workload("urban")
     wu = synth.Workload(wu.name, wu.grid, wu.scans[:20], wu.params)
-    leg = plain_leg(ctx, wu, paper, 20, 3, autotune=False)
+    leg = plain_leg(ctx, wu, paper, 20, 3, autotune=not args.no_autotune)
     leg.pop("_state")
     leg["config"] = workload_config_of("urban", wu, paper)
     pp["urban"] = leg
@@ -782,6 +782,19 @@ def maps_leg(ctx, steps: int, warmup: int, autotune: bool, n_maps: int = 32) -> 
         for m, x, pose in items:
             dbt.dbt_integrate_scan(grids[m], k, wss[m], x, pose)
 
+    # each map's workspace tuned on its first scan (the grids are
+    # re-initialised before the timed passes)
+    plain_tunings = []
+    for m in range(len(maps)):
+        x, pose = next((x, pose) for mm, x, pose in items if mm == m)
+        plain_tunings.append(ctx.B.dbt_workspace_autotune(grids[m], k, wss[m], x, pose, n_trials=2)
+                             if autotune else wss[m].tuning())
+    depths = sorted({t["brick_depth"] for t in plain_tunings})
+    plain_tuning = {"brick_depth_maps": {str(d): sum(t["brick_depth"] == d for t in plain_tunings)
+                                         for d in depths},
+                    "what": "per map workspace, autotuned on its first scan" if autotune
+                            else "default tuning"}
+
     b = dbt.Batch(grids, k, npts, len(items))
     b.set_items(items)
     cap = torch.cuda.Stream()
@@ -832,7 +845,8 @@ def maps_leg(ctx, steps: int, warmup: int, autotune: bool, n_maps: int = 32) -> 
             "plain": {"value": ctx.world * kept / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                       "raw_points_per_s": ctx.world * npts / (ms_plain * 1e-3),
                       "launch": f"{len(items)} dbt_integrate_scan calls "
-                                f"({KERNELS_PER_SCAN} kernels each)"},
+                                f"({KERNELS_PER_SCAN} kernels each)",
+                      "tuning": plain_tuning},
             "batched_over_plain": ms_plain / ms_batch, "steps": steps}
 
 

@@ -336,10 +336,18 @@ dbt_status dbt_batch_destroy(dbt_batch *b);
  *                  (default 64; >= 0).
  *  integrate_ctas  CTAs of the persistent integrate kernel; 0 = every SM
  *                  filled to its occupancy limit (the default); at most 4x
- *                  that. */
+ *                  that.
+ *  brick_depth     z-extent of the 32 x 8 x brick_depth voxel bricks the
+ *                  integration is split into: 4, 8 or 16 (16 only up to
+ *                  kernel_size 17); 0 = 8, the default.  Workspaces and
+ *                  batches are laid out for every depth; the getters report
+ *                  the depth in use (never 0).  Shallow bricks give more,
+ *                  smaller work items (fewer pairs per brick); deep ones
+ *                  fewer pairs per return. */
 typedef struct {
     int32_t heavy_pairs;
     int32_t integrate_ctas;
+    int32_t brick_depth;
 } dbt_tuning;
 
 dbt_status dbt_workspace_set_tuning(dbt_workspace *ws, const dbt_kernels *k, const dbt_tuning *t);
@@ -347,10 +355,11 @@ dbt_status dbt_workspace_get_tuning(const dbt_workspace *ws, dbt_tuning *t);
 dbt_status dbt_batch_set_tuning(dbt_batch *b, const dbt_tuning *t);
 dbt_status dbt_batch_get_tuning(const dbt_batch *b, dbt_tuning *t);
 
-/* Times every candidate tuning (heavy_pairs 16..256 x one, two, three or
- * the maximum CTAs per SM) over n_trials runs of the batch's current items (one
- * warm-up run each) with CUDA events on stream, keeps the fastest in *best
- * and sets it on the batch.  The items are integrated (1 + n_trials) times
+/* Times candidate tunings over n_trials runs of the batch's current items
+ * (one warm-up run each) with CUDA events on stream, in two rounds: every
+ * brick_depth (8, 4, and 16 where allowed) x heavy_pairs 16..256 on the
+ * occupancy-maximum grid, then the winner on three, two and one CTAs per SM.
+ * Keeps the fastest in *best and sets it on the batch.  The items are integrated (1 + n_trials) times
  * per candidate, so the batch's grids end in an unspecified state: run it
  * on scratch grids of the production shapes (fresh maps, or copies), then
  * apply *best with dbt_batch_set_tuning.  Synchronous. */

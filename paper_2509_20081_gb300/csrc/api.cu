@@ -371,7 +371,8 @@ static dbt_status check_grid(const dbt_grid *g) {
     return DBT_OK;
 }
 
-static DevGrid dev_grid(const dbt_grid *g) {
+// Grid view for bricks of depth bz (4, 8 or 16).
+static DevGrid dev_grid(const dbt_grid *g, int bz = BZ_DEFAULT) {
     DevGrid d;
     d.mask = g->mask;
     d.sign = g->sign;
@@ -382,7 +383,8 @@ static DevGrid dev_grid(const dbt_grid *g) {
     d.pitch = g->pitch_x;
     d.nbx = g->pitch_x / BX;
     d.nby = (g->ny + BY - 1) / BY;
-    d.nbz = (g->nz + BZ - 1) / BZ;
+    d.nbz = (g->nz + bz - 1) / bz;
+    d.bzs = bz_shift(bz);
     d.res = g->res;
     d.inv_res = 1.0 / g->res;
     d.ox = g->origin[0];
@@ -438,22 +440,28 @@ struct WsLayout {
 static size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
 
 
+// Bricks of depth bz over a grid of pitch_x x ny x nz voxels.
+static unsigned long long bricks_of(int pitch_x, int ny, int nz, int bz) {
+    return (unsigned long long)(pitch_x / BX) * ((ny + BY - 1) / BY) * ((nz + bz - 1) / bz);
+}
+
 // staging: two host-input staging buffers (dbt_integrate_scan_host copies
 // the next scan into one while the previous scan reads the other); the
 // no-allocation entry point takes device input only and needs none.
-// Scratch layout for grids of pitch_x x ny x nz voxels and kernel size K.
+// Scratch layout for grids of pitch_x x ny x nz voxels and kernel size K,
+// with room for the brick counters and pair slots of bricks of depth bz
+// (the shallowest depth a workspace may be tuned to has the most of both).
 static dbt_status ws_layout_dims(int pitch_x, int ny, int nz, int K, long long max_points,
-                                 WsLayout *L, bool staging) {
+                                 WsLayout *L, bool staging, int bz) {
     if (max_points < 1 || max_points > (1ll << 30))
         return fail(DBT_EINVAL, "max_points must be in [1, 2^30]");
-    const unsigned long long nb = (unsigned long long)(pitch_x / BX) * ((ny + BY - 1) / BY) *
-                                  ((nz + BZ - 1) / BZ);
+    const unsigned long long nb = bricks_of(pitch_x, ny, nz, bz);
     if (nb >= (1ull << 32)) return fail(DBT_EINVAL, "too many bricks");
     L->nbricks = (uint32_t)nb;
     uint32_t hc = 64;
     while (hc < 2ull * (unsigned long long)max_points) hc <<= 1;
     L->hcap_alloc = hc;
-    L->pairs_cap = (unsigned long long)max_points * max_pairs_per_return(K);
+    L->pairs_cap = (unsigned long long)max_points * max_pairs_per_return(K, bz);
     L->max_touched = (uint32_t)std::min<unsigned long long>(nb, L->pairs_cap);
     size_t o = 0;
     L->hdr = o;      o += up256(sizeof(WsHeader));
@@ -475,8 +483,8 @@ static dbt_status ws_layout_dims(int pitch_x, int ny, int nz, int K, long long m
 }
 
 static dbt_status ws_layout(const dbt_grid *g, const dbt_kernels *k, long long max_points, WsLayout *L,
-                            bool staging = true) {
-    return ws_layout_dims(g->pitch_x, g->ny, g->nz, k->dp.K, max_points, L, staging);
+                            bool staging = true, int bz = BZ_MIN) {
+    return ws_layout_dims(g->pitch_x, g->ny, g->nz, k->dp.K, max_points, L, staging, bz);
 }
 
 struct dbt_workspace {
@@ -487,6 +495,7 @@ struct dbt_workspace {
     int nx, ny, nz, pitch, K;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;   // optional timing of the integrate kernel
     int ctas = 0;                                       // integrate grid; 0 = occupancy maximum
+    int bz = BZ_DEFAULT;                                // brick depth
     // dbt_integrate_scan_host: the second staging buffer, the copy stream and
     // per buffer an event after its copy and one after the scan that read it
     float *stage_b = nullptr;
@@ -554,7 +563,8 @@ static dbt_status ws_bind(dbt_workspace *w, const dbt_grid *g, const dbt_kernels
     w->d.pairs_cap = L.pairs_cap;
     w->d.poses = (Pose *)(base + L.poses);
     w->d.heavy = HEAVY_PAIRS;
-    w->d.nbricks = L.nbricks;
+    w->bz = BZ_DEFAULT;
+    w->d.nbricks = (uint32_t)bricks_of(g->pitch_x, g->ny, g->nz, BZ_DEFAULT);   // <= L.nbricks
     return DBT_OK;
 }
 
@@ -681,7 +691,7 @@ static dbt_status enqueue_scan(const dbt_grid *g, const dbt_kernels *k, dbt_work
     launch_fill(dg, k->dp, ni, ws->d, hcap, s);
     if (ws->ev_begin) DBT_CUDA(cudaEventRecord(ws->ev_begin, s));
     launch_integrate(dg, k->dp, k->dt, (long long)n, ws->d,
-                     ws->ctas ? ws->ctas : integrate_grid_ctas(k->dp), s);
+                     ws->ctas ? ws->ctas : integrate_grid_ctas(k->dp, ws->bz), s);
     if (ws->ev_end) DBT_CUDA(cudaEventRecord(ws->ev_end, s));
     DBT_CUDA(cudaGetLastError());
     return DBT_OK;
@@ -704,7 +714,7 @@ static dbt_status enqueue_prep(const dbt_grid *g, const dbt_kernels *k, dbt_work
         return fail(DBT_EINVAL, "n = %lld outside [0, max_points = %lld]", (long long)n, ws->max_points);
     if (n > 0 && (!d_xyz || ((uintptr_t)d_xyz & 3u)))
         return fail(DBT_EINVAL, "points must be a non-NULL 4-byte aligned device pointer");
-    const DevGrid dg = dev_grid(g);
+    const DevGrid dg = dev_grid(g, ws->bz);
     Pose P{};
     ScanEx ex{1, 0, 1};
     const bool use_ex = opt != nullptr;
@@ -908,7 +918,7 @@ dbt_status dbt::scratch_fits(int32_t pitch_x, int32_t ny, int32_t nz, int32_t K,
         return fail(DBT_EINVAL, "n = %lld exceeds the no-allocation limit of %lld returns per scan",
                     (long long)n, max_points);
     WsLayout L;
-    dbt_status st = ws_layout_dims(pitch_x, ny, nz, K, max_points, &L, false);
+    dbt_status st = ws_layout_dims(pitch_x, ny, nz, K, max_points, &L, false, BZ_DEFAULT);
     if (st != DBT_OK) return st;
     if (L.total > bytes)
         return fail(DBT_EINVAL,
@@ -933,7 +943,7 @@ dbt_status dbt::integrate_on_scratch(const dbt_grid *g, const dbt_kernels *k, co
     if (st != DBT_OK) return st;
     if (!scratch) return fail(DBT_EINVAL, "scratch is NULL");
     WsLayout L;
-    st = ws_layout(g, k, max_points, &L, false);
+    st = ws_layout(g, k, max_points, &L, false, BZ_DEFAULT);   // the default depth only
     if (st != DBT_OK) return st;
     dbt_workspace w;
     st = ws_bind(&w, g, k, max_points, L, scratch);
@@ -953,12 +963,19 @@ dbt_status dbt::integrate_on_scratch(const dbt_grid *g, const dbt_kernels *k, co
 }
 
 // ------------------------------------------------------------------ batches
+// The grid views and brick bases of every brick depth live in the batch's
+// buffer side by side (depth index 0, 1, 2 = 4, 8, 16), so a tuning changes
+// the depth by pointing the launch at another set: nothing is written to the
+// device, and a captured graph keeps the set it was captured with.
+constexpr int N_DEPTHS = 3;
+static int depth_index(int bz) { return bz_shift(bz) - 2; }
+
 struct dbt_batch {
     const dbt_kernels *k = nullptr;
     int n_grids = 0;
-    std::vector<DevGrid> grids;          // host copies
+    std::vector<DevGrid> grids;          // host copies at the default depth
     std::vector<dbt_grid> cgrids;
-    std::vector<uint32_t> bbase;         // n_grids + 1
+    std::vector<uint32_t> bbase;         // per depth n_grids + 1
     long long max_points = 0;
     int max_items = 0;
     WsLayout L;                          // integration scratch (bricks of all grids)
@@ -971,7 +988,19 @@ struct dbt_batch {
     long long n_total = 0;
     BatchDev bd;
     int ctas = 0;                        // integrate grid; 0 = occupancy maximum
+    int bz = BZ_DEFAULT;                 // brick depth
 };
+
+// Points the batch's launches at the grid views and brick bases of depth bz.
+static void batch_use_depth(dbt_batch *b, int bz) {
+    const int d = depth_index(bz);
+    char *base = (char *)b->buf;
+    b->bz = bz;
+    b->bd.grids = (const DevGrid *)(base + b->off_grids) + (size_t)d * b->n_grids;
+    b->bd.bbase = (const uint32_t *)(base + b->off_bbase) + (size_t)d * (b->n_grids + 1);
+    b->bd.bzs = bz_shift(bz);
+    b->d.nbricks = b->bbase[(size_t)d * (b->n_grids + 1) + b->n_grids];
+}
 
 static dbt_status batch_layout(const dbt_grid *grids, int n_grids, const dbt_kernels *k,
                                long long max_points, int max_items, WsLayout *L,
@@ -982,23 +1011,28 @@ static dbt_status batch_layout(const dbt_grid *grids, int n_grids, const dbt_ker
         return fail(DBT_EINVAL, "max_items must be in [1, %d]", MAX_BATCH_ITEMS);
     if (max_points < 1 || max_points > (1ll << 31) - 1)
         return fail(DBT_EINVAL, "max_points must be in [1, 2^31 - 1]");
-    bbase->assign(n_grids + 1, 0u);
-    unsigned long long nb = 0;
     for (int m = 0; m < n_grids; ++m) {
         dbt_status st = check_grid(&grids[m]);
         if (st != DBT_OK) return fail(st, "grid %d: %s", m, dbt_last_error());
-        const DevGrid d = dev_grid(&grids[m]);
-        (*bbase)[m] = (uint32_t)nb;
-        nb += (unsigned long long)d.nbx * d.nby * d.nbz;
-        if (nb >= (1ull << 32)) return fail(DBT_EINVAL, "too many bricks over the batch's grids");
     }
-    (*bbase)[n_grids] = (uint32_t)nb;
+    bbase->assign((size_t)N_DEPTHS * (n_grids + 1), 0u);
+    unsigned long long nb = 0;                    // bricks at the shallowest depth: the most
+    for (int d = N_DEPTHS - 1; d >= 0; --d) {
+        uint32_t *bb = bbase->data() + (size_t)d * (n_grids + 1);
+        nb = 0;
+        for (int m = 0; m < n_grids; ++m) {
+            bb[m] = (uint32_t)nb;
+            nb += bricks_of(grids[m].pitch_x, grids[m].ny, grids[m].nz, 4 << d);
+            if (nb >= (1ull << 32)) return fail(DBT_EINVAL, "too many bricks over the batch's grids");
+        }
+        bb[n_grids] = (uint32_t)nb;
+    }
     // the single-grid layout with the batch's total brick count
     uint32_t hc = 64;
     while (hc < 2ull * (unsigned long long)max_points) hc <<= 1;
     L->nbricks = (uint32_t)nb;
     L->hcap_alloc = hc;
-    L->pairs_cap = (unsigned long long)max_points * max_pairs_per_return(k->dp.K);
+    L->pairs_cap = (unsigned long long)max_points * max_pairs_per_return(k->dp.K, BZ_MIN);
     L->max_touched = (uint32_t)std::min<unsigned long long>(nb, L->pairs_cap);
     size_t o = 0;
     L->hdr = o;      o += up256(sizeof(WsHeader));
@@ -1016,8 +1050,8 @@ static dbt_status batch_layout(const dbt_grid *grids, int n_grids, const dbt_ker
     L->pairs = o;    o += up256((size_t)L->pairs_cap * 4);
     L->poses = o;    o += up256((size_t)MAX_SCAN_POSES * sizeof(Pose));
     L->total = o;
-    tail_offs[0] = o;  o += up256((size_t)n_grids * sizeof(DevGrid));
-    tail_offs[1] = o;  o += up256((size_t)(n_grids + 1) * 4);
+    tail_offs[0] = o;  o += up256((size_t)N_DEPTHS * n_grids * sizeof(DevGrid));
+    tail_offs[1] = o;  o += up256((size_t)N_DEPTHS * (n_grids + 1) * 4);
     tail_offs[2] = o;  o += up256((size_t)max_items * sizeof(ItemDev));
     tail_offs[3] = o;  o += up256((size_t)(max_items + 1) * 8);
     tail_offs[4] = o;  o += up256((size_t)max_items * sizeof(ItemCounters));
@@ -1080,8 +1114,10 @@ extern "C" dbt_status dbt_batch_create(const dbt_grid *grids, int32_t n_grids, c
         return bst;
     }
     b->d = w.d;
-    b->bd.grids = (const DevGrid *)(base + b->off_grids);
-    b->bd.bbase = (const uint32_t *)(base + b->off_bbase);
+    std::vector<DevGrid> views;                  // every depth's grid views, depth-major
+    for (int d = 0; d < N_DEPTHS; ++d)
+        for (int m = 0; m < n_grids; ++m) views.push_back(dev_grid(&grids[m], 4 << d));
+    batch_use_depth(b, BZ_DEFAULT);
     b->bd.items = (const ItemDev *)(base + b->off_items);
     b->bd.istart = (const long long *)(base + b->off_istart);
     b->bd.icnt = (ItemCounters *)(base + b->off_icnt);
@@ -1090,10 +1126,10 @@ extern "C" dbt_status dbt_batch_create(const dbt_grid *grids, int32_t n_grids, c
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(d_buf, 0, b->total, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + b->off_grids, b->grids.data(), n_grids * sizeof(DevGrid),
+        e = cudaMemcpyAsync(base + b->off_grids, views.data(), views.size() * sizeof(DevGrid),
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + b->off_bbase, b->bbase.data(), (n_grids + 1) * 4,
+        e = cudaMemcpyAsync(base + b->off_bbase, b->bbase.data(), b->bbase.size() * 4,
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -1165,16 +1201,23 @@ extern "C" dbt_status dbt_batch_run(dbt_batch *b, void *stream) {
     launch_alloc_batch(b->bd, k->dp, b->n_total, b->d, hcap, s);
     if (b->n_items > 0) launch_fill_batch(b->bd, k->dp, b->n_total, b->d, hcap, s);
     launch_integrate_batch(b->bd, k->dp, k->dt, b->n_total, b->d,
-                           b->ctas ? b->ctas : integrate_grid_ctas(k->dp), s);
+                           b->ctas ? b->ctas : integrate_grid_ctas(k->dp, b->bz), s);
     DBT_CUDA(cudaGetLastError());
     return DBT_OK;
 }
 
 // ------------------------------------------------------------------ tuning
+// Brick depth of a tuning (0 = the default).
+static int tuning_depth(const dbt_tuning *t) { return t->brick_depth ? t->brick_depth : BZ_DEFAULT; }
+
 static dbt_status check_tuning(const dbt_tuning *t, const dbt_kernels *k) {
     if (!t) return fail(DBT_EINVAL, "tuning is NULL");
     if (t->heavy_pairs < 0) return fail(DBT_EINVAL, "heavy_pairs must be >= 0");
-    const int cap = 4 * integrate_grid_ctas(k->dp);
+    const int bz = tuning_depth(t);
+    if (bz != 4 && bz != 8 && bz != 16) return fail(DBT_EINVAL, "brick_depth must be 0, 4, 8 or 16");
+    if (bz == 16 && k->dp.K > BZ16_MAX_K)
+        return fail(DBT_EINVAL, "brick_depth 16 needs kernel_size <= %d", BZ16_MAX_K);
+    const int cap = 4 * integrate_grid_ctas(k->dp, bz);
     if (t->integrate_ctas < 0 || t->integrate_ctas > cap)
         return fail(DBT_EINVAL, "integrate_ctas must be in [0, %d]", cap);
     return DBT_OK;
@@ -1185,8 +1228,15 @@ extern "C" dbt_status dbt_workspace_set_tuning(dbt_workspace *ws, const dbt_kern
     if (!ws || !k) return fail(DBT_EINVAL, "workspace or kernels is NULL");
     dbt_status st = check_tuning(t, k);
     if (st != DBT_OK) return st;
+    const int bz = tuning_depth(t);
+    const unsigned long long nb = bricks_of(ws->pitch, ws->ny, ws->nz, bz);
+    if (nb > ws->L.nbricks || (unsigned long long)ws->max_points * max_pairs_per_return(ws->K, bz) >
+                                  ws->L.pairs_cap)
+        return fail(DBT_EINVAL, "the workspace has no room for bricks of depth %d", bz);
     ws->d.heavy = (uint32_t)t->heavy_pairs;
     ws->ctas = t->integrate_ctas;
+    ws->bz = bz;
+    ws->d.nbricks = (uint32_t)nb;
     return DBT_OK;
 }
 
@@ -1194,6 +1244,7 @@ extern "C" dbt_status dbt_workspace_get_tuning(const dbt_workspace *ws, dbt_tuni
     if (!ws || !t) return fail(DBT_EINVAL, "NULL argument");
     t->heavy_pairs = (int32_t)ws->d.heavy;
     t->integrate_ctas = ws->ctas;
+    t->brick_depth = ws->bz;
     return DBT_OK;
 }
 
@@ -1203,6 +1254,7 @@ extern "C" dbt_status dbt_batch_set_tuning(dbt_batch *b, const dbt_tuning *t) {
     if (st != DBT_OK) return st;
     b->d.heavy = (uint32_t)t->heavy_pairs;
     b->ctas = t->integrate_ctas;
+    batch_use_depth(b, tuning_depth(t));
     return DBT_OK;
 }
 
@@ -1210,31 +1262,39 @@ extern "C" dbt_status dbt_batch_get_tuning(const dbt_batch *b, dbt_tuning *t) {
     if (!b || !t) return fail(DBT_EINVAL, "NULL argument");
     t->heavy_pairs = (int32_t)b->d.heavy;
     t->integrate_ctas = b->ctas;
+    t->brick_depth = b->bz;
     return DBT_OK;
 }
 
-// Candidates: the heavy threshold (CTA mode from 16 to 128 pairs per brick)
-// crossed with the persistent grid (one or two CTAs per SM, or the occupancy
-// maximum).  Each is timed over n_trials runs after one warm-up run.
-static std::vector<dbt_tuning> tuning_candidates(const dbt_kernels *k) {
-    const int sms = device_sm_count(), full = integrate_grid_ctas(k->dp);
-    std::vector<int> grids = {full};
-    for (int c : {3 * sms, 2 * sms, sms})
-        if (c < full) grids.push_back(c);
+// Candidates, searched in two rounds.  Round 1: the brick depth (8, 4 and,
+// up to K = 17, 16) crossed with the heavy threshold (CTA mode from 16 to
+// 256 pairs per brick; the pairs a brick gets scale with its depth), on the
+// occupancy-maximum grid.  Round 2: the winner's depth and threshold on a
+// persistent grid of three, two or one CTAs per SM.  Each candidate is
+// timed over n_trials runs after one warm-up run.
+static std::vector<dbt_tuning> depth_heavy_candidates(const dbt_kernels *k) {
     std::vector<dbt_tuning> out;
-    for (int h : {16, 24, 32, 40, 48, 64, 96, 128, 192, 256})
-        for (int c : grids) out.push_back(dbt_tuning{h, c});
+    for (int bz : {8, 4, 16}) {
+        if (bz == 16 && k->dp.K > BZ16_MAX_K) continue;
+        for (int h : {16, 24, 32, 40, 48, 64, 96, 128, 192, 256}) out.push_back(dbt_tuning{h, 0, bz});
+    }
+    return out;
+}
+
+static std::vector<dbt_tuning> grid_candidates(const dbt_kernels *k, const dbt_tuning &best) {
+    const int sms = device_sm_count(), full = integrate_grid_ctas(k->dp, tuning_depth(&best));
+    std::vector<dbt_tuning> out;
+    for (int c : {3 * sms, 2 * sms, sms})
+        if (c < full) out.push_back(dbt_tuning{best.heavy_pairs, c, best.brick_depth});
     return out;
 }
 
 template <typename Run>
-static dbt_status autotune(const std::vector<dbt_tuning> &cands, int n_trials, cudaStream_t s,
-                           Run run, dbt_tuning *best) {
-    if (n_trials < 1 || n_trials > 1000) return fail(DBT_EINVAL, "n_trials must be in [1, 1000]");
+static dbt_status time_candidates(const std::vector<dbt_tuning> &cands, int n_trials, cudaStream_t s,
+                                  Run run, dbt_tuning *best, float *best_ms) {
     cudaEvent_t e0, e1;
     DBT_CUDA(cudaEventCreate(&e0));
     DBT_CUDA(cudaEventCreate(&e1));
-    float best_ms = 3.4e38f;
     dbt_status st = DBT_OK;
     for (const dbt_tuning &c : cands) {
         if ((st = run(c)) != DBT_OK) break;                 // warm-up with this tuning
@@ -1249,8 +1309,8 @@ static dbt_status autotune(const std::vector<dbt_tuning> &cands, int n_trials, c
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-            best_ms = ms;
+        if (ms < *best_ms) {
+            *best_ms = ms;
             *best = c;
         }
     }
@@ -1259,11 +1319,21 @@ static dbt_status autotune(const std::vector<dbt_tuning> &cands, int n_trials, c
     return st;
 }
 
+template <typename Run>
+static dbt_status autotune(const dbt_kernels *k, int n_trials, cudaStream_t s, Run run,
+                           dbt_tuning *best) {
+    if (n_trials < 1 || n_trials > 1000) return fail(DBT_EINVAL, "n_trials must be in [1, 1000]");
+    float best_ms = 3.4e38f;
+    dbt_status st = time_candidates(depth_heavy_candidates(k), n_trials, s, run, best, &best_ms);
+    if (st == DBT_OK) st = time_candidates(grid_candidates(k, *best), n_trials, s, run, best, &best_ms);
+    return st;
+}
+
 extern "C" dbt_status dbt_batch_autotune(dbt_batch *b, int32_t n_trials, void *stream,
                                          dbt_tuning *best) {
     if (!b || !best) return fail(DBT_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    dbt_status st = autotune(tuning_candidates(b->k), n_trials, s, [&](const dbt_tuning &c) {
+    dbt_status st = autotune(b->k, n_trials, s, [&](const dbt_tuning &c) {
         dbt_status r = dbt_batch_set_tuning(b, &c);
         return r == DBT_OK ? dbt_batch_run(b, stream) : r;
     }, best);
@@ -1277,7 +1347,7 @@ extern "C" dbt_status dbt_workspace_autotune(const dbt_grid *g, const dbt_kernel
                                              dbt_tuning *best) {
     if (!ws || !k || !best) return fail(DBT_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    dbt_status st = autotune(tuning_candidates(k), n_trials, s, [&](const dbt_tuning &c) {
+    dbt_status st = autotune(k, n_trials, s, [&](const dbt_tuning &c) {
         dbt_status r = dbt_workspace_set_tuning(ws, k, &c);
         return r == DBT_OK ? enqueue_scan(g, k, ws, d_xyz, n, pose, s) : r;
     }, best);

@@ -13,11 +13,16 @@ namespace dbt {
 
 // Brick = CTA ownership unit of the integration: BX x BY x BZ voxels.  BX = 32
 // makes one brick row a 128-byte mask line; chunks are 4 voxels (16 bytes).
-constexpr int BX = 32, BY = 8, BZ = 8;
-constexpr int BROWS = BY * BZ;              // 64 rows of 32 voxels
-constexpr int BVOX = BX * BY * BZ;          // 2048 voxels
+// The depth BZ is a launch choice (4, 8 or 16; 16 only up to K = 17, where a
+// contact's brick-relative z still fits the pair payload's 5 bits): the grid
+// view carries its log2 (bzs), the integrate kernel is instantiated per depth.
+constexpr int BX = 32, BY = 8;
 constexpr int CHUNKS_PER_ROW = BX / 4;      // 8
-constexpr int BCHUNKS = BROWS * CHUNKS_PER_ROW;  // 512
+constexpr int BZ_DEFAULT = 8;
+constexpr int BZ_MIN = 4;                   // the deepest brick count a scratch layout must hold
+constexpr int BZ_MAX = 16;
+constexpr int BZ16_MAX_K = 17;
+__host__ __device__ constexpr int bz_shift(int bz) { return bz == 4 ? 2 : bz == 16 ? 4 : 3; }
 
 constexpr int MAX_K = 21;
 constexpr int MAX_R = (MAX_K - 1) / 2;
@@ -31,10 +36,10 @@ constexpr uint32_t ERR_TOUCHED_OVERFLOW = 1u << 2;
 constexpr uint32_t ERR_BAD_PAYLOAD = 1u << 3;
 constexpr uint32_t ERR_MASK_FORM = 1u << 4;      // a grid mask was not of the form 2^k - 1
 
-// Bricks a return's K^3 neighbourhood can touch: its x-extent K spans at most
-// 1 + ceil((K - 1) / BX) bricks, likewise in y and z.
-__host__ __device__ inline int max_pairs_per_return(int K) {
-    return (1 + (K - 1 + BX - 1) / BX) * (1 + (K - 1 + BY - 1) / BY) * (1 + (K - 1 + BZ - 1) / BZ);
+// Bricks a return's K^3 neighbourhood can touch with bricks of depth bz: its
+// x-extent K spans at most 1 + ceil((K - 1) / BX) bricks, likewise in y and z.
+__host__ __device__ inline int max_pairs_per_return(int K, int bz) {
+    return (1 + (K - 1 + BX - 1) / BX) * (1 + (K - 1 + BY - 1) / BY) * (1 + (K - 1 + bz - 1) / bz);
 }
 
 // Shadow offsets are packed as bytes (ox + OFF_BIAS) | (oy + OFF_BIAS) << 8 |
@@ -84,6 +89,7 @@ struct DevGrid {
     uint16_t *hits;
     int nx, ny, nz, pitch;
     int nbx, nby, nbz;          // bricks per axis
+    int bzs;                    // log2 of the brick depth BZ
     double res;                 // voxel edge (the binary64 voxel floor divides by it)
     double inv_res;             // 1 / res, rounded once on the host (binary32 filter data only)
     double ox, oy, oz;          // origin
@@ -131,6 +137,7 @@ struct BatchDev {
     const long long *istart;   // n_items + 1
     ItemCounters *icnt;        // n_items
     int n_grids, n_items;
+    int bzs;                   // log2 of the brick depth of every grid view
 };
 constexpr int MAX_BATCH_GRIDS = 256;   // grid index lives in 8 bits of a return record
 constexpr int MAX_BATCH_ITEMS = 1 << 20;
@@ -274,7 +281,7 @@ void launch_fill_batch(const BatchDev &bd, const DevParams &p, long long n, cons
                        uint32_t hcap, cudaStream_t s);
 void launch_integrate_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
                             long long n_input, const WsDev &ws, int grid_ctas, cudaStream_t s);
-int integrate_grid_ctas(const DevParams &p);
+int integrate_grid_ctas(const DevParams &p, int bz);
 int device_sm_count();
 void launch_footprint(const DevGrid &g, const DevParams &p, const DevTables &t, int n,
                       const WsDev &ws, uint32_t hcap, uint32_t *bits_u, uint32_t *bits_s,

@@ -21,12 +21,13 @@
 // at ox = s - 3 - R (32, no change, outside the kernel).  A word update is a
 // table load, an area-word load, a byte-wise min and a conditional store.
 //
-// Work split.  Persistent CTAs of WPC warps.  Bricks (32 x 8 x 8 voxels)
-// with more than ws.heavy (return, brick) pairs ("heavy") are taken one per
-// group of warps: at K <= 13 by the separable dense path below, otherwise
-// each warp applies a share of the pairs to its own area and the areas are
-// merged at write-back (byte-wise min of codes, sum of counts).  The other
-// bricks are taken one per warp, in size classes, largest first.  At K <= 11
+// Work split.  Persistent CTAs of WPC warps.  Bricks (32 x 8 x BZ voxels;
+// BZ = 4, 8 or 16, one kernel instance per depth) with more than ws.heavy
+// (return, brick) pairs ("heavy") are taken one per group of warps: at
+// K <= 13 by the separable dense path below, otherwise each warp applies a
+// share of the pairs to its own area and the areas are merged at write-back
+// (byte-wise min of codes, sum of counts).  The other bricks are taken one
+// per warp, in size classes, largest first.  At K <= 11 (K <= 7 for BZ = 4)
 // a CTA holds two groups of four warps, one starting on heavy and one on
 // light bricks; otherwise the CTA is one group, heavy bricks first.  A brick
 // is only ever written by the group or warp that took it, so no atomics
@@ -53,14 +54,22 @@ namespace dbt {
 constexpr int WPC = 8;            // warps per CTA
 constexpr int NTHR = WPC * 32;
 
+// Rows of BX voxels (row = z * BY + y), chunks of four voxels and voxels of
+// a brick of depth BZ.
+template <int BZ> __host__ __device__ constexpr int brows() { return BY * BZ; }
+template <int BZ> __host__ __device__ constexpr int bchunks() { return BY * BZ * CHUNKS_PER_ROW; }
+template <int BZ> __host__ __device__ constexpr int bvox() { return BX * BY * BZ; }
+
+template <int BZ>
 struct WarpArea {
-    uint32_t kst[BROWS * 8];      // kernel codes: word kword(row, w) = voxels 4w .. 4w+3 of a row
-    uint16_t cnt[BVOX];           // shadow counts, index row * 32 + x
+    uint32_t kst[brows<BZ>() * 8];  // kernel codes: word kword(row, w) = voxels 4w .. 4w+3 of a row
+    uint16_t cnt[bvox<BZ>()];       // shadow counts, index row * 32 + x
 };
-static_assert(sizeof(WarpArea) % 16 == 0, "warp area alignment");
+static_assert(sizeof(WarpArea<4>) % 16 == 0 && sizeof(WarpArea<8>) % 16 == 0 &&
+                  sizeof(WarpArea<16>) % 16 == 0, "warp area alignment");
 constexpr uint32_t NO_CODE4 = 0x20202020u;      // four voxels without a kernel code (32)
 
-// Word w of brick row `row` (row = z * 8 + y).  The XOR with bits 2..4 of the
+// Word w of brick row `row` (row = z * BY + y).  The XOR with bits 2..4 of the
 // row spreads both access patterns over all 32 banks: phase C (8 rows x 4
 // consecutive planes, same w) and phase D (4 consecutive rows x 8 words).
 __device__ __forceinline__ int kword(int row, int w) { return row * 8 + (w ^ ((row >> 2) & 7)); }
@@ -97,6 +106,7 @@ struct PairBox {
     int x0, x1, y0, y1, z0, z1;   // kernel box clipped to the brick
 };
 
+template <int BZ>
 __device__ __forceinline__ PairBox decode_pair(uint32_t pl, int R) {
     PairBox b;
     b.cx = (int)(pl & 63u) - R;
@@ -125,8 +135,9 @@ struct RowsSetup {
     uint32_t a, b;
 };
 
+template <int BZ>
 __device__ __forceinline__ RowsSetup rows_setup(uint32_t pl, int R) {
-    const PairBox b = decode_pair(pl, R);
+    const PairBox b = decode_pair<BZ>(pl, R);
     const int wy = b.y1 - b.y0 + 1;
     const int nrows = wy * (b.z1 - b.z0 + 1);
     const int w0 = b.x0 >> 2;
@@ -139,8 +150,8 @@ __device__ __forceinline__ RowsSetup rows_setup(uint32_t pl, int R) {
     return su;
 }
 
-template <int NW>
-__device__ __forceinline__ void apply_rows(RowsSetup su, WarpArea *wa, const uint32_t *P, int W,
+template <int NW, int BZ>
+__device__ __forceinline__ void apply_rows(RowsSetup su, WarpArea<BZ> *wa, const uint32_t *P, int W,
                                            int lane) {
     const int nrows = (int)(su.a & 255u);
     const int wy = (int)((su.a >> 8) & 15u);
@@ -193,14 +204,17 @@ __device__ __forceinline__ void apply_rows(RowsSetup su, WarpArea *wa, const uin
 // z, i.e. (for power-of-two sides dividing 64) when the bits above the side
 // read 01: one AND and one compare.  Lanes past the range take 0x80 bytes,
 // which set bit 7 and fail.  The low bits of the bytes are then x, y and z.
-static_assert(BX == 32 && BY == 8 && (BZ == 4 || BZ == 8 || BZ == 16) && MAX_R <= 10 &&
-                  OFF_BIAS == 32 && BZ - 1 + 4 * MAX_R + 64 < 128,
+static_assert(BX == 32 && BY == 8 && MAX_R <= 10 && OFF_BIAS == 32 && BZ_MAX - 1 + 4 * MAX_R + 64 < 128,
               "shadow_pairs' byte packing: 32 x 8 x BZ bricks, |offsets| <= 10, no byte carry");
 constexpr uint32_t SH_PAD = 0x80808080u;
-constexpr uint32_t SH_INMASK = (uint32_t)(0xFF & ~(BX - 1)) | ((uint32_t)(0xFF & ~(BY - 1)) << 8) |
-                               ((uint32_t)(0xFF & ~(BZ - 1)) << 16);
+template <int BZ>
+__host__ __device__ constexpr uint32_t sh_inmask() {
+    static_assert(BZ == 4 || BZ == 8 || BZ == 16, "brick depth");
+    return (uint32_t)(0xFF & ~(BX - 1)) | ((uint32_t)(0xFF & ~(BY - 1)) << 8) |
+           ((uint32_t)(0xFF & ~(BZ - 1)) << 16);
+}
 constexpr uint32_t CNT_ROUND = 65535u;
-template <bool ATOMIC>
+template <int BZ, bool ATOMIC>
 __device__ __forceinline__ void shadow_pairs(uint32_t mine, int n, uint16_t *cnt, const DevTables &t,
                                              int R, int SR, int lane) {
     uint32_t e0 = 0, e1 = 0, cpk = 0;
@@ -236,7 +250,7 @@ __device__ __forceinline__ void shadow_pairs(uint32_t mine, int n, uint16_t *cnt
         for (uint32_t e = a0; e < a1; e += 32) {
             const uint32_t o = e + lane < a1 ? __ldg(sh + e + lane) : SH_PAD;
             const uint32_t u = o + pk;
-            if ((u & SH_INMASK) == 0x00404040u) {
+            if ((u & sh_inmask<BZ>()) == 0x00404040u) {
                 // v = x + 32 (y + 8 z)
                 const int v = (int)((u & 31u) | ((u >> 3) & 0xE0u) | ((u >> 8) & ((BZ - 1u) << 8)));
                 if (ATOMIC)
@@ -249,6 +263,7 @@ __device__ __forceinline__ void shadow_pairs(uint32_t mine, int n, uint16_t *cnt
     }
 }
 
+template <int BZ>
 __device__ __forceinline__ size_t chunk_index(const DevGrid &g, int bx, int by, int bz, int row,
                                               int ch) {
     const int gy = by * BY + (row & (BY - 1)), gz = bz * BZ + row / BY;
@@ -288,10 +303,11 @@ __device__ __forceinline__ void store_codes(const DevGrid &g, size_t gi, uint32_
 
 // Phase I: clears the areas [a, a + na) (no codes, zero counts), thread tid
 // of gt.
-__device__ __forceinline__ void clear_areas(WarpArea *a, int na, int tid, int gt) {
+template <int BZ>
+__device__ __forceinline__ void clear_areas(WarpArea<BZ> *a, int na, int tid, int gt) {
     const uint4 none = make_uint4(NO_CODE4, NO_CODE4, NO_CODE4, NO_CODE4);
     const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-    constexpr int K4 = BROWS * 8 / 4, C4 = BVOX / 8;          // uint4 words of kst, cnt
+    constexpr int K4 = brows<BZ>() * 8 / 4, C4 = bvox<BZ>() / 8;   // uint4 words of kst, cnt
     for (int v = 0; v < na; ++v) {
         uint4 *k = reinterpret_cast<uint4 *>(a[v].kst);
         uint4 *c = reinterpret_cast<uint4 *>(a[v].cnt);
@@ -301,15 +317,15 @@ __device__ __forceinline__ void clear_areas(WarpArea *a, int na, int tid, int gt
 }
 
 // Kernel codes and shadow counts of chunk (row, ch), merged over NA areas.
-template <int NA>
-__device__ __forceinline__ uint32_t chunk_codes(const WarpArea *a, int wd) {
+template <int NA, int BZ>
+__device__ __forceinline__ uint32_t chunk_codes(const WarpArea<BZ> *a, int wd) {
     uint32_t k = a[0].kst[wd];
 #pragma unroll
     for (int v = 1; v < NA; ++v) k = vmin4(k, a[v].kst[wd]);
     return k;
 }
-template <int NA>
-__device__ __forceinline__ uint2 chunk_counts(const WarpArea *a, int row, int ch) {
+template <int NA, int BZ>
+__device__ __forceinline__ uint2 chunk_counts(const WarpArea<BZ> *a, int row, int ch) {
     uint2 cs = *reinterpret_cast<const uint2 *>(&a[0].cnt[row * 32 + ch * 4]);
 #pragma unroll
     for (int v = 1; v < NA; ++v) {
@@ -320,16 +336,17 @@ __device__ __forceinline__ uint2 chunk_counts(const WarpArea *a, int row, int ch
     return cs;
 }
 
-// Phase D by thread tid of gt over the brick's 512 chunks (chunk c = row * 8
-// + ch), BATCH chunks per thread at a time: the grid masks of the chunks with
+// Phase D by thread tid of gt over the brick's chunks (chunk c = row * 8 +
+// ch; 512 at depth 8), BATCH chunks per thread at a time: the grid masks of the chunks with
 // kernel codes and the counters of the chunks with shadow counts are all
 // loaded before any is used; masks are lowered to the kernel codes and
 // stored where they change, counters bumped with saturation and stored, and
 // the crossing voxels' signs set (Eqs. 5-6).
-template <int NA, int BATCH>
+template <int NA, int BATCH, int BZ>
 __device__ __forceinline__ void write_back(const DevGrid &g, int bx, int by, int bz,
-                                           const WarpArea *a, int tid, int gt, uint32_t T,
+                                           const WarpArea<BZ> *a, int tid, int gt, uint32_t T,
                                            uint32_t Hmax, uint32_t &form_bad) {
+    constexpr int BCHUNKS = bchunks<BZ>();
     for (int c0 = tid; c0 < BCHUNKS; c0 += BATCH * gt) {
         uint4 m[BATCH];
         uint32_t has = 0;
@@ -342,7 +359,7 @@ __device__ __forceinline__ void write_back(const DevGrid &g, int bx, int by, int
                 if (chunk_codes<NA>(a, kword(row, ch)) != NO_CODE4) {
                     has |= 1u << q;
                     m[q] = __ldcg(reinterpret_cast<const uint4 *>(
-                        g.mask + chunk_index(g, bx, by, bz, row, ch)));
+                        g.mask + chunk_index<BZ>(g, bx, by, bz, row, ch)));
                 }
             }
         }
@@ -358,7 +375,7 @@ __device__ __forceinline__ void write_back(const DevGrid &g, int bx, int by, int
                 if (cs.x | cs.y) {
                     hc |= 1u << q;
                     hv[q] = __ldcg(reinterpret_cast<const uint2 *>(
-                        g.hits + chunk_index(g, bx, by, bz, row, ch)));
+                        g.hits + chunk_index<BZ>(g, bx, by, bz, row, ch)));
                 }
             }
         }
@@ -369,13 +386,13 @@ __device__ __forceinline__ void write_back(const DevGrid &g, int bx, int by, int
             const uint32_t k = chunk_codes<NA>(a, kword(row, ch));
             const uint32_t old = codes_of(m[q], form_bad);
             const uint32_t lt = code_lt(old, k);
-            if (lt) store_codes(g, chunk_index(g, bx, by, bz, row, ch), code_min(old, k, lt));
+            if (lt) store_codes(g, chunk_index<BZ>(g, bx, by, bz, row, ch), code_min(old, k, lt));
         }
 #pragma unroll
         for (int q = 0; q < BATCH; ++q) {
             if (!((hc >> q) & 1u)) continue;
             const int c = c0 + q * gt, row = c >> 3, ch = c & 7;
-            const size_t gi = chunk_index(g, bx, by, bz, row, ch);
+            const size_t gi = chunk_index<BZ>(g, bx, by, bz, row, ch);
             const uint32_t cross = apply_counts(hv[q], chunk_counts<NA>(a, row, ch), T, Hmax);
             __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv[q]);
             store_crossings(g, gi, cross);
@@ -400,22 +417,30 @@ constexpr uint32_t DENSE_INF = 127u;
 // The dense path's scratch (occupancy, two passes, plane masks, row list)
 // lives in the warp areas of the heavy group after the first: at R = 6 all
 // eight warps form the group; up to R = 5 four do (three spare areas).
-__host__ __device__ constexpr int dense_scratch_bytes(int R) {
+__host__ __device__ constexpr int dense_scratch_bytes(int R, int BZ) {
     return 8 * (BY + 2 * R) * (BZ + 2 * R) + 32 * (BY + 2 * R) * (BZ + 2 * R) +
            4 * 8 * BY * (BZ + 2 * R) + 4 * (BZ + 2 * R) + 4 + 2 * (BY + 2 * R) * (BZ + 2 * R);
 }
-constexpr int HALF_GROUP_MAX_R = 5;
-static_assert(dense_scratch_bytes(6) <= (WPC - 1) * (int)sizeof(WarpArea), "dense scratch, R = 6");
-static_assert(dense_scratch_bytes(HALF_GROUP_MAX_R) <= (WPC / 2 - 1) * (int)sizeof(WarpArea),
-              "dense scratch, half group");
+// Largest R whose dense scratch fits a half group's three spare areas (the
+// half-group split is used up to R = 5 where it fits).
+template <int BZ> __host__ __device__ constexpr int half_group_max_r() { return BZ == 4 ? 3 : 5; }
+template <int BZ>
+__host__ __device__ constexpr bool dense_scratch_fits() {
+    return dense_scratch_bytes(6, BZ) <= (WPC - 1) * (int)sizeof(WarpArea<BZ>) &&
+           dense_scratch_bytes(half_group_max_r<BZ>(), BZ) <= (WPC / 2 - 1) * (int)sizeof(WarpArea<BZ>);
+}
+static_assert(dense_scratch_fits<4>() && dense_scratch_fits<8>() && dense_scratch_fits<16>(),
+              "dense scratch: R = 6 in seven spare areas, half groups in three");
+static_assert(BZ_MAX + 2 * 6 <= 32, "dense path: one bit per dilated plane in a 32-bit mask");
 
 // Run by a heavy group of gt threads (gw = gt / 32 warps); tid is the
 // thread's index in the group, areas the group's first warp area, and the
 // group synchronises on named barrier bar.  The codes of area 0 are all
 // written by pass z (32 where no contact's window reaches), its counts
 // cleared here.
+template <int BZ>
 __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const uint32_t *pairs,
-                                uint32_t len, WarpArea *areas, const uint8_t *ctab,
+                                uint32_t len, WarpArea<BZ> *areas, const uint8_t *ctab,
                                 const DevTables &t, int R, int SR,
                                 uint32_t T, uint32_t Hmax, uint32_t &form_bad, int tid, int gt,
                                 int bar) {
@@ -428,12 +453,12 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
     uint32_t *pmask = g2 + DZ * BY * 8;    // per dilated plane z: bit y = row (y, z) has a contact
     uint32_t *nlist = pmask + DZ;          // number of rows with a contact
     uint16_t *list = reinterpret_cast<uint16_t *>(nlist + 1);              // those rows
-    WarpArea *a0 = areas;
+    WarpArea<BZ> *a0 = areas;
     const uint32_t inf4 = DENSE_INF * 0x01010101u;
     // clear the counts and the occupancy
     {
         uint4 *c = reinterpret_cast<uint4 *>(a0->cnt);
-        for (int i = tid; i < BVOX / 8; i += gt) c[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = tid; i < bvox<BZ>() / 8; i += gt) c[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     for (int r = tid; r < DY * DZ; r += gt) occ[r] = 0ull;
     if (tid < DZ) pmask[tid] = 0u;
@@ -493,7 +518,7 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
     group_sync(bar, gt);
     // pass z (taps only from planes with contacts) and the codes: the
     // minimum kernel code of every voxel of the brick
-    for (int idx = tid; idx < BROWS * 8; idx += gt) {
+    for (int idx = tid; idx < brows<BZ>() * 8; idx += gt) {
         const int w = idx & 7, row = idx >> 3, y = row & 7, z = row >> 3;
         uint32_t acc = inf4;
         for (uint32_t m = (planes >> z) & twin; m; m &= m - 1u) {
@@ -507,7 +532,7 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
     // Eq. 5 counts: pairs 32 at a time per warp, counted into one array
     for (uint32_t j0 = 32u * warp; j0 < len; j0 += 32u * gw) {
         const uint32_t mine = j0 + lane < len ? __ldg(pairs + j0 + lane) : 0u;
-        shadow_pairs<true>(mine, (int)min(32u, len - j0), a0->cnt, t, R, SR, lane);
+        shadow_pairs<BZ, true>(mine, (int)min(32u, len - j0), a0->cnt, t, R, SR, lane);
     }
     group_sync(bar, gt);
     write_back<1, 4>(g, bx, by, bz, a0, tid, gt, T, Hmax, form_bad);
@@ -536,7 +561,7 @@ __device__ __forceinline__ uint32_t brick_grid(const DevGrid &g, const BatchDev 
     return b - bd.bbase[gi];
 }
 
-template <int NW, bool BATCH>
+template <int NW, bool BATCH, int BZ>
 __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, DevParams p,
                                                     DevTables t, long long n_input, WsDev ws) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -552,11 +577,11 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
     const int np = (2 * R * R + 1) * W;
     uint32_t *P = smem;
     for (int j = threadIdx.x; j < np; j += NTHR) P[j] = t.prow[j];
-    WarpArea *areas = reinterpret_cast<WarpArea *>(smem + ((np + 3) & ~3));
+    WarpArea<BZ> *areas = reinterpret_cast<WarpArea<BZ> *>(smem + ((np + 3) & ~3));
     // shadow offset lists stay in global memory (read-only path,
     // L1-resident): the shared memory they would take costs a CTA per SM
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    WarpArea *wa = areas + warp;
+    WarpArea<BZ> *wa = areas + warp;
     // the tables above are the kernels' own; the workspace is the previous
     // kernels' output
     pdl_wait();
@@ -570,18 +595,18 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
     uint32_t form_bad = 0;
 
     // ---------------- work: heavy bricks by groups of hw warps, light ones by single warps
-    // At K <= 11 the dense path runs on groups of four warps (its scratch
-    // fits a group's three spare areas): group 0 (warps 0-3) takes heavy
+    // At K <= 11 (K <= 7 for BZ = 4) the dense path runs on groups of four
+    // warps (its scratch fits a group's three spare areas): group 0 (warps 0-3) takes heavy
     // bricks first, group 1 (warps 4-7) light bricks first, so the largest
     // light bricks start at the beginning of the launch instead of after the
     // heavy ones; each group then turns to the other kind.  Otherwise the
     // whole CTA is one group, heavy bricks first.
-    const int hw = (NW == 4 && R <= HALF_GROUP_MAX_R) ? WPC / 2 : WPC;
+    const int hw = (NW == 4 && R <= half_group_max_r<BZ>()) ? WPC / 2 : WPC;
     const int ht = hw * 32;
     const int gidx = warp / hw;                  // group of this warp
     const int gtid = tid - gidx * ht, gwarp = warp - gidx * hw;
     const int gbar = 1 + gidx;                   // its named barrier
-    WarpArea *garea = areas + gidx * hw;         // its first warp area
+    WarpArea<BZ> *garea = areas + gidx * hw;     // its first warp area
     // First claims are static (heavy item blockIdx.x for group 0, light item
     // blockIdx.x * hw + gwarp for group 1's warps): a launch's thousands of
     // warps claiming at once through one counter would wait on each other's
@@ -633,14 +658,14 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
                         const uint32_t jj = (base + lane) * WPC + warp;
                         const uint32_t mine = jj < rl ? __ldg(rp + jj) : 0u;
                         const int cnt = (int)min(32u, (rl - warp + WPC - 1) / WPC - base);
-                        const RowsSetup su = rows_setup(mine, R);    // lanes >= cnt: unused
+                        const RowsSetup su = rows_setup<BZ>(mine, R);    // lanes >= cnt: unused
                         for (int j = 0; j < cnt; ++j) {
                             const RowsSetup sj = {__shfl_sync(0xffffffffu, su.a, j),
                                                   __shfl_sync(0xffffffffu, su.b, j)};
-                            apply_rows<NW>(sj, wa, P, W, lane);
+                            apply_rows<NW, BZ>(sj, wa, P, W, lane);
                             __syncwarp();
                         }
-                        shadow_pairs<false>(mine, cnt, wa->cnt, t, R, SR, lane);
+                        shadow_pairs<BZ, false>(mine, cnt, wa->cnt, t, R, SR, lane);
                     }
                     group_sync(gbar, ht);
                     // D: the areas merged (byte-wise min of codes, sum of counts) and written back
@@ -694,14 +719,14 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
                     for (uint32_t base = 0; base < rl; base += 32) {
                         const uint32_t mine = base + lane < rl ? __ldg(rp + base + lane) : 0u;
                         const int cnt = (int)min(32u, rl - base);
-                        const RowsSetup su = rows_setup(mine, R);    // lanes >= cnt: unused
+                        const RowsSetup su = rows_setup<BZ>(mine, R);    // lanes >= cnt: unused
                         for (int j = 0; j < cnt; ++j) {
                             const RowsSetup sj = {__shfl_sync(0xffffffffu, su.a, j),
                                                   __shfl_sync(0xffffffffu, su.b, j)};
-                            apply_rows<NW>(sj, wa, P, W, lane);
+                            apply_rows<NW, BZ>(sj, wa, P, W, lane);
                             __syncwarp();
                         }
-                        shadow_pairs<false>(mine, cnt, wa->cnt, t, R, SR, lane);
+                        shadow_pairs<BZ, false>(mine, cnt, wa->cnt, t, R, SR, lane);
                     }
                     // D
                     __syncwarp();
@@ -749,18 +774,20 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
 }
 
 // Dynamic shared memory of one CTA: row codes and warp areas.
-static size_t integrate_smem(int K) {
+static size_t integrate_smem(int K, int bz) {
     const int R = (K - 1) / 2;
     const size_t np = (size_t)(2 * R * R + 1) * (2 * R + 4);
-    return ((np + 3) & ~size_t(3)) * 4 + WPC * sizeof(WarpArea);
+    const size_t area = bz == 4 ? sizeof(WarpArea<4>) : bz == 16 ? sizeof(WarpArea<16>)
+                                                                  : sizeof(WarpArea<8>);
+    return ((np + 3) & ~size_t(3)) * 4 + WPC * area;
 }
 
 // Launch configuration, cached per device.  Calls for different devices or
 // workspaces may come from several host threads, so the cache is guarded.
 constexpr int kCfgDevices = 64;
 struct IntegrateCfg {
-    bool limits_set[2] = {};            // shared-memory limit raised: 4-word, 6-word rows
-    int ctas[MAX_K + 1] = {};
+    bool limits_set[3][2] = {};         // per depth: shared-memory limit raised (4-word, 6-word rows)
+    int ctas[3][MAX_K + 1] = {};
 };
 static IntegrateCfg g_cfg[kCfgDevices];
 static std::mutex g_cfg_mutex;
@@ -769,18 +796,18 @@ static std::mutex g_cfg_mutex;
 // limit of each template instance is raised once per device to what its
 // largest kernel size needs (the attribute belongs to the function, so it
 // must not be lowered for a smaller K).
-template <int NW>
+template <int NW, int BZ>
 static int configure(int dev, bool &limits_set, size_t smem, size_t smem_max) {
     int sms = 0, per_sm = 0;
     if (!limits_set) {
-        cudaFuncSetAttribute(k_integrate<NW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_integrate<NW, false, BZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_max);
-        cudaFuncSetAttribute(k_integrate<NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_integrate<NW, true, BZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_max);
         limits_set = true;
     }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<NW, true>, NTHR, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<NW, true, BZ>, NTHR, smem);
     return max(1, sms * max(1, per_sm));
 }
 
@@ -794,41 +821,58 @@ int device_sm_count() {
     return sms > 0 ? sms : 1;
 }
 
-// Persistent grid for these parameters: every SM filled to its occupancy limit.
-int integrate_grid_ctas(const DevParams &p) {
+template <int BZ>
+static int configure_depth(int dev, bool limits_set[2], int K) {
+    const size_t smem = integrate_smem(K, BZ);
+    if (words_per_row(K) == 4) return configure<4, BZ>(dev, limits_set[0], smem, integrate_smem(13, BZ));
+    const int kmax = BZ == 16 ? BZ16_MAX_K : MAX_K;
+    return configure<6, BZ>(dev, limits_set[1], smem, integrate_smem(kmax, BZ));
+}
+
+// Persistent grid for these parameters and brick depth: every SM filled to
+// its occupancy limit.
+int integrate_grid_ctas(const DevParams &p, int bz) {
     int dev = 0;
     cudaGetDevice(&dev);
     IntegrateCfg local;                                 // devices past the cache: not cached
     IntegrateCfg &c = (dev >= 0 && dev < kCfgDevices) ? g_cfg[dev] : local;
+    const int d = bz_shift(bz) - 2;
     std::lock_guard<std::mutex> lock(g_cfg_mutex);
-    if (!c.ctas[p.K]) {
-        const size_t smem = integrate_smem(p.K);
-        const bool four = words_per_row(p.K) == 4;
-        const size_t smax = four ? integrate_smem(13) : integrate_smem(MAX_K);
-        c.ctas[p.K] = four ? configure<4>(dev, c.limits_set[0], smem, smax)
-                           : configure<6>(dev, c.limits_set[1], smem, smax);
+    if (!c.ctas[d][p.K]) {
+        c.ctas[d][p.K] = d == 0   ? configure_depth<4>(dev, c.limits_set[0], p.K)
+                         : d == 2 ? configure_depth<16>(dev, c.limits_set[2], p.K)
+                                  : configure_depth<8>(dev, c.limits_set[1], p.K);
     }
-    return c.ctas[p.K];
+    return c.ctas[d][p.K];
+}
+
+template <bool BATCH, int BZ>
+static void launch_depth(const DevGrid &g, const BatchDev &bd, const DevParams &p, const DevTables &t,
+                         long long n_input, const WsDev &ws, int grid_ctas, cudaStream_t s) {
+    const size_t smem = integrate_smem(p.K, BZ);
+    if (words_per_row(p.K) == 4)
+        launch_pdl(k_integrate<4, BATCH, BZ>, grid_ctas, NTHR, smem, s, g, bd, p, t, n_input, ws);
+    else
+        launch_pdl(k_integrate<6, BATCH, BZ>, grid_ctas, NTHR, smem, s, g, bd, p, t, n_input, ws);
+}
+
+template <bool BATCH>
+static void launch_any(int bzs, const DevGrid &g, const BatchDev &bd, const DevParams &p,
+                       const DevTables &t, long long n_input, const WsDev &ws, int grid_ctas,
+                       cudaStream_t s) {
+    if (bzs == 2) launch_depth<BATCH, 4>(g, bd, p, t, n_input, ws, grid_ctas, s);
+    else if (bzs == 4) launch_depth<BATCH, 16>(g, bd, p, t, n_input, ws, grid_ctas, s);
+    else launch_depth<BATCH, 8>(g, bd, p, t, n_input, ws, grid_ctas, s);
 }
 
 void launch_integrate(const DevGrid &g, const DevParams &p, const DevTables &t, long long n_input,
                       const WsDev &ws, int grid_ctas, cudaStream_t s) {
-    const size_t smem = integrate_smem(p.K);
-    const BatchDev none = {};
-    if (words_per_row(p.K) == 4)
-        launch_pdl(k_integrate<4, false>, grid_ctas, NTHR, smem, s, g, none, p, t, n_input, ws);
-    else
-        launch_pdl(k_integrate<6, false>, grid_ctas, NTHR, smem, s, g, none, p, t, n_input, ws);
+    launch_any<false>(g.bzs, g, BatchDev{}, p, t, n_input, ws, grid_ctas, s);
 }
 
 void launch_integrate_batch(const BatchDev &bd, const DevParams &p, const DevTables &t,
                             long long n_input, const WsDev &ws, int grid_ctas, cudaStream_t s) {
-    const size_t smem = integrate_smem(p.K);
-    const DevGrid none = {};
-    if (words_per_row(p.K) == 4)
-        launch_pdl(k_integrate<4, true>, grid_ctas, NTHR, smem, s, none, bd, p, t, n_input, ws);
-    else
-        launch_pdl(k_integrate<6, true>, grid_ctas, NTHR, smem, s, none, bd, p, t, n_input, ws);
+    launch_any<true>(bd.bzs, DevGrid{}, bd, p, t, n_input, ws, grid_ctas, s);
 }
 
 // ---------------------------------------------------------------- op-rate micro-benchmark

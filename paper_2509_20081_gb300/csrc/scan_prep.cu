@@ -230,14 +230,14 @@ __device__ __forceinline__ void tally_flush(CtaTally &s, const WsDev &ws) {
 struct BrickSpan {
     int x0, x1, y0, y1, z0, z1;
 };
-__device__ __forceinline__ BrickSpan brick_span(int cx, int cy, int cz, int R) {
+__device__ __forceinline__ BrickSpan brick_span(int cx, int cy, int cz, int R, int bzs) {
     BrickSpan s;
     s.x0 = (cx - R) / BX;  // contacts are >= R, so these are non-negative
     s.x1 = (cx + R) / BX;
     s.y0 = (cy - R) / BY;
     s.y1 = (cy + R) / BY;
-    s.z0 = (cz - R) / BZ;
-    s.z1 = (cz + R) / BZ;
+    s.z0 = (cz - R) >> bzs;
+    s.z1 = (cz + R) >> bzs;
     return s;
 }
 
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(256) k_voxelize(DevGrid g, DevParams p, DevTab
         if (f[1]) f[2] = !p.dedup || hash_insert(ws, hcap, voxel_key(g, rec.x, rec.y, rec.z), (uint32_t)i);
         ws.prec[i] = rec;
     }
-    count_pairs<true>(ws, g, 0u, f[2], f[2] ? brick_span(rec.x, rec.y, rec.z, p.R) : BrickSpan{});
+    count_pairs<true>(ws, g, 0u, f[2], f[2] ? brick_span(rec.x, rec.y, rec.z, p.R, g.bzs) : BrickSpan{});
     tally_warp(s_tally, f);
     tally_flush(s_tally, ws);
 }
@@ -517,10 +517,10 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(DevGrid g0, BatchDev bd
 // ------------------------------------------------------------------ K4
 // Pair payload: contact relative to the brick corner plus R (x: 6 bits,
 // y, z: 5 bits each) and the bin (16 bits).
-__device__ __forceinline__ uint32_t pair_payload(int4 r, int bx, int by, int bz, int R) {
+__device__ __forceinline__ uint32_t pair_payload(int4 r, int bx, int by, int bz, int R, int bzs) {
     const uint32_t rx = (uint32_t)(r.x - bx * BX + R);
     const uint32_t ry = (uint32_t)(r.y - by * BY + R);
-    const uint32_t rz = (uint32_t)(r.z - bz * BZ + R);
+    const uint32_t rz = (uint32_t)(r.z - (bz << bzs) + R);
     return rx | (ry << 6) | (rz << 11) | ((uint32_t)(r.w & 0xFFFF) << 16);
 }
 
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, int
         if (i < n) {
             const int4 r = ws.prec[i];
             if (r.x >= 0 && !(r.w & PREC_DUP)) {
-                const BrickSpan sp = brick_span(r.x, r.y, r.z, p.R);
+                const BrickSpan sp = brick_span(r.x, r.y, r.z, p.R, g.bzs);
                 const int sx = sp.x1 - sp.x0 + 1, sy = sp.y1 - sp.y0 + 1, sz = sp.z1 - sp.z0 + 1;
                 if (j < sx * sy * sz) {
                     // j -> (ix, iy, iz), x fastest; sx <= 2 and sy <= 4 for K <= 21
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, int
                     }
                     const int bx = sp.x0 + ix, by = sp.y0 + iy, bz = sp.z0 + iz;
                     b = ((uint32_t)bz * g.nby + by) * g.nbx + bx;
-                    pl = pair_payload(r, bx, by, bz, p.R);
+                    pl = pair_payload(r, bx, by, bz, p.R, g.bzs);
                     v = true;
                 }
             }
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(256) k_voxelize_b(BatchDev bd, DevParams p, De
             ws.prec[i] = rec;
         }
     }
-    count_pairs<true>(ws, g, b0, f[2], f[2] ? brick_span(rec.x, rec.y, rec.z, p.R) : BrickSpan{});
+    count_pairs<true>(ws, g, b0, f[2], f[2] ? brick_span(rec.x, rec.y, rec.z, p.R, g.bzs) : BrickSpan{});
     tally_warp(s_tally, f);
     add_item_counts(bd, s_tally, item, f);
     tally_flush(s_tally, ws);
@@ -698,8 +698,7 @@ __global__ void __launch_bounds__(256) k_fill_b(BatchDev bd, DevParams p, long l
         b0 = bd.bbase[gi];
     }
     const int lane = threadIdx.x & 31;
-    const uint32_t bin = (uint32_t)(r.w & 0xFFFF);
-    for_pair_bricks<true>(has, has ? brick_span(r.x, r.y, r.z, p.R) : BrickSpan{}, g, b0,
+    for_pair_bricks<true>(has, has ? brick_span(r.x, r.y, r.z, p.R, g.bzs) : BrickSpan{}, g, b0,
                           [&](bool v, uint32_t b, int bx, int by, int bz) {
         const unsigned peers = __match_any_sync(0xffffffffu, v ? b : 0xFFFFFFFFu);
         const int leader = __ffs(peers) - 1;
@@ -709,11 +708,8 @@ __global__ void __launch_bounds__(256) k_fill_b(BatchDev bd, DevParams p, long l
         if (v) {
             const unsigned long long pos = (unsigned long long)ws.boff[b] + base +
                                            (uint32_t)__popc(peers & ((1u << lane) - 1u));
-            const uint32_t rx = (uint32_t)(r.x - bx * BX + p.R);
-            const uint32_t ry = (uint32_t)(r.y - by * BY + p.R);
-            const uint32_t rz = (uint32_t)(r.z - bz * BZ + p.R);
             if (pos < ws.pairs_cap)
-                ws.pairs[pos] = rx | (ry << 6) | (rz << 11) | (bin << 16);
+                ws.pairs[pos] = pair_payload(r, bx, by, bz, p.R, g.bzs);
             else
                 atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
         }
@@ -884,7 +880,7 @@ void launch_alloc_batch(const BatchDev &bd, const DevParams &p, long long n, con
 
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                  cudaStream_t s) {
-    const int slots = max_pairs_per_return(p.K);
+    const int slots = max_pairs_per_return(p.K, 1 << g.bzs);
     launch_pdl(k_fill, dim3((unsigned)std::max(1, (n + 255) / 256), (unsigned)slots), 256, 0, s, g, p, n,
                slots, ws, hcap);
 }

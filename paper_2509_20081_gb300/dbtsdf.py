@@ -46,10 +46,12 @@ DBT_MOTION_YAW = 1
 
 
 class dbt_tuning(ctypes.Structure):
-    _fields_ = [("heavy_pairs", ctypes.c_int32), ("integrate_ctas", ctypes.c_int32)]
+    _fields_ = [("heavy_pairs", ctypes.c_int32), ("integrate_ctas", ctypes.c_int32),
+                ("brick_depth", ctypes.c_int32)]
 
     def as_dict(self):
-        return {"heavy_pairs": int(self.heavy_pairs), "integrate_ctas": int(self.integrate_ctas)}
+        return {"heavy_pairs": int(self.heavy_pairs), "integrate_ctas": int(self.integrate_ctas),
+                "brick_depth": int(self.brick_depth)}
 
 
 class dbt_quality(ctypes.Structure):
@@ -340,9 +342,10 @@ class Workspace:
     def reset(self, stream=None):
         _check(lib().dbt_workspace_reset(self.h, _stream_ptr(stream)))
 
-    def set_tuning(self, kernels: "Kernels", heavy_pairs: int = 64, integrate_ctas: int = 0):
+    def set_tuning(self, kernels: "Kernels", heavy_pairs: int = 64, integrate_ctas: int = 0,
+                   brick_depth: int = 0):
         """dbt_workspace_set_tuning (launch choices only; results do not change)."""
-        t = dbt_tuning(int(heavy_pairs), int(integrate_ctas))
+        t = dbt_tuning(int(heavy_pairs), int(integrate_ctas), int(brick_depth))
         _check(lib().dbt_workspace_set_tuning(self.h, kernels.h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
@@ -640,9 +643,9 @@ class Batch:
     def run(self, stream=None):
         _check(lib().dbt_batch_run(self.h, _stream_ptr(stream)))
 
-    def set_tuning(self, heavy_pairs: int = 64, integrate_ctas: int = 0):
+    def set_tuning(self, heavy_pairs: int = 64, integrate_ctas: int = 0, brick_depth: int = 0):
         """dbt_batch_set_tuning (launch choices only; results do not change)."""
-        t = dbt_tuning(int(heavy_pairs), int(integrate_ctas))
+        t = dbt_tuning(int(heavy_pairs), int(integrate_ctas), int(brick_depth))
         _check(lib().dbt_batch_set_tuning(self.h, ctypes.byref(t)))
 
     def tuning(self) -> dict:

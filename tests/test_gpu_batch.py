@@ -158,11 +158,13 @@ def test_every_tuning_gives_the_same_maps(orc):
     dims = (w.grid.nx, w.grid.ny, w.grid.nz)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     ref = None
-    for heavy, ctas in [(48, 0), (0, 0), (16, sms), (1 << 30, 2 * sms), (96, 1), (24, 4 * sms)]:
+    for heavy, ctas, depth in [(48, 0, 8), (0, 0, 8), (16, sms, 4), (1 << 30, 2 * sms, 8),
+                               (96, 1, 16), (24, 4 * sms, 8), (0, 0, 4), (8, 0, 16),
+                               (1 << 30, 0, 4), (64, 3 * sms, 16)]:
         g = dbt.Grid(*dims, w.grid.res)
         ws = dbt.Workspace(g, k, max(len(p) for p, _ in w.scans))
-        ws.set_tuning(k, heavy, ctas)
-        assert ws.tuning() == {"heavy_pairs": heavy, "integrate_ctas": ctas}
+        ws.set_tuning(k, heavy, ctas, depth)
+        assert ws.tuning() == {"heavy_pairs": heavy, "integrate_ctas": ctas, "brick_depth": depth}
         for pts, pose in w.scans:
             dbt.dbt_integrate_scan(g, k, ws, torch.from_numpy(pts).cuda(), pose)
         st = dbt.dbt_get_scan_stats(ws)
@@ -175,7 +177,7 @@ def test_every_tuning_gives_the_same_maps(orc):
                 np.testing.assert_array_equal(a, b)
         gb = dbt.Grid(*dims, w.grid.res)
         b = dbt.Batch([gb], k, sum(len(p) for p, _ in w.scans), len(w.scans))
-        b.set_tuning(heavy, ctas)
+        b.set_tuning(heavy, ctas, depth)
         b.set_items([(0, torch.from_numpy(p).cuda(), pose) for p, pose in w.scans])
         b.run()
         for a, r in zip(gb.numpy(), ref):
@@ -194,6 +196,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(orc):
     b.set_items(items)
     best = b.autotune(n_trials=2)
     assert best["heavy_pairs"] in (16, 24, 32, 40, 48, 64, 96, 128, 192, 256)
+    assert best["brick_depth"] in (4, 8, 16)
     assert best == b.tuning()
     b.close()
     g = dbt.Grid(*dims, w.grid.res)

@@ -3,11 +3,12 @@
 Every voxel's mask, sign and hit counter (bit-exact, the state is integer)
 after integrating, in the launch forms the benchmark times:
   - urban sequence (1600 x 1600 x 320 at 0.05 m, scans of 65,536 returns):
-    the first 8 scans by per-scan launches, and the same 8 as one batch at
-    another launch tuning;
+    the first 8 scans by per-scan launches (32 x 8 x 8 bricks), and the same
+    8 as one batch at another launch tuning (32 x 8 x 4 bricks);
   - high resolution (2000 x 2000 x 400 at 0.02 m, 262,144 returns per scan):
-    4 scans by per-scan launches;
-  - 32 uneven maps (64^3 to 512^3) x 8 scans, all in one dbt_batch_run;
+    4 scans by per-scan launches (32 x 8 x 16 bricks);
+  - 32 uneven maps (64^3 to 512^3) x 8 scans, all in one dbt_batch_run
+    (32 x 8 x 4 bricks);
   - serving (16 robots, Poisson arrivals over 60 s simulated): every map
     after the first 5 s of the trace went through the continuous-batching
     loop, then the two robots with the smallest streams for the full 60 s.
@@ -71,7 +72,7 @@ def test_urban_full_size_eight_scans(orc):
     # the same scans as one batch, another tuning: equal to the per-scan map
     gb = dbt.Grid(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.res, w.grid.origin)
     b = dbt.Batch([gb], k, 8 * 65536, 8)
-    b.set_tuning(heavy_pairs=96, integrate_ctas=304)
+    b.set_tuning(heavy_pairs=96, integrate_ctas=304, brick_depth=4)
     b.set_items([(0, x, pose) for x, (_, pose) in zip(xs, w.scans)])
     b.run()
     torch.cuda.synchronize()
@@ -87,6 +88,7 @@ def test_highres_full_size_four_scans(orc):
     k = dbt.Kernels(dbt.make_params(**w.params))
     g = dbt.Grid(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.res, w.grid.origin)
     ws = dbt.Workspace(g, k, 262144)
+    ws.set_tuning(k, brick_depth=16)
     kept = []
     for pts, pose in w.scans:
         dbt.dbt_integrate_scan(g, k, ws, torch.from_numpy(pts).cuda(), pose)
@@ -103,6 +105,7 @@ def test_maps_all_32_in_one_batch():
     grids = [dbt.Grid(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.res) for w in maps]
     items = [(m, torch.from_numpy(p).cuda(), pose) for m, w in enumerate(maps) for p, pose in w.scans]
     b = dbt.Batch(grids, k, sum(int(x.shape[0]) for _, x, _ in items), len(items))
+    b.set_tuning(brick_depth=4)
     b.set_items(items)
     b.run()
     per, tot = b.stats()

@@ -26,13 +26,16 @@ def _dbt():
     return dbt
 
 
-def run_gpu(pdict, dims, res, scans, origin=(0.0, 0.0, 0.0), max_points=None, host=False):
+def run_gpu(pdict, dims, res, scans, origin=(0.0, 0.0, 0.0), max_points=None, host=False,
+            tuning=None):
     dbt = _dbt()
     p = dbt.make_params(**pdict)
     k = dbt.Kernels(p)
     g = dbt.Grid(*dims, res, origin)
     mp = max_points or max([len(s[0]) for s in scans] + [1])
     ws = dbt.Workspace(g, k, mp)
+    if tuning:
+        ws.set_tuning(k, **tuning)
     stats = []
     for pts, pose in scans:
         if host:
@@ -166,6 +169,39 @@ def test_group_schedules_match_oracle(orc, room3, K, heavy):
     assert_same(g.numpy(), ora, gs, os_)
 
 
+@pytest.mark.parametrize("depth,K", [(4, 3), (4, 9), (4, 13), (4, 21), (16, 5), (16, 11), (16, 13),
+                                     (16, 17)])
+def test_brick_depths_match_oracle(orc, room3, depth, K):
+    """Bricks 32 x 8 x 4 and 32 x 8 x 16: every brick heavy (0), a mix with
+    very heavy bricks (8) and every brick light (2^30), whole grids against
+    the oracle.  Depth 4 runs the dense path on the whole CTA from K = 9 on
+    (two four-warp groups below), depth 16 keeps the two groups up to K = 11;
+    K = 17 is the deepest kernel depth 16 takes."""
+    dbt = _dbt()
+    pd = params(kernel_size=K, shadow_radius=min(3.0, (K - 1) / 2))
+    ora, os_ = run_oracle(orc, pd, (128, 128, 128), 0.1, room3.scans[:2])
+    for heavy in (0, 8, 1 << 30):
+        gpu, gs, (g, k, ws) = run_gpu(pd, (128, 128, 128), 0.1, room3.scans[:2],
+                                      tuning=dict(heavy_pairs=heavy, brick_depth=depth))
+        assert ws.tuning()["brick_depth"] == depth
+        assert_same(gpu, ora, gs, os_)
+
+
+def test_brick_depth_16_refused_above_k17():
+    dbt = _dbt()
+    k = dbt.Kernels(dbt.make_params(**params(kernel_size=19)))
+    g = dbt.Grid(64, 64, 64, 0.1)
+    ws = dbt.Workspace(g, k, 1000)
+    with pytest.raises(dbt.DbtError):
+        ws.set_tuning(k, 64, 0, 16)
+    with pytest.raises(dbt.DbtError):
+        ws.set_tuning(k, 64, 0, 12)
+    ws.set_tuning(k, 64, 0, 4)
+    assert ws.tuning() == {"heavy_pairs": 64, "integrate_ctas": 0, "brick_depth": 4}
+    ws.set_tuning(k, 64, 0, 0)
+    assert ws.tuning()["brick_depth"] == 8
+
+
 def _tiny(seed, n, dims, res, dup):
     rng = synth.Rng(seed)
     nx, ny, nz = dims
@@ -184,15 +220,19 @@ def _tiny(seed, n, dims, res, dup):
     ((97, 13, 41), 11, 1), ((40, 40, 40), 21, 0), ((21, 21, 21), 21, 1), ((64, 8, 8), 1, 0),
 ])
 def test_ragged_grids(orc, dims, K, scheme):
-    """Grids that are not whole bricks, random poses, duplicates in voxels."""
+    """Grids that are not whole bricks, random poses, duplicates in voxels;
+    at every brick depth the kernel size allows (a ragged last brick layer
+    in z for depths 4, 8 and 16 alike)."""
     a, b = (8, 8) if scheme == 0 else (40, 40)
     pd = params(kernel_size=K, scheme=scheme, bins_a=a, bins_b=b,
                 shadow_radius=min(3.0, (K - 1) / 2))
     scans = [_tiny(100 + i + K, 3000, dims, 0.07, 5) for i in range(3)]
-    gpu, gs, _ = run_gpu(pd, dims, 0.07, scans, origin=(0.0, 0.0, 0.0))
     ora, os_ = run_oracle(orc, pd, dims, 0.07, scans)
     assert sum(s["n_kept"] for s in os_) > 0
-    assert_same(gpu, ora, gs, os_)
+    for depth in (8, 4, 16) if K <= 17 else (8, 4):
+        gpu, gs, _ = run_gpu(pd, dims, 0.07, scans, origin=(0.0, 0.0, 0.0),
+                             tuning=dict(brick_depth=depth))
+        assert_same(gpu, ora, gs, os_)
 
 
 def test_origin_offset_and_negative_coords(orc):
