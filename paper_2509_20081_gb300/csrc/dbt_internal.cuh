@@ -171,7 +171,8 @@ struct WsHeader {
     uint32_t n_vheavy;          // of those, bricks with more than 4 x `heavy` (taken first)
     unsigned long long acc_valid, acc_inside, acc_kept;
     uint32_t n_cls[LIGHT_CLASSES];   // light bricks per size class
-    uint32_t pad1[8 - LIGHT_CLASSES];
+    uint32_t next_vheavy;       // dynamic queue of very heavy bricks (whole CTAs)
+    uint32_t pad1[7 - LIGHT_CLASSES];
     ScanStats last;             // published by the last integrate CTA
 };
 

@@ -77,9 +77,11 @@ __device__ __forceinline__ int kword(int row, int w) { return row * 8 + (w ^ ((r
 __device__ __forceinline__ uint32_t vmin4(uint32_t a, uint32_t b) { return __vminu4(a, b); }
 
 // Named barrier `id` (1 + group index) over the n threads of a heavy-brick
-// group of warps.
+// group of warps; id 0 is the whole CTA.
 __device__ __forceinline__ void group_sync(int id, int n) {
-    if (id == 1)   // immediate barrier ids: the kernel then holds three barriers, not all 16
+    if (id == 0)
+        __syncthreads();
+    else if (id == 1)   // immediate barrier ids: the kernel then holds three barriers, not all 16
         asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
     else
         asm volatile("bar.sync 2, %0;" ::"r"(n) : "memory");
@@ -400,6 +402,78 @@ __device__ __forceinline__ void write_back(const DevGrid &g, int bx, int by, int
     }
 }
 
+// Phase D of a light brick, by one warp.  Lane l visits chunk i (i < NI) at
+// row 4 i + l / 8, word (l + i) mod 8: every chunk once, and a kernel box's
+// few covered words of a row fall to different lanes in different rows, so
+// each lane holds about the same number of covered chunks (with lanes fixed
+// to a word, the lanes of the covered words would walk every row while the
+// others idle).  The covered chunks (those with kernel codes; a chunk with
+// shadow counts lies in its contact's K^3 box and so has codes too) are
+// noted in a bit mask first, then taken four per lane at a time: their
+// masks and counters loaded together, then lowered, bumped and stored as in
+// write_back.
+template <int BZ>
+__device__ __forceinline__ void write_back_light(const DevGrid &g, int bx, int by, int bz,
+                                                 const WarpArea<BZ> *a, int lane, uint32_t T,
+                                                 uint32_t Hmax, uint32_t &form_bad) {
+    constexpr int NI = bchunks<BZ>() / 32;
+    static_assert(NI <= 32, "one bit per visited chunk");
+    uint32_t cov = 0;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int row = 4 * i + (lane >> 3), ch = (lane + i) & 7;
+        if (a->kst[kword(row, ch)] != NO_CODE4) cov |= 1u << i;
+    }
+    while (__any_sync(0xffffffffu, cov != 0u)) {
+        int rc[4];                            // row * 8 + ch of each taken chunk, -1 = none
+        uint4 m[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            rc[q] = -1;
+            m[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (cov) {
+                const int i = __ffs(cov) - 1;
+                cov &= cov - 1u;
+                const int row = 4 * i + (lane >> 3), ch = (lane + i) & 7;
+                rc[q] = row * 8 + ch;
+                m[q] = __ldcg(reinterpret_cast<const uint4 *>(g.mask + chunk_index<BZ>(g, bx, by, bz, row, ch)));
+            }
+        }
+        uint2 hv[4];
+        uint32_t hc = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            hv[q] = make_uint2(0u, 0u);
+            if (rc[q] >= 0) {
+                const uint2 cs = chunk_counts<1>(a, rc[q] >> 3, rc[q] & 7);
+                if (cs.x | cs.y) {
+                    hc |= 1u << q;
+                    hv[q] = __ldcg(reinterpret_cast<const uint2 *>(
+                        g.hits + chunk_index<BZ>(g, bx, by, bz, rc[q] >> 3, rc[q] & 7)));
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (rc[q] < 0) continue;
+            const int row = rc[q] >> 3, ch = rc[q] & 7;
+            const uint32_t k = a->kst[kword(row, ch)];
+            const uint32_t old = codes_of(m[q], form_bad);
+            const uint32_t lt = code_lt(old, k);
+            if (lt) store_codes(g, chunk_index<BZ>(g, bx, by, bz, row, ch), code_min(old, k, lt));
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!((hc >> q) & 1u)) continue;
+            const int row = rc[q] >> 3, ch = rc[q] & 7;
+            const size_t gi = chunk_index<BZ>(g, bx, by, bz, row, ch);
+            const uint32_t cross = apply_counts(hv[q], chunk_counts<1>(a, row, ch), T, Hmax);
+            __stcg(reinterpret_cast<uint2 *>(g.hits + gi), hv[q]);
+            store_crossings(g, gi, cross);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- dense bricks
 // For a brick with many pairs, the Eq. 4 result is computed once per voxel
 // instead of once per pair: the mask left by AND-ing the kernels of all
@@ -529,10 +603,14 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
                                  ((uint32_t)ctab[(acc >> 16) & 255u] << 16) |
                                  ((uint32_t)ctab[acc >> 24] << 24);
     }
-    // Eq. 5 counts: pairs 32 at a time per warp, counted into one array
-    for (uint32_t j0 = 32u * warp; j0 < len; j0 += 32u * gw) {
-        const uint32_t mine = j0 + lane < len ? __ldg(pairs + j0 + lane) : 0u;
-        shadow_pairs<BZ, true>(mine, (int)min(32u, len - j0), a0->cnt, t, R, SR, lane);
+    // Eq. 5 counts into one array: warp w takes an equal share of the pairs
+    // (len * w / gw onwards), 32 at a time; the phase ends at the barrier
+    // below, so the largest share sets its length
+    const uint32_t jlo = len * (uint32_t)warp / (uint32_t)gw;
+    const uint32_t jhi = len * (uint32_t)(warp + 1) / (uint32_t)gw;
+    for (uint32_t j0 = jlo; j0 < jhi; j0 += 32u) {
+        const uint32_t mine = j0 + lane < jhi ? __ldg(pairs + j0 + lane) : 0u;
+        shadow_pairs<BZ, true>(mine, (int)min(32u, jhi - j0), a0->cnt, t, R, SR, lane);
     }
     group_sync(bar, gt);
     write_back<1, 4>(g, bx, by, bz, a0, tid, gt, T, Hmax, form_bad);
@@ -566,6 +644,7 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
                                                     DevTables t, long long n_input, WsDev ws) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t s_item[2];                        // per heavy group
+    __shared__ uint32_t s_vitem;                          // the CTA's very heavy brick
     __shared__ uint8_t s_ctab[256];
     for (int j = threadIdx.x; j < 256; j += NTHR) {
         int kk = 0;
@@ -596,33 +675,70 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
 
     // ---------------- work: heavy bricks by groups of hw warps, light ones by single warps
     // At K <= 11 (K <= 7 for BZ = 4) the dense path runs on groups of four
-    // warps (its scratch fits a group's three spare areas): group 0 (warps 0-3) takes heavy
-    // bricks first, group 1 (warps 4-7) light bricks first, so the largest
-    // light bricks start at the beginning of the launch instead of after the
-    // heavy ones; each group then turns to the other kind.  Otherwise the
-    // whole CTA is one group, heavy bricks first.
+    // warps (its scratch fits a group's three spare areas): the very heavy
+    // bricks are taken first by whole CTAs (their Eq. 5 counts grow with the
+    // pairs, so on four warps the largest would outlast the launch), then
+    // group 0 (warps 0-3) takes heavy bricks first, group 1 (warps 4-7) light
+    // bricks first, so the largest light bricks start at the beginning of the
+    // launch instead of after the heavy ones; each group then turns to the
+    // other kind.  Otherwise the whole CTA is one group, heavy bricks (very
+    // heavy first) first.
     const int hw = (NW == 4 && R <= half_group_max_r<BZ>()) ? WPC / 2 : WPC;
     const int ht = hw * 32;
     const int gidx = warp / hw;                  // group of this warp
     const int gtid = tid - gidx * ht, gwarp = warp - gidx * hw;
     const int gbar = 1 + gidx;                   // its named barrier
     WarpArea<BZ> *garea = areas + gidx * hw;     // its first warp area
-    // First claims are static (heavy item blockIdx.x for group 0, light item
-    // blockIdx.x * hw + gwarp for group 1's warps): a launch's thousands of
-    // warps claiming at once through one counter would wait on each other's
-    // atomics.  Later claims take counter values past the static ranges.
-    const uint32_t n_static_heavy = gridDim.x;
-    const uint32_t n_static_light = hw < WPC ? gridDim.x * (uint32_t)(WPC - hw) : 0u;
-    bool first_heavy = gidx == 0, first_light = gidx == 1;
+    // First claims are static (heavy item f for group 0, light item f * hw +
+    // gwarp for group 1's warps, f = the CTA's rank among those that do not
+    // start on a very heavy brick): a launch's thousands of warps claiming at
+    // once through one counter would wait on each other's atomics.  The CTAs
+    // that start on a very heavy brick (the first nv_cta) claim through the
+    // counters only, so the largest light bricks are not held back until
+    // they finish.  Later claims take counter values past the static ranges.
+    const uint32_t nv_cta = hw < WPC ? min(nvheavy, gridDim.x) : 0u;
+    const uint32_t n_free = gridDim.x - nv_cta, f = blockIdx.x - nv_cta;
+    const uint32_t n_static_heavy = n_free;
+    const uint32_t n_static_light = hw < WPC ? n_free * (uint32_t)(WPC - hw) : 0u;
+    bool first_heavy = gidx == 0 && blockIdx.x >= nv_cta, first_light = gidx == 1 && blockIdx.x >= nv_cta;
+    // heavy items [h0, nheavy) go to the groups; items < nvheavy are the very
+    // heavy bricks (back of order)
+    const uint32_t h0 = hw < WPC ? nvheavy : 0u;
     __syncthreads();                             // tables above, for every warp
+    if constexpr (NW == 4) {
+        // very heavy bricks by whole CTAs: item blockIdx.x first, then counter
+        // values past the grid
+        for (uint32_t it = hw < WPC ? blockIdx.x : nvheavy; it < nvheavy;) {
+            const uint32_t b = ws.order[ws.max_touched - 1 - it];
+            const uint32_t start = ws.boff[b];
+            uint32_t len = ws.bcnt[b];
+            if ((unsigned long long)start + len > ws.pairs_cap) len = 0;   // cannot happen by sizing
+            DevGrid g;
+            const uint32_t lb = brick_grid<BATCH>(g0, bd, b, g);
+            const int bx = (int)(lb % (uint32_t)g.nbx);
+            const uint32_t byz = lb / (uint32_t)g.nbx;
+            const int by = (int)(byz % (uint32_t)g.nby), bz = (int)(byz / (uint32_t)g.nby);
+            for (uint32_t r0 = 0; r0 < len; r0 += CNT_ROUND) {
+                integrate_dense(g, bx, by, bz, ws.pairs + start + r0, min(len - r0, CNT_ROUND), areas,
+                                s_ctab, t, R, SR, T, Hmax, form_bad, tid, NTHR, 0);
+                __syncthreads();
+            }
+            if (tid == 0) {
+                ws.bcnt[b] = 0u;
+                s_vitem = gridDim.x + atomicAdd(&ws.hdr->next_vheavy, 1u);
+            }
+            __syncthreads();
+            it = s_vitem;   // written again only after the next brick's barriers
+        }
+    }
     for (int phase = 0; phase < 2; ++phase) {
         if ((phase == 0) == (gidx == 0)) {
             // heavy bricks, one per group
             for (;;) {
                 group_sync(gbar, ht);
                 if (gtid == 0)
-                    s_item[gidx] = first_heavy ? blockIdx.x
-                                               : n_static_heavy + atomicAdd(&ws.hdr->next_heavy, 1u);
+                    s_item[gidx] = h0 + (first_heavy ? f
+                                                     : n_static_heavy + atomicAdd(&ws.hdr->next_heavy, 1u));
                 first_heavy = false;
                 group_sync(gbar, ht);
                 const uint32_t it = s_item[gidx];
@@ -679,7 +795,7 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
             for (;;) {
                 uint32_t w = 0;
                 if (first_light) {
-                    w = blockIdx.x * (uint32_t)hw + (uint32_t)gwarp;
+                    w = f * (uint32_t)hw + (uint32_t)gwarp;
                     first_light = false;
                 } else {
                     if (lane == 0) w = atomicAdd(&ws.hdr->next_work, 1u);
@@ -730,7 +846,7 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
                     }
                     // D
                     __syncwarp();
-                    write_back<1, 4>(g, bx, by, bz, wa, lane, 32, T, Hmax, form_bad);
+                    write_back_light<BZ>(g, bx, by, bz, wa, lane, T, Hmax, form_bad);
                     __syncwarp();
                 }
                 if (lane == 0) ws.bcnt[b] = 0u;
@@ -764,6 +880,7 @@ __global__ void __launch_bounds__(NTHR, 4) k_integrate(DevGrid g0, BatchDev bd, 
             h->n_vheavy = 0u;
             for (int c = 0; c < LIGHT_CLASSES; ++c) h->n_cls[c] = 0u;
             h->next_heavy = 0u;
+            h->next_vheavy = 0u;
             h->acc_valid = 0ull;
             h->acc_inside = 0ull;
             h->acc_kept = 0ull;

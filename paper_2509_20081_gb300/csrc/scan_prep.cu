@@ -781,6 +781,7 @@ __global__ void k_ws_rearm_header(WsDev ws) {
     h->n_vheavy = 0u;
     for (int c = 0; c < LIGHT_CLASSES; ++c) h->n_cls[c] = 0u;
     h->next_heavy = 0u;
+    h->next_vheavy = 0u;
     h->acc_valid = 0ull;
     h->acc_inside = 0ull;
     h->acc_kept = 0ull;
