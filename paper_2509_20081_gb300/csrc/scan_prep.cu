@@ -420,6 +420,10 @@ __device__ __forceinline__ unsigned long long batch_key(const DevGrid &g, int it
 // memory and one thread takes each counter's range with a single atomic.
 constexpr int ALLOC_THREADS = 1024;
 constexpr int ALLOC_CTRS = 3 + LIGHT_CLASSES;          // pairs, heavy, very heavy, light classes
+// The per-CTA counter scan gives lane j of warp k warp j's entry of counter
+// k: one entry per lane, so exactly 32 warps, and a warp per counter.
+static_assert(ALLOC_THREADS == 32 * 32 && ALLOC_CTRS <= ALLOC_THREADS / 32,
+              "k_alloc's counter scan: 32 warps of 32 lanes, one warp per counter");
 
 // The first-return rule resolved for every return of the scan(s): a kept
 // contact that is not its voxel's lowest index is flagged PREC_DUP (grid
