@@ -529,60 +529,87 @@ __device__ __forceinline__ uint32_t pair_payload(int4 r, int bx, int by, int bz,
 }
 
 // Pair payloads into the segments, slots from the per-brick cursors.  One
-// thread per (brick j of a span, return): grid row j = blockIdx.y, returns
-// along x, so a warp holds the j-th bricks of 32 consecutive returns, which
-// mostly name the same brick: lanes naming one brick take their slots with
-// one atomic of their leader.
-static_assert(MAX_K - 1 <= BX && MAX_K - 1 <= 3 * BY, "k_fill's span decomposition: sx <= 2, sy <= 4");
-__global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, int slots, WsDev ws,
-                                              uint32_t hcap) {
+// thread per (return, block of FILL_UNROLL consecutive bricks of its span):
+// grid row y = blockIdx.y takes bricks j = y * FILL_UNROLL ... of the spans
+// (x fastest), returns along x.  A warp walks its 32 returns' bricks j in
+// lock-step, and the lanes that name one brick take their slots with one
+// atomic of their leader (the j-th bricks of consecutive returns mostly
+// coincide).  The FILL_UNROLL bricks of a thread are issued together --
+// their cursor atomics and segment-offset loads are all in flight before
+// the first result is used -- so a thread waits once for its block.  b0:
+// first brick index of the return's grid (batches).
+constexpr int FILL_UNROLL = 4;
+static_assert(MAX_K - 1 <= BX && MAX_K - 1 <= 3 * BY, "fill_span's decomposition: sx <= 2, sy <= 4");
+__device__ __forceinline__ void fill_span(bool has, int4 r, const DevGrid &g, uint32_t b0, int R,
+                                          const WsDev &ws) {
+    const BrickSpan sp = has ? brick_span(r.x, r.y, r.z, R, g.bzs) : BrickSpan{};
+    const int sx = sp.x1 - sp.x0 + 1, sy = sp.y1 - sp.y0 + 1, sz = sp.z1 - sp.z0 + 1;
+    const int np = has ? sx * sy * sz : 0;
+    const int jbeg = (int)blockIdx.y * FILL_UNROLL;
+    const int nsteps = min(__reduce_max_sync(0xffffffffu, np), jbeg + FILL_UNROLL);
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    for (int j0 = jbeg; j0 < nsteps; j0 += FILL_UNROLL) {
+        uint32_t b[FILL_UNROLL], pl[FILL_UNROLL], old[FILL_UNROLL], off[FILL_UNROLL];
+        unsigned peers[FILL_UNROLL];
+#pragma unroll
+        for (int u = 0; u < FILL_UNROLL; ++u) {
+            const int j = j0 + u;
+            b[u] = 0xFFFFFFFFu;                      // no brick (never a brick index: < 2^32 - 1 bricks)
+            pl[u] = 0u;
+            if (j < np) {
+                // j -> (ix, iy, iz), x fastest; sx <= 2 and sy <= 4 for K <= 21
+                const int ix = sx == 1 ? 0 : (j & 1);
+                int iy = sx == 1 ? j : (j >> 1), iz = 0;
+                while (iy >= sy) {
+                    iy -= sy;
+                    ++iz;
+                }
+                const int bx = sp.x0 + ix, by = sp.y0 + iy, bz = sp.z0 + iz;
+                b[u] = b0 + ((uint32_t)bz * g.nby + by) * g.nbx + bx;
+                pl[u] = pair_payload(r, bx, by, bz, R, g.bzs);
+            }
+            peers[u] = __match_any_sync(0xffffffffu, b[u]);
+            old[u] = 0u;
+            off[u] = 0u;
+            if (b[u] != 0xFFFFFFFFu) {
+                if (lane == __ffs(peers[u]) - 1) old[u] = atomicAdd(&ws.bcnt[b[u]], (uint32_t)__popc(peers[u]));
+                off[u] = ws.boff[b[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < FILL_UNROLL; ++u) {
+            const uint32_t base = __shfl_sync(0xffffffffu, old[u], __ffs(peers[u]) - 1);
+            if (b[u] != 0xFFFFFFFFu) {
+                const unsigned long long pos =
+                    (unsigned long long)off[u] + base + (uint32_t)__popc(peers[u] & below);
+                if (pos < ws.pairs_cap) ws.pairs[pos] = pl[u];
+                else atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
+            }
+        }
+    }
+}
+
+// Clears the first-return hash table for the next scan (grid stride over
+// every thread of the 2-D grid).
+__device__ __forceinline__ void clear_hash(const WsDev &ws, uint32_t hcap) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * gridDim.y * blockDim.x;
+    for (unsigned long long k = ((unsigned long long)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x +
+                                threadIdx.x;
+         k < hcap; k += stride) {
+        ws.hkey[k] = 0ull;
+        ws.hidx[k] = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fill(DevGrid g, DevParams p, int n, WsDev ws, uint32_t hcap) {
     pdl_wait();
     pdl_launch_dependents();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = (int)blockIdx.y;
-    {
-        bool v = false;
-        uint32_t b = 0xFFFFFFFFu, pl = 0;
-        if (i < n) {
-            const int4 r = ws.prec[i];
-            if (r.x >= 0 && !(r.w & PREC_DUP)) {
-                const BrickSpan sp = brick_span(r.x, r.y, r.z, p.R, g.bzs);
-                const int sx = sp.x1 - sp.x0 + 1, sy = sp.y1 - sp.y0 + 1, sz = sp.z1 - sp.z0 + 1;
-                if (j < sx * sy * sz) {
-                    // j -> (ix, iy, iz), x fastest; sx <= 2 and sy <= 4 for K <= 21
-                    const int ix = sx == 1 ? 0 : (j & 1);
-                    int iy = sx == 1 ? j : (j >> 1), iz = 0;
-                    while (iy >= sy) {
-                        iy -= sy;
-                        ++iz;
-                    }
-                    const int bx = sp.x0 + ix, by = sp.y0 + iy, bz = sp.z0 + iz;
-                    b = ((uint32_t)bz * g.nby + by) * g.nbx + bx;
-                    pl = pair_payload(r, bx, by, bz, p.R, g.bzs);
-                    v = true;
-                }
-            }
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
-        uint32_t base = 0;
-        if (v && lane == leader) base = atomicAdd(&ws.bcnt[b], (uint32_t)__popc(peers));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (v) {
-            const unsigned long long pos =
-                (unsigned long long)ws.boff[b] + base + __popc(peers & ((1u << lane) - 1u));
-            if (pos < ws.pairs_cap) ws.pairs[pos] = pl;
-            else atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
-        }
-    }
-    if (p.dedup) {
-        const uint32_t stride = gridDim.x * gridDim.y * blockDim.x;
-        for (uint32_t k = (blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x; k < hcap;
-             k += stride) {
-            ws.hkey[k] = 0ull;
-            ws.hidx[k] = 0u;
-        }
-    }
+    int4 r = make_int4(-1, 0, 0, 0);
+    if (i < n) r = ws.prec[i];
+    fill_span(r.x >= 0 && !(r.w & PREC_DUP), r, g, 0u, p.R, ws);
+    if (p.dedup) clear_hash(ws, hcap);
 }
 
 // ------------------------------------------------------------------ batches
@@ -682,10 +709,8 @@ __global__ void __launch_bounds__(256) k_voxelize_b(BatchDev bd, DevParams p, De
     flush_item_counts(bd, s_tally);
 }
 
-// Batches: many scans put many pairs on the same bricks, so the cursor bumps
-// of a warp's lanes that name one brick are aggregated (one atomic per
-// brick and warp, each lane taking its rank in the group) over the lanes'
-// spans walked in lock-step, one thread per return.
+// The same for the returns of all scans of a batch (each return in its
+// grid's brick range).
 __global__ void __launch_bounds__(256) k_fill_b(BatchDev bd, DevParams p, long long n, WsDev ws,
                                                 uint32_t hcap) {
     pdl_wait();
@@ -701,31 +726,8 @@ __global__ void __launch_bounds__(256) k_fill_b(BatchDev bd, DevParams p, long l
         g = bd.grids[gi];
         b0 = bd.bbase[gi];
     }
-    const int lane = threadIdx.x & 31;
-    for_pair_bricks<true>(has, has ? brick_span(r.x, r.y, r.z, p.R, g.bzs) : BrickSpan{}, g, b0,
-                          [&](bool v, uint32_t b, int bx, int by, int bz) {
-        const unsigned peers = __match_any_sync(0xffffffffu, v ? b : 0xFFFFFFFFu);
-        const int leader = __ffs(peers) - 1;
-        uint32_t base = 0;
-        if (v && lane == leader) base = atomicAdd(&ws.bcnt[b], (uint32_t)__popc(peers));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (v) {
-            const unsigned long long pos = (unsigned long long)ws.boff[b] + base +
-                                           (uint32_t)__popc(peers & ((1u << lane) - 1u));
-            if (pos < ws.pairs_cap)
-                ws.pairs[pos] = pair_payload(r, bx, by, bz, p.R, g.bzs);
-            else
-                atomicOr(&ws.hdr->err, ERR_PAIRS_OVERFLOW);
-        }
-    });
-    if (p.dedup) {
-        const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-        for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-             j < hcap; j += stride) {
-            ws.hkey[j] = 0ull;
-            ws.hidx[j] = 0u;
-        }
-    }
+    fill_span(has, r, g, b0, p.R, ws);
+    if (p.dedup) clear_hash(ws, hcap);
 }
 
 // ------------------------------------------------------------------ footprint
@@ -883,11 +885,15 @@ void launch_alloc_batch(const BatchDev &bd, const DevParams &p, long long n, con
                hcap);
 }
 
+// Grid rows of the fill: blocks of FILL_UNROLL bricks of the longest span.
+static unsigned fill_rows(const DevParams &p, int bz) {
+    return (unsigned)((max_pairs_per_return(p.K, bz) + FILL_UNROLL - 1) / FILL_UNROLL);
+}
+
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                  cudaStream_t s) {
-    const int slots = max_pairs_per_return(p.K, 1 << g.bzs);
-    launch_pdl(k_fill, dim3((unsigned)std::max(1, (n + 255) / 256), (unsigned)slots), 256, 0, s, g, p, n,
-               slots, ws, hcap);
+    launch_pdl(k_fill, dim3((unsigned)std::max(1, (n + 255) / 256), fill_rows(p, 1 << g.bzs)), 256, 0, s,
+               g, p, n, ws, hcap);
 }
 
 static inline unsigned batch_blocks(long long n) { return (unsigned)max(1ll, (n + 255) / 256); }
@@ -899,7 +905,7 @@ void launch_voxelize_batch(const BatchDev &bd, const DevParams &p, const DevTabl
 
 void launch_fill_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
                        uint32_t hcap, cudaStream_t s) {
-    launch_pdl(k_fill_b, batch_blocks(n), 256, 0, s, bd, p, n, ws, hcap);
+    launch_pdl(k_fill_b, dim3(batch_blocks(n), fill_rows(p, 1 << bd.bzs)), 256, 0, s, bd, p, n, ws, hcap);
 }
 
 void launch_bin_dirs(const DevParams &p, const DevTables &t, const double *dirs, int n, int *bins,
