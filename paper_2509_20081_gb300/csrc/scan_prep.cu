@@ -531,13 +531,14 @@ __device__ __forceinline__ uint32_t pair_payload(int4 r, int bx, int by, int bz,
 // Pair payloads into the segments, slots from the per-brick cursors.  One
 // thread per (return, block of FILL_UNROLL consecutive bricks of its span):
 // grid row y = blockIdx.y takes bricks j = y * FILL_UNROLL ... of the spans
-// (x fastest), returns along x.  A warp walks its 32 returns' bricks j in
-// lock-step, and the lanes that name one brick take their slots with one
-// atomic of their leader (the j-th bricks of consecutive returns mostly
-// coincide).  The FILL_UNROLL bricks of a thread are issued together --
+// (x fastest), returns along x; with a single grid row a thread takes its
+// whole span, FILL_UNROLL bricks at a time.  A warp walks its 32 returns'
+// bricks j in lock-step, and the lanes that name one brick take their slots
+// with one atomic of their leader (the j-th bricks of consecutive returns
+// mostly coincide).  The FILL_UNROLL bricks of a block are issued together --
 // their cursor atomics and segment-offset loads are all in flight before
-// the first result is used -- so a thread waits once for its block.  b0:
-// first brick index of the return's grid (batches).
+// the first result is used -- so a thread waits once per block.  b0: first
+// brick index of the return's grid (batches).
 constexpr int FILL_UNROLL = 4;
 static_assert(MAX_K - 1 <= BX && MAX_K - 1 <= 3 * BY, "fill_span's decomposition: sx <= 2, sy <= 4");
 __device__ __forceinline__ void fill_span(bool has, int4 r, const DevGrid &g, uint32_t b0, int R,
@@ -546,7 +547,8 @@ __device__ __forceinline__ void fill_span(bool has, int4 r, const DevGrid &g, ui
     const int sx = sp.x1 - sp.x0 + 1, sy = sp.y1 - sp.y0 + 1, sz = sp.z1 - sp.z0 + 1;
     const int np = has ? sx * sy * sz : 0;
     const int jbeg = (int)blockIdx.y * FILL_UNROLL;
-    const int nsteps = min(__reduce_max_sync(0xffffffffu, np), jbeg + FILL_UNROLL);
+    const int jend = gridDim.y == 1 ? np : jbeg + FILL_UNROLL;
+    const int nsteps = __reduce_max_sync(0xffffffffu, min(np, jend));
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     for (int j0 = jbeg; j0 < nsteps; j0 += FILL_UNROLL) {
@@ -885,14 +887,17 @@ void launch_alloc_batch(const BatchDev &bd, const DevParams &p, long long n, con
                hcap);
 }
 
-// Grid rows of the fill: blocks of FILL_UNROLL bricks of the longest span.
-static unsigned fill_rows(const DevParams &p, int bz) {
+// Grid rows of the fill: one when a thread per return already fills the
+// GPU several times over (large batches: more rows would only add waves),
+// else blocks of FILL_UNROLL bricks of the longest span.
+static unsigned fill_rows(long long n, const DevParams &p, int bz) {
+    if (n >= 2048ll * device_sm_count()) return 1u;
     return (unsigned)((max_pairs_per_return(p.K, bz) + FILL_UNROLL - 1) / FILL_UNROLL);
 }
 
 void launch_fill(const DevGrid &g, const DevParams &p, int n, const WsDev &ws, uint32_t hcap,
                  cudaStream_t s) {
-    launch_pdl(k_fill, dim3((unsigned)std::max(1, (n + 255) / 256), fill_rows(p, 1 << g.bzs)), 256, 0, s,
+    launch_pdl(k_fill, dim3((unsigned)std::max(1, (n + 255) / 256), fill_rows(n, p, 1 << g.bzs)), 256, 0, s,
                g, p, n, ws, hcap);
 }
 
@@ -905,7 +910,7 @@ void launch_voxelize_batch(const BatchDev &bd, const DevParams &p, const DevTabl
 
 void launch_fill_batch(const BatchDev &bd, const DevParams &p, long long n, const WsDev &ws,
                        uint32_t hcap, cudaStream_t s) {
-    launch_pdl(k_fill_b, dim3(batch_blocks(n), fill_rows(p, 1 << bd.bzs)), 256, 0, s, bd, p, n, ws, hcap);
+    launch_pdl(k_fill_b, dim3(batch_blocks(n), fill_rows(n, p, 1 << bd.bzs)), 256, 0, s, bd, p, n, ws, hcap);
 }
 
 void launch_bin_dirs(const DevParams &p, const DevTables &t, const double *dirs, int n, int *bins,
