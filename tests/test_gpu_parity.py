@@ -202,6 +202,34 @@ def test_brick_depth_16_refused_above_k17():
     assert ws.tuning()["brick_depth"] == 8
 
 
+@pytest.mark.parametrize("K,tuning", [
+    (11, {}),                               # very heavy: whole CTA, dense path
+    (11, {"heavy_pairs": 1 << 30}),          # every brick light: one warp
+    (15, {}),                               # K > 13: warps' own areas, merged
+    (9, {"heavy_pairs": 1 << 30, "brick_depth": 4}),
+])
+def test_brick_with_more_pairs_than_a_count_round(orc, K, tuning):
+    """100,000 returns (first-return rule off) in a 2 x 2 x 2-voxel cube: the
+    brick that holds it gets more (return, brick) pairs than one round of
+    16-bit counts takes (65,535), so its pairs are integrated in two rounds;
+    with hit_max = 65535 some counters receive more increments than that and
+    saturate across the rounds."""
+    rng = synth.Rng(4242 + K)
+    dims, res = (64, 64, 64), 0.1
+    lo = np.array([30.0, 30.0, 30.0]) * res
+    pts = synth.random_points(rng, 100000, tuple(lo + 0.001), tuple(lo + 2 * res - 0.001))
+    pose = synth.make_pose(np.eye(3), (0.0, 0.0, 0.0))
+    scans = [(np.ascontiguousarray(pts, np.float32), pose)]
+    pd = params(kernel_size=K, dedup_first=0, hit_max=65535, hit_threshold=3,
+                shadow_radius=min(3.0, (K - 1) / 2))
+    gpu, gs, _ = run_gpu(pd, dims, res, scans, tuning=tuning)
+    ora, os_ = run_oracle(orc, pd, dims, res, scans)
+    assert os_[0]["n_kept"] == 100000
+    assert gs[0]["n_pairs"] > 100000
+    assert int(ora.hits.max()) == 65535
+    assert_same(gpu, ora, gs, os_)
+
+
 def _tiny(seed, n, dims, res, dup):
     rng = synth.Rng(seed)
     nx, ny, nz = dims
