@@ -169,7 +169,9 @@ dbt_status dbt_scan_contacts(const dbt_grid *g, const dbt_kernels *k, const floa
 typedef struct dbt_workspace dbt_workspace;
 
 /* Bytes of device scratch a workspace needs for grid g, tables k and scans
- * of up to max_points returns (max_points >= 1). */
+ * of up to max_points returns (max_points >= 1).  The brick counters and
+ * pair lists are sized for the shallowest brick depth (4), so the workspace
+ * can be tuned to any depth (dbt_tuning). */
 dbt_status dbt_workspace_size(const dbt_grid *g, const dbt_kernels *k, int64_t max_points,
                               size_t *bytes);
 
@@ -301,7 +303,8 @@ typedef struct {
 } dbt_batch_item;
 
 /* Bytes of device scratch for a batch over n_grids grids (<= 256), up to
- * max_points returns in total and max_items scans per run. */
+ * max_points returns in total and max_items scans per run (sized, like a
+ * workspace, for every brick depth). */
 dbt_status dbt_batch_size(const dbt_grid *grids, int32_t n_grids, const dbt_kernels *k,
                           int64_t max_points, int32_t max_items, size_t *bytes);
 
