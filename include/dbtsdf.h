@@ -359,7 +359,7 @@ dbt_status dbt_batch_set_tuning(dbt_batch *b, const dbt_tuning *t);
 dbt_status dbt_batch_get_tuning(const dbt_batch *b, dbt_tuning *t);
 
 /* Times candidate tunings over n_trials runs of the batch's current items
- * (one warm-up run each) with CUDA events on stream, in two rounds: every
+ * (one warm-up run each) with CUDA events on stream, in two stages: every
  * brick_depth (8, 4, and 16 where allowed) x heavy_pairs 16..256 on the
  * occupancy-maximum grid, then the winner on three, two and one CTAs per SM.
  * Keeps the fastest in *best and sets it on the batch.  The items are integrated (1 + n_trials) times

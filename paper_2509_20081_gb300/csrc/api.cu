@@ -1266,10 +1266,10 @@ extern "C" dbt_status dbt_batch_get_tuning(const dbt_batch *b, dbt_tuning *t) {
     return DBT_OK;
 }
 
-// Candidates, searched in two rounds.  Round 1: the brick depth (8, 4 and,
+// Candidates, searched in two stages.  Stage 1: the brick depth (8, 4 and,
 // up to K = 17, 16) crossed with the heavy threshold (CTA mode from 16 to
 // 256 pairs per brick; the pairs a brick gets scale with its depth), on the
-// occupancy-maximum grid.  Round 2: the winner's depth and threshold on a
+// occupancy-maximum grid.  Stage 2: the winner's depth and threshold on a
 // persistent grid of three, two or one CTAs per SM.  Each candidate is
 // timed over n_trials runs after one warm-up run.
 static std::vector<dbt_tuning> depth_heavy_candidates(const dbt_kernels *k) {
