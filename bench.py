@@ -65,7 +65,7 @@ INTEGRATE_SRC = os.path.join(ROOT, "paper_2509_20081_gb300", "csrc", "integrate.
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_integrate, per kept
 # return, from the capture summarised under profiles/ (valid only for the
 # integrate.cu source with this sha256 prefix; otherwise traffic is null).
-NCU_TRAFFIC = {"integrate_sha": "cff33a9a6b576961", "bytes_per_kept_return": 855.8,
+NCU_TRAFFIC = {"integrate_sha": "80ab203c51b11876", "bytes_per_kept_return": 855.8,
                "source": "profiles/k_integrate_urban_half.md (urban_half, 39.9 k kept returns "
                          "per scan, 34.2 MB DRAM read+write per launch), scaled by kept returns"}
 

@@ -409,9 +409,11 @@ __device__ __forceinline__ void write_back(const DevGrid &g, int bx, int by, int
 // to a word, the lanes of the covered words would walk every row while the
 // others idle).  The covered chunks (those with kernel codes; a chunk with
 // shadow counts lies in its contact's K^3 box and so has codes too) are
-// noted in a bit mask first, then taken four per lane at a time: their
+// noted in a bit mask first, then taken WBL_PICKS per lane at a time: their
 // masks and counters loaded together, then lowered, bumped and stored as in
-// write_back.
+// write_back (three at a time measured fastest: more keep more registers
+// live across the loads).
+constexpr int WBL_PICKS = 3;
 template <int BZ>
 __device__ __forceinline__ void write_back_light(const DevGrid &g, int bx, int by, int bz,
                                                  const WarpArea<BZ> *a, int lane, uint32_t T,
@@ -425,10 +427,10 @@ __device__ __forceinline__ void write_back_light(const DevGrid &g, int bx, int b
         if (a->kst[kword(row, ch)] != NO_CODE4) cov |= 1u << i;
     }
     while (__any_sync(0xffffffffu, cov != 0u)) {
-        int rc[4];                            // row * 8 + ch of each taken chunk, -1 = none
-        uint4 m[4];
+        int rc[WBL_PICKS];                            // row * 8 + ch of each taken chunk, -1 = none
+        uint4 m[WBL_PICKS];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < WBL_PICKS; ++q) {
             rc[q] = -1;
             m[q] = make_uint4(0u, 0u, 0u, 0u);
             if (cov) {
@@ -439,10 +441,10 @@ __device__ __forceinline__ void write_back_light(const DevGrid &g, int bx, int b
                 m[q] = __ldcg(reinterpret_cast<const uint4 *>(g.mask + chunk_index<BZ>(g, bx, by, bz, row, ch)));
             }
         }
-        uint2 hv[4];
+        uint2 hv[WBL_PICKS];
         uint32_t hc = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < WBL_PICKS; ++q) {
             hv[q] = make_uint2(0u, 0u);
             if (rc[q] >= 0) {
                 const uint2 cs = chunk_counts<1>(a, rc[q] >> 3, rc[q] & 7);
@@ -454,7 +456,7 @@ __device__ __forceinline__ void write_back_light(const DevGrid &g, int bx, int b
             }
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < WBL_PICKS; ++q) {
             if (rc[q] < 0) continue;
             const int row = rc[q] >> 3, ch = rc[q] & 7;
             const uint32_t k = a->kst[kword(row, ch)];
@@ -463,7 +465,7 @@ __device__ __forceinline__ void write_back_light(const DevGrid &g, int bx, int b
             if (lt) store_codes(g, chunk_index<BZ>(g, bx, by, bz, row, ch), code_min(old, k, lt));
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < WBL_PICKS; ++q) {
             if (!((hc >> q) & 1u)) continue;
             const int row = rc[q] >> 3, ch = rc[q] & 7;
             const size_t gi = chunk_index<BZ>(g, bx, by, bz, row, ch);
@@ -613,7 +615,7 @@ __device__ void integrate_dense(const DevGrid &g, int bx, int by, int bz, const 
         shadow_pairs<BZ, true>(mine, (int)min(32u, jhi - j0), a0->cnt, t, R, SR, lane);
     }
     group_sync(bar, gt);
-    write_back<1, 4>(g, bx, by, bz, a0, tid, gt, T, Hmax, form_bad);
+    write_back<1, 2>(g, bx, by, bz, a0, tid, gt, T, Hmax, form_bad);
 }
 
 // Grid of global brick b in a batch (bricks of grid m are [bbase[m], bbase[m+1])).
